@@ -1,0 +1,497 @@
+/*
+ * espnmf_oracle.c -- plain, slow, FP64 CPU oracle for enforced-sparsity
+ * ALS non-negative matrix factorisation (Gavin, Gadepally, Kepner,
+ * "Enforced Sparse Non-Negative Matrix Factorization", arXiv:1510.05237).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file.  The product (the CUDA
+ * library and its Python binding) never calls it, and the two share no code,
+ * header, table or helper.
+ *
+ * Everything is FP64, single-threaded, written as the paper states it:
+ *   - Alg. 2 (Enforced Sparsity ALS), steps 1-4: V = A^T U (U^T U)^-1,
+ *     clamp negatives, keep the t_v largest; U = A V (V^T V)^-1, clamp,
+ *     keep the t_u largest.  With enforcement off it is Alg. 1.
+ *   - Sec. 2 (after Alg. 2): the top-t rule keeps the entries at or above
+ *     the t-th largest magnitude; Sec. 4 (first paragraph) gives the
+ *     column-by-column variant.
+ *   - Sec. 3.1: R = ||U_i - U_{i-1}|| / ||U_i||, E = ||A - U V^T|| / ||A||.
+ *   - Sec. 4, Eq. 6 (the squared objective) gives the loss used by the
+ *     gradient helpers.
+ *
+ * Readings where the paper is silent (all norms Frobenius; exactly
+ * min(t, #positive) entries kept, ties to the lower index; zero Gram
+ * columns dropped and their output set to 0; other Cholesky breakdowns
+ * reported as singular) are listed in the design notes and in the comments
+ * of the functions below.
+ *
+ * Matrix A is n x m (terms x documents) in CSR over rows: rowptr[n+1],
+ * colidx[nnz], val[nnz].  Factors are dense row-major: U is n x k, V is m x k.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Status codes (same meanings as the library's, defined independently). */
+enum {
+    OR_OK = 0,
+    OR_ERR_INVALID_ARG = 1,
+    OR_ERR_BAD_MATRIX = 2,
+    OR_ERR_SINGULAR = 3,
+    OR_ERR_NONFINITE = 4,
+    OR_ERR_OOM = 5
+};
+
+/* Enforcement modes. */
+enum { OR_TOPT_COLUMN = 0, OR_TOPT_MATRIX = 1, OR_TOPT_NONE = 2 };
+
+/* ------------------------------------------------------------------------ */
+/* Sparse products, Alg. 2 steps 1 and 3: the "A^T U" and "A V" factors.    */
+
+/* B (m x k) = A^T U.  Loops over A's rows; for every stored a_ij adds
+ * a_ij * U[i,:] to B[j,:].  For each B[j,c] the additions therefore come in
+ * increasing row index i. */
+void or_spmm_At(int64_t n, int64_t m, const int64_t *rowptr,
+                const int32_t *colidx, const double *val, int32_t k,
+                const double *U, double *B)
+{
+    memset(B, 0, sizeof(double) * (size_t)m * (size_t)k);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int64_t j = colidx[p];
+            double a = val[p];
+            for (int32_t c = 0; c < k; ++c)
+                B[j * k + c] += a * U[i * k + c];
+        }
+}
+
+/* B (n x k) = A V. */
+void or_spmm_A(int64_t n, int64_t m, const int64_t *rowptr,
+               const int32_t *colidx, const double *val, int32_t k,
+               const double *V, double *B)
+{
+    (void)m;
+    memset(B, 0, sizeof(double) * (size_t)n * (size_t)k);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int64_t j = colidx[p];
+            double a = val[p];
+            for (int32_t c = 0; c < k; ++c)
+                B[i * k + c] += a * V[j * k + c];
+        }
+}
+
+/* G (k x k) = F^T F for a rows x k factor F: the "U^T U" / "V^T V" of
+ * Alg. 2 steps 1 and 3. */
+void or_gram(int64_t rows, int32_t k, const double *F, double *G)
+{
+    for (int32_t c = 0; c < k; ++c)
+        for (int32_t d = 0; d < k; ++d) {
+            double s = 0.0;
+            for (int64_t i = 0; i < rows; ++i)
+                s += F[i * k + c] * F[i * k + d];
+            G[c * k + d] = s;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The k x k solve of Alg. 2 steps 1 and 3: X = B G^-1 row by row, i.e.
+ * x G = b for every row b of B (G symmetric, so G x^T = b^T).
+ *
+ * Reading (the paper is silent on a singular Gram): an index j with
+ * G_jj == 0 belongs to an all-zero factor column; it is dropped, the reduced
+ * system is solved, and output column j is 0 (the minimum-norm solution).
+ * Any other Cholesky pivot <= 64 * eps * max_j G_jj is reported as
+ * OR_ERR_SINGULAR. */
+int or_cholesky(int32_t k, const double *G, double *L, int32_t *active)
+{
+    double maxdiag = 0.0;
+    for (int32_t j = 0; j < k; ++j) {
+        double d = G[j * k + j];
+        if (!isfinite(d)) return OR_ERR_NONFINITE;
+        active[j] = d != 0.0;
+        if (d > maxdiag) maxdiag = d;
+    }
+    memset(L, 0, sizeof(double) * (size_t)k * (size_t)k);
+    double tol = 64.0 * 2.220446049250313e-16 * maxdiag;
+    for (int32_t j = 0; j < k; ++j) {
+        if (!active[j]) continue;
+        double s = G[j * k + j];
+        for (int32_t e = 0; e < j; ++e)
+            if (active[e]) s -= L[j * k + e] * L[j * k + e];
+        if (!(s > tol)) return OR_ERR_SINGULAR;
+        double ljj = sqrt(s);
+        L[j * k + j] = ljj;
+        for (int32_t i = j + 1; i < k; ++i) {
+            if (!active[i]) continue;
+            double t = G[i * k + j];
+            for (int32_t e = 0; e < j; ++e)
+                if (active[e]) t -= L[i * k + e] * L[j * k + e];
+            L[i * k + j] = t / ljj;
+        }
+    }
+    return OR_OK;
+}
+
+/* Solves x (L L^T) = b for every row: forward substitution L z = b, then
+ * back substitution L^T x = z, on the active indices only. */
+void or_solve_rows(int64_t rows, int32_t k, const double *L,
+                   const int32_t *active, const double *B, double *X)
+{
+    double *z = (double *)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    for (int64_t r = 0; r < rows; ++r) {
+        const double *b = B + r * k;
+        double *x = X + r * k;
+        for (int32_t j = 0; j < k; ++j) {
+            if (!active[j]) { z[j] = 0.0; continue; }
+            double s = b[j];
+            for (int32_t e = 0; e < j; ++e)
+                if (active[e]) s -= L[j * k + e] * z[e];
+            z[j] = s / L[j * k + j];
+        }
+        for (int32_t j = k - 1; j >= 0; --j) {
+            if (!active[j]) { x[j] = 0.0; continue; }
+            double s = z[j];
+            for (int32_t e = j + 1; e < k; ++e)
+                if (active[e]) s -= L[e * k + j] * x[e];
+            x[j] = s / L[j * k + j];
+        }
+    }
+    free(z);
+}
+
+/* X = B G^-1 (the least-squares step before projection). */
+int or_ls_solve(int64_t rows, int32_t k, const double *B, const double *G,
+                double *X)
+{
+    double *L = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k + 8);
+    int32_t *act = (int32_t *)malloc(sizeof(int32_t) * (size_t)k + 8);
+    if (!L || !act) { free(L); free(act); return OR_ERR_OOM; }
+    int st = or_cholesky(k, G, L, act);
+    if (st == OR_OK) or_solve_rows(rows, k, L, act, B, X);
+    free(L);
+    free(act);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Projection, Alg. 2 steps 1 and 3: negative entries become zero.
+ * Non-finite values are an error, never clamped away.  Everything that is
+ * not > 0 (including -0.0) becomes +0.0. */
+int or_project(double *X, int64_t count)
+{
+    for (int64_t q = 0; q < count; ++q)
+        if (!isfinite(X[q])) return OR_ERR_NONFINITE;
+    for (int64_t q = 0; q < count; ++q)
+        X[q] = X[q] > 0.0 ? X[q] : 0.0;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Enforcement, Alg. 2 steps 2 and 4 with the rule stated after Alg. 2:
+ * order the entries that are nonzero (after the projection: positive) by
+ * size and zero all but the t biggest.  Readings: exactly min(t, #positive) entries are kept; among
+ * equal values the lower index wins (row index in column mode, row-major
+ * linear index i*k+c in matrix mode); zeros are never kept.
+ * OR_TOPT_COLUMN applies the rule to each column separately (Sec. 4),
+ * OR_TOPT_MATRIX to the whole matrix (Alg. 2 as printed), OR_TOPT_NONE
+ * keeps everything (Alg. 1). */
+typedef struct { double v; int64_t idx; } or_entry;
+
+static int or_entry_cmp(const void *a, const void *b)
+{
+    const or_entry *x = (const or_entry *)a, *y = (const or_entry *)b;
+    if (x->v > y->v) return -1;
+    if (x->v < y->v) return 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+int or_topt(double *X, int64_t rows, int32_t k, int64_t t, int mode)
+{
+    if (t < 0) return OR_ERR_INVALID_ARG;
+    if (mode == OR_TOPT_NONE) return OR_OK;
+    if (mode == OR_TOPT_COLUMN) {
+        or_entry *e = (or_entry *)malloc(sizeof(or_entry) * (size_t)(rows > 0 ? rows : 1));
+        if (!e) return OR_ERR_OOM;
+        for (int32_t c = 0; c < k; ++c) {
+            int64_t cnt = 0;
+            for (int64_t i = 0; i < rows; ++i)
+                if (X[i * k + c] > 0.0) { e[cnt].v = X[i * k + c]; e[cnt].idx = i; ++cnt; }
+            if (cnt <= t) continue;
+            qsort(e, (size_t)cnt, sizeof(or_entry), or_entry_cmp);
+            for (int64_t q = t; q < cnt; ++q) X[e[q].idx * k + c] = 0.0;
+        }
+        free(e);
+        return OR_OK;
+    }
+    if (mode == OR_TOPT_MATRIX) {
+        int64_t total = rows * (int64_t)k;
+        or_entry *e = (or_entry *)malloc(sizeof(or_entry) * (size_t)(total > 0 ? total : 1));
+        if (!e) return OR_ERR_OOM;
+        int64_t cnt = 0;
+        for (int64_t q = 0; q < total; ++q)
+            if (X[q] > 0.0) { e[cnt].v = X[q]; e[cnt].idx = q; ++cnt; }
+        if (cnt > t) {
+            qsort(e, (size_t)cnt, sizeof(or_entry), or_entry_cmp);
+            for (int64_t q = t; q < cnt; ++q) X[e[q].idx] = 0.0;
+        }
+        free(e);
+        return OR_OK;
+    }
+    return OR_ERR_INVALID_ARG;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One half-step of Alg. 2.
+ * or_update_V: steps 1-2 -- V = A^T U (U^T U)^-1, clamp, keep t_v largest.
+ * or_update_U: steps 3-4 -- U = A V (V^T V)^-1, clamp, keep t_u largest.
+ * If `pre` is non-NULL it receives the least-squares step before the
+ * projection. */
+int or_update_V(int64_t n, int64_t m, const int64_t *rowptr,
+                const int32_t *colidx, const double *val, int32_t k,
+                const double *U, int64_t t_v, int mode, double *V, double *pre)
+{
+    double *B = (double *)malloc(sizeof(double) * (size_t)m * (size_t)k + 8);
+    double *G = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k + 8);
+    if (!B || !G) { free(B); free(G); return OR_ERR_OOM; }
+    or_spmm_At(n, m, rowptr, colidx, val, k, U, B);
+    or_gram(n, k, U, G);
+    int st = or_ls_solve(m, k, B, G, V);
+    if (st == OR_OK && pre) memcpy(pre, V, sizeof(double) * (size_t)m * (size_t)k);
+    if (st == OR_OK) st = or_project(V, m * (int64_t)k);
+    if (st == OR_OK) st = or_topt(V, m, k, t_v, mode);
+    free(B);
+    free(G);
+    return st;
+}
+
+int or_update_U(int64_t n, int64_t m, const int64_t *rowptr,
+                const int32_t *colidx, const double *val, int32_t k,
+                const double *V, int64_t t_u, int mode, double *U, double *pre)
+{
+    double *B = (double *)malloc(sizeof(double) * (size_t)n * (size_t)k + 8);
+    double *G = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k + 8);
+    if (!B || !G) { free(B); free(G); return OR_ERR_OOM; }
+    or_spmm_A(n, m, rowptr, colidx, val, k, V, B);
+    or_gram(m, k, V, G);
+    int st = or_ls_solve(n, k, B, G, U);
+    if (st == OR_OK && pre) memcpy(pre, U, sizeof(double) * (size_t)n * (size_t)k);
+    if (st == OR_OK) st = or_project(U, n * (int64_t)k);
+    if (st == OR_OK) st = or_topt(U, n, k, t_u, mode);
+    free(B);
+    free(G);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1 measures.
+ * R = ||U_new - U_old||_F / ||U_new||_F.  Reading for ||U_new|| = 0:
+ * R = 0 if U_old is also 0, else +inf. */
+double or_residual(int64_t rows, int32_t k, const double *Unew,
+                   const double *Uold)
+{
+    double num = 0.0, den = 0.0, old = 0.0;
+    for (int64_t q = 0; q < rows * (int64_t)k; ++q) {
+        double d = Unew[q] - Uold[q];
+        num += d * d;
+        den += Unew[q] * Unew[q];
+        old += Uold[q] * Uold[q];
+    }
+    if (den == 0.0) return old == 0.0 ? 0.0 : INFINITY;
+    return sqrt(num) / sqrt(den);
+}
+
+/* ||A||_F^2 */
+double or_norm2_A(int64_t nnz, const double *val)
+{
+    double s = 0.0;
+    for (int64_t p = 0; p < nnz; ++p) s += val[p] * val[p];
+    return s;
+}
+
+/* f = ||A - U V^T||_F^2 without forming U V^T:
+ *   ||A||^2 - 2 <U, A V> + <U^T U, V^T V>.
+ * The middle term is sum_ij U_ic (A V)_ic; the last is trace(U^TU V^TV). */
+double or_loss(int64_t n, int64_t m, const int64_t *rowptr,
+               const int32_t *colidx, const double *val, int32_t k,
+               const double *U, const double *V)
+{
+    double *AV = (double *)malloc(sizeof(double) * (size_t)n * (size_t)k + 8);
+    double *GU = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k + 8);
+    double *GV = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k + 8);
+    or_spmm_A(n, m, rowptr, colidx, val, k, V, AV);
+    or_gram(n, k, U, GU);
+    or_gram(m, k, V, GV);
+    double a2 = or_norm2_A(rowptr[n], val);
+    double cross = 0.0;
+    for (int64_t q = 0; q < n * (int64_t)k; ++q) cross += U[q] * AV[q];
+    double tr = 0.0;
+    for (int32_t q = 0; q < k * k; ++q) tr += GU[q] * GV[q];
+    free(AV);
+    free(GU);
+    free(GV);
+    return a2 - 2.0 * cross + tr;
+}
+
+/* E = ||A - U V^T||_F / ||A||_F through the identity above, clamped at 0
+ * before the square root.  E = 0 when ||A|| = 0. */
+double or_error_identity(int64_t n, int64_t m, const int64_t *rowptr,
+                         const int32_t *colidx, const double *val, int32_t k,
+                         const double *U, const double *V)
+{
+    double a2 = or_norm2_A(rowptr[n], val);
+    if (a2 == 0.0) return 0.0;
+    double f = or_loss(n, m, rowptr, colidx, val, k, U, V);
+    return sqrt(f > 0.0 ? f : 0.0) / sqrt(a2);
+}
+
+/* E from the dense reconstruction A - U V^T (tiny inputs only). */
+double or_error_direct(int64_t n, int64_t m, const int64_t *rowptr,
+                       const int32_t *colidx, const double *val, int32_t k,
+                       const double *U, const double *V)
+{
+    double *D = (double *)calloc((size_t)n * (size_t)m + 1, sizeof(double));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            D[i * m + colidx[p]] = val[p];
+    double num = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < m; ++j) {
+            double s = 0.0;
+            for (int32_t c = 0; c < k; ++c) s += U[i * k + c] * V[j * k + c];
+            double d = D[i * m + j] - s;
+            num += d * d;
+        }
+    free(D);
+    double a2 = or_norm2_A(rowptr[n], val);
+    if (a2 == 0.0) return 0.0;
+    return sqrt(num) / sqrt(a2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 2 driver: U = U0 (not enforced); every sweep runs steps 1-4, then
+ * R (against the U of the previous sweep, U0 for the first) and E with the
+ * current U and V.  R_out / E_out may be NULL. */
+int or_iterate(int64_t n, int64_t m, const int64_t *rowptr,
+               const int32_t *colidx, const double *val, int32_t k,
+               const double *U0, int64_t t_u, int64_t t_v, int mode,
+               int32_t iters, double *R_out, double *E_out, double *U_out,
+               double *V_out)
+{
+    double *Uprev = (double *)malloc(sizeof(double) * (size_t)n * (size_t)k + 8);
+    if (!Uprev) return OR_ERR_OOM;
+    memcpy(U_out, U0, sizeof(double) * (size_t)n * (size_t)k);
+    memcpy(Uprev, U0, sizeof(double) * (size_t)n * (size_t)k);
+    int st = OR_OK;
+    for (int32_t it = 0; it < iters && st == OR_OK; ++it) {
+        st = or_update_V(n, m, rowptr, colidx, val, k, U_out, t_v, mode, V_out, NULL);
+        if (st != OR_OK) break;
+        st = or_update_U(n, m, rowptr, colidx, val, k, V_out, t_u, mode, U_out, NULL);
+        if (st != OR_OK) break;
+        if (R_out) R_out[it] = or_residual(n, k, U_out, Uprev);
+        if (E_out) E_out[it] = or_error_identity(n, m, rowptr, colidx, val, k, U_out, V_out);
+        memcpy(Uprev, U_out, sizeof(double) * (size_t)n * (size_t)k);
+    }
+    free(Uprev);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradients of f(U, V) = ||A - U V^T||_F^2 (the squared objective, Eq. 6):
+ *   grad_U = 2 (U V^T V - A V),   grad_V = 2 (V U^T U - A^T U). */
+void or_grad_U(int64_t n, int64_t m, const int64_t *rowptr,
+               const int32_t *colidx, const double *val, int32_t k,
+               const double *U, const double *V, double *gU)
+{
+    double *AV = (double *)malloc(sizeof(double) * (size_t)n * (size_t)k + 8);
+    double *GV = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k + 8);
+    or_spmm_A(n, m, rowptr, colidx, val, k, V, AV);
+    or_gram(m, k, V, GV);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t c = 0; c < k; ++c) {
+            double s = 0.0;
+            for (int32_t d = 0; d < k; ++d) s += U[i * k + d] * GV[d * k + c];
+            gU[i * k + c] = 2.0 * (s - AV[i * k + c]);
+        }
+    free(AV);
+    free(GV);
+}
+
+void or_grad_V(int64_t n, int64_t m, const int64_t *rowptr,
+               const int32_t *colidx, const double *val, int32_t k,
+               const double *U, const double *V, double *gV)
+{
+    double *AtU = (double *)malloc(sizeof(double) * (size_t)m * (size_t)k + 8);
+    double *GU = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k + 8);
+    or_spmm_At(n, m, rowptr, colidx, val, k, U, AtU);
+    or_gram(n, k, U, GU);
+    for (int64_t j = 0; j < m; ++j)
+        for (int32_t c = 0; c < k; ++c) {
+            double s = 0.0;
+            for (int32_t d = 0; d < k; ++d) s += V[j * k + d] * GU[d * k + c];
+            gV[j * k + c] = 2.0 * (s - AtU[j * k + c]);
+        }
+    free(AtU);
+    free(GU);
+}
+
+/* Largest eigenvalue of a k x k symmetric non-negative matrix by 20 steps
+ * of power iteration from the normalised all-ones vector. */
+double or_lambda_max(int32_t k, const double *G)
+{
+    double *x = (double *)malloc(sizeof(double) * (size_t)k + 8);
+    double *y = (double *)malloc(sizeof(double) * (size_t)k + 8);
+    for (int32_t c = 0; c < k; ++c) x[c] = 1.0 / sqrt((double)k);
+    double lam = 0.0;
+    for (int it = 0; it < 20; ++it) {
+        double nrm = 0.0;
+        for (int32_t c = 0; c < k; ++c) {
+            double s = 0.0;
+            for (int32_t d = 0; d < k; ++d) s += G[c * k + d] * x[d];
+            y[c] = s;
+            nrm += s * s;
+        }
+        lam = sqrt(nrm);
+        if (lam == 0.0) break;
+        for (int32_t c = 0; c < k; ++c) x[c] = y[c] / lam;
+    }
+    free(x);
+    free(y);
+    return lam;
+}
+
+/* Projected-gradient polish on a fixed support (not in the paper; an
+ * addition on top of Alg. 2): U <- P_S(U - eta grad_U f) with
+ * eta = 1 / (2 lambda_max(V^T V)), where P_S clamps to >= 0 and zeroes
+ * every entry outside the current support S = {U != 0}.  which = 0 polishes
+ * U (V fixed), which = 1 polishes V (U fixed). */
+int or_pg_step(int64_t n, int64_t m, const int64_t *rowptr,
+               const int32_t *colidx, const double *val, int32_t k,
+               double *U, double *V, int which)
+{
+    int64_t rows = which == 0 ? n : m;
+    double *g = (double *)malloc(sizeof(double) * (size_t)rows * (size_t)k + 8);
+    double *G = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k + 8);
+    if (!g || !G) { free(g); free(G); return OR_ERR_OOM; }
+    double *F = which == 0 ? U : V;
+    if (which == 0) {
+        or_grad_U(n, m, rowptr, colidx, val, k, U, V, g);
+        or_gram(m, k, V, G);
+    } else {
+        or_grad_V(n, m, rowptr, colidx, val, k, U, V, g);
+        or_gram(n, k, U, G);
+    }
+    double lam = or_lambda_max(k, G);
+    if (lam > 0.0) {
+        double eta = 1.0 / (2.0 * lam);
+        for (int64_t q = 0; q < rows * (int64_t)k; ++q) {
+            if (F[q] == 0.0) continue;
+            double x = F[q] - eta * g[q];
+            F[q] = x > 0.0 ? x : 0.0;
+        }
+    }
+    free(g);
+    free(G);
+    return OR_OK;
+}
