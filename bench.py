@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Benchmark: enforced-sparsity ALS NMF sweeps on one GB300 (or N replicas).
+
+Workload: the planted-topic corpus of 50k terms x 100k documents (~10M nnz,
+50 planted topics, Dirichlet(0.1) mixtures, 5% noise, TF-IDF FP32 values),
+k = 50, t = 1000 per factor column, uniform[0,1) initial guess.  A step is
+one sweep of Alg. 2 (update V, update U, with the residual R and error E).
+
+Prints one JSON line: iterations/s of the FP32 form (value, device-timed,
+inputs resident in HBM), the same metric end to end from host buffers
+(e2e), the roofline of the dominant kernel (from per-launch CUDA events),
+the FP64 form and the final-error comparison, clocks during the timed
+region, and the FP64 CPU oracle timed on the host as the baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ALS iters/s at 10M nnz k=50 t=1000; SpMM HBM GB/s; mixed vs FP64 at equal err"
+UNIT = "iters/s"
+K_TOPICS, T_KEEP, JOB_ITERS = 50, 1000, 50
+WORKLOAD = "planted-50k-100k"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--e2e-jobs", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--seed", type=int, default=2)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(kernel: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel's file; else None."""
+    src = os.path.join(ROOT, "paper_1510_05237_gb300", "csrc", "k_spmm.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}_{WORKLOAD}.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m1 = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if m1 and m2 and m1.group(1) == sha:
+        return float(m2.group(1))
+    return None
+
+
+def make_inputs(seed):
+    from gen import planted_50k_100k, uniform_init
+    A = planted_50k_100k(seed=seed)
+    U0 = uniform_init(A.n, K_TOPICS, seed)
+    return A, U0
+
+
+def cpu_baseline(A, U0, sweeps=1):
+    import oracle
+    A32 = A.astype(np.float32)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.iterate(A32, U0, T_KEEP, T_KEEP, oracle.COLUMN, sweeps)
+    dt = time.perf_counter() - t0
+    return {"value": sweeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sweeps} sweep(s) of the full {WORKLOAD} workload "
+                      f"(n={A.n}, m={A.m}, nnz={A.nnz}) from U0, FP64 C oracle, 1 thread"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    A, U0 = make_inputs(args.seed)
+    import oracle
+    A32 = A.astype(np.float32)
+    oracle.build()
+    U = U0.copy()
+    for _ in range(max(args.warmup, 0) and 1):
+        oracle.iterate(A32, U, T_KEEP, T_KEEP, oracle.COLUMN, 1)
+    t0 = time.perf_counter()
+    steps = max(args.steps, 1)
+    for _ in range(steps):
+        U, V, R, E = oracle.iterate(A32, U, T_KEEP, T_KEEP, oracle.COLUMN, 1)
+    dt = time.perf_counter() - t0
+    value = steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * dt / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": A.n, "m": A.m, "nnz": A.nnz,
+                       "k": K_TOPICS, "t": T_KEEP, "mode": "column"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} sweep(s) of the full workload, FP64 C oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1510_05237_gb300 as E
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    # replicas: every rank factors its own corpus (seed + rank)
+    A, U0 = make_inputs(args.seed + rank)
+    A32v = A.val.astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    stream = torch.cuda.Stream()
+    rp, ci, va, u0 = dev(A.rowptr), dev(A.colidx), dev(A32v), dev(U0)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region (FP32 form) ----------------
+    ctx = E.espnmf_init(rp, ci, va, A.n, A.m, K_TOPICS, T_KEEP, T_KEEP, E.TOPT_COLUMN,
+                        E.F32, u0, stream=stream)
+    E.espnmf_iterate(ctx, max(args.warmup, 3), want_measures=False)
+    E.espnmf_sync(ctx)
+    launches = E.espnmf_launches_per_sweep(ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        E.espnmf_iterate(ctx, args.steps, want_measures=False)
+        ev1.record(stream)
+        ev1.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps / (ms / 1000.0)
+    R, Es = E.espnmf_iterate(ctx, 1)
+
+    # ---------------- per-kernel CUDA-event profile (same workload) ----------
+    E.espnmf_set_option(ctx, E.OPT_PROFILE, 1)
+    E.espnmf_kernel_stats_reset(ctx)
+    prof_steps = max(10, min(args.steps, 100))
+    E.espnmf_iterate(ctx, prof_steps, want_measures=False)
+    stats = E.espnmf_kernel_stats(ctx)
+    E.espnmf_set_option(ctx, E.OPT_PROFILE, 0)
+    dom = max(stats.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms, dbytes) = dom
+    hbm, src = peaks()
+    spmm = stats["spmm_sell"]
+    achieved = (spmm[2] / spmm[0]) / ((spmm[1] / spmm[0]) / 1000.0) / 1e9
+    kstats = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1),
+                  "share": v[1] / max(sum(x[1] for x in stats.values()), 1e-12)}
+              for k, v in stats.items() if v[0] > 0}
+    roofline = {"bound": "hbm", "kernel": "spmm_sell", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"
+                if src == "measured" else "fallback 6800 GB/s",
+                "bytes_per_launch": spmm[2] / spmm[0], "ms_per_launch": spmm[1] / spmm[0],
+                "traffic": kernel_traffic("spmm_sell"),
+                "dominant_by_time": dname}
+    E.espnmf_destroy(ctx)
+
+    # ---------------- FP64 form and the equal-error comparison ---------------
+    fp64 = None
+    if not args.no_fp64:
+        ctx64 = E.espnmf_init(rp, ci, dev(A.val), A.n, A.m, K_TOPICS, T_KEEP, T_KEEP,
+                              E.TOPT_COLUMN, E.F64, u0, stream=stream)
+        R64, E64 = E.espnmf_iterate(ctx64, JOB_ITERS)
+        n64 = max(3, min(args.steps // 4, 50))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        E.espnmf_iterate(ctx64, n64, want_measures=False)
+        b.record(stream)
+        b.synchronize()
+        v64 = n64 / (a.elapsed_time(b) / 1000.0)
+        E.espnmf_destroy(ctx64)
+        ctx32 = E.espnmf_init(rp, ci, va, A.n, A.m, K_TOPICS, T_KEEP, T_KEEP, E.TOPT_COLUMN,
+                              E.F32, u0, stream=stream)
+        R32, E32 = E.espnmf_iterate(ctx32, JOB_ITERS)
+        E.espnmf_destroy(ctx32)
+        fp64 = {"value": v64 * ws, "unit": UNIT, "final_E_fp64": float(E64[-1]),
+                "final_E_fp32": float(E32[-1]), "abs_dE": abs(float(E64[-1]) - float(E32[-1])),
+                "iters": JOB_ITERS, "speedup_fp32_over_fp64": value / (v64 * ws)}
+
+    # ---------------- end to end from host buffers ----------------------------
+    # A whole job as a user runs it: init from pinned host CSR + U0 (H2D and
+    # the context's layout build), JOB_ITERS sweeps with R/E read back, and
+    # both factors copied out in compact CSC form.
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_rp, h_ci, h_va, h_u0 = pin(A.rowptr), pin(A.colidx), pin(A32v), pin(U0)
+    h2d = sum(x.numel() * x.element_size() for x in (h_rp, h_ci, h_va, h_u0))
+    times, d2h = [], 0
+    for _ in range(max(args.e2e_jobs, 1)):
+        barrier()
+        t0 = time.perf_counter()
+        c = E.espnmf_init(h_rp, h_ci, h_va, A.n, A.m, K_TOPICS, T_KEEP, T_KEEP, E.TOPT_COLUMN,
+                          E.F32, h_u0, stream=stream)
+        Rj, Ej = E.espnmf_iterate(c, JOB_ITERS)
+        fu = E.espnmf_get_factor(c, E.U, E.CSC, np.float32)
+        fv = E.espnmf_get_factor(c, E.V, E.CSC, np.float32)
+        E.espnmf_destroy(c)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        d2h = sum(x.nbytes for x in (*fu, *fv, Rj, Ej))
+    tj = min(times)
+    if dist is not None:
+        t = torch.tensor([tj], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tj = float(t.item())
+    e2e = {"value": ws * JOB_ITERS / tj, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "step": f"one {JOB_ITERS}-iteration job from host CSR",
+           "seconds_per_job": tj}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(A, U0, 1)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": max(args.warmup, 3),
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": A.n, "m": A.m, "nnz": A.nnz,
+                           "k": K_TOPICS, "t": T_KEEP, "mode": "column",
+                           "forms": "f32 factors/SpMM/solve, f64 Gram/Cholesky/norms",
+                           "l2": "inputs larger than L2: A is streamed twice per sweep "
+                                 "(sliced-ELL f32, ~170 MB > 129 MB L2)",
+                           "parallelism": f"replicas x{ws}"},
+                "final_R": float(R[0]), "final_E": float(Es[0]),
+                "gpu_launches": launches * args.steps,
+                "clocks": clk.summary(), "roofline": roofline, "kernels": kstats,
+                "fp64_form": fp64, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,268 @@
+/*
+ * espnmf.h -- C ABI of the GB300 (sm_103a) library for enforced-sparsity
+ * alternating-least-squares non-negative matrix factorisation
+ * (Gavin, Gadepally, Kepner, arXiv:1510.05237).
+ *
+ * The problem (Eq. 1, Eq. 2): a non-negative data matrix A (n terms x m
+ * documents) is approximated by U V^T with U (n x k) >= 0 and V (m x k) >= 0.
+ * Alg. 2 alternates two half-steps, each a sparse product, a k x k Gram
+ * solve, a projection onto U, V >= 0 and an enforcement step that keeps
+ * only the t largest entries (per column by default, Sec. 4; or over the
+ * whole matrix as Alg. 2 prints it; or none, which is Alg. 1).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an espnmf_status; nothing throws across the ABI.
+ *     After a failure, espnmf_last_error(ctx) holds a one-line message.
+ *   - Sizes are int64_t; row/column indices are int32_t; CSR row pointers
+ *     are int64_t.  Dense matrices are row-major and contiguous (ld = cols).
+ *   - A context owns all device memory it allocates and copies every input
+ *     it is given, so the caller may free its buffers once a call returns.
+ *   - A context is used by one host thread at a time.  All device work is
+ *     enqueued on the context's stream (the caller's, or its own if the
+ *     caller passed NULL).  Calls that return host values synchronise that
+ *     stream; the others are asynchronous.
+ *   - The device that is current at espnmf_init is used for the context's
+ *     lifetime; every call makes it current again.
+ *   - There is no CPU fallback: without a usable CUDA device the calls
+ *     return ESPNMF_ERR_CUDA.
+ */
+#ifndef ESPNMF_H
+#define ESPNMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ESPNMF_OK = 0,
+    ESPNMF_ERR_INVALID_ARG = 1,   /* a size, pointer or option is out of range */
+    ESPNMF_ERR_BAD_MATRIX = 2,    /* A is not a valid non-negative CSR matrix (Eq. 1: A >= 0) */
+    ESPNMF_ERR_SINGULAR = 3,      /* a Gram matrix (U^T U or V^T V) is singular beyond its zero columns */
+    ESPNMF_ERR_NONFINITE = 4,     /* a NaN or Inf appeared in an input or an iterate */
+    ESPNMF_ERR_OOM = 5,           /* device or host allocation failed */
+    ESPNMF_ERR_CUDA = 6,          /* a CUDA call failed (no device, launch error, ...) */
+    ESPNMF_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+    ESPNMF_ERR_UNSUPPORTED = 8    /* a valid request this build does not implement */
+} espnmf_status;
+
+/* Arithmetic of a context (or the element type of a buffer).
+ * ESPNMF_F64: everything in FP64 (the plain form).
+ * ESPNMF_F32: A's values, the factors, the sparse products and the k x k
+ *   solve applied to each row in FP32; the Gram matrices, their Cholesky
+ *   factorisation and inverse, and the residual/error reductions in FP64. */
+typedef enum { ESPNMF_F64 = 0, ESPNMF_F32 = 1, ESPNMF_BF16 = 2 } espnmf_dtype;
+
+/* Enforcement step of Alg. 2 (steps 2 and 4).
+ * COLUMN: keep the t largest positive entries of every column (Sec. 4).
+ * MATRIX: keep the t largest positive entries of the whole factor (Alg. 2).
+ * NONE:   keep every positive entry (Alg. 1, projected ALS).
+ * In every mode exactly min(t, #positive) entries survive; among equal
+ * values the lower row index (COLUMN) or the lower row-major index i*k+c
+ * (MATRIX) wins; zeros are never kept. */
+typedef enum {
+    ESPNMF_TOPT_COLUMN = 0,
+    ESPNMF_TOPT_MATRIX = 1,
+    ESPNMF_TOPT_NONE = 2
+} espnmf_topt_mode;
+
+typedef enum { ESPNMF_U = 0, ESPNMF_V = 1 } espnmf_which;
+
+typedef enum {
+    ESPNMF_DENSE_ROWMAJOR = 0,   /* rows x k values, zeros included */
+    ESPNMF_CSC = 1,              /* ptr[k+1], idx[nnz] = row (ascending), val[nnz] */
+    ESPNMF_CSR = 2               /* ptr[rows+1], idx[nnz] = column (ascending), val[nnz] */
+} espnmf_layout;
+
+/* The data matrix A (n x m, Eq. 1), compressed sparse rows over terms.
+ * rowptr[n+1] non-decreasing from 0 to nnz; colidx[nnz] in [0, m),
+ * strictly increasing within each row; values[nnz] finite and >= 0, of
+ * type vdtype (F64 or F32).  on_device = 1 means all three arrays live in
+ * device memory of the current device, 0 means host memory. */
+typedef struct {
+    int64_t n;
+    int64_t m;
+    int64_t nnz;
+    const int64_t *rowptr;
+    const int32_t *colidx;
+    const void *values;
+    espnmf_dtype vdtype;
+    int32_t on_device;
+} espnmf_csr;
+
+typedef struct espnmf_ctx espnmf_ctx;
+
+/* ------------------------------------------------------------------------ */
+/* Set-up and tear-down                                                     */
+
+/* espnmf_init -- Alg. 2 "START": validate and copy A, set U = U0.
+ *   out      receives the new context (NULL on failure).
+ *   A        the data matrix (see espnmf_csr); validated: monotone rowptr,
+ *            sorted in-range column indices, finite non-negative values.
+ *   k        rank, 1 <= k <= min(n, m) and k <= 256.
+ *   t_u,t_v  maximum nonzeros kept in U and V (Alg. 2 input): per column in
+ *            COLUMN mode (values above the column length behave as the
+ *            column length), in total in MATRIX mode; ignored for NONE.
+ *            Must be >= 0.
+ *   mode     enforcement mode (see espnmf_topt_mode).
+ *   compute  ESPNMF_F64 or ESPNMF_F32 (ESPNMF_BF16 returns UNSUPPORTED).
+ *   U0       initial guess, n x k row-major of type U0_dtype (F64 or F32),
+ *            host (U0_on_device = 0) or device memory; entries must be
+ *            finite and >= 0.  U0 is not enforced (Alg. 2 starts from it
+ *            as given).
+ *   stream   a cudaStream_t for all of the context's work, or NULL to let
+ *            the context create its own.
+ * The context builds on the device: A in two sliced-ELLPACK layouts (rows
+ * of A and rows of A^T), U0 in the row-packed sparse factor layout, and
+ * the FP64 Gram U0^T U0 with its Cholesky factorisation. */
+espnmf_status espnmf_init(espnmf_ctx **out, const espnmf_csr *A, int32_t k,
+                          int64_t t_u, int64_t t_v, espnmf_topt_mode mode,
+                          espnmf_dtype compute, const void *U0,
+                          espnmf_dtype U0_dtype, int32_t U0_on_device,
+                          void *stream);
+
+/* espnmf_destroy -- frees everything the context owns (NULL is a no-op).
+ * Waits for the context's outstanding work first. */
+espnmf_status espnmf_destroy(espnmf_ctx *ctx);
+
+/* One-line description of the last failure on ctx ("" if none).  The
+ * pointer stays valid until the next call on ctx.  ctx may be NULL, which
+ * returns the message of the last failed espnmf_init on this thread. */
+const char *espnmf_last_error(const espnmf_ctx *ctx);
+
+/* Name of a status code. */
+const char *espnmf_status_string(espnmf_status st);
+
+/* ------------------------------------------------------------------------ */
+/* The alternating update (Alg. 2)                                          */
+
+/* espnmf_als_update_V -- Alg. 2 steps 1-2:
+ *   V = A^T U (U^T U)^-1, negative entries set to zero, then only the t_v
+ *   largest nonzeros kept (mode of the context).
+ * Also forms V^T V and its Cholesky factorisation for the next U update.
+ * Asynchronous.  Errors found on the device (a non-finite value, a singular
+ * V^T V) are reported by the next synchronising call. */
+espnmf_status espnmf_als_update_V(espnmf_ctx *ctx);
+
+/* espnmf_als_update_U -- Alg. 2 steps 3-4:
+ *   U = A V (V^T V)^-1, negative entries set to zero, then only the t_u
+ *   largest nonzeros kept.
+ * Also computes, on the device and without forming U V^T, the relative
+ * residual R = ||U_new - U_old||_F / ||U_new||_F and the relative error
+ * E = ||A - U V^T||_F / ||A||_F (Sec. 3.1), and U^T U with its Cholesky
+ * factorisation for the next V update.  Asynchronous. */
+espnmf_status espnmf_als_update_U(espnmf_ctx *ctx);
+
+/* espnmf_iterate -- `iters` sweeps of Alg. 2 (each: update_V then
+ * update_U).  R_out and E_out are host arrays of `iters` doubles receiving
+ * R and E after each sweep, or NULL.  Synchronises once at the end (only
+ * if R_out or E_out is non-NULL; otherwise it stays asynchronous).
+ * The sweep is replayed from a captured CUDA graph unless graphs were
+ * switched off with espnmf_set_option. */
+espnmf_status espnmf_iterate(espnmf_ctx *ctx, int32_t iters, double *R_out,
+                             double *E_out);
+
+/* espnmf_enforce_topt -- applies the enforcement rule (Alg. 2 step 2 or 4,
+ * per the context's mode) with a new limit t to the current U or V in
+ * place, then refreshes that factor's Gram matrix.  The context's own t_u /
+ * t_v are unchanged. */
+espnmf_status espnmf_enforce_topt(espnmf_ctx *ctx, espnmf_which which,
+                                  int64_t t);
+
+/* espnmf_set_factor -- replaces U or V with a dense rows x k row-major
+ * matrix (F64 or F32, host or device), finite and >= 0, without
+ * enforcement; refreshes its Gram matrix.  Used to start a step from a
+ * chosen iterate. */
+espnmf_status espnmf_set_factor(espnmf_ctx *ctx, espnmf_which which,
+                                const void *F, espnmf_dtype dtype,
+                                int32_t on_device);
+
+/* ------------------------------------------------------------------------ */
+/* Measures (Sec. 3.1)                                                      */
+
+/* espnmf_residual -- R = ||U_i - U_{i-1}||_F / ||U_i||_F of the last
+ * espnmf_als_update_U (U_{i-1} being U before that update).  R = 0 when
+ * both are zero, +inf when only U_i is zero.  Returns INVALID_ARG if no U
+ * update has run.  Synchronises. */
+espnmf_status espnmf_residual(espnmf_ctx *ctx, double *R);
+
+/* espnmf_error -- E = ||A - U V^T||_F / ||A||_F for the current U and V,
+ * through ||A||^2 - 2 <U, A V> + <U^T U, V^T V> (clamped at 0 before the
+ * square root; UV^T is never formed).  Reuses the last update's A V when V
+ * has not changed since, otherwise runs one sparse product.  E = 0 when
+ * ||A|| = 0.  Synchronises. */
+espnmf_status espnmf_error(espnmf_ctx *ctx, double *E);
+
+/* ------------------------------------------------------------------------ */
+/* Factors out                                                              */
+
+/* espnmf_factor_nnz -- number of nonzeros of U or V.  Synchronises. */
+espnmf_status espnmf_factor_nnz(espnmf_ctx *ctx, espnmf_which which,
+                                int64_t *nnz);
+
+/* espnmf_get_factor -- copies U (n x k) or V (m x k) out in `layout`.
+ *   DENSE_ROWMAJOR: val[rows*k]; ptr and idx unused (may be NULL).
+ *   CSC: ptr int64[k+1], idx int32[nnz] rows ascending per column, val[nnz].
+ *   CSR: ptr int64[rows+1], idx int32[nnz] columns ascending per row, val[nnz].
+ * nnz from espnmf_factor_nnz sizes the buffers.  Values are written as
+ * `dtype` (F64 or F32).  All buffers are host (on_device = 0) or device
+ * memory.  Synchronises. */
+espnmf_status espnmf_get_factor(espnmf_ctx *ctx, espnmf_which which,
+                                espnmf_layout layout, int64_t *ptr,
+                                int32_t *idx, void *val, espnmf_dtype dtype,
+                                int32_t on_device);
+
+/* ------------------------------------------------------------------------ */
+/* Options and instrumentation                                              */
+
+typedef enum {
+    ESPNMF_OPT_USE_GRAPH = 0,     /* 1 (default): espnmf_iterate replays a CUDA graph */
+    ESPNMF_OPT_PROFILE = 1,       /* 1: time every kernel launch with CUDA events (eager launches) */
+    ESPNMF_OPT_WAIT_LIMIT = 2     /* iteration limit of bounded device waits (default 1<<26) */
+} espnmf_option;
+
+espnmf_status espnmf_set_option(espnmf_ctx *ctx, espnmf_option opt,
+                                int64_t value);
+
+/* Kernel statistics gathered while ESPNMF_OPT_PROFILE is on.
+ * espnmf_kernel_stat_count gives the number of kernel kinds; for index i,
+ * espnmf_kernel_stat returns its name, launch count, summed event time (ms)
+ * and the algorithmic bytes it moved in total.  espnmf_kernel_stats_reset
+ * clears them.  Synchronises. */
+espnmf_status espnmf_kernel_stat_count(espnmf_ctx *ctx, int32_t *count);
+espnmf_status espnmf_kernel_stat(espnmf_ctx *ctx, int32_t i,
+                                 const char **name, int64_t *launches,
+                                 double *total_ms, double *bytes);
+espnmf_status espnmf_kernel_stats_reset(espnmf_ctx *ctx);
+
+/* Number of kernel launches one sweep (update_V + update_U) enqueues. */
+espnmf_status espnmf_launches_per_sweep(espnmf_ctx *ctx, int32_t *count);
+
+/* espnmf_sync -- waits for the context's stream; reports device errors. */
+espnmf_status espnmf_sync(espnmf_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Stand-alone selector                                                     */
+
+/* espnmf_enforce_topt_buffer -- projection plus enforcement (Alg. 2 steps
+ * 1-2 after the solve) on a caller's device buffer, in place:
+ *   X        rows x k row-major device matrix with leading dimension ld
+ *            (ld >= k), element type dtype (F64 or F32).
+ *   t, mode  as for the context (t >= 0).
+ * Every entry that is not > 0 becomes +0; of the positive entries only
+ * min(t, #positive) per column (COLUMN) or in total (MATRIX) survive.
+ * Scratch memory is allocated from the stream-ordered allocator and freed
+ * before the call returns.  Enqueued on `stream` (NULL: legacy default
+ * stream); synchronises that stream to report errors. */
+espnmf_status espnmf_enforce_topt_buffer(void *X, int64_t rows, int32_t k,
+                                         int64_t ld, espnmf_dtype dtype,
+                                         int64_t t, espnmf_topt_mode mode,
+                                         void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESPNMF_H */

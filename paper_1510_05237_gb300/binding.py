@@ -1,0 +1,307 @@
+"""Thin ctypes binding of the C ABI in include/espnmf.h.
+
+Argument marshalling only: every step of the factorisation runs in the CUDA
+library.  Functions keep the ABI's names.  Arrays may be numpy arrays (host
+memory) or torch tensors (host or CUDA memory); torch supplies device memory
+and streams.  A non-OK status raises EspnmfError.  There is no fallback: if
+the library has not been built, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "BAD_MATRIX", 3: "SINGULAR",
+                4: "NONFINITE", 5: "OOM", 6: "CUDA", 7: "TIMEOUT", 8: "UNSUPPORTED"}
+ERR_INVALID_ARG, ERR_BAD_MATRIX, ERR_SINGULAR, ERR_NONFINITE = 1, 2, 3, 4
+ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = 5, 6, 7, 8
+
+F64, F32, BF16 = 0, 1, 2
+TOPT_COLUMN, TOPT_MATRIX, TOPT_NONE = 0, 1, 2
+U, V = 0, 1
+DENSE_ROWMAJOR, CSC, CSR = 0, 1, 2
+OPT_USE_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT = 0, 1, 2
+
+
+class EspnmfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class _CSR(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p),
+                ("values", ctypes.c_void_p), ("vdtype", ctypes.c_int),
+                ("on_device", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads the built library (never builds it)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library not built: {_build.LIB} is missing "
+                               "(run __graft_entry__.build())")
+        lib = ctypes.CDLL(_build.LIB)
+        P, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        st = ctypes.c_int
+        sig = {
+            "espnmf_init": [ctypes.POINTER(P), ctypes.POINTER(_CSR), i32, i64, i64, st, st,
+                            P, st, i32, P],
+            "espnmf_destroy": [P],
+            "espnmf_als_update_V": [P],
+            "espnmf_als_update_U": [P],
+            "espnmf_iterate": [P, i32, P, P],
+            "espnmf_enforce_topt": [P, st, i64],
+            "espnmf_set_factor": [P, st, P, st, i32],
+            "espnmf_residual": [P, ctypes.POINTER(d)],
+            "espnmf_error": [P, ctypes.POINTER(d)],
+            "espnmf_factor_nnz": [P, st, ctypes.POINTER(i64)],
+            "espnmf_get_factor": [P, st, st, P, P, P, st, i32],
+            "espnmf_set_option": [P, st, i64],
+            "espnmf_kernel_stat_count": [P, ctypes.POINTER(i32)],
+            "espnmf_kernel_stat": [P, i32, ctypes.POINTER(ctypes.c_char_p),
+                                   ctypes.POINTER(i64), ctypes.POINTER(d), ctypes.POINTER(d)],
+            "espnmf_kernel_stats_reset": [P],
+            "espnmf_launches_per_sweep": [P, ctypes.POINTER(i32)],
+            "espnmf_sync": [P],
+            "espnmf_enforce_topt_buffer": [P, i64, i32, i64, st, i64, st, P],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        lib.espnmf_last_error.argtypes = [P]
+        lib.espnmf_last_error.restype = ctypes.c_char_p
+        lib.espnmf_status_string.argtypes = [ctypes.c_int]
+        lib.espnmf_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    """Names the binding resolves in the library (all must exist)."""
+    lib = load()
+    names = ["espnmf_init", "espnmf_destroy", "espnmf_last_error", "espnmf_status_string",
+             "espnmf_als_update_V", "espnmf_als_update_U", "espnmf_iterate",
+             "espnmf_enforce_topt", "espnmf_set_factor", "espnmf_residual", "espnmf_error",
+             "espnmf_factor_nnz", "espnmf_get_factor", "espnmf_set_option",
+             "espnmf_kernel_stat_count", "espnmf_kernel_stat", "espnmf_kernel_stats_reset",
+             "espnmf_launches_per_sweep", "espnmf_sync", "espnmf_enforce_topt_buffer"]
+    return {n: hasattr(lib, n) for n in names}
+
+
+def _check(st: int, handle=None):
+    if st != OK:
+        msg = load().espnmf_last_error(handle)
+        raise EspnmfError(st, (msg or b"").decode(errors="replace"))
+
+
+# --- array marshalling ---------------------------------------------------------
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, on_device, keepalive) of a contiguous numpy array / torch tensor."""
+    if _is_torch(x):
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda), x
+    a = np.ascontiguousarray(x)
+    return ctypes.c_void_p(a.ctypes.data), 0, a
+
+
+def _dtype_code(x) -> int:
+    name = str(x.dtype)
+    if "float64" in name:
+        return F64
+    if "float32" in name:
+        return F32
+    raise TypeError(f"unsupported element type {x.dtype}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """Owns an espnmf_ctx handle; freed by espnmf_destroy."""
+
+    def __init__(self, handle, n, m, k, compute):
+        self.handle = handle
+        self.n, self.m, self.k, self.compute = n, m, k, compute
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().espnmf_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+# --- the ABI, by name -------------------------------------------------------------
+
+def espnmf_init(rowptr, colidx, values, n: int, m: int, k: int, t_u: int, t_v: int,
+                mode: int = TOPT_COLUMN, compute: int = F32, U0=None, stream=None) -> Context:
+    lib = load()
+    rp, d1, k1 = _ptr(rowptr)
+    ci, d2, k2 = _ptr(colidx)
+    va, d3, k3 = _ptr(values)
+    if not (d1 == d2 == d3):
+        raise ValueError("rowptr, colidx and values must all be host or all device arrays")
+    if str(rowptr.dtype).split(".")[-1] != "int64" or str(colidx.dtype).split(".")[-1] != "int32":
+        raise TypeError("rowptr must be int64 and colidx int32")
+    csr = _CSR(int(n), int(m), int(len(colidx)), rp, ci, va, _dtype_code(values), d1)
+    up, ud, uk = _ptr(U0)
+    h = ctypes.c_void_p()
+    st = lib.espnmf_init(ctypes.byref(h), ctypes.byref(csr), int(k), int(t_u), int(t_v),
+                         int(mode), int(compute), up, _dtype_code(U0), ud,
+                         _stream_handle(stream))
+    _check(st, None)
+    return Context(h, int(n), int(m), int(k), int(compute))
+
+
+def espnmf_destroy(ctx: Context):
+    if ctx.handle:
+        _check(load().espnmf_destroy(ctx.handle))
+        ctx.handle = None
+
+
+def espnmf_als_update_V(ctx: Context):
+    _check(load().espnmf_als_update_V(ctx.handle), ctx.handle)
+
+
+def espnmf_als_update_U(ctx: Context):
+    _check(load().espnmf_als_update_U(ctx.handle), ctx.handle)
+
+
+def espnmf_iterate(ctx: Context, iters: int, want_measures: bool = True):
+    """Runs `iters` sweeps; returns (R, E) numpy arrays (or None)."""
+    if want_measures:
+        R = np.zeros(max(iters, 1))
+        E = np.zeros(max(iters, 1))
+        _check(load().espnmf_iterate(ctx.handle, int(iters), R.ctypes.data_as(ctypes.c_void_p),
+                                     E.ctypes.data_as(ctypes.c_void_p)), ctx.handle)
+        return R[:iters], E[:iters]
+    _check(load().espnmf_iterate(ctx.handle, int(iters), None, None), ctx.handle)
+    return None
+
+
+def espnmf_enforce_topt(ctx: Context, which: int, t: int):
+    _check(load().espnmf_enforce_topt(ctx.handle, int(which), int(t)), ctx.handle)
+
+
+def espnmf_set_factor(ctx: Context, which: int, F):
+    p, dev, keep = _ptr(F)
+    _check(load().espnmf_set_factor(ctx.handle, int(which), p, _dtype_code(F), dev), ctx.handle)
+
+
+def espnmf_residual(ctx: Context) -> float:
+    r = ctypes.c_double()
+    _check(load().espnmf_residual(ctx.handle, ctypes.byref(r)), ctx.handle)
+    return r.value
+
+
+def espnmf_error(ctx: Context) -> float:
+    e = ctypes.c_double()
+    _check(load().espnmf_error(ctx.handle, ctypes.byref(e)), ctx.handle)
+    return e.value
+
+
+def espnmf_factor_nnz(ctx: Context, which: int) -> int:
+    z = ctypes.c_int64()
+    _check(load().espnmf_factor_nnz(ctx.handle, int(which), ctypes.byref(z)), ctx.handle)
+    return z.value
+
+
+def espnmf_get_factor(ctx: Context, which: int, layout: int = DENSE_ROWMAJOR,
+                      dtype=np.float64):
+    """Returns the factor as numpy: a dense rows x k array, or (ptr, idx, val)."""
+    rows = ctx.n if which == U else ctx.m
+    code = F64 if np.dtype(dtype) == np.float64 else F32
+    lib = load()
+    if layout == DENSE_ROWMAJOR:
+        out = np.zeros((rows, ctx.k), dtype=dtype)
+        _check(lib.espnmf_get_factor(ctx.handle, int(which), layout, None, None,
+                                     out.ctypes.data_as(ctypes.c_void_p), code, 0), ctx.handle)
+        return out
+    nnz = espnmf_factor_nnz(ctx, which)
+    nptr = ctx.k + 1 if layout == CSC else rows + 1
+    ptr = np.zeros(nptr, dtype=np.int64)
+    idx = np.zeros(max(nnz, 1), dtype=np.int32)
+    val = np.zeros(max(nnz, 1), dtype=dtype)
+    _check(lib.espnmf_get_factor(ctx.handle, int(which), layout,
+                                 ptr.ctypes.data_as(ctypes.c_void_p),
+                                 idx.ctypes.data_as(ctypes.c_void_p),
+                                 val.ctypes.data_as(ctypes.c_void_p), code, 0), ctx.handle)
+    return ptr, idx[:nnz], val[:nnz]
+
+
+def espnmf_set_option(ctx: Context, opt: int, value: int):
+    _check(load().espnmf_set_option(ctx.handle, int(opt), int(value)), ctx.handle)
+
+
+def espnmf_kernel_stats(ctx: Context):
+    """{name: (launches, total_ms, bytes)} of the profiled kernel launches."""
+    lib = load()
+    n = ctypes.c_int32()
+    _check(lib.espnmf_kernel_stat_count(ctx.handle, ctypes.byref(n)), ctx.handle)
+    out = {}
+    for i in range(n.value):
+        name = ctypes.c_char_p()
+        cnt = ctypes.c_int64()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        _check(lib.espnmf_kernel_stat(ctx.handle, i, ctypes.byref(name), ctypes.byref(cnt),
+                                      ctypes.byref(ms), ctypes.byref(by)), ctx.handle)
+        out[name.value.decode()] = (cnt.value, ms.value, by.value)
+    return out
+
+
+def espnmf_kernel_stats_reset(ctx: Context):
+    _check(load().espnmf_kernel_stats_reset(ctx.handle), ctx.handle)
+
+
+def espnmf_launches_per_sweep(ctx: Context) -> int:
+    c = ctypes.c_int32()
+    _check(load().espnmf_launches_per_sweep(ctx.handle, ctypes.byref(c)), ctx.handle)
+    return c.value
+
+
+def espnmf_sync(ctx: Context):
+    _check(load().espnmf_sync(ctx.handle), ctx.handle)
+
+
+def espnmf_enforce_topt_buffer(X, t: int, mode: int = TOPT_COLUMN, stream=None):
+    """In-place projection + top-t on a CUDA tensor X (rows x k, row-major)."""
+    if not (_is_torch(X) and X.is_cuda):
+        raise TypeError("X must be a CUDA tensor")
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be 2-D with unit column stride")
+    _check(load().espnmf_enforce_topt_buffer(ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                             X.shape[1], X.stride(0), _dtype_code(X), int(t),
+                                             int(mode), _stream_handle(stream)))

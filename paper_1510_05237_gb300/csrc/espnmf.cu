@@ -1,0 +1,1211 @@
+// espnmf.cu -- the C ABI declared in include/espnmf.h: context set-up, the
+// alternating update of Alg. 2, the Sec. 3.1 measures, factor export,
+// options, profiling and CUDA-graph replay of whole sweeps.
+//
+// One sweep (update_V then update_U) enqueues, per half:
+//   cholesky(other factor's Gram)  on the auxiliary stream, concurrently with
+//   spmm (+ combine for split rows) on the main stream, then
+//   solve+project -> select -> finalize -> gram_reduce (+ measures for U).
+// The Cholesky of a factor's Gram only feeds the *next* half-step's solve,
+// so it is deferred to the start of that half and runs beside its SpMM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/espnmf.h"
+#include "common.cuh"
+
+using namespace espnmf;
+
+namespace espnmf {
+const char* kernel_name(int kind)
+{
+    static const char* names[K_COUNT] = {"spmm_sell", "spmm_combine", "solve_project",
+                                         "select_topt", "finalize", "gram_reduce",
+                                         "cholesky", "dense_to_ell", "norm2", "ell_dot",
+                                         "scatter"};
+    return kind >= 0 && kind < K_COUNT ? names[kind] : "?";
+}
+}  // namespace espnmf
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct Factor {
+    int64_t rows = 0;
+    EllDev buf[2];
+    int cur = 0;
+    double* G = nullptr;       // k x k FP64 Gram of the current factor
+    double* Ginv64 = nullptr;  // k x k FP64 inverse
+    void* GinvT = nullptr;     // k x k inverse in T
+    bool chol_pending = true;
+    bool valid = false;        // holds a value (V is empty until the first update)
+};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+    double bytes;
+};
+
+struct Stat {
+    int64_t launches = 0;
+    double ms = 0.0;
+    double bytes = 0.0;
+};
+
+}  // namespace
+
+struct espnmf_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
+    int64_t n = 0, m = 0, nnz = 0;
+    int k = 0;
+    int64_t t_u = 0, t_v = 0;
+    int mode = 0;
+    espnmf_dtype dt = ESPNMF_F32;
+    size_t esz = 4;
+
+    SellDev sA;   // rows of A   -> Y = A V
+    SellDev sAt;  // rows of A^T -> Y = A^T U
+    Factor U, V;
+
+    void* Y = nullptr;
+    int64_t ldy = 0;
+    void* Xt = nullptr;
+    int64_t ldx = 0;
+
+    int fin_blocks = 0;
+    double* gram_part = nullptr;
+    double* scal_part = nullptr;
+    double* scal = nullptr;
+    unsigned* gram_counter = nullptr;
+    double* A2 = nullptr;
+    double* norm_part = nullptr;
+    double* met = nullptr;      // [0] R, [1] E, [2] f, [3] trace
+    double* dot = nullptr;      // scratch scalar
+    double* hist_R = nullptr;
+    double* hist_E = nullptr;
+    int* hist_counter = nullptr;
+    int hist_cap = 0;
+    unsigned* status_d = nullptr;
+    unsigned* status_h = nullptr;
+
+    bool have_R = false;
+    bool Y_is_AV = false;
+    bool met_valid = false;
+
+    bool use_graph = true;
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+
+    bool profile = false;
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> ev_pool;
+    Stat stats[K_COUNT];
+    int launches_this = 0;
+    int64_t wait_limit = 1ll << 26;
+
+    std::vector<void*> allocs;
+    std::string err;
+};
+
+namespace {
+
+espnmf_status set_err(espnmf_ctx* c, espnmf_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_init_error = buf;
+    return s;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return set_err(ctx, ESPNMF_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__,    \
+                           #call, cudaGetErrorString(e_));                              \
+    } while (0)
+
+#define TRY(expr)                                \
+    do {                                         \
+        espnmf_status s_ = (expr);               \
+        if (s_ != ESPNMF_OK) return s_;          \
+    } while (0)
+
+template <typename P>
+espnmf_status dmalloc(espnmf_ctx* ctx, P** p, size_t bytes)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, ESPNMF_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes,
+                       cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(q);
+    *p = static_cast<P*>(q);
+    return ESPNMF_OK;
+}
+
+template <typename P>
+espnmf_status dupload(espnmf_ctx* ctx, P** p, const void* src, size_t bytes)
+{
+    TRY(dmalloc(ctx, p, bytes));
+    if (bytes) CU(cudaMemcpyAsync(*p, src, bytes, cudaMemcpyHostToDevice, ctx->st));
+    return ESPNMF_OK;
+}
+
+// --- kernel launches with optional event timing ------------------------------
+
+cudaEvent_t pool_event(espnmf_ctx* ctx)
+{
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+template <typename F>
+espnmf_status run(espnmf_ctx* ctx, int kind, double bytes, cudaStream_t s, F&& launch)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (ctx->profile) {
+        a = pool_event(ctx);
+        b = pool_event(ctx);
+        CU(cudaEventRecord(a, s));
+    }
+    cudaError_t e = launch();
+    if (e != cudaSuccess)
+        return set_err(ctx, ESPNMF_ERR_CUDA, "launch of %s failed: %s", kernel_name(kind),
+                       cudaGetErrorString(e));
+    ctx->launches_this++;
+    if (ctx->profile) {
+        CU(cudaEventRecord(b, s));
+        ctx->pending.push_back({kind, a, b, bytes});
+    }
+    return ESPNMF_OK;
+}
+
+espnmf_status collect_profile(espnmf_ctx* ctx)
+{
+    for (auto& r : ctx->pending) {
+        CU(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, r.a, r.b));
+        Stat& s = ctx->stats[r.kind];
+        s.launches++;
+        s.ms += ms;
+        s.bytes += r.bytes;
+        ctx->ev_pool.push_back(r.a);
+        ctx->ev_pool.push_back(r.b);
+    }
+    ctx->pending.clear();
+    return ESPNMF_OK;
+}
+
+// --- device status -------------------------------------------------------------
+
+espnmf_status check_status(espnmf_ctx* ctx)
+{
+    CU(cudaMemcpyAsync(ctx->status_h, ctx->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    CU(cudaGetLastError());
+    const unsigned s = *ctx->status_h;
+    if (s == 0) return ESPNMF_OK;
+    CU(cudaMemsetAsync(ctx->status_d, 0, sizeof(unsigned), ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    if (s & ST_SINGULAR)
+        return set_err(ctx, ESPNMF_ERR_SINGULAR,
+                       "a Gram matrix (U^T U or V^T V) is singular beyond its zero columns");
+    if (s & ST_NONFINITE) return set_err(ctx, ESPNMF_ERR_NONFINITE, "non-finite value in an iterate");
+    if (s & ST_BADINPUT) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "negative entry in a factor");
+    if (s & ST_TIMEOUT) return set_err(ctx, ESPNMF_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (s & ST_OVERFLOW) return set_err(ctx, ESPNMF_ERR_CUDA, "internal: factor row overflow");
+    return set_err(ctx, ESPNMF_ERR_CUDA, "unknown device status 0x%x", s);
+}
+
+// --- host-side layout of A ------------------------------------------------------
+
+template <typename T>
+struct SellHost {
+    int64_t rows = 0, nseg = 0, nslices = 0, total = 0, nnz = 0, npart = 0;
+    std::vector<int64_t> slice_ptr;
+    std::vector<int32_t> slice_len, idx, seg_row, seg_part, split_row, split_first,
+        split_count;
+    std::vector<T> val;
+};
+
+template <typename T>
+void build_sell(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
+                SellHost<T>& S)
+{
+    struct Seg {
+        int32_t row, len, part;
+        int64_t start;
+    };
+    std::vector<Seg> segs;
+    segs.reserve((size_t)rows + (size_t)(ptr[rows] / kSegMax) + 1);
+    int64_t npart = 0;
+    for (int64_t r = 0; r < rows; ++r) {
+        const int64_t len = ptr[r + 1] - ptr[r];
+        if (len <= kSegMax) {
+            segs.push_back({(int32_t)r, (int32_t)len, -1, ptr[r]});
+        } else {
+            const int64_t nsg = (len + kSegMax - 1) / kSegMax;
+            S.split_row.push_back((int32_t)r);
+            S.split_first.push_back((int32_t)npart);
+            S.split_count.push_back((int32_t)nsg);
+            for (int64_t q = 0; q < nsg; ++q) {
+                const int64_t l = std::min<int64_t>(kSegMax, len - q * kSegMax);
+                segs.push_back({(int32_t)r, (int32_t)l, (int32_t)npart++, ptr[r] + q * kSegMax});
+            }
+        }
+    }
+    // counting sort by length, longest first, stable
+    std::vector<int64_t> bucket(kSegMax + 2, 0);
+    for (auto& s : segs) bucket[kSegMax - s.len + 1]++;
+    for (int i = 1; i < kSegMax + 2; ++i) bucket[i] += bucket[i - 1];
+    std::vector<Seg> sorted(segs.size());
+    for (auto& s : segs) sorted[bucket[kSegMax - s.len]++] = s;
+    S.rows = rows;
+    S.nnz = ptr[rows];
+    S.npart = npart;
+    S.nseg = (int64_t)sorted.size();
+    S.nslices = (S.nseg + 31) / 32;
+    S.slice_ptr.assign(S.nslices + 1, 0);
+    S.slice_len.assign(S.nslices, 0);
+    for (int64_t s = 0; s < S.nslices; ++s) {
+        S.slice_len[s] = sorted[s * 32].len;
+        S.slice_ptr[s + 1] = S.slice_ptr[s] + (int64_t)S.slice_len[s] * 32;
+    }
+    S.total = S.slice_ptr[S.nslices];
+    S.idx.assign(S.total, -1);
+    S.val.assign(S.total, T(0));
+    S.seg_row.assign(S.nslices * 32, -1);
+    S.seg_part.assign(S.nslices * 32, -1);
+    for (int64_t g = 0; g < S.nseg; ++g) {
+        const Seg& sg = sorted[g];
+        const int64_t s = g / 32, lane = g % 32;
+        S.seg_row[g] = sg.row;
+        S.seg_part[g] = sg.part;
+        int64_t o = S.slice_ptr[s] + lane;
+        for (int p = 0; p < sg.len; ++p, o += 32) {
+            S.idx[o] = ind[sg.start + p];
+            S.val[o] = (T)vals[sg.start + p];
+        }
+    }
+}
+
+template <typename T>
+espnmf_status upload_sell(espnmf_ctx* ctx, const SellHost<T>& H, SellDev& D)
+{
+    D.rows = H.rows;
+    D.nseg = H.nseg;
+    D.nslices = H.nslices;
+    D.total = H.total;
+    D.nnz = H.nnz;
+    D.nsplit = (int64_t)H.split_row.size();
+    D.npart = H.npart;
+    TRY(dupload(ctx, &D.slice_ptr, H.slice_ptr.data(), H.slice_ptr.size() * 8));
+    TRY(dupload(ctx, &D.slice_len, H.slice_len.data(), H.slice_len.size() * 4));
+    TRY(dupload(ctx, &D.idx, H.idx.data(), H.idx.size() * 4));
+    TRY(dupload(ctx, &D.val, H.val.data(), H.val.size() * sizeof(T)));
+    TRY(dupload(ctx, &D.seg_row, H.seg_row.data(), H.seg_row.size() * 4));
+    TRY(dupload(ctx, &D.seg_part, H.seg_part.data(), H.seg_part.size() * 4));
+    TRY(dupload(ctx, &D.split_row, H.split_row.data(), H.split_row.size() * 4));
+    TRY(dupload(ctx, &D.split_first, H.split_first.data(), H.split_first.size() * 4));
+    TRY(dupload(ctx, &D.split_count, H.split_count.data(), H.split_count.size() * 4));
+    TRY(dmalloc(ctx, &D.partials, (size_t)H.npart * ctx->k * sizeof(T)));
+    // host vectors die with H: make sure the copies are done
+    CU(cudaStreamSynchronize(ctx->st));
+    return ESPNMF_OK;
+}
+
+// --- per-dtype dispatch ------------------------------------------------------------
+
+bool is_f64(const espnmf_ctx* ctx) { return ctx->dt == ESPNMF_F64; }
+
+espnmf_status do_spmm(espnmf_ctx* ctx, bool transA, const EllDev& F)
+{
+    const SellDev& S = transA ? ctx->sAt : ctx->sA;
+    const double bytes = (double)S.nnz * (4.0 + ctx->esz) + (double)(S.rows + 1) * 8.0 +
+                         (double)S.rows * ctx->k * ctx->esz;
+    TRY(run(ctx, K_SPMM, bytes, ctx->st, [&] {
+        return is_f64(ctx) ? launch_spmm<double>(S, F, ctx->k, (double*)ctx->Y, ctx->ldy, ctx->st,
+                                                 ctx->sm_count)
+                           : launch_spmm<float>(S, F, ctx->k, (float*)ctx->Y, ctx->ldy, ctx->st,
+                                                ctx->sm_count);
+    }));
+    if (S.nsplit > 0) {
+        const double cb = (double)S.npart * ctx->k * ctx->esz;
+        TRY(run(ctx, K_COMBINE, cb, ctx->st, [&] {
+            return is_f64(ctx) ? launch_spmm_combine<double>(S, ctx->k, (double*)ctx->Y, ctx->ldy, ctx->st)
+                               : launch_spmm_combine<float>(S, ctx->k, (float*)ctx->Y, ctx->ldy, ctx->st);
+        }));
+    }
+    return ESPNMF_OK;
+}
+
+espnmf_status do_cholesky(espnmf_ctx* ctx, Factor& F, cudaStream_t s)
+{
+    const double bytes = (double)ctx->k * ctx->k * (8.0 + 8.0 + ctx->esz);
+    return run(ctx, K_CHOLESKY, bytes, s, [&] {
+        return is_f64(ctx) ? launch_cholesky<double>(F.G, ctx->k, F.Ginv64, (double*)F.GinvT,
+                                                     ctx->status_d, s)
+                           : launch_cholesky<float>(F.G, ctx->k, F.Ginv64, (float*)F.GinvT,
+                                                    ctx->status_d, s);
+    });
+}
+
+// Gram partials + reduction of factor F (its current buffer); optional old
+// buffer for the residual / count zeroing, optional Y for the cross term.
+espnmf_status do_finalize(espnmf_ctx* ctx, Factor& F, const EllDev& cur, const EllDev* old,
+                          bool residual, const void* Y, bool metrics)
+{
+    EllDev none;
+    const EllDev& o = old ? *old : none;
+    const double bytes = (double)F.rows * 4.0 * (old ? 2.0 : 1.0) +
+                         (double)ctx->fin_blocks * ctx->k * ctx->k * 8.0;
+    TRY(run(ctx, K_FINALIZE, bytes, ctx->st, [&] {
+        return is_f64(ctx)
+                   ? launch_finalize<double>(F.rows, ctx->k, cur, o, residual, old != nullptr,
+                                             (const double*)Y, ctx->ldy, ctx->gram_part,
+                                             ctx->scal_part, ctx->fin_blocks, ctx->st)
+                   : launch_finalize<float>(F.rows, ctx->k, cur, o, residual, old != nullptr,
+                                            (const float*)Y, ctx->ldy, ctx->gram_part,
+                                            ctx->scal_part, ctx->fin_blocks, ctx->st);
+    }));
+    MetricsArgs ma;
+    if (metrics) {
+        ma.enabled = true;
+        ma.G_other = ctx->V.G;
+        ma.A2 = ctx->A2;
+        ma.out = ctx->met;
+        ma.hist_R = ctx->hist_R;
+        ma.hist_E = ctx->hist_E;
+        ma.hist_counter = ctx->hist_counter;
+        ma.hist_cap = ctx->hist_cap;
+    }
+    const double rb = (double)ctx->fin_blocks * ctx->k * ctx->k * 8.0;
+    TRY(run(ctx, K_GRAM_REDUCE, rb, ctx->st, [&] {
+        return launch_gram_reduce(ctx->gram_part, ctx->scal_part, ctx->fin_blocks, ctx->k, F.G,
+                                  ctx->scal, ctx->gram_counter, ma, ctx->st);
+    }));
+    F.chol_pending = true;
+    return ESPNMF_OK;
+}
+
+// Alg. 2 steps 1-2 (updV) or 3-4.
+espnmf_status half_update(espnmf_ctx* ctx, bool updV)
+{
+    Factor& F = updV ? ctx->V : ctx->U;
+    Factor& O = updV ? ctx->U : ctx->V;
+    const int64_t rows = F.rows;
+    // The other factor's Cholesky runs beside the SpMM.
+    CU(cudaEventRecord(ctx->ev_fork, ctx->st));
+    CU(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    TRY(do_cholesky(ctx, O, ctx->aux));
+    CU(cudaEventRecord(ctx->ev_join, ctx->aux));
+    O.chol_pending = false;
+
+    TRY(do_spmm(ctx, updV, O.buf[O.cur]));
+    CU(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
+
+    const double sb = (double)rows * ctx->k * ctx->esz * 2.0;
+    TRY(run(ctx, K_SOLVE, sb, ctx->st, [&] {
+        return is_f64(ctx) ? launch_solve<double>((const double*)ctx->Y, ctx->ldy, rows, ctx->k,
+                                                  (const double*)O.GinvT, (double*)ctx->Xt,
+                                                  ctx->ldx, ctx->status_d, ctx->st, ctx->sm_count)
+                           : launch_solve<float>((const float*)ctx->Y, ctx->ldy, rows, ctx->k,
+                                                 (const float*)O.GinvT, (float*)ctx->Xt, ctx->ldx,
+                                                 ctx->status_d, ctx->st, ctx->sm_count);
+    }));
+    const int64_t t = updV ? ctx->t_v : ctx->t_u;
+    EllDev& nxt = F.buf[F.cur ^ 1];
+    const double selb = (double)rows * ctx->k * ctx->esz;
+    TRY(run(ctx, K_SELECT, selb, ctx->st, [&] {
+        return is_f64(ctx) ? launch_select<double>((const double*)ctx->Xt, ctx->ldx, rows, ctx->k,
+                                                   t, ctx->mode, nxt, ctx->status_d, ctx->st, ctx->sm_count)
+                           : launch_select<float>((const float*)ctx->Xt, ctx->ldx, rows, ctx->k,
+                                                  t, ctx->mode, nxt, ctx->status_d, ctx->st, ctx->sm_count);
+    }));
+    EllDev old = F.buf[F.cur];
+    TRY(do_finalize(ctx, F, nxt, &old, !updV && F.valid, updV ? nullptr : ctx->Y, !updV));
+    F.cur ^= 1;
+    F.valid = true;
+    if (updV) {
+        ctx->Y_is_AV = false;
+        ctx->met_valid = false;
+    } else {
+        ctx->Y_is_AV = true;
+        ctx->met_valid = true;
+        ctx->have_R = true;
+    }
+    return ESPNMF_OK;
+}
+
+espnmf_status enqueue_sweep(espnmf_ctx* ctx)
+{
+    TRY(half_update(ctx, true));
+    TRY(half_update(ctx, false));
+    return ESPNMF_OK;
+}
+
+struct HostState {
+    int ucur, vcur;
+    bool upend, vpend, uvalid, vvalid, have_R, Y_is_AV, met_valid;
+};
+
+HostState save_state(const espnmf_ctx* c)
+{
+    return {c->U.cur, c->V.cur, c->U.chol_pending, c->V.chol_pending, c->U.valid, c->V.valid,
+            c->have_R, c->Y_is_AV, c->met_valid};
+}
+
+void restore_state(espnmf_ctx* c, const HostState& s)
+{
+    c->U.cur = s.ucur;
+    c->V.cur = s.vcur;
+    c->U.chol_pending = s.upend;
+    c->V.chol_pending = s.vpend;
+    c->U.valid = s.uvalid;
+    c->V.valid = s.vvalid;
+    c->have_R = s.have_R;
+    c->Y_is_AV = s.Y_is_AV;
+    c->met_valid = s.met_valid;
+}
+
+void drop_graphs(espnmf_ctx* ctx)
+{
+    for (auto& row : ctx->gexec)
+        for (auto& g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+}
+
+espnmf_status sweep_graph(espnmf_ctx* ctx, cudaGraphExec_t* out)
+{
+    const HostState s0 = save_state(ctx);
+    // the graph is captured once V exists; a sweep always has it afterwards
+    CU(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+    espnmf_status st = enqueue_sweep(ctx);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+    restore_state(ctx, s0);
+    if (st != ESPNMF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return set_err(ctx, ESPNMF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_err(ctx, ESPNMF_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return ESPNMF_OK;
+}
+
+void after_sweep_state(espnmf_ctx* c)
+{
+    c->U.cur ^= 1;
+    c->V.cur ^= 1;
+    c->U.chol_pending = true;
+    c->V.chol_pending = true;
+    c->U.valid = c->V.valid = true;
+    c->have_R = c->Y_is_AV = c->met_valid = true;
+}
+
+espnmf_status ensure_hist(espnmf_ctx* ctx, int need)
+{
+    if (need <= ctx->hist_cap) return ESPNMF_OK;
+    int cap = std::max(need, std::max(64, ctx->hist_cap * 2));
+    double *r = nullptr, *e = nullptr;
+    TRY(dmalloc(ctx, &r, sizeof(double) * cap));
+    TRY(dmalloc(ctx, &e, sizeof(double) * cap));
+    ctx->hist_R = r;
+    ctx->hist_E = e;
+    ctx->hist_cap = cap;
+    drop_graphs(ctx);   // the captured sweeps point at the old arrays
+    return ESPNMF_OK;
+}
+
+espnmf_status enter(espnmf_ctx* ctx)
+{
+    if (!ctx) return ESPNMF_ERR_INVALID_ARG;
+    ctx->err.clear();
+    CU(cudaSetDevice(ctx->device));
+    return ESPNMF_OK;
+}
+
+template <typename Tin>
+espnmf_status load_factor_dense(espnmf_ctx* ctx, Factor& F, const Tin* dptr)
+{
+    EllDev& cur = F.buf[F.cur];
+    return run(ctx, K_DENSE_TO_ELL, (double)F.rows * ctx->k * sizeof(Tin), ctx->st, [&] {
+        return is_f64(ctx) ? launch_dense_to_ell<Tin, double>(dptr, F.rows, ctx->k, cur,
+                                                              ctx->status_d, ctx->st)
+                           : launch_dense_to_ell<Tin, float>(dptr, F.rows, ctx->k, cur,
+                                                             ctx->status_d, ctx->st);
+    });
+}
+
+// Replaces factor F by a dense rows x k matrix (host or device).
+espnmf_status set_factor_impl(espnmf_ctx* ctx, Factor& F, const void* src, espnmf_dtype dtype,
+                              int on_device)
+{
+    if (!src) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "factor pointer is NULL");
+    if (dtype != ESPNMF_F64 && dtype != ESPNMF_F32)
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "factor dtype must be F64 or F32");
+    const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
+    const size_t bytes = (size_t)F.rows * ctx->k * es;
+    const void* dptr = src;
+    void* tmp = nullptr;
+    if (!on_device) {
+        CU(cudaMallocAsync(&tmp, bytes ? bytes : 16, ctx->st));
+        CU(cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, ctx->st));
+        dptr = tmp;
+    }
+    espnmf_status s = dtype == ESPNMF_F64 ? load_factor_dense(ctx, F, (const double*)dptr)
+                                          : load_factor_dense(ctx, F, (const float*)dptr);
+    if (tmp) CU(cudaFreeAsync(tmp, ctx->st));
+    TRY(s);
+    TRY(check_status(ctx));
+    TRY(do_finalize(ctx, F, F.buf[F.cur], nullptr, false, nullptr, false));
+    F.valid = true;
+    return ESPNMF_OK;
+}
+
+espnmf_status fail_init(espnmf_ctx* ctx, espnmf_status s)
+{
+    g_init_error = ctx->err;
+    espnmf_destroy(ctx);
+    return s;
+}
+
+}  // namespace
+
+// =================================================================================
+// Public entry points
+
+extern "C" {
+
+const char* espnmf_status_string(espnmf_status s)
+{
+    switch (s) {
+    case ESPNMF_OK: return "ESPNMF_OK";
+    case ESPNMF_ERR_INVALID_ARG: return "ESPNMF_ERR_INVALID_ARG";
+    case ESPNMF_ERR_BAD_MATRIX: return "ESPNMF_ERR_BAD_MATRIX";
+    case ESPNMF_ERR_SINGULAR: return "ESPNMF_ERR_SINGULAR";
+    case ESPNMF_ERR_NONFINITE: return "ESPNMF_ERR_NONFINITE";
+    case ESPNMF_ERR_OOM: return "ESPNMF_ERR_OOM";
+    case ESPNMF_ERR_CUDA: return "ESPNMF_ERR_CUDA";
+    case ESPNMF_ERR_TIMEOUT: return "ESPNMF_ERR_TIMEOUT";
+    case ESPNMF_ERR_UNSUPPORTED: return "ESPNMF_ERR_UNSUPPORTED";
+    }
+    return "ESPNMF_ERR_UNKNOWN";
+}
+
+const char* espnmf_last_error(const espnmf_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int64_t t_u,
+                          int64_t t_v, espnmf_topt_mode mode, espnmf_dtype compute,
+                          const void* U0, espnmf_dtype U0_dtype, int32_t U0_on_device,
+                          void* stream)
+{
+    g_init_error.clear();
+    if (!out) return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!A || !U0) return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "A or U0 is NULL");
+    if (compute == ESPNMF_BF16)
+        return set_err(nullptr, ESPNMF_ERR_UNSUPPORTED, "BF16 compute is not implemented");
+    if (compute != ESPNMF_F64 && compute != ESPNMF_F32)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "compute must be F64 or F32");
+    if (A->n < 1 || A->m < 1 || A->nnz < 0)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "A must have n >= 1, m >= 1, nnz >= 0");
+    if (A->n >= (1ll << 31) || A->m >= (1ll << 31))
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "n and m must be < 2^31");
+    if (k < 1 || k > 128 || k > A->n || k > A->m)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "k must satisfy 1 <= k <= min(n, m, 128)");
+    if (t_u < 0 || t_v < 0) return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "t must be >= 0");
+    if (mode != ESPNMF_TOPT_COLUMN && mode != ESPNMF_TOPT_MATRIX && mode != ESPNMF_TOPT_NONE)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "unknown enforcement mode");
+    if (mode == ESPNMF_TOPT_MATRIX &&
+        ((int64_t)k * A->n >= (1ll << 31) || (int64_t)k * A->m >= (1ll << 31)))
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "matrix mode needs rows*k < 2^31");
+    if (A->vdtype != ESPNMF_F64 && A->vdtype != ESPNMF_F32)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "A values must be F64 or F32");
+    if (U0_dtype != ESPNMF_F64 && U0_dtype != ESPNMF_F32)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "U0 dtype must be F64 or F32");
+    if (A->nnz > 0 && (!A->rowptr || !A->colidx || !A->values))
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "A arrays are NULL");
+
+    espnmf_ctx* ctx = new (std::nothrow) espnmf_ctx();
+    if (!ctx) return set_err(nullptr, ESPNMF_ERR_OOM, "host allocation failed");
+    ctx->n = A->n;
+    ctx->m = A->m;
+    ctx->nnz = A->nnz;
+    ctx->k = k;
+    ctx->t_u = t_u;
+    ctx->t_v = t_v;
+    ctx->mode = (int)mode;
+    ctx->dt = compute;
+    ctx->esz = compute == ESPNMF_F64 ? 8 : 4;
+    {
+        cudaError_t e = cudaGetDevice(&ctx->device);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+        if (e != cudaSuccess) {
+            set_err(ctx, ESPNMF_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+            cudaGetLastError();
+            return fail_init(ctx, ESPNMF_ERR_CUDA);
+        }
+    }
+    espnmf_status s = [&]() -> espnmf_status {
+        if (stream) {
+            ctx->st = (cudaStream_t)stream;
+        } else {
+            CU(cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking));
+            ctx->own_stream = true;
+        }
+        CU(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+        CU(setup_spmm());
+        CU(setup_solve());
+        CU(setup_select());
+        CU(setup_factor());
+
+        // ---- A: bring to the host, validate, build both layouts
+        const int64_t n = A->n, m = A->m, nnz = A->nnz;
+        std::vector<int64_t> rp(n + 1);
+        std::vector<int32_t> ci(nnz);
+        std::vector<double> vv(nnz);
+        const size_t vsz = A->vdtype == ESPNMF_F64 ? 8 : 4;
+        std::vector<unsigned char> vraw(nnz * vsz);
+        if (A->on_device) {
+            CU(cudaMemcpy(rp.data(), A->rowptr, (n + 1) * 8, cudaMemcpyDeviceToHost));
+            if (nnz) {
+                CU(cudaMemcpy(ci.data(), A->colidx, nnz * 4, cudaMemcpyDeviceToHost));
+                CU(cudaMemcpy(vraw.data(), A->values, nnz * vsz, cudaMemcpyDeviceToHost));
+            }
+        } else {
+            if (!A->rowptr) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "rowptr is NULL");
+            memcpy(rp.data(), A->rowptr, (n + 1) * 8);
+            if (nnz) {
+                memcpy(ci.data(), A->colidx, nnz * 4);
+                memcpy(vraw.data(), A->values, nnz * vsz);
+            }
+        }
+        for (int64_t p = 0; p < nnz; ++p) {
+            double x;
+            if (vsz == 8) memcpy(&x, &vraw[p * 8], 8);
+            else {
+                float f;
+                memcpy(&f, &vraw[p * 4], 4);
+                x = f;
+            }
+            vv[p] = x;
+        }
+        if (rp[0] != 0 || rp[n] != nnz)
+            return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "rowptr must run from 0 to nnz");
+        for (int64_t r = 0; r < n; ++r) {
+            if (rp[r + 1] < rp[r]) return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "rowptr decreases at row %lld", (long long)r);
+            for (int64_t p = rp[r]; p < rp[r + 1]; ++p) {
+                if (ci[p] < 0 || ci[p] >= m)
+                    return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "column index out of range in row %lld", (long long)r);
+                if (p > rp[r] && ci[p] <= ci[p - 1])
+                    return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "column indices not strictly increasing in row %lld", (long long)r);
+                if (!std::isfinite(vv[p]))
+                    return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "non-finite value in row %lld", (long long)r);
+                if (vv[p] < 0.0)
+                    return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "negative value in row %lld (A >= 0 is required)", (long long)r);
+            }
+        }
+        // CSC (= CSR of A^T), rows ascending inside each column
+        std::vector<int64_t> cp(m + 1, 0);
+        for (int64_t p = 0; p < nnz; ++p) cp[ci[p] + 1]++;
+        for (int64_t j = 0; j < m; ++j) cp[j + 1] += cp[j];
+        std::vector<int32_t> ri(nnz);
+        std::vector<double> cv(nnz);
+        {
+            std::vector<int64_t> nx(cp.begin(), cp.end() - 1);
+            for (int64_t r = 0; r < n; ++r)
+                for (int64_t p = rp[r]; p < rp[r + 1]; ++p) {
+                    const int64_t q = nx[ci[p]]++;
+                    ri[q] = (int32_t)r;
+                    cv[q] = vv[p];
+                }
+        }
+        if (compute == ESPNMF_F64) {
+            SellHost<double> h1, h2;
+            build_sell(n, rp.data(), ci.data(), vv.data(), h1);
+            TRY(upload_sell(ctx, h1, ctx->sA));
+            build_sell(m, cp.data(), ri.data(), cv.data(), h2);
+            TRY(upload_sell(ctx, h2, ctx->sAt));
+        } else {
+            SellHost<float> h1, h2;
+            build_sell(n, rp.data(), ci.data(), vv.data(), h1);
+            TRY(upload_sell(ctx, h1, ctx->sA));
+            build_sell(m, cp.data(), ri.data(), cv.data(), h2);
+            TRY(upload_sell(ctx, h2, ctx->sAt));
+        }
+
+        // ---- work buffers
+        const int64_t rmax = std::max(n, m);
+        ctx->ldy = ctx->esz == 8 ? (k + 1) / 2 * 2 : (k + 3) / 4 * 4;
+        ctx->ldx = (rmax + 31) / 32 * 32;
+        TRY(dmalloc(ctx, &ctx->Y, (size_t)rmax * ctx->ldy * ctx->esz));
+        TRY(dmalloc(ctx, &ctx->Xt, (size_t)k * ctx->ldx * ctx->esz));
+        CU(cudaMemsetAsync(ctx->Xt, 0, (size_t)k * ctx->ldx * ctx->esz, ctx->st));
+        ctx->fin_blocks = ctx->sm_count;
+        TRY(dmalloc(ctx, &ctx->gram_part, sizeof(double) * ctx->fin_blocks * k * k));
+        TRY(dmalloc(ctx, &ctx->scal_part, sizeof(double) * ctx->fin_blocks * 4));
+        TRY(dmalloc(ctx, &ctx->scal, sizeof(double) * 4));
+        TRY(dmalloc(ctx, &ctx->gram_counter, sizeof(unsigned)));
+        CU(cudaMemsetAsync(ctx->gram_counter, 0, sizeof(unsigned), ctx->st));
+        TRY(dmalloc(ctx, &ctx->A2, sizeof(double)));
+        TRY(dmalloc(ctx, &ctx->norm_part, sizeof(double) * ctx->sm_count));
+        TRY(dmalloc(ctx, &ctx->met, sizeof(double) * 4));
+        CU(cudaMemsetAsync(ctx->met, 0, sizeof(double) * 4, ctx->st));
+        TRY(dmalloc(ctx, &ctx->dot, sizeof(double)));
+        TRY(dmalloc(ctx, &ctx->hist_counter, sizeof(int)));
+        CU(cudaMemsetAsync(ctx->hist_counter, 0, sizeof(int), ctx->st));
+        TRY(ensure_hist(ctx, 64));
+        TRY(dmalloc(ctx, &ctx->status_d, sizeof(unsigned)));
+        CU(cudaMemsetAsync(ctx->status_d, 0, sizeof(unsigned), ctx->st));
+        CU(cudaMallocHost(&ctx->status_h, sizeof(unsigned)));
+
+        for (Factor* F : {&ctx->U, &ctx->V}) {
+            F->rows = F == &ctx->U ? n : m;
+            for (int b = 0; b < 2; ++b) {
+                TRY(dmalloc(ctx, &F->buf[b].cnt, sizeof(int32_t) * F->rows));
+                TRY(dmalloc(ctx, &F->buf[b].col, sizeof(int32_t) * F->rows * k));
+                TRY(dmalloc(ctx, &F->buf[b].val, ctx->esz * F->rows * k));
+                CU(cudaMemsetAsync(F->buf[b].cnt, 0, sizeof(int32_t) * F->rows, ctx->st));
+            }
+            TRY(dmalloc(ctx, &F->G, sizeof(double) * k * k));
+            CU(cudaMemsetAsync(F->G, 0, sizeof(double) * k * k, ctx->st));
+            TRY(dmalloc(ctx, &F->Ginv64, sizeof(double) * k * k));
+            TRY(dmalloc(ctx, &F->GinvT, ctx->esz * k * k));
+        }
+
+        // ---- ||A||^2 from the values the kernels use
+        if (is_f64(ctx))
+            TRY(run(ctx, K_NORM2, (double)ctx->sA.total * 8, ctx->st, [&] {
+                return launch_norm2<double>((const double*)ctx->sA.val, ctx->sA.total,
+                                            ctx->norm_part, ctx->sm_count, ctx->A2, ctx->st);
+            }));
+        else
+            TRY(run(ctx, K_NORM2, (double)ctx->sA.total * 4, ctx->st, [&] {
+                return launch_norm2<float>((const float*)ctx->sA.val, ctx->sA.total,
+                                           ctx->norm_part, ctx->sm_count, ctx->A2, ctx->st);
+            }));
+
+        // ---- U = U0 (Alg. 2 START; not enforced)
+        TRY(set_factor_impl(ctx, ctx->U, U0, U0_dtype, U0_on_device));
+        TRY(check_status(ctx));
+        return ESPNMF_OK;
+    }();
+    if (s != ESPNMF_OK) return fail_init(ctx, s);
+    *out = ctx;
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_destroy(espnmf_ctx* ctx)
+{
+    if (!ctx) return ESPNMF_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    if (ctx->aux) cudaStreamSynchronize(ctx->aux);
+    drop_graphs(ctx);
+    for (auto& r : ctx->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->status_h) cudaFreeHost(ctx->status_h);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
+    cudaGetLastError();
+    delete ctx;
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_als_update_V(espnmf_ctx* ctx)
+{
+    TRY(enter(ctx));
+    ctx->launches_this = 0;
+    return half_update(ctx, true);
+}
+
+espnmf_status espnmf_als_update_U(espnmf_ctx* ctx)
+{
+    TRY(enter(ctx));
+    if (!ctx->V.valid)
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "V has no value yet: update V (or set it) first");
+    ctx->launches_this = 0;
+    return half_update(ctx, false);
+}
+
+espnmf_status espnmf_iterate(espnmf_ctx* ctx, int32_t iters, double* R_out, double* E_out)
+{
+    TRY(enter(ctx));
+    if (iters < 0) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "iters must be >= 0");
+    if (iters == 0) return ESPNMF_OK;
+    TRY(ensure_hist(ctx, iters));
+    CU(cudaMemsetAsync(ctx->hist_counter, 0, sizeof(int), ctx->st));
+    int it = 0;
+    // the first sweep from U0 runs eagerly: V does not exist before it
+    if (!ctx->V.valid || !ctx->use_graph || ctx->profile) {
+        TRY(enqueue_sweep(ctx));
+        ++it;
+    }
+    if (ctx->use_graph && !ctx->profile) {
+        for (; it < iters; ++it) {
+            cudaGraphExec_t& g = ctx->gexec[ctx->U.cur][ctx->V.cur];
+            if (!g) TRY(sweep_graph(ctx, &g));
+            CU(cudaGraphLaunch(g, ctx->st));
+            after_sweep_state(ctx);
+        }
+    } else {
+        for (; it < iters; ++it) TRY(enqueue_sweep(ctx));
+    }
+    if (R_out || E_out) {
+        TRY(check_status(ctx));
+        if (R_out) CU(cudaMemcpy(R_out, ctx->hist_R, sizeof(double) * iters, cudaMemcpyDeviceToHost));
+        if (E_out) CU(cudaMemcpy(E_out, ctx->hist_E, sizeof(double) * iters, cudaMemcpyDeviceToHost));
+    }
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_enforce_topt(espnmf_ctx* ctx, espnmf_which which, int64_t t)
+{
+    TRY(enter(ctx));
+    if (which != ESPNMF_U && which != ESPNMF_V) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "which");
+    if (t < 0) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "t must be >= 0");
+    Factor& F = which == ESPNMF_U ? ctx->U : ctx->V;
+    if (!F.valid) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "factor has no value yet");
+    EllDev& cur = F.buf[F.cur];
+    EllDev& nxt = F.buf[F.cur ^ 1];
+    TRY(run(ctx, K_SCATTER, (double)F.rows * ctx->k * ctx->esz, ctx->st, [&] {
+        return is_f64(ctx) ? launch_ell_to_colmajor<double>(F.rows, ctx->k, cur, (double*)ctx->Xt, ctx->ldx, ctx->st)
+                           : launch_ell_to_colmajor<float>(F.rows, ctx->k, cur, (float*)ctx->Xt, ctx->ldx, ctx->st);
+    }));
+    TRY(run(ctx, K_SELECT, (double)F.rows * ctx->k * ctx->esz, ctx->st, [&] {
+        return is_f64(ctx) ? launch_select<double>((const double*)ctx->Xt, ctx->ldx, F.rows, ctx->k, t,
+                                                   ctx->mode, nxt, ctx->status_d, ctx->st, ctx->sm_count)
+                           : launch_select<float>((const float*)ctx->Xt, ctx->ldx, F.rows, ctx->k, t,
+                                                  ctx->mode, nxt, ctx->status_d, ctx->st, ctx->sm_count);
+    }));
+    TRY(do_finalize(ctx, F, nxt, &cur, false, nullptr, false));
+    F.cur ^= 1;
+    ctx->met_valid = false;
+    if (which == ESPNMF_V) ctx->Y_is_AV = false;
+    return check_status(ctx);
+}
+
+espnmf_status espnmf_set_factor(espnmf_ctx* ctx, espnmf_which which, const void* F,
+                                espnmf_dtype dtype, int32_t on_device)
+{
+    TRY(enter(ctx));
+    if (which != ESPNMF_U && which != ESPNMF_V) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "which");
+    Factor& Fa = which == ESPNMF_U ? ctx->U : ctx->V;
+    TRY(set_factor_impl(ctx, Fa, F, dtype, on_device));
+    ctx->met_valid = false;
+    if (which == ESPNMF_V) ctx->Y_is_AV = false;
+    else ctx->have_R = false;
+    return check_status(ctx);
+}
+
+espnmf_status espnmf_residual(espnmf_ctx* ctx, double* R)
+{
+    TRY(enter(ctx));
+    if (!R) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "R is NULL");
+    if (!ctx->have_R) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "no U update has run");
+    TRY(check_status(ctx));
+    CU(cudaMemcpy(R, ctx->met, sizeof(double), cudaMemcpyDeviceToHost));
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_error(espnmf_ctx* ctx, double* E)
+{
+    TRY(enter(ctx));
+    if (!E) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "E is NULL");
+    if (!ctx->V.valid) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "V has no value yet");
+    if (!ctx->met_valid) {
+        if (!ctx->Y_is_AV) {
+            TRY(do_spmm(ctx, false, ctx->V.buf[ctx->V.cur]));
+            ctx->Y_is_AV = true;
+        }
+        EllDev& u = ctx->U.buf[ctx->U.cur];
+        TRY(run(ctx, K_DOT, (double)ctx->n * 4, ctx->st, [&] {
+            return is_f64(ctx) ? launch_ell_dot<double>(ctx->n, ctx->k, u, (const double*)ctx->Y, ctx->ldy,
+                                                        ctx->norm_part, ctx->sm_count, ctx->dot, ctx->st)
+                               : launch_ell_dot<float>(ctx->n, ctx->k, u, (const float*)ctx->Y, ctx->ldy,
+                                                       ctx->norm_part, ctx->sm_count, ctx->dot, ctx->st);
+        }));
+        // E from ||A||^2, <U, AV> and <U^T U, V^T V>
+        TRY(run(ctx, K_DOT, 0.0, ctx->st, [&] {
+            return launch_error_metrics(ctx->U.G, ctx->V.G, ctx->k, ctx->A2, ctx->dot, ctx->met,
+                                        ctx->st);
+        }));
+        ctx->met_valid = true;
+    }
+    TRY(check_status(ctx));
+    CU(cudaMemcpy(E, ctx->met + 1, sizeof(double), cudaMemcpyDeviceToHost));
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_factor_nnz(espnmf_ctx* ctx, espnmf_which which, int64_t* nnz)
+{
+    TRY(enter(ctx));
+    if (!nnz) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "nnz is NULL");
+    Factor& F = which == ESPNMF_U ? ctx->U : ctx->V;
+    TRY(check_status(ctx));
+    std::vector<int32_t> cnt(F.rows);
+    CU(cudaMemcpy(cnt.data(), F.buf[F.cur].cnt, 4 * F.rows, cudaMemcpyDeviceToHost));
+    int64_t s = 0;
+    for (auto c : cnt) s += c;
+    *nnz = s;
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_get_factor(espnmf_ctx* ctx, espnmf_which which, espnmf_layout layout,
+                                int64_t* ptr, int32_t* idx, void* val, espnmf_dtype dtype,
+                                int32_t on_device)
+{
+    TRY(enter(ctx));
+    if (which != ESPNMF_U && which != ESPNMF_V) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "which");
+    if (dtype != ESPNMF_F64 && dtype != ESPNMF_F32)
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "dtype must be F64 or F32");
+    if (!val) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "val is NULL");
+    if (layout != ESPNMF_DENSE_ROWMAJOR && (!ptr || !idx))
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "ptr/idx are NULL");
+    Factor& F = which == ESPNMF_U ? ctx->U : ctx->V;
+    TRY(check_status(ctx));
+    const int64_t rows = F.rows;
+    const int k = ctx->k;
+    std::vector<int32_t> cnt(rows), col((size_t)rows * k);
+    std::vector<double> v((size_t)rows * k);
+    const EllDev& E = F.buf[F.cur];
+    CU(cudaMemcpy(cnt.data(), E.cnt, 4 * rows, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(col.data(), E.col, 4 * rows * k, cudaMemcpyDeviceToHost));
+    if (is_f64(ctx)) {
+        CU(cudaMemcpy(v.data(), E.val, 8 * rows * k, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> f((size_t)rows * k);
+        CU(cudaMemcpy(f.data(), E.val, 4 * rows * k, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < f.size(); ++i) v[i] = f[i];
+    }
+    const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
+    auto put = [&](std::vector<unsigned char>& dst, size_t i, double x) {
+        if (es == 8) memcpy(&dst[i * 8], &x, 8);
+        else {
+            float f = (float)x;
+            memcpy(&dst[i * 4], &f, 4);
+        }
+    };
+    int64_t nnz = 0;
+    for (auto c : cnt) nnz += c;
+    std::vector<unsigned char> vo;
+    std::vector<int64_t> po;
+    std::vector<int32_t> io;
+    if (layout == ESPNMF_DENSE_ROWMAJOR) {
+        vo.assign((size_t)rows * k * es, 0);
+        for (int64_t r = 0; r < rows; ++r)
+            for (int q = 0; q < cnt[r]; ++q) put(vo, (size_t)r * k + col[r * k + q], v[r * k + q]);
+    } else if (layout == ESPNMF_CSR) {
+        po.assign(rows + 1, 0);
+        io.resize(nnz);
+        vo.resize(nnz * es);
+        int64_t o = 0;
+        std::vector<std::pair<int32_t, double>> tmp;
+        for (int64_t r = 0; r < rows; ++r) {
+            tmp.clear();
+            for (int q = 0; q < cnt[r]; ++q) tmp.push_back({col[r * k + q], v[r * k + q]});
+            std::sort(tmp.begin(), tmp.end());
+            for (auto& pr : tmp) {
+                io[o] = pr.first;
+                put(vo, o, pr.second);
+                ++o;
+            }
+            po[r + 1] = o;
+        }
+    } else if (layout == ESPNMF_CSC) {
+        po.assign(k + 1, 0);
+        for (int64_t r = 0; r < rows; ++r)
+            for (int q = 0; q < cnt[r]; ++q) po[col[r * k + q] + 1]++;
+        for (int c = 0; c < k; ++c) po[c + 1] += po[c];
+        std::vector<int64_t> nx(po.begin(), po.end() - 1);
+        io.resize(nnz);
+        vo.resize(nnz * es);
+        for (int64_t r = 0; r < rows; ++r)   // rows ascending -> sorted columns
+            for (int q = 0; q < cnt[r]; ++q) {
+                const int c = col[r * k + q];
+                const int64_t o = nx[c]++;
+                io[o] = (int32_t)r;
+                put(vo, o, v[r * k + q]);
+            }
+    } else {
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "unknown layout");
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    if (!vo.empty()) CU(cudaMemcpy(val, vo.data(), vo.size(), kind));
+    if (!po.empty()) CU(cudaMemcpy(ptr, po.data(), po.size() * 8, kind));
+    if (!io.empty()) CU(cudaMemcpy(idx, io.data(), io.size() * 4, kind));
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_set_option(espnmf_ctx* ctx, espnmf_option opt, int64_t value)
+{
+    TRY(enter(ctx));
+    switch (opt) {
+    case ESPNMF_OPT_USE_GRAPH: ctx->use_graph = value != 0; return ESPNMF_OK;
+    case ESPNMF_OPT_PROFILE: ctx->profile = value != 0; return ESPNMF_OK;
+    case ESPNMF_OPT_WAIT_LIMIT:
+        if (value < 1) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "wait limit must be >= 1");
+        ctx->wait_limit = value;
+        return ESPNMF_OK;
+    }
+    return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "unknown option");
+}
+
+espnmf_status espnmf_kernel_stat_count(espnmf_ctx* ctx, int32_t* count)
+{
+    TRY(enter(ctx));
+    if (!count) return ESPNMF_ERR_INVALID_ARG;
+    *count = K_COUNT;
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_kernel_stat(espnmf_ctx* ctx, int32_t i, const char** name,
+                                 int64_t* launches, double* total_ms, double* bytes)
+{
+    TRY(enter(ctx));
+    if (i < 0 || i >= K_COUNT) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "kernel index");
+    TRY(collect_profile(ctx));
+    if (name) *name = kernel_name(i);
+    if (launches) *launches = ctx->stats[i].launches;
+    if (total_ms) *total_ms = ctx->stats[i].ms;
+    if (bytes) *bytes = ctx->stats[i].bytes;
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_kernel_stats_reset(espnmf_ctx* ctx)
+{
+    TRY(enter(ctx));
+    TRY(collect_profile(ctx));
+    for (auto& s : ctx->stats) s = Stat();
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_launches_per_sweep(espnmf_ctx* ctx, int32_t* count)
+{
+    TRY(enter(ctx));
+    if (!count) return ESPNMF_ERR_INVALID_ARG;
+    int per_half_A = 5 + (ctx->sA.nsplit > 0 ? 1 : 0);
+    int per_half_At = 5 + (ctx->sAt.nsplit > 0 ? 1 : 0);
+    *count = per_half_A + per_half_At + 2;   // + the two Cholesky launches
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_sync(espnmf_ctx* ctx)
+{
+    TRY(enter(ctx));
+    return check_status(ctx);
+}
+
+espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64_t ld,
+                                         espnmf_dtype dtype, int64_t t, espnmf_topt_mode mode,
+                                         void* stream)
+{
+    g_init_error.clear();
+    if (!X || rows < 0 || k < 1 || k > 128 || ld < k || t < 0)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "bad X/rows/k/ld/t");
+    if (dtype != ESPNMF_F64 && dtype != ESPNMF_F32)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "dtype must be F64 or F32");
+    if (mode != ESPNMF_TOPT_COLUMN && mode != ESPNMF_TOPT_MATRIX && mode != ESPNMF_TOPT_NONE)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "unknown enforcement mode");
+    if (rows >= (1ll << 31) || (mode == ESPNMF_TOPT_MATRIX && rows * k >= (1ll << 31)))
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "too many rows");
+    if (rows == 0) return ESPNMF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    auto cuerr = [&](cudaError_t e, const char* what) {
+        cudaGetLastError();
+        return set_err(nullptr, ESPNMF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuerr(e, "device");
+    static bool setup_done[64] = {};
+    if (dev < 64 && !setup_done[dev]) {
+        if ((e = setup_select()) != cudaSuccess) return cuerr(e, "setup");
+        setup_done[dev] = true;
+    }
+    const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
+    const int64_t ldx = (rows + 31) / 32 * 32;
+    auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t bx = a256((size_t)k * ldx * es), bc = a256((size_t)rows * 4),
+                 bl = a256((size_t)rows * k * 4), bv = a256((size_t)rows * k * es);
+    unsigned char* ws = nullptr;
+    e = cudaMallocAsync((void**)&ws, bx + bc + bl + bv + 64, st);
+    if (e != cudaSuccess) return cuerr(e, "cudaMallocAsync");
+    unsigned* status = (unsigned*)(ws + bx + bc + bl + bv);
+    EllDev out;
+    out.cnt = (int32_t*)(ws + bx);
+    out.col = (int32_t*)(ws + bx + bc);
+    out.val = ws + bx + bc + bl;
+    e = cudaMemsetAsync(out.cnt, 0, bc, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess)
+        e = dtype == ESPNMF_F64
+                ? launch_dense_to_colmajor<double>((const double*)X, rows, k, ld, (double*)ws, ldx, status, st)
+                : launch_dense_to_colmajor<float>((const float*)X, rows, k, ld, (float*)ws, ldx, status, st);
+    if (e == cudaSuccess)
+        e = dtype == ESPNMF_F64
+                ? launch_select<double>((const double*)ws, ldx, rows, k, t, (int)mode, out, status, st, sms)
+                : launch_select<float>((const float*)ws, ldx, rows, k, t, (int)mode, out, status, st, sms);
+    if (e == cudaSuccess)
+        e = dtype == ESPNMF_F64 ? launch_ell_to_dense<double>(rows, k, out, (double*)X, ld, st)
+                                : launch_ell_to_dense<float>(rows, k, out, (float*)X, ld, st);
+    unsigned hstat = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaFreeAsync(ws, st);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuerr(e, "enforce_topt_buffer");
+    if (hstat & ST_NONFINITE) return set_err(nullptr, ESPNMF_ERR_NONFINITE, "non-finite value in X");
+    if (hstat & ST_OVERFLOW) return set_err(nullptr, ESPNMF_ERR_CUDA, "internal: row overflow");
+    return ESPNMF_OK;
+}
+
+}  // extern "C"

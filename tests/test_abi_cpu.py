@@ -1,0 +1,85 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every entry point include/espnmf.h declares; argument validation
+that needs no device; and no silent CPU path (without a GPU the calls that
+need one fail with ESPNMF_ERR_CUDA)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1510_05237_gb300 import build
+    build.build()
+    import paper_1510_05237_gb300 as E
+    return E.load()
+
+
+def header_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(espnmf_[A-Za-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_functions()
+    assert len(names) >= 18
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_resolves_every_symbol(lib):
+    import paper_1510_05237_gb300 as E
+    assert all(E.exported_symbols().values())
+    assert set(E.exported_symbols()) <= set(header_functions())
+
+
+def test_status_strings(lib):
+    lib.espnmf_status_string.restype = ctypes.c_char_p
+    assert lib.espnmf_status_string(0) == b"ESPNMF_OK"
+    assert lib.espnmf_status_string(3) == b"ESPNMF_ERR_SINGULAR"
+
+
+def test_argument_validation_before_any_device_work(lib):
+    import paper_1510_05237_gb300 as E
+    from gen import small_zipf, uniform_init
+    A = small_zipf(1)
+    U0 = uniform_init(A.n, 4, 1)
+    for kw, code in [(dict(k=0), E.ERR_INVALID_ARG), (dict(k=A.m + 1), E.ERR_INVALID_ARG),
+                     (dict(t_u=-1), E.ERR_INVALID_ARG), (dict(mode=7), E.ERR_INVALID_ARG),
+                     (dict(compute=E.BF16), E.ERR_UNSUPPORTED)]:
+        args = dict(k=4, t_u=10, t_v=10, mode=E.TOPT_COLUMN, compute=E.F64)
+        args.update(kw)
+        with pytest.raises(E.EspnmfError) as ei:
+            E.espnmf_init(A.rowptr, A.colidx, A.val, A.n, A.m, args["k"], args["t_u"],
+                          args["t_v"], args["mode"], args["compute"], U0)
+        assert ei.value.status == code
+
+
+def test_no_cpu_fallback(lib):
+    """With no CUDA device the library refuses to work instead of falling
+    back to a host implementation."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_1510_05237_gb300 as E
+    from gen import small_zipf, uniform_init
+    A = small_zipf(1)
+    with pytest.raises(E.EspnmfError) as ei:
+        E.espnmf_init(A.rowptr, A.colidx, A.val, A.n, A.m, 4, 10, 10, E.TOPT_COLUMN, E.F64,
+                      uniform_init(A.n, 4, 1))
+    assert ei.value.status == E.ERR_CUDA
+
+
+def test_library_is_built_for_sm103a():
+    from paper_1510_05237_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
