@@ -22,18 +22,20 @@ enum : unsigned {
 
 enum TopMode : int { TOPT_COLUMN = 0, TOPT_MATRIX = 1, TOPT_NONE = 2 };
 
-// Rows longer than this are cut into segments whose partial products are
-// added in segment order by spmm_combine.
-constexpr int kSegMax = 256;
+// Rows are cut into segments of at most this many entries, one per lane.
+constexpr int kSegTarget = 64;
 constexpr int kMaxK = 256;
 
 // ---------------------------------------------------------------------------
-// A in sliced ELLPACK (SELL-32, segments sorted by length).  One layout per
-// orientation: rows of A (n rows, gathers rows of V) and rows of A^T
-// (m rows, gathers rows of U).  A row of length > kSegMax becomes several
-// segments.  Segment s sits in slice s/32, lane s%32; entry p of that lane
-// is at slice_ptr[s/32] + p*32 + s%32 (so a warp reads 32 consecutive
-// entries per step).  Padding entries have idx = -1.
+// A in sliced ELLPACK (SELL-32).  One layout per orientation: rows of A
+// (n rows, gathers rows of V) and rows of A^T (m rows, gathers rows of U).
+// A row is split into 1..32 segments of at most kSegTarget entries placed
+// in adjacent lanes [head, end) of one slice (seg_grp = head << 8 | end);
+// the lanes' sums are combined inside the warp.  Rows too long for 32
+// segments are cut into chunks that write partial rows (seg_part >= 0),
+// added by spmm_combine.  Lane s%32 of slice s/32 owns segment s; its entry
+// p is at slice_ptr[s/32] + p*32 + s%32, so a warp reads 32 consecutive
+// entries per step.  Padding entries have idx = -1.
 struct SellDev {
     int64_t rows = 0;        // output rows
     int64_t nseg = 0;
@@ -46,6 +48,7 @@ struct SellDev {
     void* val = nullptr;           // [total] of T
     int32_t* seg_row = nullptr;    // [nslices*32], -1 for padding lanes
     int32_t* seg_part = nullptr;   // [nslices*32], partial slot or -1
+    int32_t* seg_grp = nullptr;    // [nslices*32], head lane << 8 | end lane
     int64_t nsplit = 0;            // rows cut into segments
     int32_t* split_row = nullptr;  // [nsplit]
     int32_t* split_first = nullptr;// [nsplit] first partial slot
@@ -55,13 +58,26 @@ struct SellDev {
 };
 
 // A factor (U: n x k, V: m x k) in row-packed sparse form: row i holds
-// cnt[i] pairs (col[i*k+q], val[i*k+q]), q < cnt[i], columns distinct, all
-// values > 0.  Pair order inside a row is unspecified.
+// cnt[i] pairs (col[i*ld+q], val[i*ld+q]), q < cnt[i], columns distinct, all
+// values > 0, pair order unspecified.  ld = factor_ld(k) keeps every row
+// 16-byte aligned so a row's pairs load as 128-bit vectors.  Rows with at
+// least `heavy` nonzeros also have a dense copy dense[i*ld + c] (zeros and
+// the padding columns included), which the sparse product reads instead of
+// the pairs.
 struct EllDev {
     int32_t* cnt = nullptr;
     int32_t* col = nullptr;
     void* val = nullptr;
+    void* dense = nullptr;
+    int ld = 0;
+    int heavy = 1 << 30;
 };
+
+// Row stride of factors, Y and the dense heavy rows: k rounded up to 4
+// (k <= 64) or to 16.
+inline __host__ __device__ int factor_ld(int k) { return k <= 64 ? (k + 3) / 4 * 4 : (k + 15) / 16 * 16; }
+// A row with at least this many nonzeros is "heavy" (gathered densely).
+inline __host__ __device__ int heavy_threshold(int ld) { return ld / 4 > 4 ? ld / 4 : 4; }
 
 // ---------------------------------------------------------------------------
 // Launchers.  Every launcher enqueues on `st` and returns the CUDA error of

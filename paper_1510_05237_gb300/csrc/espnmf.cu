@@ -252,68 +252,108 @@ template <typename T>
 struct SellHost {
     int64_t rows = 0, nseg = 0, nslices = 0, total = 0, nnz = 0, npart = 0;
     std::vector<int64_t> slice_ptr;
-    std::vector<int32_t> slice_len, idx, seg_row, seg_part, split_row, split_first,
+    std::vector<int32_t> slice_len, idx, seg_row, seg_part, seg_grp, split_row, split_first,
         split_count;
     std::vector<T> val;
 };
 
+// Lays out the rows of a CSR matrix for spmm_sell.  Every row becomes a
+// group of 1..32 segments of at most kSegTarget entries (split evenly),
+// placed in adjacent lanes of one 32-lane slice, so the lanes' partial sums
+// are combined inside the warp.  A row with more than 32*kSegTarget entries
+// is cut into chunks of up to 32 segments; each chunk writes a partial row
+// that spmm_combine adds in chunk order.  Groups are sorted by segment
+// length (longest first) and packed greedily, so the lanes of a slice walk
+// segments of about the same length.
 template <typename T>
 void build_sell(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
                 SellHost<T>& S)
 {
-    struct Seg {
-        int32_t row, len, part;
-        int64_t start;
+    struct Grp {
+        int32_t row, part, nseg, seglen;
+        int64_t start, len;
     };
-    std::vector<Seg> segs;
-    segs.reserve((size_t)rows + (size_t)(ptr[rows] / kSegMax) + 1);
+    std::vector<Grp> grps;
+    grps.reserve((size_t)rows + 16);
     int64_t npart = 0;
+    auto ceil_div = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
     for (int64_t r = 0; r < rows; ++r) {
         const int64_t len = ptr[r + 1] - ptr[r];
-        if (len <= kSegMax) {
-            segs.push_back({(int32_t)r, (int32_t)len, -1, ptr[r]});
+        const int64_t nseg = std::max<int64_t>(1, ceil_div(len, kSegTarget));
+        if (nseg <= 32) {
+            grps.push_back({(int32_t)r, -1, (int32_t)nseg, (int32_t)ceil_div(len, nseg), ptr[r], len});
         } else {
-            const int64_t nsg = (len + kSegMax - 1) / kSegMax;
+            const int64_t nch = ceil_div(nseg, 32);
             S.split_row.push_back((int32_t)r);
             S.split_first.push_back((int32_t)npart);
-            S.split_count.push_back((int32_t)nsg);
-            for (int64_t q = 0; q < nsg; ++q) {
-                const int64_t l = std::min<int64_t>(kSegMax, len - q * kSegMax);
-                segs.push_back({(int32_t)r, (int32_t)l, (int32_t)npart++, ptr[r] + q * kSegMax});
+            S.split_count.push_back((int32_t)nch);
+            for (int64_t c = 0; c < nch; ++c) {
+                const int64_t s0 = len * c / nch, s1 = len * (c + 1) / nch, cl = s1 - s0;
+                const int64_t ns = std::min<int64_t>(32, std::max<int64_t>(1, ceil_div(cl, kSegTarget)));
+                grps.push_back({(int32_t)r, (int32_t)npart++, (int32_t)ns, (int32_t)ceil_div(cl, ns),
+                                ptr[r] + s0, cl});
             }
         }
     }
-    // counting sort by length, longest first, stable
-    std::vector<int64_t> bucket(kSegMax + 2, 0);
-    for (auto& s : segs) bucket[kSegMax - s.len + 1]++;
-    for (int i = 1; i < kSegMax + 2; ++i) bucket[i] += bucket[i - 1];
-    std::vector<Seg> sorted(segs.size());
-    for (auto& s : segs) sorted[bucket[kSegMax - s.len]++] = s;
+    // counting sort by segment length, longest first, stable
+    std::vector<int64_t> bucket(kSegTarget + 2, 0);
+    for (auto& g : grps) bucket[kSegTarget - g.seglen + 1]++;
+    for (int i = 1; i < kSegTarget + 2; ++i) bucket[i] += bucket[i - 1];
+    std::vector<Grp> sorted(grps.size());
+    for (auto& g : grps) sorted[bucket[kSegTarget - g.seglen]++] = g;
+    // pack groups into slices
+    struct Lane {
+        int32_t row, part, grp, len;
+        int64_t start;
+    };
+    std::vector<Lane> lanes;
+    lanes.reserve(sorted.size() * 2 + 32);
+    int used = 0;
+    auto pad_to_slice = [&]() {
+        while (used % 32 != 0) {
+            lanes.push_back({-1, -1, ((used % 32) << 8) | ((used % 32) + 1), 0, 0});
+            ++used;
+        }
+    };
+    for (auto& g : sorted) {
+        if ((used % 32) + g.nseg > 32) pad_to_slice();
+        const int head = used % 32;
+        for (int q = 0; q < g.nseg; ++q) {
+            const int64_t a0 = g.len * q / g.nseg, a1 = g.len * (q + 1) / g.nseg;
+            lanes.push_back({g.row, g.part, (head << 8) | (head + g.nseg), (int32_t)(a1 - a0),
+                             g.start + a0});
+            ++used;
+        }
+    }
+    pad_to_slice();
     S.rows = rows;
     S.nnz = ptr[rows];
     S.npart = npart;
-    S.nseg = (int64_t)sorted.size();
-    S.nslices = (S.nseg + 31) / 32;
+    S.nseg = (int64_t)lanes.size();
+    S.nslices = S.nseg / 32;
     S.slice_ptr.assign(S.nslices + 1, 0);
     S.slice_len.assign(S.nslices, 0);
     for (int64_t s = 0; s < S.nslices; ++s) {
-        S.slice_len[s] = sorted[s * 32].len;
-        S.slice_ptr[s + 1] = S.slice_ptr[s] + (int64_t)S.slice_len[s] * 32;
+        int mx = 0;
+        for (int l = 0; l < 32; ++l) mx = std::max(mx, lanes[s * 32 + l].len);
+        S.slice_len[s] = mx;
+        S.slice_ptr[s + 1] = S.slice_ptr[s] + (int64_t)mx * 32;
     }
     S.total = S.slice_ptr[S.nslices];
     S.idx.assign(S.total, -1);
     S.val.assign(S.total, T(0));
-    S.seg_row.assign(S.nslices * 32, -1);
-    S.seg_part.assign(S.nslices * 32, -1);
+    S.seg_row.resize(S.nseg);
+    S.seg_part.resize(S.nseg);
+    S.seg_grp.resize(S.nseg);
     for (int64_t g = 0; g < S.nseg; ++g) {
-        const Seg& sg = sorted[g];
-        const int64_t s = g / 32, lane = g % 32;
-        S.seg_row[g] = sg.row;
-        S.seg_part[g] = sg.part;
-        int64_t o = S.slice_ptr[s] + lane;
-        for (int p = 0; p < sg.len; ++p, o += 32) {
-            S.idx[o] = ind[sg.start + p];
-            S.val[o] = (T)vals[sg.start + p];
+        const Lane& ln = lanes[g];
+        S.seg_row[g] = ln.row;
+        S.seg_part[g] = ln.part;
+        S.seg_grp[g] = ln.grp;
+        int64_t o = S.slice_ptr[g / 32] + g % 32;
+        for (int p = 0; p < ln.len; ++p, o += 32) {
+            S.idx[o] = ind[ln.start + p];
+            S.val[o] = (T)vals[ln.start + p];
         }
     }
 }
@@ -334,10 +374,11 @@ espnmf_status upload_sell(espnmf_ctx* ctx, const SellHost<T>& H, SellDev& D)
     TRY(dupload(ctx, &D.val, H.val.data(), H.val.size() * sizeof(T)));
     TRY(dupload(ctx, &D.seg_row, H.seg_row.data(), H.seg_row.size() * 4));
     TRY(dupload(ctx, &D.seg_part, H.seg_part.data(), H.seg_part.size() * 4));
+    TRY(dupload(ctx, &D.seg_grp, H.seg_grp.data(), H.seg_grp.size() * 4));
     TRY(dupload(ctx, &D.split_row, H.split_row.data(), H.split_row.size() * 4));
     TRY(dupload(ctx, &D.split_first, H.split_first.data(), H.split_first.size() * 4));
     TRY(dupload(ctx, &D.split_count, H.split_count.data(), H.split_count.size() * 4));
-    TRY(dmalloc(ctx, &D.partials, (size_t)H.npart * ctx->k * sizeof(T)));
+    TRY(dmalloc(ctx, &D.partials, (size_t)H.npart * factor_ld(ctx->k) * sizeof(T)));
     // host vectors die with H: make sure the copies are done
     CU(cudaStreamSynchronize(ctx->st));
     return ESPNMF_OK;
@@ -359,10 +400,10 @@ espnmf_status do_spmm(espnmf_ctx* ctx, bool transA, const EllDev& F)
                                                 ctx->sm_count);
     }));
     if (S.nsplit > 0) {
-        const double cb = (double)S.npart * ctx->k * ctx->esz;
+        const double cb = (double)S.npart * ctx->ldy * ctx->esz;
         TRY(run(ctx, K_COMBINE, cb, ctx->st, [&] {
-            return is_f64(ctx) ? launch_spmm_combine<double>(S, ctx->k, (double*)ctx->Y, ctx->ldy, ctx->st)
-                               : launch_spmm_combine<float>(S, ctx->k, (float*)ctx->Y, ctx->ldy, ctx->st);
+            return is_f64(ctx) ? launch_spmm_combine<double>(S, (int)ctx->ldy, (double*)ctx->Y, ctx->ldy, ctx->st)
+                               : launch_spmm_combine<float>(S, (int)ctx->ldy, (float*)ctx->Y, ctx->ldy, ctx->st);
         }));
     }
     return ESPNMF_OK;
@@ -777,7 +818,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
 
         // ---- work buffers
         const int64_t rmax = std::max(n, m);
-        ctx->ldy = ctx->esz == 8 ? (k + 1) / 2 * 2 : (k + 3) / 4 * 4;
+        ctx->ldy = factor_ld(k);
         ctx->ldx = (rmax + 31) / 32 * 32;
         TRY(dmalloc(ctx, &ctx->Y, (size_t)rmax * ctx->ldy * ctx->esz));
         TRY(dmalloc(ctx, &ctx->Xt, (size_t)k * ctx->ldx * ctx->esz));
@@ -802,11 +843,17 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
 
         for (Factor* F : {&ctx->U, &ctx->V}) {
             F->rows = F == &ctx->U ? n : m;
+            const int ld = factor_ld(k);
+            void* dense = nullptr;
+            TRY(dmalloc(ctx, &dense, ctx->esz * F->rows * ld));
             for (int b = 0; b < 2; ++b) {
                 TRY(dmalloc(ctx, &F->buf[b].cnt, sizeof(int32_t) * F->rows));
-                TRY(dmalloc(ctx, &F->buf[b].col, sizeof(int32_t) * F->rows * k));
-                TRY(dmalloc(ctx, &F->buf[b].val, ctx->esz * F->rows * k));
+                TRY(dmalloc(ctx, &F->buf[b].col, sizeof(int32_t) * F->rows * ld));
+                TRY(dmalloc(ctx, &F->buf[b].val, ctx->esz * F->rows * ld));
                 CU(cudaMemsetAsync(F->buf[b].cnt, 0, sizeof(int32_t) * F->rows, ctx->st));
+                F->buf[b].dense = dense;   // one dense copy, rewritten by each finalize
+                F->buf[b].ld = ld;
+                F->buf[b].heavy = heavy_threshold(ld);
             }
             TRY(dmalloc(ctx, &F->G, sizeof(double) * k * k));
             CU(cudaMemsetAsync(F->G, 0, sizeof(double) * k * k, ctx->st));
@@ -1013,16 +1060,17 @@ espnmf_status espnmf_get_factor(espnmf_ctx* ctx, espnmf_which which, espnmf_layo
     TRY(check_status(ctx));
     const int64_t rows = F.rows;
     const int k = ctx->k;
-    std::vector<int32_t> cnt(rows), col((size_t)rows * k);
-    std::vector<double> v((size_t)rows * k);
     const EllDev& E = F.buf[F.cur];
+    const int ld = E.ld;
+    std::vector<int32_t> cnt(rows), col((size_t)rows * ld);
+    std::vector<double> v((size_t)rows * ld);
     CU(cudaMemcpy(cnt.data(), E.cnt, 4 * rows, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(col.data(), E.col, 4 * rows * k, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(col.data(), E.col, 4 * rows * ld, cudaMemcpyDeviceToHost));
     if (is_f64(ctx)) {
-        CU(cudaMemcpy(v.data(), E.val, 8 * rows * k, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(v.data(), E.val, 8 * rows * ld, cudaMemcpyDeviceToHost));
     } else {
-        std::vector<float> f((size_t)rows * k);
-        CU(cudaMemcpy(f.data(), E.val, 4 * rows * k, cudaMemcpyDeviceToHost));
+        std::vector<float> f((size_t)rows * ld);
+        CU(cudaMemcpy(f.data(), E.val, 4 * rows * ld, cudaMemcpyDeviceToHost));
         for (size_t i = 0; i < f.size(); ++i) v[i] = f[i];
     }
     const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
@@ -1041,7 +1089,7 @@ espnmf_status espnmf_get_factor(espnmf_ctx* ctx, espnmf_which which, espnmf_layo
     if (layout == ESPNMF_DENSE_ROWMAJOR) {
         vo.assign((size_t)rows * k * es, 0);
         for (int64_t r = 0; r < rows; ++r)
-            for (int q = 0; q < cnt[r]; ++q) put(vo, (size_t)r * k + col[r * k + q], v[r * k + q]);
+            for (int q = 0; q < cnt[r]; ++q) put(vo, (size_t)r * k + col[r * ld + q], v[r * ld + q]);
     } else if (layout == ESPNMF_CSR) {
         po.assign(rows + 1, 0);
         io.resize(nnz);
@@ -1050,7 +1098,7 @@ espnmf_status espnmf_get_factor(espnmf_ctx* ctx, espnmf_which which, espnmf_layo
         std::vector<std::pair<int32_t, double>> tmp;
         for (int64_t r = 0; r < rows; ++r) {
             tmp.clear();
-            for (int q = 0; q < cnt[r]; ++q) tmp.push_back({col[r * k + q], v[r * k + q]});
+            for (int q = 0; q < cnt[r]; ++q) tmp.push_back({col[r * ld + q], v[r * ld + q]});
             std::sort(tmp.begin(), tmp.end());
             for (auto& pr : tmp) {
                 io[o] = pr.first;
@@ -1062,17 +1110,17 @@ espnmf_status espnmf_get_factor(espnmf_ctx* ctx, espnmf_which which, espnmf_layo
     } else if (layout == ESPNMF_CSC) {
         po.assign(k + 1, 0);
         for (int64_t r = 0; r < rows; ++r)
-            for (int q = 0; q < cnt[r]; ++q) po[col[r * k + q] + 1]++;
+            for (int q = 0; q < cnt[r]; ++q) po[col[r * ld + q] + 1]++;
         for (int c = 0; c < k; ++c) po[c + 1] += po[c];
         std::vector<int64_t> nx(po.begin(), po.end() - 1);
         io.resize(nnz);
         vo.resize(nnz * es);
         for (int64_t r = 0; r < rows; ++r)   // rows ascending -> sorted columns
             for (int q = 0; q < cnt[r]; ++q) {
-                const int c = col[r * k + q];
+                const int c = col[r * ld + q];
                 const int64_t o = nx[c]++;
                 io[o] = (int32_t)r;
-                put(vo, o, v[r * k + q]);
+                put(vo, o, v[r * ld + q]);
             }
     } else {
         return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "unknown layout");
@@ -1174,8 +1222,9 @@ espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64
     const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
     const int64_t ldx = (rows + 31) / 32 * 32;
     auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const int eld = factor_ld(k);
     const size_t bx = a256((size_t)k * ldx * es), bc = a256((size_t)rows * 4),
-                 bl = a256((size_t)rows * k * 4), bv = a256((size_t)rows * k * es);
+                 bl = a256((size_t)rows * eld * 4), bv = a256((size_t)rows * eld * es);
     unsigned char* ws = nullptr;
     e = cudaMallocAsync((void**)&ws, bx + bc + bl + bv + 64, st);
     if (e != cudaSuccess) return cuerr(e, "cudaMallocAsync");
@@ -1184,6 +1233,7 @@ espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64
     out.cnt = (int32_t*)(ws + bx);
     out.col = (int32_t*)(ws + bx + bc);
     out.val = ws + bx + bc + bl;
+    out.ld = eld;
     e = cudaMemsetAsync(out.cnt, 0, bc, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
     if (e == cudaSuccess)

@@ -27,9 +27,12 @@ template <typename T>
 struct FinArgs {
     int64_t rows;
     int k;
+    int ld;
+    int heavy;
     const int32_t* cnt_new;
     const int32_t* col_new;
     const T* val_new;
+    T* dense_new;          // dense copies of heavy rows (may be null)
     int32_t* cnt_old;
     const int32_t* col_old;
     const T* val_old;
@@ -42,10 +45,12 @@ struct FinArgs {
 };
 
 template <typename T>
-static __host__ __device__ size_t fin_warp_bytes(int k, bool residual)
+static __host__ __device__ size_t fin_warp_bytes(int k, int ld, bool residual)
 {
-    return align16((size_t)k * k * sizeof(double)) + align16((size_t)32 * k * sizeof(int)) +
-           align16((size_t)32 * k * sizeof(T)) +
+    // Gram accumulator, staged rows (columns, values), and per-lane dense
+    // scratch rows of the new (and old) values, slot c of lane l at c*32+l
+    return align16((size_t)k * k * sizeof(double)) + align16((size_t)32 * ld * sizeof(int)) +
+           align16((size_t)32 * ld * sizeof(T)) + align16((size_t)32 * k * sizeof(T)) +
            (residual ? align16((size_t)32 * k * sizeof(T)) : 0);
 }
 
@@ -55,23 +60,41 @@ __device__ inline double warp_sum(double v)
     return v;
 }
 
+// Copies n (a multiple of 4 not exceeding the row stride) ints / values of
+// a 16-byte aligned row with 128-bit loads.
+__device__ inline void copy_row4(int* dst, const int32_t* src, int n)
+{
+    for (int q = 0; q < n; q += 4) *reinterpret_cast<int4*>(dst + q) = __ldg(reinterpret_cast<const int4*>(src + q));
+}
+__device__ inline void copy_row4(float* dst, const float* src, int n)
+{
+    for (int q = 0; q < n; q += 4) *reinterpret_cast<float4*>(dst + q) = __ldg(reinterpret_cast<const float4*>(src + q));
+}
+__device__ inline void copy_row4(double* dst, const double* src, int n)
+{
+    for (int q = 0; q < n; q += 2) *reinterpret_cast<double2*>(dst + q) = __ldg(reinterpret_cast<const double2*>(src + q));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128)
 finalize_kernel(FinArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4][4];
-    const int k = a.k;
+    const int k = a.k, ld = a.ld;
     const int W = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t pw = fin_warp_bytes<T>(k, a.residual);
-    double* G = reinterpret_cast<double*>(smem_raw + warp * pw);
-    int* sc = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(G) + align16((size_t)k * k * sizeof(double)));
-    T* sv = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(sc) + align16((size_t)32 * k * sizeof(int)));
-    T* sl = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(sv) + align16((size_t)32 * k * sizeof(T)));
+    const size_t pw = fin_warp_bytes<T>(k, ld, a.residual);
+    unsigned char* wbase = smem_raw + warp * pw;
+    double* G = reinterpret_cast<double*>(wbase);
+    int* sc = reinterpret_cast<int*>(wbase + align16((size_t)k * k * sizeof(double)));
+    T* sv = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(sc) + align16((size_t)32 * ld * sizeof(int)));
+    T* sn = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(sv) + align16((size_t)32 * ld * sizeof(T)));
+    T* so = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(sn) + align16((size_t)32 * k * sizeof(T)));
     for (int e = lane; e < k * k; e += 32) G[e] = 0.0;
+    for (int e = lane; e < 32 * k; e += 32) sn[e] = T(0);
     if (a.residual)
-        for (int e = lane; e < 32 * k; e += 32) sl[e] = T(0);
+        for (int e = lane; e < 32 * k; e += 32) so[e] = T(0);
     double s_diff = 0.0, s_new = 0.0, s_old = 0.0, s_cross = 0.0;
 
     const int64_t chunk = (a.rows + gridDim.x - 1) / gridDim.x;
@@ -82,62 +105,81 @@ finalize_kernel(FinArgs<T> a)
         const int64_t r = base + lane;
         const bool valid = r < b1;
         const int Ln = valid ? a.cnt_new[r] : 0;
-        const int32_t* cn = a.col_new + r * k;
-        const T* vn = a.val_new + r * k;
-        for (int q = 0; q < Ln; ++q) {
-            const int c = cn[q];
-            const T v = vn[q];
-            sc[lane * k + q] = c;
-            sv[lane * k + q] = v;
-            s_new += (double)v * (double)v;
-            if (a.Y) s_cross += (double)v * (double)a.Y[r * a.ldy + c];
+        const int Ln4 = (Ln + 3) & ~3;
+        int* mc = sc + lane * ld;
+        T* mv = sv + lane * ld;
+        copy_row4(mc, a.col_new + r * ld, Ln4);
+        copy_row4(mv, a.val_new + r * ld, Ln4);
+        for (int q = 0; q < Ln; ++q) sn[mc[q] * 32 + lane] = mv[q];
+        if (a.dense_new && Ln >= a.heavy) {
+            T* dr = a.dense_new + r * ld;
+            for (int c = 0; c < ld; ++c) dr[c] = c < k ? sn[c * 32 + lane] : T(0);
         }
+        int Lo = 0;
         if (valid && (a.residual || a.zero_old)) {
-            const int Lo = a.cnt_old[r];
+            Lo = a.cnt_old[r];
             if (a.residual) {
-                const int32_t* co = a.col_old + r * k;
-                const T* vo = a.val_old + r * k;
-                for (int q = 0; q < Lo; ++q) {
-                    const T v = vo[q];
-                    sl[co[q] * 32 + lane] = v;
-                    s_old += (double)v * (double)v;
-                }
-                for (int q = 0; q < Ln; ++q) {
-                    const int c = sc[lane * k + q];
-                    const double d = (double)sv[lane * k + q] - (double)sl[c * 32 + lane];
-                    s_diff += d * d;
-                    sl[c * 32 + lane] = T(0);
-                }
-                for (int q = 0; q < Lo; ++q) {
-                    const int c = co[q];
-                    const double o = (double)sl[c * 32 + lane];
-                    s_diff += o * o;
-                    sl[c * 32 + lane] = T(0);
-                }
+                const int32_t* co = a.col_old + r * ld;
+                const T* vo = a.val_old + r * ld;
+                for (int q = 0; q < Lo; ++q) so[co[q] * 32 + lane] = vo[q];
             }
             if (a.zero_old) a.cnt_old[r] = 0;
         }
+        // row sums in column order (independent of the pair order in a row)
+        if (Ln > 0 || Lo > 0) {
+            for (int c = 0; c < k; ++c) {
+                const double n = (double)sn[c * 32 + lane];
+                s_new += n * n;
+                if (a.Y && n != 0.0) s_cross += n * (double)a.Y[r * a.ldy + c];
+                if (a.residual) {
+                    const double o = (double)so[c * 32 + lane];
+                    s_old += o * o;
+                    s_diff += (n - o) * (n - o);
+                    so[c * 32 + lane] = T(0);
+                }
+                sn[c * 32 + lane] = T(0);
+            }
+        }
         __syncwarp();
-        // Gram: the 32 staged rows one after another, a row's pairs across
-        // the lanes (distinct (c, d) within a row, so no two lanes collide).
+        // Gram: the 32 staged rows one after another; a row's pairs (ia <= ib)
+        // across the lanes, accumulated into the upper triangle (canonical
+        // slot min(c,d)*k + max(c,d)); distinct slots within a row.
         for (int j = 0; j < 32; ++j) {
             const int Lj = __shfl_sync(0xffffffffu, Ln, j);
-            const int P = Lj * Lj;
-            for (int p = lane; p < P; p += 32) {
-                const int ia = p / Lj, ib = p - ia * Lj;
-                const int ca = sc[j * k + ia], cb = sc[j * k + ib];
-                G[ca * k + cb] += (double)sv[j * k + ia] * (double)sv[j * k + ib];
+            const int* jc = sc + j * ld;
+            const T* jv = sv + j * ld;
+            for (int ia = 0; ia < Lj; ++ia) {
+                const int ca = jc[ia];
+                const double va = (double)jv[ia];
+                for (int ib = ia + lane; ib < Lj; ib += 64) {
+                    const int cb = jc[ib];
+                    const int s0 = ca < cb ? ca * k + cb : cb * k + ca;
+                    const double p0 = va * (double)jv[ib];
+                    const int ib2 = ib + 32;
+                    if (ib2 < Lj) {
+                        const int cb2 = jc[ib2];
+                        const int s1 = ca < cb2 ? ca * k + cb2 : cb2 * k + ca;
+                        const double p1 = va * (double)jv[ib2];
+                        G[s0] += p0;
+                        G[s1] += p1;
+                    } else {
+                        G[s0] += p0;
+                    }
+                }
             }
             __syncwarp();
         }
     }
     __syncthreads();
+    // block partial: warps in order, upper triangle mirrored
     double* gp = a.gram_part + (size_t)blockIdx.x * k * k;
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-        double s = 0.0;
+        const int c = e / k, d = e - c * k;
+        const int src = c <= d ? c * k + d : d * k + c;
+        double sum = 0.0;
         for (int w = 0; w < W; ++w)
-            s += reinterpret_cast<const double*>(smem_raw + w * pw)[e];
-        gp[e] = s;
+            sum += reinterpret_cast<const double*>(smem_raw + w * pw)[src];
+        gp[e] = sum;
     }
     s_diff = warp_sum(s_diff);
     s_new = warp_sum(s_new);
@@ -151,9 +193,9 @@ finalize_kernel(FinArgs<T> a)
     }
     __syncthreads();
     if (threadIdx.x < 4) {
-        double s = 0.0;
-        for (int w = 0; w < W; ++w) s += red[w][threadIdx.x];
-        a.scal_part[(size_t)blockIdx.x * 4 + threadIdx.x] = s;
+        double sum = 0.0;
+        for (int w = 0; w < W; ++w) sum += red[w][threadIdx.x];
+        a.scal_part[(size_t)blockIdx.x * 4 + threadIdx.x] = sum;
     }
 }
 
@@ -166,9 +208,12 @@ cudaError_t launch_finalize(int64_t rows, int k, EllDev cur, EllDev old,
     FinArgs<T> a;
     a.rows = rows;
     a.k = k;
+    a.ld = cur.ld;
+    a.heavy = cur.heavy;
     a.cnt_new = cur.cnt;
     a.col_new = cur.col;
     a.val_new = static_cast<const T*>(cur.val);
+    a.dense_new = static_cast<T*>(cur.dense);
     a.cnt_old = old.cnt;
     a.col_old = old.col;
     a.val_old = static_cast<const T*>(old.val);
@@ -178,7 +223,7 @@ cudaError_t launch_finalize(int64_t rows, int k, EllDev cur, EllDev old,
     a.ldy = ldy;
     a.gram_part = gram_part;
     a.scal_part = scal_part;
-    const size_t pw = fin_warp_bytes<T>(k, a.residual);
+    const size_t pw = fin_warp_bytes<T>(k, cur.ld, a.residual);
     int W = (int)((210 * 1024) / pw);
     if (W > 4) W = 4;
     if (W < 1) W = 1;
@@ -195,15 +240,25 @@ __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
 {
     const int kk = k * k;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    // eight interleaved partial sums, combined in a fixed order (FP64 adds
+    // have a long latency on this part)
     if (e < kk) {
-        double s = 0.0;
-        for (int p = 0; p < P; ++p) s += gram_part[(size_t)p * kk + e];
-        G[e] = s;
+        double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int p = 0;
+        for (; p + 7 < P; p += 8)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s[u] += gram_part[(size_t)(p + u) * kk + e];
+        for (; p < P; ++p) s[0] += gram_part[(size_t)p * kk + e];
+        G[e] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
     }
     if (blockIdx.x == 0 && threadIdx.x < 4) {
-        double s = 0.0;
-        for (int p = 0; p < P; ++p) s += scal_part[(size_t)p * 4 + threadIdx.x];
-        scal[threadIdx.x] = s;
+        double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int p = 0;
+        for (; p + 7 < P; p += 8)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s[u] += scal_part[(size_t)(p + u) * 4 + threadIdx.x];
+        for (; p < P; ++p) s[0] += scal_part[(size_t)p * 4 + threadIdx.x];
+        scal[threadIdx.x] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
     }
     if (!m.enabled) return;
     // The last block to finish forms the measures.
@@ -302,11 +357,13 @@ cudaError_t launch_error_metrics(const double* GU, const double* GV, int k,
 template <typename T>
 __global__ void __launch_bounds__(1024)
 cholesky_kernel(const double* __restrict__ G, int k, double* Ginv64,
-                T* GinvT, unsigned* status)
+                T* GinvT, unsigned* status, int li_in_smem)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* A = reinterpret_cast<double*>(smem_raw);          // k*k
-    int* act = reinterpret_cast<int*>(A + (size_t)k * k);     // k
+    double* A = reinterpret_cast<double*>(smem_raw);                 // k*k
+    double* Li = li_in_smem ? A + (size_t)k * k : Ginv64;             // k*k
+    double* dinv = A + (size_t)k * k * (li_in_smem ? 2 : 1);          // k
+    int* act = reinterpret_cast<int*>(dinv + k);
     __shared__ double inv_piv, maxdiag;
     __shared__ int sing, nonfin;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -333,6 +390,7 @@ cholesky_kernel(const double* __restrict__ G, int k, double* Ginv64,
     }
     __syncthreads();
     const double tol = 64.0 * DBL_EPSILON * maxdiag;
+    // right-looking Cholesky, lower triangle of A
     for (int j = 0; j < k; ++j) {
         if (tid == 0) {
             double s = A[j * k + j];
@@ -340,9 +398,10 @@ cholesky_kernel(const double* __restrict__ G, int k, double* Ginv64,
                 sing = 1;
                 s = 1.0;
             }
-            const double l = sqrt(s);
-            A[j * k + j] = l;
-            inv_piv = 1.0 / l;
+            const double ri = rsqrt(s);
+            A[j * k + j] = s * ri;   // sqrt(s)
+            inv_piv = ri;
+            dinv[j] = ri;
         }
         __syncthreads();
         for (int i = j + 1 + tid; i < k; i += nt) A[i * k + j] *= inv_piv;
@@ -357,32 +416,45 @@ cholesky_kernel(const double* __restrict__ G, int k, double* Ginv64,
         }
         __syncthreads();
     }
-    // Li = L^-1 (lower), built row by row into the global Ginv64 buffer.
-    double* Li = Ginv64;
+    // Li = L^-1 (lower), row by row; each entry a dot product split over
+    // four independent accumulators (FP64 FMA latency is long on this part).
     for (int i = 0; i < k; ++i) {
-        const double dinv = 1.0 / A[i * k + i];
+        const double di = dinv[i];
         for (int c = tid; c < k; c += nt) {
             double v;
             if (c > i) v = 0.0;
-            else if (c == i) v = dinv;
+            else if (c == i) v = di;
             else {
-                double s = 0.0;
-                for (int e = c; e < i; ++e) s += A[i * k + e] * Li[e * k + c];
-                v = -s * dinv;
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                int e = c;
+                for (; e + 3 < i; e += 4) {
+                    s0 += A[i * k + e] * Li[e * k + c];
+                    s1 += A[i * k + e + 1] * Li[(e + 1) * k + c];
+                    s2 += A[i * k + e + 2] * Li[(e + 2) * k + c];
+                    s3 += A[i * k + e + 3] * Li[(e + 3) * k + c];
+                }
+                for (; e < i; ++e) s0 += A[i * k + e] * Li[e * k + c];
+                v = -((s0 + s1) + (s2 + s3)) * di;
             }
             Li[i * k + c] = v;
         }
         __syncthreads();
     }
-    // G^-1 = Li^T Li into shared memory (A is no longer needed).
+    // G^-1 = Li^T Li into A (L is no longer needed).
     for (int e = tid; e < kk; e += nt) {
         const int c = e / k, d = e - c * k;
-        double s = 0.0;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         if (act[c] && act[d]) {
-            const int e0 = c > d ? c : d;
-            for (int q = e0; q < k; ++q) s += Li[q * k + c] * Li[q * k + d];
+            int q = c > d ? c : d;
+            for (; q + 3 < k; q += 4) {
+                s0 += Li[q * k + c] * Li[q * k + d];
+                s1 += Li[(q + 1) * k + c] * Li[(q + 1) * k + d];
+                s2 += Li[(q + 2) * k + c] * Li[(q + 2) * k + d];
+                s3 += Li[(q + 3) * k + c] * Li[(q + 3) * k + d];
+            }
+            for (; q < k; ++q) s0 += Li[q * k + c] * Li[q * k + d];
         }
-        A[e] = s;
+        A[e] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
     for (int e = tid; e < kk; e += nt) {
@@ -399,9 +471,13 @@ template <typename T>
 cudaError_t launch_cholesky(const double* G, int k, double* Ginv64, T* GinvT,
                             unsigned* status, cudaStream_t st)
 {
-    const size_t smem = (size_t)k * k * sizeof(double) + (size_t)k * sizeof(int) + 16;
-    const int threads = k * k >= 1024 ? 1024 : ((k * k + 31) / 32) * 32;
-    cholesky_kernel<T><<<1, threads < 32 ? 32 : threads, smem, st>>>(G, k, Ginv64, GinvT, status);
+    const size_t kk8 = (size_t)k * k * sizeof(double);
+    const size_t extra = (size_t)k * (sizeof(double) + sizeof(int)) + 16;
+    const int li_smem = 2 * kk8 + extra <= 210 * 1024;
+    const size_t smem = kk8 * (li_smem ? 2 : 1) + extra;
+    int threads = k * k >= 1024 ? 1024 : ((k * k + 31) / 32) * 32;
+    if (threads < 32) threads = 32;
+    cholesky_kernel<T><<<1, threads, smem, st>>>(G, k, Ginv64, GinvT, status, li_smem);
     return cudaGetLastError();
 }
 
@@ -412,8 +488,8 @@ cudaError_t launch_cholesky(const double* G, int k, double* Ginv64, T* GinvT,
 
 template <typename Tin, typename T>
 __global__ void dense_to_ell_kernel(const Tin* __restrict__ F, int64_t rows,
-                                    int k, int32_t* cnt, int32_t* col, T* val,
-                                    unsigned* status)
+                                    int k, int ld, int32_t* cnt, int32_t* col,
+                                    T* val, unsigned* status)
 {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -431,8 +507,8 @@ __global__ void dense_to_ell_kernel(const Tin* __restrict__ F, int64_t rows,
             const unsigned b = __ballot_sync(0xffffffffu, keep);
             if (keep) {
                 const int pos = base + __popc(b & ((1u << lane) - 1u));
-                col[r * k + pos] = c;
-                val[r * k + pos] = xv;
+                col[r * ld + pos] = c;
+                val[r * ld + pos] = xv;
             }
             base += __popc(b);
         }
@@ -451,7 +527,7 @@ cudaError_t launch_dense_to_ell(const Tin* F, int64_t rows, int k, EllDev out,
     int64_t grid = (rows * 32 + B - 1) / B;
     if (grid > 65535) grid = 65535;
     dense_to_ell_kernel<Tin, T><<<(unsigned)grid, B, 0, st>>>(
-        F, rows, k, out.cnt, out.col, static_cast<T*>(out.val), status);
+        F, rows, k, out.ld, out.cnt, out.col, static_cast<T*>(out.val), status);
     return cudaGetLastError();
 }
 
@@ -500,7 +576,7 @@ cudaError_t launch_norm2(const T* val, int64_t count, double* part,
 }
 
 template <typename T>
-__global__ void ell_dot_part_kernel(int64_t rows, int k, const int32_t* cnt,
+__global__ void ell_dot_part_kernel(int64_t rows, int ld, const int32_t* cnt,
                                     const int32_t* col, const T* val,
                                     const T* Y, int64_t ldy, double* part)
 {
@@ -512,7 +588,7 @@ __global__ void ell_dot_part_kernel(int64_t rows, int k, const int32_t* cnt,
     for (int64_t r = b0 + threadIdx.x; r < b1; r += blockDim.x) {
         const int L = cnt[r];
         for (int q = 0; q < L; ++q)
-            s += (double)val[r * k + q] * (double)Y[r * ldy + col[r * k + q]];
+            s += (double)val[r * ld + q] * (double)Y[r * ldy + col[r * ld + q]];
     }
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -529,7 +605,8 @@ cudaError_t launch_ell_dot(int64_t rows, int k, EllDev F, const T* Y,
                            int64_t ldy, double* part, int nparts, double* out,
                            cudaStream_t st)
 {
-    ell_dot_part_kernel<T><<<nparts, 256, 0, st>>>(rows, k, F.cnt, F.col,
+    (void)k;
+    ell_dot_part_kernel<T><<<nparts, 256, 0, st>>>(rows, F.ld, F.cnt, F.col,
                                                    static_cast<const T*>(F.val), Y, ldy, part);
     sum_parts_kernel<<<1, 32, 0, st>>>(part, nparts, out);
     return cudaGetLastError();
@@ -539,7 +616,7 @@ cudaError_t launch_ell_dot(int64_t rows, int k, EllDev F, const T* Y,
 // Layout conversions used by the enforcement entry points.
 
 template <typename T>
-__global__ void ell_scatter_colmajor_kernel(int64_t rows, int k,
+__global__ void ell_scatter_colmajor_kernel(int64_t rows, int ld,
                                             const int32_t* cnt,
                                             const int32_t* col, const T* val,
                                             T* Xt, int64_t ldx)
@@ -547,7 +624,7 @@ __global__ void ell_scatter_colmajor_kernel(int64_t rows, int k,
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int L = cnt[r];
-        for (int q = 0; q < L; ++q) Xt[(int64_t)col[r * k + q] * ldx + r] = val[r * k + q];
+        for (int q = 0; q < L; ++q) Xt[(int64_t)col[r * ld + q] * ldx + r] = val[r * ld + q];
     }
 }
 
@@ -561,7 +638,7 @@ cudaError_t launch_ell_to_colmajor(int64_t rows, int k, EllDev F, T* Xt,
     int64_t grid = (rows + 255) / 256;
     if (grid > 65535) grid = 65535;
     ell_scatter_colmajor_kernel<T><<<(unsigned)grid, 256, 0, st>>>(
-        rows, k, F.cnt, F.col, static_cast<const T*>(F.val), Xt, ldx);
+        rows, F.ld, F.cnt, F.col, static_cast<const T*>(F.val), Xt, ldx);
     return cudaGetLastError();
 }
 
@@ -596,9 +673,9 @@ cudaError_t launch_dense_to_colmajor(const T* X, int64_t rows, int k,
 }
 
 template <typename T>
-__global__ void ell_to_dense_kernel(int64_t rows, int k, const int32_t* cnt,
-                                    const int32_t* col, const T* val, T* X,
-                                    int64_t ld)
+__global__ void ell_to_dense_kernel(int64_t rows, int k, int eld,
+                                    const int32_t* cnt, const int32_t* col,
+                                    const T* val, T* X, int64_t ld)
 {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -607,7 +684,7 @@ __global__ void ell_to_dense_kernel(int64_t rows, int k, const int32_t* cnt,
         for (int c = lane; c < k; c += 32) X[r * ld + c] = T(0);
         __syncwarp();
         const int L = cnt[r];
-        for (int q = lane; q < L; q += 32) X[r * ld + col[r * k + q]] = val[r * k + q];
+        for (int q = lane; q < L; q += 32) X[r * ld + col[r * eld + q]] = val[r * eld + q];
         __syncwarp();
     }
 }
@@ -620,7 +697,7 @@ cudaError_t launch_ell_to_dense(int64_t rows, int k, EllDev F, T* X,
     int64_t grid = (rows * 32 + 255) / 256;
     if (grid > 65535) grid = 65535;
     ell_to_dense_kernel<T><<<(unsigned)grid, 256, 0, st>>>(
-        rows, k, F.cnt, F.col, static_cast<const T*>(F.val), X, ld);
+        rows, k, F.ld, F.cnt, F.col, static_cast<const T*>(F.val), X, ld);
     return cudaGetLastError();
 }
 

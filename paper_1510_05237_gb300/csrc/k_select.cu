@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kSelThreads)
 select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
               int64_t t, int mode, int32_t* __restrict__ cnt,
               int32_t* __restrict__ colo, T* __restrict__ valo,
-              int64_t cache_elems, unsigned* status)
+              int64_t cache_elems, unsigned* status, int ld)
 {
     using K = typename Bits<T>::K;
     constexpr int NB = Bits<T>::nbits;
@@ -263,8 +263,8 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
             atomicOr(status, ST_OVERFLOW);
             continue;
         }
-        colo[i * k + pos] = (int32_t)c;
-        valo[i * k + pos] = x;
+        colo[i * ld + pos] = (int32_t)c;
+        valo[i * ld + pos] = x;
     }
 }
 
@@ -304,7 +304,7 @@ cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, select_kernel<T>, Xt, ldx, rows, k, t, mode,
                               out.cnt, out.col, static_cast<T*>(out.val),
-                              cache_elems, status);
+                              cache_elems, status, out.ld);
 }
 
 cudaError_t setup_select()
