@@ -261,6 +261,38 @@ espnmf_status espnmf_enforce_topt_buffer(void *X, int64_t rows, int32_t k,
                                          int64_t t, espnmf_topt_mode mode,
                                          void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Stand-alone selector that allocates nothing                              */
+
+/* Largest rows * ld(k) (and largest rows) that
+ * espnmf_enforce_topt_buffer_noalloc accepts, where ld(k) is k rounded up
+ * to a multiple of 4 (k <= 64) or of 16 (k > 64). */
+#define ESPNMF_NOALLOC_MAX_ELEMS 262144
+
+/* espnmf_enforce_topt_buffer_noalloc -- the paper has no counterpart: this
+ * is espnmf_enforce_topt_buffer (same arguments, same result) for callers
+ * that must not allocate device memory while it runs, for instance a
+ * service whose device memory is budgeted once at start-up, or a host
+ * program that hands all device memory to its own pool.  It calls no
+ * cudaMalloc, cudaFree or stream-ordered allocator; its scratch memory is a
+ * fixed array compiled into the library (about 6.5 MB, held on every GPU
+ * that loads the library until the process exits).
+ *   - X larger than ESPNMF_NOALLOC_MAX_ELEMS (rows * ld(k) or rows) is
+ *     rejected with ESPNMF_ERR_INVALID_ARG; nothing is modified.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address once; make that first call before any stream
+ *     capture.
+ *   - All calls share the array: calls whose work overlaps on the GPU
+ *     (other streams, other host threads on the same device) race on it and
+ *     must be serialised by the caller.
+ *   - Synchronises `stream` (NULL: the legacy default stream); failures are
+ *     described by espnmf_last_error(NULL). */
+espnmf_status espnmf_enforce_topt_buffer_noalloc(void *X, int64_t rows,
+                                                 int32_t k, int64_t ld,
+                                                 espnmf_dtype dtype, int64_t t,
+                                                 espnmf_topt_mode mode,
+                                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

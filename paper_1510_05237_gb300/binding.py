@@ -83,6 +83,7 @@ def load():
             "espnmf_launches_per_sweep": [P, ctypes.POINTER(i32)],
             "espnmf_sync": [P],
             "espnmf_enforce_topt_buffer": [P, i64, i32, i64, st, i64, st, P],
+            "espnmf_enforce_topt_buffer_noalloc": [P, i64, i32, i64, st, i64, st, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -104,7 +105,8 @@ def exported_symbols():
              "espnmf_enforce_topt", "espnmf_set_factor", "espnmf_residual", "espnmf_error",
              "espnmf_factor_nnz", "espnmf_get_factor", "espnmf_set_option",
              "espnmf_kernel_stat_count", "espnmf_kernel_stat", "espnmf_kernel_stats_reset",
-             "espnmf_launches_per_sweep", "espnmf_sync", "espnmf_enforce_topt_buffer"]
+             "espnmf_launches_per_sweep", "espnmf_sync", "espnmf_enforce_topt_buffer",
+             "espnmf_enforce_topt_buffer_noalloc"]
     return {n: hasattr(lib, n) for n in names}
 
 
@@ -305,3 +307,19 @@ def espnmf_enforce_topt_buffer(X, t: int, mode: int = TOPT_COLUMN, stream=None):
     _check(load().espnmf_enforce_topt_buffer(ctypes.c_void_p(X.data_ptr()), X.shape[0],
                                              X.shape[1], X.stride(0), _dtype_code(X), int(t),
                                              int(mode), _stream_handle(stream)))
+
+
+NOALLOC_MAX_ELEMS = 262144
+
+
+def espnmf_enforce_topt_buffer_noalloc(X, t: int, mode: int = TOPT_COLUMN, stream=None):
+    """espnmf_enforce_topt_buffer without any device allocation (scratch in
+    a fixed array inside the library; see include/espnmf.h for the size
+    limit and the rules on concurrent calls)."""
+    if not (_is_torch(X) and X.is_cuda):
+        raise TypeError("X must be a CUDA tensor")
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be 2-D with unit column stride")
+    _check(load().espnmf_enforce_topt_buffer_noalloc(ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                                     X.shape[1], X.stride(0), _dtype_code(X),
+                                                     int(t), int(mode), _stream_handle(stream)))

@@ -171,6 +171,9 @@ cudaError_t setup_solve();
 cudaError_t setup_select();
 cudaError_t setup_factor();
 
+// Records the message espnmf_last_error(NULL) returns on this thread.
+void set_thread_error(const char* msg);
+
 // Kernel kinds the profiler keeps statistics for.
 enum KernelKind : int {
     K_SPMM = 0, K_COMBINE, K_SOLVE, K_SELECT, K_FINALIZE, K_GRAM_REDUCE,

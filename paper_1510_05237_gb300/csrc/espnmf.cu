@@ -38,6 +38,12 @@ namespace {
 
 thread_local std::string g_init_error;
 
+}  // namespace
+
+void espnmf::set_thread_error(const char* msg) { g_init_error = msg ? msg : ""; }
+
+namespace {
+
 struct Factor {
     int64_t rows = 0;
     EllDev buf[2];

@@ -1,0 +1,145 @@
+// espnmf_noalloc.cu -- the stand-alone selector without any allocation.
+//
+// espnmf_enforce_topt_buffer takes its scratch memory (a column-major copy
+// of X and the row-packed survivors) from the stream-ordered allocator on
+// every call.  Some callers must not allocate device memory on their call
+// path -- a service whose device memory is budgeted once at start-up, or a
+// host that hands all device memory to its own pool -- so this variant runs
+// the same kernels on a fixed scratch array that lives in this file:
+//
+//   static __device__ g_noalloc_scratch[kNoallocBytes]
+//
+// Every GPU that loads the library holds the array until the process exits.
+// Host code cannot use the array's name as a device address (on the host it
+// is only a stand-in), so the first call on each device, with that device
+// current, asks the runtime for the array's device address once
+// (cudaGetSymbolAddress) and keeps it.  All calls share the array and it
+// keeps the previous call's contents: the parts that must start at zero are
+// cleared on every call, and calls that overlap on the GPU (different
+// streams, or different host threads on one device) race on it.
+#include <mutex>
+
+#include "../../include/espnmf.h"
+#include "common.cuh"
+
+using namespace espnmf;
+
+namespace {
+
+// Largest rows * factor_ld(k) (and largest rows) one call may use.
+constexpr int64_t kNoallocMaxElems = ESPNMF_NOALLOC_MAX_ELEMS;
+
+constexpr size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+// Worst case over k <= 128 and element size 8: column-major copy
+// (k * ceil32(rows) <= MaxElems + 31 * 128 elements), row counts, and the
+// row-packed survivors (columns and values), plus the status word.
+constexpr size_t kXtBytes = a256((size_t)(kNoallocMaxElems + 31 * 128) * 8);
+constexpr size_t kCntBytes = a256((size_t)kNoallocMaxElems * 4);
+constexpr size_t kColBytes = a256((size_t)kNoallocMaxElems * 4);
+constexpr size_t kValBytes = a256((size_t)kNoallocMaxElems * 8);
+constexpr size_t kNoallocBytes = kXtBytes + kCntBytes + kColBytes + kValBytes + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+std::mutex g_setup_mu;
+constexpr int kMaxDevices = 64;
+unsigned char* g_scratch_addr[kMaxDevices] = {};
+
+// Failures are described through espnmf_last_error(NULL), like the other
+// context-free calls.
+espnmf_status fail(espnmf_status s, const char* msg, cudaError_t e = cudaSuccess)
+{
+    std::string m = msg;
+    if (e != cudaSuccess) {
+        m += ": ";
+        m += cudaGetErrorString(e);
+        cudaGetLastError();
+    }
+    set_thread_error(m.c_str());
+    return s;
+}
+
+// Device address of the scratch array on the current device (set up once).
+espnmf_status scratch_for(int dev, unsigned char** out)
+{
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (!g_scratch_addr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "cudaGetSymbolAddress", e);
+        e = setup_select();
+        if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "selector set-up", e);
+        g_scratch_addr[dev] = static_cast<unsigned char*>(ptr);
+    }
+    *out = g_scratch_addr[dev];
+    return ESPNMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+espnmf_status espnmf_enforce_topt_buffer_noalloc(void* X, int64_t rows, int32_t k, int64_t ld,
+                                                 espnmf_dtype dtype, int64_t t,
+                                                 espnmf_topt_mode mode, void* stream)
+{
+    set_thread_error("");
+    if (!X || rows < 0 || k < 1 || k > 128 || ld < k || t < 0)
+        return fail(ESPNMF_ERR_INVALID_ARG, "bad X/rows/k/ld/t");
+    if (dtype != ESPNMF_F64 && dtype != ESPNMF_F32)
+        return fail(ESPNMF_ERR_INVALID_ARG, "dtype must be F64 or F32");
+    if (mode != ESPNMF_TOPT_COLUMN && mode != ESPNMF_TOPT_MATRIX && mode != ESPNMF_TOPT_NONE)
+        return fail(ESPNMF_ERR_INVALID_ARG, "unknown enforcement mode");
+    const int eld = factor_ld(k);
+    if (rows > kNoallocMaxElems || rows * (int64_t)eld > kNoallocMaxElems)
+        return fail(ESPNMF_ERR_INVALID_ARG,
+                    "X is larger than the static scratch allows (rows * ld(k) must be <= "
+                    "ESPNMF_NOALLOC_MAX_ELEMS)");
+    if (rows == 0) return ESPNMF_OK;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "device", e);
+    if (dev >= kMaxDevices) return fail(ESPNMF_ERR_UNSUPPORTED, "device index too large");
+    unsigned char* ws = nullptr;
+    espnmf_status st0 = scratch_for(dev, &ws);
+    if (st0 != ESPNMF_OK) return st0;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
+    const int64_t ldx = (rows + 31) / 32 * 32;
+    const size_t bx = a256((size_t)k * ldx * es), bc = a256((size_t)rows * 4),
+                 bl = a256((size_t)rows * eld * 4), bv = a256((size_t)rows * eld * es);
+    if (bx + bc + bl + bv + 256 > kNoallocBytes)
+        return fail(ESPNMF_ERR_INVALID_ARG, "X is larger than the static scratch allows");
+    unsigned* status = (unsigned*)(ws + bx + bc + bl + bv);
+    EllDev out;
+    out.cnt = (int32_t*)(ws + bx);
+    out.col = (int32_t*)(ws + bx + bc);
+    out.val = ws + bx + bc + bl;
+    out.ld = eld;
+    // the array keeps the last call's contents: clear the row counts and
+    // the status word
+    e = cudaMemsetAsync(out.cnt, 0, (size_t)rows * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess)
+        e = dtype == ESPNMF_F64
+                ? launch_dense_to_colmajor<double>((const double*)X, rows, k, ld, (double*)ws, ldx, status, st)
+                : launch_dense_to_colmajor<float>((const float*)X, rows, k, ld, (float*)ws, ldx, status, st);
+    if (e == cudaSuccess)
+        e = dtype == ESPNMF_F64
+                ? launch_select<double>((const double*)ws, ldx, rows, k, t, (int)mode, out, status, st, sms)
+                : launch_select<float>((const float*)ws, ldx, rows, k, t, (int)mode, out, status, st, sms);
+    if (e == cudaSuccess)
+        e = dtype == ESPNMF_F64 ? launch_ell_to_dense<double>(rows, k, out, (double*)X, ld, st)
+                                : launch_ell_to_dense<float>(rows, k, out, (float*)X, ld, st);
+    unsigned hstat = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "enforce_topt_buffer_noalloc", e);
+    if (hstat & ST_NONFINITE) return fail(ESPNMF_ERR_NONFINITE, "non-finite value in X");
+    if (hstat & ST_OVERFLOW) return fail(ESPNMF_ERR_CUDA, "internal: row overflow");
+    return ESPNMF_OK;
+}
+
+}  // extern "C"
