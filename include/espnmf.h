@@ -101,7 +101,7 @@ typedef struct espnmf_ctx espnmf_ctx;
  *   out      receives the new context (NULL on failure).
  *   A        the data matrix (see espnmf_csr); validated: monotone rowptr,
  *            sorted in-range column indices, finite non-negative values.
- *   k        rank, 1 <= k <= min(n, m) and k <= 256.
+ *   k        rank, 1 <= k <= min(n, m) and k <= 128.
  *   t_u,t_v  maximum nonzeros kept in U and V (Alg. 2 input): per column in
  *            COLUMN mode (values above the column length behave as the
  *            column length), in total in MATRIX mode; ignored for NONE.
@@ -275,7 +275,7 @@ espnmf_status espnmf_enforce_topt_buffer(void *X, int64_t rows, int32_t k,
  * service whose device memory is budgeted once at start-up, or a host
  * program that hands all device memory to its own pool.  It calls no
  * cudaMalloc, cudaFree or stream-ordered allocator; its scratch memory is a
- * fixed array compiled into the library (about 6.5 MB, held on every GPU
+ * fixed array compiled into the library (about 2.1 MB, held on every GPU
  * that loads the library until the process exits).
  *   - X larger than ESPNMF_NOALLOC_MAX_ELEMS (rows * ld(k) or rows) is
  *     rejected with ESPNMF_ERR_INVALID_ARG; nothing is modified.

@@ -22,6 +22,30 @@ enum : unsigned {
 
 enum TopMode : int { TOPT_COLUMN = 0, TOPT_MATRIX = 1, TOPT_NONE = 2 };
 
+// For non-negative IEEE numbers the bit pattern read as an unsigned integer
+// orders exactly like the value; the selector works on these keys.
+template <typename T> struct KeyBits;
+template <> struct KeyBits<float> {
+    using K = uint32_t;
+    static constexpr int top_shift = 20;   // first histogram: bits 30..20
+    __device__ static K of(float x) { return __float_as_uint(x); }
+};
+template <> struct KeyBits<double> {
+    using K = unsigned long long;
+    static constexpr int top_shift = 52;   // first histogram: the exponent
+    __device__ static K of(double x) { return (K)__double_as_longlong(x); }
+};
+
+// Survival rule of the enforcement step, given the selector's threshold
+// (tau, cut) for the entry's segment and the entry's tie index.
+template <typename T>
+__device__ __forceinline__ bool keep_entry(T v, typename KeyBits<T>::K tau, uint32_t cut,
+                                           uint32_t ix)
+{
+    const typename KeyBits<T>::K key = KeyBits<T>::of(v);
+    return key != 0 && (key > tau || (key == tau && ix <= cut));
+}
+
 // Rows are cut into segments of at most this many entries, one per lane.
 constexpr int kSegTarget = 64;
 constexpr int kMaxK = 256;
@@ -95,24 +119,30 @@ cudaError_t launch_solve(const T* Y, int64_t ldy, int64_t rows, int k,
                          const T* Ginv, T* Xt, int64_t ldx, unsigned* status,
                          cudaStream_t st, int sm_count);
 
-// Top-t selection on the column-major candidate Xt (k columns of length
-// rows, leading dimension ldx, entries >= +0, padding rows are +0), writing
-// the kept entries into the row-packed factor `out` (out.cnt zeroed
-// beforehand).
+// Threshold of the enforcement step per column (or one for the whole matrix)
+// from the column-major projected candidate Xt (k columns of length rows,
+// leading dimension ldx, entries >= +0): tau[s] (key) and cut[s] (tie index).
 template <typename T>
 cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
-                          int64_t t, int mode, EllDev out, unsigned* status,
-                          cudaStream_t st, int sm_count,
-                          int64_t* smem_need_out = nullptr);
+                          int64_t t, int mode, void* tau, uint32_t* cut,
+                          cudaStream_t st, int sm_count);
 
-// Row-wise pass over a freshly written factor: per-block FP64 Gram
-// partials, residual/error partials, and zeroing of the previous buffer's
-// counts.
+// Projects and enforces a caller's dense rows x k buffer in place.
 template <typename T>
-cudaError_t launch_finalize(int64_t rows, int k, EllDev cur, EllDev old,
-                            bool residual, bool zero_old, const T* Y,
-                            int64_t ldy, double* gram_part,
-                            double* scal_part, int nblocks, cudaStream_t st);
+cudaError_t launch_apply_thresholds(T* X, int64_t rows, int k, int64_t ld, int mode,
+                                    const void* tau, const uint32_t* cut,
+                                    unsigned* status, cudaStream_t st);
+
+// Row-wise pass after the selector: writes the new factor's rows in column
+// order (and dense copies of heavy rows), zeroes the old buffer's counts,
+// and leaves per-block FP64 partials of the Gram matrix (entry-major:
+// gram_part[e * nblocks + b]) and of ||F_new - F_old||^2, ||F_new||^2,
+// ||F_old||^2 and <F_new, Y> (scal_part[j * nblocks + b]).
+template <typename T>
+cudaError_t launch_emit(const T* Xt, int64_t ldx, int64_t rows, int k, int mode,
+                        const void* tau, const uint32_t* cut, EllDev cur, EllDev old,
+                        bool residual, const T* Y, int64_t ldy, double* gram_part,
+                        double* scal_part, int nblocks, cudaStream_t st);
 
 struct MetricsArgs {
     bool enabled = false;
@@ -138,10 +168,6 @@ template <typename T>
 cudaError_t launch_cholesky(const double* G, int k, double* Ginv64, T* GinvT,
                             unsigned* status, cudaStream_t st);
 
-template <typename Tin, typename T>
-cudaError_t launch_dense_to_ell(const Tin* F, int64_t rows, int k, EllDev out,
-                                unsigned* status, cudaStream_t st);
-
 template <typename T>
 cudaError_t launch_norm2(const T* val, int64_t count, double* part,
                          int nparts, double* out, cudaStream_t st);
@@ -156,10 +182,14 @@ template <typename T>
 cudaError_t launch_ell_to_colmajor(int64_t rows, int k, EllDev F, T* Xt,
                                    int64_t ldx, cudaStream_t st);
 
-template <typename T>
-cudaError_t launch_dense_to_colmajor(const T* X, int64_t rows, int k,
+// Projected, column-major copy of a dense rows x k matrix (leading
+// dimension ld); a non-finite entry raises ST_NONFINITE and, when
+// reject_negative, a negative one ST_BADINPUT.
+template <typename Tin, typename T>
+cudaError_t launch_dense_to_colmajor(const Tin* X, int64_t rows, int k,
                                      int64_t ld, T* Xt, int64_t ldx,
-                                     unsigned* status, cudaStream_t st);
+                                     unsigned* status, bool reject_negative,
+                                     cudaStream_t st);
 template <typename T>
 cudaError_t launch_ell_to_dense(int64_t rows, int k, EllDev F, T* X,
                                 int64_t ld, cudaStream_t st);
@@ -176,8 +206,8 @@ void set_thread_error(const char* msg);
 
 // Kernel kinds the profiler keeps statistics for.
 enum KernelKind : int {
-    K_SPMM = 0, K_COMBINE, K_SOLVE, K_SELECT, K_FINALIZE, K_GRAM_REDUCE,
-    K_CHOLESKY, K_DENSE_TO_ELL, K_NORM2, K_DOT, K_SCATTER, K_COUNT
+    K_SPMM = 0, K_COMBINE, K_SOLVE, K_SELECT, K_EMIT, K_GRAM_REDUCE,
+    K_CHOLESKY, K_TO_COLMAJOR, K_NORM2, K_DOT, K_SCATTER, K_COUNT
 };
 const char* kernel_name(int kind);
 

@@ -27,8 +27,8 @@ namespace espnmf {
 const char* kernel_name(int kind)
 {
     static const char* names[K_COUNT] = {"spmm_sell", "spmm_combine", "solve_project",
-                                         "select_topt", "finalize", "gram_reduce",
-                                         "cholesky", "dense_to_ell", "norm2", "ell_dot",
+                                         "select_topt", "emit", "gram_reduce",
+                                         "cholesky", "to_colmajor", "norm2", "ell_dot",
                                          "scatter"};
     return kind >= 0 && kind < K_COUNT ? names[kind] : "?";
 }
@@ -102,6 +102,8 @@ struct espnmf_ctx {
     double* norm_part = nullptr;
     double* met = nullptr;      // [0] R, [1] E, [2] f, [3] trace
     double* dot = nullptr;      // scratch scalar
+    void* tau = nullptr;        // selector thresholds (k keys of 8 bytes)
+    uint32_t* cut = nullptr;    // selector tie cut-offs (k)
     double* hist_R = nullptr;
     double* hist_E = nullptr;
     int* hist_counter = nullptr;
@@ -426,23 +428,27 @@ espnmf_status do_cholesky(espnmf_ctx* ctx, Factor& F, cudaStream_t s)
     });
 }
 
-// Gram partials + reduction of factor F (its current buffer); optional old
-// buffer for the residual / count zeroing, optional Y for the cross term.
-espnmf_status do_finalize(espnmf_ctx* ctx, Factor& F, const EllDev& cur, const EllDev* old,
-                          bool residual, const void* Y, bool metrics)
+// Writes factor F's next buffer from the projected candidate in Xt and the
+// selector's thresholds (tau/cut), zeroes the current buffer's counts, and
+// reduces the new Gram matrix (with R and E when `metrics`).  The buffers
+// are swapped afterwards.
+espnmf_status do_emit(espnmf_ctx* ctx, Factor& F, bool residual, const void* Y, bool metrics,
+                      int mode)
 {
-    EllDev none;
-    const EllDev& o = old ? *old : none;
-    const double bytes = (double)F.rows * 4.0 * (old ? 2.0 : 1.0) +
+    EllDev& nxt = F.buf[F.cur ^ 1];
+    EllDev& cur = F.buf[F.cur];
+    const double bytes = (double)F.rows * ctx->k * ctx->esz + (double)F.rows * 8.0 +
                          (double)ctx->fin_blocks * ctx->k * ctx->k * 8.0;
-    TRY(run(ctx, K_FINALIZE, bytes, ctx->st, [&] {
+    TRY(run(ctx, K_EMIT, bytes, ctx->st, [&] {
         return is_f64(ctx)
-                   ? launch_finalize<double>(F.rows, ctx->k, cur, o, residual, old != nullptr,
-                                             (const double*)Y, ctx->ldy, ctx->gram_part,
-                                             ctx->scal_part, ctx->fin_blocks, ctx->st)
-                   : launch_finalize<float>(F.rows, ctx->k, cur, o, residual, old != nullptr,
-                                            (const float*)Y, ctx->ldy, ctx->gram_part,
-                                            ctx->scal_part, ctx->fin_blocks, ctx->st);
+                   ? launch_emit<double>((const double*)ctx->Xt, ctx->ldx, F.rows, ctx->k, mode,
+                                         ctx->tau, ctx->cut, nxt, cur, residual, (const double*)Y,
+                                         ctx->ldy, ctx->gram_part, ctx->scal_part,
+                                         ctx->fin_blocks, ctx->st)
+                   : launch_emit<float>((const float*)ctx->Xt, ctx->ldx, F.rows, ctx->k, mode,
+                                        ctx->tau, ctx->cut, nxt, cur, residual, (const float*)Y,
+                                        ctx->ldy, ctx->gram_part, ctx->scal_part,
+                                        ctx->fin_blocks, ctx->st);
     }));
     MetricsArgs ma;
     if (metrics) {
@@ -460,8 +466,21 @@ espnmf_status do_finalize(espnmf_ctx* ctx, Factor& F, const EllDev& cur, const E
         return launch_gram_reduce(ctx->gram_part, ctx->scal_part, ctx->fin_blocks, ctx->k, F.G,
                                   ctx->scal, ctx->gram_counter, ma, ctx->st);
     }));
+    F.cur ^= 1;
     F.chol_pending = true;
     return ESPNMF_OK;
+}
+
+espnmf_status do_select(espnmf_ctx* ctx, int64_t rows, int64_t t)
+{
+    return run(ctx, K_SELECT, (double)rows * ctx->k * ctx->esz, ctx->st, [&] {
+        return is_f64(ctx) ? launch_select<double>((const double*)ctx->Xt, ctx->ldx, rows, ctx->k,
+                                                   t, ctx->mode, ctx->tau, ctx->cut, ctx->st,
+                                                   ctx->sm_count)
+                           : launch_select<float>((const float*)ctx->Xt, ctx->ldx, rows, ctx->k,
+                                                  t, ctx->mode, ctx->tau, ctx->cut, ctx->st,
+                                                  ctx->sm_count);
+    });
 }
 
 // Alg. 2 steps 1-2 (updV) or 3-4.
@@ -490,17 +509,8 @@ espnmf_status half_update(espnmf_ctx* ctx, bool updV)
                                                  ctx->status_d, ctx->st, ctx->sm_count);
     }));
     const int64_t t = updV ? ctx->t_v : ctx->t_u;
-    EllDev& nxt = F.buf[F.cur ^ 1];
-    const double selb = (double)rows * ctx->k * ctx->esz;
-    TRY(run(ctx, K_SELECT, selb, ctx->st, [&] {
-        return is_f64(ctx) ? launch_select<double>((const double*)ctx->Xt, ctx->ldx, rows, ctx->k,
-                                                   t, ctx->mode, nxt, ctx->status_d, ctx->st, ctx->sm_count)
-                           : launch_select<float>((const float*)ctx->Xt, ctx->ldx, rows, ctx->k,
-                                                  t, ctx->mode, nxt, ctx->status_d, ctx->st, ctx->sm_count);
-    }));
-    EllDev old = F.buf[F.cur];
-    TRY(do_finalize(ctx, F, nxt, &old, !updV && F.valid, updV ? nullptr : ctx->Y, !updV));
-    F.cur ^= 1;
+    TRY(do_select(ctx, rows, t));
+    TRY(do_emit(ctx, F, !updV && F.valid, updV ? nullptr : ctx->Y, !updV, ctx->mode));
     F.valid = true;
     if (updV) {
         ctx->Y_is_AV = false;
@@ -606,18 +616,6 @@ espnmf_status enter(espnmf_ctx* ctx)
     return ESPNMF_OK;
 }
 
-template <typename Tin>
-espnmf_status load_factor_dense(espnmf_ctx* ctx, Factor& F, const Tin* dptr)
-{
-    EllDev& cur = F.buf[F.cur];
-    return run(ctx, K_DENSE_TO_ELL, (double)F.rows * ctx->k * sizeof(Tin), ctx->st, [&] {
-        return is_f64(ctx) ? launch_dense_to_ell<Tin, double>(dptr, F.rows, ctx->k, cur,
-                                                              ctx->status_d, ctx->st)
-                           : launch_dense_to_ell<Tin, float>(dptr, F.rows, ctx->k, cur,
-                                                             ctx->status_d, ctx->st);
-    });
-}
-
 // Replaces factor F by a dense rows x k matrix (host or device).
 espnmf_status set_factor_impl(espnmf_ctx* ctx, Factor& F, const void* src, espnmf_dtype dtype,
                               int on_device)
@@ -634,12 +632,29 @@ espnmf_status set_factor_impl(espnmf_ctx* ctx, Factor& F, const void* src, espnm
         CU(cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, ctx->st));
         dptr = tmp;
     }
-    espnmf_status s = dtype == ESPNMF_F64 ? load_factor_dense(ctx, F, (const double*)dptr)
-                                          : load_factor_dense(ctx, F, (const float*)dptr);
+    const double cb = (double)F.rows * ctx->k * (es + ctx->esz);
+    espnmf_status s = run(ctx, K_TO_COLMAJOR, cb, ctx->st, [&] {
+        if (dtype == ESPNMF_F64)
+            return is_f64(ctx) ? launch_dense_to_colmajor<double, double>(
+                                     (const double*)dptr, F.rows, ctx->k, ctx->k, (double*)ctx->Xt,
+                                     ctx->ldx, ctx->status_d, true, ctx->st)
+                               : launch_dense_to_colmajor<double, float>(
+                                     (const double*)dptr, F.rows, ctx->k, ctx->k, (float*)ctx->Xt,
+                                     ctx->ldx, ctx->status_d, true, ctx->st);
+        return is_f64(ctx) ? launch_dense_to_colmajor<float, double>(
+                                 (const float*)dptr, F.rows, ctx->k, ctx->k, (double*)ctx->Xt,
+                                 ctx->ldx, ctx->status_d, true, ctx->st)
+                           : launch_dense_to_colmajor<float, float>(
+                                 (const float*)dptr, F.rows, ctx->k, ctx->k, (float*)ctx->Xt,
+                                 ctx->ldx, ctx->status_d, true, ctx->st);
+    });
     if (tmp) CU(cudaFreeAsync(tmp, ctx->st));
     TRY(s);
     TRY(check_status(ctx));
-    TRY(do_finalize(ctx, F, F.buf[F.cur], nullptr, false, nullptr, false));
+    // thresholds that keep every positive entry (U0 is not enforced)
+    CU(cudaMemsetAsync(ctx->tau, 0, 8 * (size_t)ctx->k, ctx->st));
+    CU(cudaMemsetAsync(ctx->cut, 0xff, 4 * (size_t)ctx->k, ctx->st));
+    TRY(do_emit(ctx, F, false, nullptr, false, TOPT_COLUMN));
     F.valid = true;
     return ESPNMF_OK;
 }
@@ -829,7 +844,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         TRY(dmalloc(ctx, &ctx->Y, (size_t)rmax * ctx->ldy * ctx->esz));
         TRY(dmalloc(ctx, &ctx->Xt, (size_t)k * ctx->ldx * ctx->esz));
         CU(cudaMemsetAsync(ctx->Xt, 0, (size_t)k * ctx->ldx * ctx->esz, ctx->st));
-        ctx->fin_blocks = ctx->sm_count;
+        ctx->fin_blocks = 2 * ctx->sm_count;
         TRY(dmalloc(ctx, &ctx->gram_part, sizeof(double) * ctx->fin_blocks * k * k));
         TRY(dmalloc(ctx, &ctx->scal_part, sizeof(double) * ctx->fin_blocks * 4));
         TRY(dmalloc(ctx, &ctx->scal, sizeof(double) * 4));
@@ -840,6 +855,8 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         TRY(dmalloc(ctx, &ctx->met, sizeof(double) * 4));
         CU(cudaMemsetAsync(ctx->met, 0, sizeof(double) * 4, ctx->st));
         TRY(dmalloc(ctx, &ctx->dot, sizeof(double)));
+        TRY(dmalloc(ctx, &ctx->tau, 8 * (size_t)k));
+        TRY(dmalloc(ctx, &ctx->cut, 4 * (size_t)k));
         TRY(dmalloc(ctx, &ctx->hist_counter, sizeof(int)));
         CU(cudaMemsetAsync(ctx->hist_counter, 0, sizeof(int), ctx->st));
         TRY(ensure_hist(ctx, 64));
@@ -967,19 +984,12 @@ espnmf_status espnmf_enforce_topt(espnmf_ctx* ctx, espnmf_which which, int64_t t
     Factor& F = which == ESPNMF_U ? ctx->U : ctx->V;
     if (!F.valid) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "factor has no value yet");
     EllDev& cur = F.buf[F.cur];
-    EllDev& nxt = F.buf[F.cur ^ 1];
     TRY(run(ctx, K_SCATTER, (double)F.rows * ctx->k * ctx->esz, ctx->st, [&] {
         return is_f64(ctx) ? launch_ell_to_colmajor<double>(F.rows, ctx->k, cur, (double*)ctx->Xt, ctx->ldx, ctx->st)
                            : launch_ell_to_colmajor<float>(F.rows, ctx->k, cur, (float*)ctx->Xt, ctx->ldx, ctx->st);
     }));
-    TRY(run(ctx, K_SELECT, (double)F.rows * ctx->k * ctx->esz, ctx->st, [&] {
-        return is_f64(ctx) ? launch_select<double>((const double*)ctx->Xt, ctx->ldx, F.rows, ctx->k, t,
-                                                   ctx->mode, nxt, ctx->status_d, ctx->st, ctx->sm_count)
-                           : launch_select<float>((const float*)ctx->Xt, ctx->ldx, F.rows, ctx->k, t,
-                                                  ctx->mode, nxt, ctx->status_d, ctx->st, ctx->sm_count);
-    }));
-    TRY(do_finalize(ctx, F, nxt, &cur, false, nullptr, false));
-    F.cur ^= 1;
+    TRY(do_select(ctx, F.rows, t));
+    TRY(do_emit(ctx, F, false, nullptr, false, ctx->mode));
     ctx->met_valid = false;
     if (which == ESPNMF_V) ctx->Y_is_AV = false;
     return check_status(ctx);
@@ -1228,31 +1238,25 @@ espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64
     const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
     const int64_t ldx = (rows + 31) / 32 * 32;
     auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const int eld = factor_ld(k);
-    const size_t bx = a256((size_t)k * ldx * es), bc = a256((size_t)rows * 4),
-                 bl = a256((size_t)rows * eld * 4), bv = a256((size_t)rows * eld * es);
+    const size_t bx = a256((size_t)k * ldx * es), bt = a256((size_t)k * 8), bc = a256((size_t)k * 4);
     unsigned char* ws = nullptr;
-    e = cudaMallocAsync((void**)&ws, bx + bc + bl + bv + 64, st);
+    e = cudaMallocAsync((void**)&ws, bx + bt + bc + 256, st);
     if (e != cudaSuccess) return cuerr(e, "cudaMallocAsync");
-    unsigned* status = (unsigned*)(ws + bx + bc + bl + bv);
-    EllDev out;
-    out.cnt = (int32_t*)(ws + bx);
-    out.col = (int32_t*)(ws + bx + bc);
-    out.val = ws + bx + bc + bl;
-    out.ld = eld;
-    e = cudaMemsetAsync(out.cnt, 0, bc, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
+    void* tau = ws + bx;
+    uint32_t* cut = (uint32_t*)(ws + bx + bt);
+    unsigned* status = (unsigned*)(ws + bx + bt + bc);
+    e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
     if (e == cudaSuccess)
         e = dtype == ESPNMF_F64
-                ? launch_dense_to_colmajor<double>((const double*)X, rows, k, ld, (double*)ws, ldx, status, st)
-                : launch_dense_to_colmajor<float>((const float*)X, rows, k, ld, (float*)ws, ldx, status, st);
+                ? launch_dense_to_colmajor<double, double>((const double*)X, rows, k, ld, (double*)ws, ldx, status, false, st)
+                : launch_dense_to_colmajor<float, float>((const float*)X, rows, k, ld, (float*)ws, ldx, status, false, st);
     if (e == cudaSuccess)
         e = dtype == ESPNMF_F64
-                ? launch_select<double>((const double*)ws, ldx, rows, k, t, (int)mode, out, status, st, sms)
-                : launch_select<float>((const float*)ws, ldx, rows, k, t, (int)mode, out, status, st, sms);
+                ? launch_select<double>((const double*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms)
+                : launch_select<float>((const float*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms);
     if (e == cudaSuccess)
-        e = dtype == ESPNMF_F64 ? launch_ell_to_dense<double>(rows, k, out, (double*)X, ld, st)
-                                : launch_ell_to_dense<float>(rows, k, out, (float*)X, ld, st);
+        e = dtype == ESPNMF_F64 ? launch_apply_thresholds<double>((double*)X, rows, k, ld, (int)mode, tau, cut, status, st)
+                                : launch_apply_thresholds<float>((float*)X, rows, k, ld, (int)mode, tau, cut, status, st);
     unsigned hstat = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     cudaError_t e2 = cudaFreeAsync(ws, st);
@@ -1260,7 +1264,6 @@ espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuerr(e, "enforce_topt_buffer");
     if (hstat & ST_NONFINITE) return set_err(nullptr, ESPNMF_ERR_NONFINITE, "non-finite value in X");
-    if (hstat & ST_OVERFLOW) return set_err(nullptr, ESPNMF_ERR_CUDA, "internal: row overflow");
     return ESPNMF_OK;
 }
 

@@ -1,7 +1,7 @@
 // espnmf_noalloc.cu -- the stand-alone selector without any allocation.
 //
 // espnmf_enforce_topt_buffer takes its scratch memory (a column-major copy
-// of X and the row-packed survivors) from the stream-ordered allocator on
+// of X and the per-column thresholds) from the stream-ordered allocator on
 // every call.  Some callers must not allocate device memory on their call
 // path -- a service whose device memory is budgeted once at start-up, or a
 // host that hands all device memory to its own pool -- so this variant runs
@@ -30,14 +30,13 @@ namespace {
 constexpr int64_t kNoallocMaxElems = ESPNMF_NOALLOC_MAX_ELEMS;
 
 constexpr size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
-// Worst case over k <= 128 and element size 8: column-major copy
-// (k * ceil32(rows) <= MaxElems + 31 * 128 elements), row counts, and the
-// row-packed survivors (columns and values), plus the status word.
+// Worst case over k <= 128 and element size 8: the column-major copy
+// (k * ceil32(rows) <= MaxElems + 31 * 128 elements), the thresholds and
+// tie cut-offs of up to 128 columns, and the status word.
 constexpr size_t kXtBytes = a256((size_t)(kNoallocMaxElems + 31 * 128) * 8);
-constexpr size_t kCntBytes = a256((size_t)kNoallocMaxElems * 4);
-constexpr size_t kColBytes = a256((size_t)kNoallocMaxElems * 4);
-constexpr size_t kValBytes = a256((size_t)kNoallocMaxElems * 8);
-constexpr size_t kNoallocBytes = kXtBytes + kCntBytes + kColBytes + kValBytes + 256;
+constexpr size_t kTauBytes = a256(128 * 8);
+constexpr size_t kCutBytes = a256(128 * 4);
+constexpr size_t kNoallocBytes = kXtBytes + kTauBytes + kCutBytes + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -90,8 +89,7 @@ espnmf_status espnmf_enforce_topt_buffer_noalloc(void* X, int64_t rows, int32_t 
         return fail(ESPNMF_ERR_INVALID_ARG, "dtype must be F64 or F32");
     if (mode != ESPNMF_TOPT_COLUMN && mode != ESPNMF_TOPT_MATRIX && mode != ESPNMF_TOPT_NONE)
         return fail(ESPNMF_ERR_INVALID_ARG, "unknown enforcement mode");
-    const int eld = factor_ld(k);
-    if (rows > kNoallocMaxElems || rows * (int64_t)eld > kNoallocMaxElems)
+    if (rows > kNoallocMaxElems || rows * (int64_t)factor_ld(k) > kNoallocMaxElems)
         return fail(ESPNMF_ERR_INVALID_ARG,
                     "X is larger than the static scratch allows (rows * ld(k) must be <= "
                     "ESPNMF_NOALLOC_MAX_ELEMS)");
@@ -108,37 +106,31 @@ espnmf_status espnmf_enforce_topt_buffer_noalloc(void* X, int64_t rows, int32_t 
     cudaStream_t st = (cudaStream_t)stream;
     const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
     const int64_t ldx = (rows + 31) / 32 * 32;
-    const size_t bx = a256((size_t)k * ldx * es), bc = a256((size_t)rows * 4),
-                 bl = a256((size_t)rows * eld * 4), bv = a256((size_t)rows * eld * es);
-    if (bx + bc + bl + bv + 256 > kNoallocBytes)
+    const size_t bx = a256((size_t)k * ldx * es);
+    if (bx + kTauBytes + kCutBytes + 256 > kNoallocBytes)
         return fail(ESPNMF_ERR_INVALID_ARG, "X is larger than the static scratch allows");
-    unsigned* status = (unsigned*)(ws + bx + bc + bl + bv);
-    EllDev out;
-    out.cnt = (int32_t*)(ws + bx);
-    out.col = (int32_t*)(ws + bx + bc);
-    out.val = ws + bx + bc + bl;
-    out.ld = eld;
-    // the array keeps the last call's contents: clear the row counts and
-    // the status word
-    e = cudaMemsetAsync(out.cnt, 0, (size_t)rows * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
+    void* tau = ws + bx;
+    uint32_t* cut = (uint32_t*)(ws + bx + kTauBytes);
+    unsigned* status = (unsigned*)(ws + bx + kTauBytes + kCutBytes);
+    // the array keeps the last call's contents: clear the status word (the
+    // rest is fully rewritten before it is read)
+    e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
     if (e == cudaSuccess)
         e = dtype == ESPNMF_F64
-                ? launch_dense_to_colmajor<double>((const double*)X, rows, k, ld, (double*)ws, ldx, status, st)
-                : launch_dense_to_colmajor<float>((const float*)X, rows, k, ld, (float*)ws, ldx, status, st);
+                ? launch_dense_to_colmajor<double, double>((const double*)X, rows, k, ld, (double*)ws, ldx, status, false, st)
+                : launch_dense_to_colmajor<float, float>((const float*)X, rows, k, ld, (float*)ws, ldx, status, false, st);
     if (e == cudaSuccess)
         e = dtype == ESPNMF_F64
-                ? launch_select<double>((const double*)ws, ldx, rows, k, t, (int)mode, out, status, st, sms)
-                : launch_select<float>((const float*)ws, ldx, rows, k, t, (int)mode, out, status, st, sms);
+                ? launch_select<double>((const double*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms)
+                : launch_select<float>((const float*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms);
     if (e == cudaSuccess)
-        e = dtype == ESPNMF_F64 ? launch_ell_to_dense<double>(rows, k, out, (double*)X, ld, st)
-                                : launch_ell_to_dense<float>(rows, k, out, (float*)X, ld, st);
+        e = dtype == ESPNMF_F64 ? launch_apply_thresholds<double>((double*)X, rows, k, ld, (int)mode, tau, cut, status, st)
+                                : launch_apply_thresholds<float>((float*)X, rows, k, ld, (int)mode, tau, cut, status, st);
     unsigned hstat = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "enforce_topt_buffer_noalloc", e);
     if (hstat & ST_NONFINITE) return fail(ESPNMF_ERR_NONFINITE, "non-finite value in X");
-    if (hstat & ST_OVERFLOW) return fail(ESPNMF_ERR_CUDA, "internal: row overflow");
     return ESPNMF_OK;
 }
 

@@ -1,10 +1,13 @@
 // k_factor.cu -- everything that happens to a factor after its selection:
 //
-//   finalize      row-wise pass over the new factor: per-block FP64 partial
-//                 sums of its Gram matrix F^T F (the "U^T U" / "V^T V" of
-//                 Alg. 2 steps 1 and 3), of ||F_new - F_old||^2, ||F_new||^2,
+//   emit          row-wise pass over the projected candidate and the
+//                 selector's thresholds: writes the new factor's rows in
+//                 column order (and dense copies of heavy rows), zeroes the
+//                 old buffer's counts, and leaves per-block FP64 partial sums
+//                 of its Gram matrix F^T F (the "U^T U" / "V^T V" of Alg. 2
+//                 steps 1 and 3), of ||F_new - F_old||^2, ||F_new||^2,
 //                 ||F_old||^2 (Sec. 3.1 residual) and of <U, A V> (the cross
-//                 term of the error identity); zeroes the old buffer's counts.
+//                 term of the error identity).
 //   gram_reduce   adds the block partials in a fixed order; its last block
 //                 also forms R and E (Sec. 3.1) without ever forming U V^T:
 //                 E^2 ||A||^2 = ||A||^2 - 2 <U, A V> + <U^T U, V^T V>.
@@ -23,163 +26,253 @@ namespace espnmf {
 
 static __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-template <typename T>
-struct FinArgs {
-    int64_t rows;
-    int k;
-    int ld;
-    int heavy;
-    const int32_t* cnt_new;
-    const int32_t* col_new;
-    const T* val_new;
-    T* dense_new;          // dense copies of heavy rows (may be null)
-    int32_t* cnt_old;
-    const int32_t* col_old;
-    const T* val_old;
-    bool residual;
-    bool zero_old;
-    const T* Y;
-    int64_t ldy;
-    double* gram_part;
-    double* scal_part;
-};
-
-template <typename T>
-static __host__ __device__ size_t fin_warp_bytes(int k, int ld, bool residual)
-{
-    // Gram accumulator, staged rows (columns, values), and per-lane dense
-    // scratch rows of the new (and old) values, slot c of lane l at c*32+l
-    return align16((size_t)k * k * sizeof(double)) + align16((size_t)32 * ld * sizeof(int)) +
-           align16((size_t)32 * ld * sizeof(T)) + align16((size_t)32 * k * sizeof(T)) +
-           (residual ? align16((size_t)32 * k * sizeof(T)) : 0);
-}
-
 __device__ inline double warp_sum(double v)
 {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     return v;
 }
 
-// Copies n (a multiple of 4 not exceeding the row stride) ints / values of
-// a 16-byte aligned row with 128-bit loads.
-__device__ inline void copy_row4(int* dst, const int32_t* src, int n)
+constexpr int kEmitThreads = 128;   // 4 warps
+constexpr int kSlots = 40;          // heavy-Gram register slots per thread
+
+template <typename T>
+struct EmitArgs {
+    const T* Xt;
+    int64_t ldx;
+    int64_t rows;
+    int k, mode, nseg;
+    const typename KeyBits<T>::K* tau;
+    const uint32_t* cut;
+    int32_t* cnt;
+    int32_t* col;
+    T* val;
+    T* dense;
+    int ld, heavy, SL;   // SL: staged pairs per lane (light rows)
+    bool heavy_gram;     // heavy rows' Gram by register slots
+    int32_t* cnt_old;
+    const int32_t* col_old;
+    const T* val_old;
+    bool residual, zero_old;
+    const T* Y;
+    int64_t ldy;
+    double* gram_part;   // [k*k][gridDim.x]
+    double* scal_part;   // [4][gridDim.x]
+};
+
+template <typename T>
+static size_t emit_smem(int k, int ld, int nseg, int SL, int W)
 {
-    for (int q = 0; q < n; q += 4) *reinterpret_cast<int4*>(dst + q) = __ldg(reinterpret_cast<const int4*>(src + q));
-}
-__device__ inline void copy_row4(float* dst, const float* src, int n)
-{
-    for (int q = 0; q < n; q += 4) *reinterpret_cast<float4*>(dst + q) = __ldg(reinterpret_cast<const float4*>(src + q));
-}
-__device__ inline void copy_row4(double* dst, const double* src, int n)
-{
-    for (int q = 0; q < n; q += 2) *reinterpret_cast<double2*>(dst + q) = __ldg(reinterpret_cast<const double2*>(src + q));
+    using K = typename KeyBits<T>::K;
+    return align16((size_t)nseg * sizeof(K)) + align16((size_t)nseg * 4) +
+           (size_t)W * align16((size_t)k * k * 8) +
+           (size_t)W * (align16((size_t)32 * SL * 4) + align16((size_t)32 * SL * sizeof(T))) +
+           align16((size_t)kEmitThreads * 4) + align16((size_t)ld * 8) + 64;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128)
-finalize_kernel(FinArgs<T> a)
+__global__ void __launch_bounds__(kEmitThreads)
+emit_kernel(EmitArgs<T> a)
 {
+    using K = typename KeyBits<T>::K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4][4];
-    const int k = a.k, ld = a.ld;
+    __shared__ int wcnt[4];
+    const int k = a.k, ld = a.ld, SL = a.SL;
     const int W = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t pw = fin_warp_bytes<T>(k, ld, a.residual);
-    unsigned char* wbase = smem_raw + warp * pw;
-    double* G = reinterpret_cast<double*>(wbase);
-    int* sc = reinterpret_cast<int*>(wbase + align16((size_t)k * k * sizeof(double)));
-    T* sv = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(sc) + align16((size_t)32 * ld * sizeof(int)));
-    T* sn = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(sv) + align16((size_t)32 * ld * sizeof(T)));
-    T* so = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(sn) + align16((size_t)32 * k * sizeof(T)));
-    for (int e = lane; e < k * k; e += 32) G[e] = 0.0;
-    for (int e = lane; e < 32 * k; e += 32) sn[e] = T(0);
-    if (a.residual)
-        for (int e = lane; e < 32 * k; e += 32) so[e] = T(0);
-    double s_diff = 0.0, s_new = 0.0, s_old = 0.0, s_cross = 0.0;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* p = smem_raw;
+    K* stau = reinterpret_cast<K*>(p);
+    p += align16((size_t)a.nseg * sizeof(K));
+    uint32_t* scut = reinterpret_cast<uint32_t*>(p);
+    p += align16((size_t)a.nseg * 4);
+    double* Gall = reinterpret_cast<double*>(p);
+    p += (size_t)W * align16((size_t)k * k * 8);
+    int* stc_all = reinterpret_cast<int*>(p);
+    p += (size_t)W * align16((size_t)32 * SL * 4);
+    T* stv_all = reinterpret_cast<T*>(p);
+    p += (size_t)W * align16((size_t)32 * SL * sizeof(T));
+    int* hlist = reinterpret_cast<int*>(p);
+    p += align16((size_t)kEmitThreads * 4);
+    double* drow = reinterpret_cast<double*>(p);
 
+    const size_t gstride = align16((size_t)k * k * 8) / 8;
+    double* G = Gall + (size_t)warp * gstride;
+    int* stc = stc_all + (size_t)warp * (align16((size_t)32 * SL * 4) / 4);
+    T* stv = stv_all + (size_t)warp * (align16((size_t)32 * SL * sizeof(T)) / sizeof(T));
+    for (int c = tid; c < a.nseg; c += blockDim.x) {
+        stau[c] = a.tau[c];
+        scut[c] = a.cut[c];
+    }
+    for (int e = lane; e < k * k; e += 32) G[e] = 0.0;
+    __syncthreads();
+
+    const bool matrix = a.mode == TOPT_MATRIX;
     const int64_t chunk = (a.rows + gridDim.x - 1) / gridDim.x;
     const int64_t b0 = (int64_t)blockIdx.x * chunk;
     const int64_t b1 = b0 + chunk < a.rows ? b0 + chunk : a.rows;
-    __syncwarp();
+    double s_diff = 0.0, s_new = 0.0, s_old = 0.0, s_cross = 0.0;
+
     for (int64_t base = b0 + (int64_t)warp * 32; base < b1; base += (int64_t)W * 32) {
         const int64_t r = base + lane;
         const bool valid = r < b1;
-        const int Ln = valid ? a.cnt_new[r] : 0;
-        const int Ln4 = (Ln + 3) & ~3;
-        int* mc = sc + lane * ld;
-        T* mv = sv + lane * ld;
-        copy_row4(mc, a.col_new + r * ld, Ln4);
-        copy_row4(mv, a.val_new + r * ld, Ln4);
-        for (int q = 0; q < Ln; ++q) sn[mc[q] * 32 + lane] = mv[q];
-        if (a.dense_new && Ln >= a.heavy) {
-            T* dr = a.dense_new + r * ld;
-            for (int c = 0; c < ld; ++c) dr[c] = c < k ? sn[c * 32 + lane] : T(0);
-        }
-        int Lo = 0;
-        if (valid && (a.residual || a.zero_old)) {
-            Lo = a.cnt_old[r];
-            if (a.residual) {
-                const int32_t* co = a.col_old + r * ld;
-                const T* vo = a.val_old + r * ld;
-                for (int q = 0; q < Lo; ++q) so[co[q] * 32 + lane] = vo[q];
-            }
-            if (a.zero_old) a.cnt_old[r] = 0;
-        }
-        // row sums in column order (independent of the pair order in a row)
-        if (Ln > 0 || Lo > 0) {
-            for (int c = 0; c < k; ++c) {
-                const double n = (double)sn[c * 32 + lane];
-                s_new += n * n;
-                if (a.Y && n != 0.0) s_cross += n * (double)a.Y[r * a.ldy + c];
-                if (a.residual) {
-                    const double o = (double)so[c * 32 + lane];
-                    s_old += o * o;
-                    s_diff += (n - o) * (n - o);
-                    so[c * 32 + lane] = T(0);
+        auto keep = [&](int c, T x) -> bool {
+            const int sg = matrix ? 0 : c;
+            const uint32_t ix = matrix ? (uint32_t)(r * k + c) : (uint32_t)r;
+            return keep_entry<T>(x, stau[sg], scut[sg], ix);
+        };
+        int nl = 0;
+        if (valid) {
+            int pos = 0, q = 0;
+            const int Lo = (a.residual || a.zero_old) ? a.cnt_old[r] : 0;
+            const int32_t* co = a.col_old + r * ld;
+            const T* vo = a.val_old + r * ld;
+            int oc = (a.residual && Lo > 0) ? co[0] : k;
+            int32_t* wc = a.col + r * ld;
+            T* wv = a.val + r * ld;
+            // one pass over the row's k candidates, eight loads in flight
+            for (int c0 = 0; c0 < k; c0 += 8) {
+                T xs[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    xs[u] = c0 + u < k ? a.Xt[(int64_t)(c0 + u) * a.ldx + r] : T(0);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int c = c0 + u;
+                    if (c >= k) break;
+                    const T x = xs[u];
+                    const bool kp = keep(c, x);
+                    if (kp) {
+                        wc[pos] = c;
+                        wv[pos] = x;
+                        s_new += (double)x * (double)x;
+                        if (a.Y) s_cross += (double)x * (double)a.Y[r * a.ldy + c];
+                        if (pos < SL) {
+                            stc[lane * SL + pos] = c;
+                            stv[lane * SL + pos] = x;
+                        }
+                        ++pos;
+                    }
+                    if (a.residual) {
+                        double o = 0.0;
+                        if (oc == c) {
+                            o = (double)vo[q];
+                            ++q;
+                            oc = q < Lo ? co[q] : k;
+                            s_old += o * o;
+                        }
+                        if (kp || o != 0.0) {
+                            const double d = (kp ? (double)x : 0.0) - o;
+                            s_diff += d * d;
+                        }
+                    }
                 }
-                sn[c * 32 + lane] = T(0);
             }
+            const bool hv = pos >= a.heavy && a.dense != nullptr;
+            if (hv) {
+                // dense copy of a heavy row, from the pairs just written
+                T* dr = a.dense + r * ld;
+                for (int c = 0; c < ld; ++c) dr[c] = T(0);
+                for (int j = 0; j < pos; ++j) dr[wc[j]] = wv[j];
+            }
+            a.cnt[r] = pos;
+            if (a.zero_old) a.cnt_old[r] = 0;
+            nl = (hv && a.heavy_gram) ? 0 : pos;
         }
         __syncwarp();
-        // Gram: the 32 staged rows one after another; a row's pairs (ia <= ib)
-        // across the lanes, accumulated into the upper triangle (canonical
-        // slot min(c,d)*k + max(c,d)); distinct slots within a row.
+        // Gram of the light rows: a row's pairs (ia <= ib) across the lanes,
+        // into the upper triangle (slot min*k + max); slots are distinct
+        // within a row, rows follow each other.
         for (int j = 0; j < 32; ++j) {
-            const int Lj = __shfl_sync(0xffffffffu, Ln, j);
-            const int* jc = sc + j * ld;
-            const T* jv = sv + j * ld;
+            const int Lj = __shfl_sync(0xffffffffu, nl, j);
+            const int* jc = stc + j * SL;
+            const T* jv = stv + j * SL;
             for (int ia = 0; ia < Lj; ++ia) {
                 const int ca = jc[ia];
                 const double va = (double)jv[ia];
-                for (int ib = ia + lane; ib < Lj; ib += 64) {
+                for (int ib = ia + lane; ib < Lj; ib += 32) {
                     const int cb = jc[ib];
-                    const int s0 = ca < cb ? ca * k + cb : cb * k + ca;
-                    const double p0 = va * (double)jv[ib];
-                    const int ib2 = ib + 32;
-                    if (ib2 < Lj) {
-                        const int cb2 = jc[ib2];
-                        const int s1 = ca < cb2 ? ca * k + cb2 : cb2 * k + ca;
-                        const double p1 = va * (double)jv[ib2];
-                        G[s0] += p0;
-                        G[s1] += p1;
-                    } else {
-                        G[s0] += p0;
-                    }
+                    G[ca < cb ? ca * k + cb : cb * k + ca] += va * (double)jv[ib];
                 }
             }
             __syncwarp();
         }
     }
     __syncthreads();
-    // block partial: warps in order, upper triangle mirrored
-    double* gp = a.gram_part + (size_t)blockIdx.x * k * k;
-    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-        const int c = e / k, d = e - c * k;
-        const int src = c <= d ? c * k + d : d * k + c;
-        double sum = 0.0;
-        for (int w = 0; w < W; ++w)
-            sum += reinterpret_cast<const double*>(smem_raw + w * pw)[src];
-        gp[e] = sum;
+
+    // Gram of the heavy rows from their dense copies: thread tid owns the
+    // upper-triangle entries e = tid + NT * s, in registers.
+    const int ntri = k * (k + 1) / 2;
+    const int NT = blockDim.x;
+    int cd[kSlots];
+    double acc[kSlots];
+    {
+        // (c, d) of entry e, c <= d, entries ordered by c then d
+        int e0 = tid, c = 0, rowlen = k, start = 0;
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+            acc[s] = 0.0;
+            const int e = e0 + s * NT;
+            if (e < ntri) {
+                while (e >= start + rowlen) {
+                    start += rowlen;
+                    ++c;
+                    --rowlen;
+                }
+                cd[s] = (c << 16) | (c + (e - start));
+            } else {
+                cd[s] = -1;
+            }
+        }
+    }
+    if (a.heavy_gram && a.dense != nullptr) {
+        for (int64_t base = b0; base < b1; base += NT) {
+            const int64_t r = base + tid;
+            const bool f = r < b1 && a.cnt[r] >= a.heavy;
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (lane == 0) wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int off = 0, nh = 0;
+            for (int w = 0; w < W; ++w) {
+                if (w < warp) off += wcnt[w];
+                nh += wcnt[w];
+            }
+            if (f) hlist[off + __popc(bal & ((1u << lane) - 1u))] = (int)r;
+            __syncthreads();
+            for (int h = 0; h < nh; ++h) {
+                const int64_t rr = hlist[h];
+                for (int c = tid; c < k; c += blockDim.x) drow[c] = (double)a.dense[rr * ld + c];
+                __syncthreads();
+#pragma unroll
+                for (int s = 0; s < kSlots; ++s)
+                    if (cd[s] >= 0) acc[s] += drow[cd[s] >> 16] * drow[cd[s] & 0xffff];
+                __syncthreads();
+            }
+        }
+    }
+    // block partial, entry-major, the upper triangle mirrored
+    const int P = gridDim.x;
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+        if (cd[s] < 0) continue;
+        const int c = cd[s] >> 16, d = cd[s] & 0xffff;
+        double v = acc[s];
+        for (int w = 0; w < W; ++w) v += Gall[(size_t)w * gstride + c * k + d];
+        a.gram_part[(size_t)(c * k + d) * P + blockIdx.x] = v;
+        if (c != d) a.gram_part[(size_t)(d * k + c) * P + blockIdx.x] = v;
+    }
+    // entries beyond the register slots (only for k too large for them)
+    for (int e = kSlots * NT + tid; e < ntri; e += NT) {
+        int c = 0, start = 0, rowlen = k;
+        while (e >= start + rowlen) {
+            start += rowlen;
+            ++c;
+            --rowlen;
+        }
+        const int d = c + (e - start);
+        double v = 0.0;
+        for (int w = 0; w < W; ++w) v += Gall[(size_t)w * gstride + c * k + d];
+        a.gram_part[(size_t)(c * k + d) * P + blockIdx.x] = v;
+        if (c != d) a.gram_part[(size_t)(d * k + c) * P + blockIdx.x] = v;
     }
     s_diff = warp_sum(s_diff);
     s_new = warp_sum(s_new);
@@ -192,42 +285,58 @@ finalize_kernel(FinArgs<T> a)
         red[warp][3] = s_cross;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (tid < 4) {
         double sum = 0.0;
-        for (int w = 0; w < W; ++w) sum += red[w][threadIdx.x];
-        a.scal_part[(size_t)blockIdx.x * 4 + threadIdx.x] = sum;
+        for (int w = 0; w < W; ++w) sum += red[w][tid];
+        a.scal_part[(size_t)tid * P + blockIdx.x] = sum;
     }
 }
 
 template <typename T>
-cudaError_t launch_finalize(int64_t rows, int k, EllDev cur, EllDev old,
-                            bool residual, bool zero_old, const T* Y,
-                            int64_t ldy, double* gram_part,
-                            double* scal_part, int nblocks, cudaStream_t st)
+cudaError_t launch_emit(const T* Xt, int64_t ldx, int64_t rows, int k, int mode,
+                        const void* tau, const uint32_t* cut, EllDev cur, EllDev old,
+                        bool residual, const T* Y, int64_t ldy, double* gram_part,
+                        double* scal_part, int nblocks, cudaStream_t st)
 {
-    FinArgs<T> a;
+    using K = typename KeyBits<T>::K;
+    EmitArgs<T> a;
+    a.Xt = Xt;
+    a.ldx = ldx;
     a.rows = rows;
     a.k = k;
+    a.mode = mode;
+    a.nseg = mode == TOPT_MATRIX ? 1 : k;
+    a.tau = static_cast<const K*>(tau);
+    a.cut = cut;
+    a.cnt = cur.cnt;
+    a.col = cur.col;
+    a.val = static_cast<T*>(cur.val);
+    a.dense = static_cast<T*>(cur.dense);
     a.ld = cur.ld;
     a.heavy = cur.heavy;
-    a.cnt_new = cur.cnt;
-    a.col_new = cur.col;
-    a.val_new = static_cast<const T*>(cur.val);
-    a.dense_new = static_cast<T*>(cur.dense);
+    const int ntri = k * (k + 1) / 2;
     a.cnt_old = old.cnt;
     a.col_old = old.col;
     a.val_old = static_cast<const T*>(old.val);
     a.residual = residual && old.cnt != nullptr;
-    a.zero_old = zero_old && old.cnt != nullptr;
+    a.zero_old = old.cnt != nullptr;
     a.Y = Y;
     a.ldy = ldy;
     a.gram_part = gram_part;
     a.scal_part = scal_part;
-    const size_t pw = fin_warp_bytes<T>(k, cur.ld, a.residual);
-    int W = (int)((210 * 1024) / pw);
-    if (W > 4) W = 4;
-    if (W < 1) W = 1;
-    finalize_kernel<T><<<nblocks, W * 32, W * pw, st>>>(a);
+    // 4 warps unless shared memory says otherwise; the heavy rows' Gram
+    // uses register slots when they cover the triangle, else every row is
+    // staged for the pair loop
+    int W = 4;
+    size_t smem = 0;
+    for (;;) {
+        a.heavy_gram = cur.dense != nullptr && ntri <= kSlots * W * 32;
+        a.SL = a.heavy_gram ? (cur.heavy - 1 > 0 ? cur.heavy - 1 : 1) : k;
+        smem = emit_smem<T>(k, cur.ld, a.nseg, a.SL, W);
+        if (smem <= 200 * 1024 || W == 1) break;
+        --W;
+    }
+    emit_kernel<T><<<nblocks, W * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -238,27 +347,26 @@ __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
                                    int P, int k, double* G, double* scal,
                                    unsigned* counter, MetricsArgs m)
 {
+    // one warp per output: the k*k Gram entries, then the 4 scalars; a lane
+    // adds parts lane, lane+32, ... and the warp adds the lanes in a fixed
+    // tree, so the sum is reproducible
     const int kk = k * k;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    // eight interleaved partial sums, combined in a fixed order (FP64 adds
-    // have a long latency on this part)
-    if (e < kk) {
-        double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int p = 0;
-        for (; p + 7 < P; p += 8)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) s[u] += gram_part[(size_t)(p + u) * kk + e];
-        for (; p < P; ++p) s[0] += gram_part[(size_t)p * kk + e];
-        G[e] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
-    }
-    if (blockIdx.x == 0 && threadIdx.x < 4) {
-        double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int p = 0;
-        for (; p + 7 < P; p += 8)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) s[u] += scal_part[(size_t)(p + u) * 4 + threadIdx.x];
-        for (; p < P; ++p) s[0] += scal_part[(size_t)p * 4 + threadIdx.x];
-        scal[threadIdx.x] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w < kk + 4) {
+        const double* src = w < kk ? gram_part + (size_t)w * P : scal_part + (size_t)(w - kk) * P;
+        double s0 = 0.0, s1 = 0.0;
+        int p = lane;
+        for (; p + 32 < P; p += 64) {
+            s0 += src[p];
+            s1 += src[p + 32];
+        }
+        if (p < P) s0 += src[p];
+        const double v = warp_sum(s0 + s1);
+        if (lane == 0) {
+            if (w < kk) G[w] = v;
+            else scal[w - kk] = v;
+        }
     }
     if (!m.enabled) return;
     // The last block to finish forms the measures.
@@ -273,12 +381,11 @@ __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
     double tr = 0.0;
     for (int q = threadIdx.x; q < kk; q += blockDim.x) tr += __ldcg(G + q) * m.G_other[q];
     tr = warp_sum(tr);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = tr;
+    if (lane == 0) red[threadIdx.x >> 5] = tr;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
         const double diff = __ldcg(scal + 0), nw = __ldcg(scal + 1);
         const double od = __ldcg(scal + 2), cross = __ldcg(scal + 3);
         double R;
@@ -309,7 +416,7 @@ cudaError_t launch_gram_reduce(const double* gram_part,
                                MetricsArgs m, cudaStream_t st)
 {
     const int B = 256;
-    const int grid = (k * k + B - 1) / B;
+    const int grid = ((k * k + 4) * 32 + B - 1) / B;
     gram_reduce_kernel<<<grid, B, 0, st>>>(gram_part, scal_part, nparts, k, G,
                                            scal, counter, m);
     return cudaGetLastError();
@@ -348,23 +455,40 @@ cudaError_t launch_error_metrics(const double* GU, const double* GV, int k,
 }
 
 // ---------------------------------------------------------------------------
-// FP64 Cholesky G = L L^T and G^-1 = L^-T L^-1 in one CTA.  An index whose
-// diagonal is exactly 0 belongs to an all-zero factor column: it is taken
-// out (identity row/column during the factorisation, zero row/column in the
-// inverse), which gives the minimum-norm solution.  A pivot <= 64 eps
-// max_j G_jj elsewhere raises ST_SINGULAR.
+// FP64 inverse of the Gram matrix through its square-root-free Cholesky
+// factorisation G = L D L^T (L unit lower triangular), in one CTA:
+//   G^-1 = L^-T D^-1 L^-1.
+// An index whose diagonal is exactly 0 belongs to an all-zero factor column:
+// it is taken out (identity row/column during the factorisation, zero
+// row/column in the inverse), which gives the minimum-norm solution.  A pivot
+// d_j <= 64 eps max_j G_jj elsewhere raises ST_SINGULAR (d_j is the square
+// of the Cholesky diagonal, so this is the LL^T pivot test).
+// FP64 on this GPU has a long latency, so the column loop has one barrier
+// per column and takes pivot reciprocals from an FP32 seed refined by two
+// FP64 Newton steps.
+
+__device__ __forceinline__ double recip_fp64(double d)
+{
+    const double ad = fabs(d);
+    if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+    double x = (double)__frcp_rn((float)d);
+    double e = fma(-d, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-d, x, 1.0);
+    return fma(x, e, x);
+}
 
 template <typename T>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 cholesky_kernel(const double* __restrict__ G, int k, double* Ginv64,
-                T* GinvT, unsigned* status, int li_in_smem)
+                T* GinvT, unsigned* status, int w_in_smem)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* A = reinterpret_cast<double*>(smem_raw);                 // k*k
-    double* Li = li_in_smem ? A + (size_t)k * k : Ginv64;             // k*k
-    double* dinv = A + (size_t)k * k * (li_in_smem ? 2 : 1);          // k
+    double* W = w_in_smem ? A + (size_t)k * k : Ginv64;               // k*k: L^-1
+    double* dinv = A + (size_t)k * k * (w_in_smem ? 2 : 1);          // k
     int* act = reinterpret_cast<int*>(dinv + k);
-    __shared__ double inv_piv, maxdiag;
+    __shared__ double maxdiag;
     __shared__ int sing, nonfin;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int kk = k * k;
@@ -390,71 +514,75 @@ cholesky_kernel(const double* __restrict__ G, int k, double* Ginv64,
     }
     __syncthreads();
     const double tol = 64.0 * DBL_EPSILON * maxdiag;
-    // right-looking Cholesky, lower triangle of A
+    // L D L^T, lower triangle of A: after step j, A[i][j] (i > j) = l_ij
     for (int j = 0; j < k; ++j) {
-        if (tid == 0) {
-            double s = A[j * k + j];
-            if (act[j] && !(s > tol)) {
-                sing = 1;
-                s = 1.0;
-            }
-            const double ri = rsqrt(s);
-            A[j * k + j] = s * ri;   // sqrt(s)
-            inv_piv = ri;
-            dinv[j] = ri;
-        }
-        __syncthreads();
-        for (int i = j + 1 + tid; i < k; i += nt) A[i * k + j] *= inv_piv;
-        __syncthreads();
+        const double d0 = A[j * k + j];
+        const bool bad = act[j] && !(d0 > tol);
+        const double r = recip_fp64(bad ? 1.0 : d0);
+        // trailing update with the unscaled column: a_il -= a_ij a_lj / d_j
         const int nrem = k - j - 1;
         for (int e = tid; e < nrem * nrem; e += nt) {
             const int ii = e / nrem, ll = e - ii * nrem;
             if (ll <= ii) {
                 const int i = j + 1 + ii, l = j + 1 + ll;
-                A[i * k + l] -= A[i * k + j] * A[l * k + j];
+                A[i * k + l] -= A[i * k + j] * (A[l * k + j] * r);
             }
         }
-        __syncthreads();
+        __syncthreads();   // column j is read by everyone; scale it now
+        if (tid == 0) {
+            if (bad) sing = 1;
+            dinv[j] = r;
+            A[j * k + j] = 1.0;
+        }
+        for (int i = j + 1 + tid; i < k; i += nt) A[i * k + j] *= r;
     }
-    // Li = L^-1 (lower), row by row; each entry a dot product split over
-    // four independent accumulators (FP64 FMA latency is long on this part).
+    __syncthreads();
+    // W = L^-1 (unit lower), row by row; dot products over four accumulators
     for (int i = 0; i < k; ++i) {
-        const double di = dinv[i];
         for (int c = tid; c < k; c += nt) {
             double v;
             if (c > i) v = 0.0;
-            else if (c == i) v = di;
+            else if (c == i) v = 1.0;
             else {
                 double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
                 int e = c;
                 for (; e + 3 < i; e += 4) {
-                    s0 += A[i * k + e] * Li[e * k + c];
-                    s1 += A[i * k + e + 1] * Li[(e + 1) * k + c];
-                    s2 += A[i * k + e + 2] * Li[(e + 2) * k + c];
-                    s3 += A[i * k + e + 3] * Li[(e + 3) * k + c];
+                    s0 += A[i * k + e] * W[e * k + c];
+                    s1 += A[i * k + e + 1] * W[(e + 1) * k + c];
+                    s2 += A[i * k + e + 2] * W[(e + 2) * k + c];
+                    s3 += A[i * k + e + 3] * W[(e + 3) * k + c];
                 }
-                for (; e < i; ++e) s0 += A[i * k + e] * Li[e * k + c];
-                v = -((s0 + s1) + (s2 + s3)) * di;
+                for (; e < i; ++e) s0 += A[i * k + e] * W[e * k + c];
+                v = -((s0 + s1) + (s2 + s3));
             }
-            Li[i * k + c] = v;
+            W[i * k + c] = v;
         }
         __syncthreads();
     }
-    // G^-1 = Li^T Li into A (L is no longer needed).
-    for (int e = tid; e < kk; e += nt) {
-        const int c = e / k, d = e - c * k;
+    // G^-1 = W^T D^-1 W on the upper triangle, mirrored into A
+    const int ntri = k * (k + 1) / 2;
+    for (int e = tid; e < ntri; e += nt) {
+        int c = 0, start = 0, rowlen = k;
+        while (e >= start + rowlen) {
+            start += rowlen;
+            ++c;
+            --rowlen;
+        }
+        const int d = c + (e - start);
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         if (act[c] && act[d]) {
-            int q = c > d ? c : d;
+            int q = d;
             for (; q + 3 < k; q += 4) {
-                s0 += Li[q * k + c] * Li[q * k + d];
-                s1 += Li[(q + 1) * k + c] * Li[(q + 1) * k + d];
-                s2 += Li[(q + 2) * k + c] * Li[(q + 2) * k + d];
-                s3 += Li[(q + 3) * k + c] * Li[(q + 3) * k + d];
+                s0 += W[q * k + c] * dinv[q] * W[q * k + d];
+                s1 += W[(q + 1) * k + c] * dinv[q + 1] * W[(q + 1) * k + d];
+                s2 += W[(q + 2) * k + c] * dinv[q + 2] * W[(q + 2) * k + d];
+                s3 += W[(q + 3) * k + c] * dinv[q + 3] * W[(q + 3) * k + d];
             }
-            for (; q < k; ++q) s0 += Li[q * k + c] * Li[q * k + d];
+            for (; q < k; ++q) s0 += W[q * k + c] * dinv[q] * W[q * k + d];
         }
-        A[e] = (s0 + s1) + (s2 + s3);
+        const double v = (s0 + s1) + (s2 + s3);
+        A[c * k + d] = v;
+        A[d * k + c] = v;
     }
     __syncthreads();
     for (int e = tid; e < kk; e += nt) {
@@ -473,61 +601,11 @@ cudaError_t launch_cholesky(const double* G, int k, double* Ginv64, T* GinvT,
 {
     const size_t kk8 = (size_t)k * k * sizeof(double);
     const size_t extra = (size_t)k * (sizeof(double) + sizeof(int)) + 16;
-    const int li_smem = 2 * kk8 + extra <= 210 * 1024;
-    const size_t smem = kk8 * (li_smem ? 2 : 1) + extra;
-    int threads = k * k >= 1024 ? 1024 : ((k * k + 31) / 32) * 32;
+    const int w_smem = 2 * kk8 + extra <= 210 * 1024;
+    const size_t smem = kk8 * (w_smem ? 2 : 1) + extra;
+    int threads = k * k >= 256 ? 256 : ((k * k + 31) / 32) * 32;
     if (threads < 32) threads = 32;
-    cholesky_kernel<T><<<1, threads, smem, st>>>(G, k, Ginv64, GinvT, status, li_smem);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// dense rows x k (row-major) -> row-packed factor; entries that are not > 0
-// after conversion to T are dropped; negative entries raise ST_BADINPUT,
-// non-finite ones ST_NONFINITE.
-
-template <typename Tin, typename T>
-__global__ void dense_to_ell_kernel(const Tin* __restrict__ F, int64_t rows,
-                                    int k, int ld, int32_t* cnt, int32_t* col,
-                                    T* val, unsigned* status)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    bool bad = false, neg = false;
-    for (int64_t r = w0; r < rows; r += nw) {
-        int base = 0;
-        for (int cc = 0; cc < k; cc += 32) {
-            const int c = cc + lane;
-            const Tin x = c < k ? F[r * k + c] : Tin(0);
-            if (c < k && !isfinite((double)x)) bad = true;
-            if (c < k && x < Tin(0)) neg = true;
-            const T xv = (T)x;
-            const bool keep = c < k && xv > T(0) && isfinite((double)x);
-            const unsigned b = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int pos = base + __popc(b & ((1u << lane) - 1u));
-                col[r * ld + pos] = c;
-                val[r * ld + pos] = xv;
-            }
-            base += __popc(b);
-        }
-        if (lane == 0) cnt[r] = base;
-    }
-    if (bad) atomicOr(status, ST_NONFINITE);
-    if (neg) atomicOr(status, ST_BADINPUT);
-}
-
-template <typename Tin, typename T>
-cudaError_t launch_dense_to_ell(const Tin* F, int64_t rows, int k, EllDev out,
-                                unsigned* status, cudaStream_t st)
-{
-    if (rows == 0) return cudaSuccess;
-    const int B = 256;
-    int64_t grid = (rows * 32 + B - 1) / B;
-    if (grid > 65535) grid = 65535;
-    dense_to_ell_kernel<Tin, T><<<(unsigned)grid, B, 0, st>>>(
-        F, rows, k, out.ld, out.cnt, out.col, static_cast<T*>(out.val), status);
+    cholesky_kernel<T><<<1, threads, smem, st>>>(G, k, Ginv64, GinvT, status, w_smem);
     return cudaGetLastError();
 }
 
@@ -642,33 +720,39 @@ cudaError_t launch_ell_to_colmajor(int64_t rows, int k, EllDev F, T* Xt,
     return cudaGetLastError();
 }
 
-template <typename T>
-__global__ void dense_to_colmajor_kernel(const T* __restrict__ X, int64_t rows,
+template <typename Tin, typename T>
+__global__ void dense_to_colmajor_kernel(const Tin* __restrict__ X, int64_t rows,
                                          int k, int64_t ld, T* Xt,
-                                         int64_t ldx, unsigned* status)
+                                         int64_t ldx, unsigned* status,
+                                         bool reject_negative)
 {
-    bool bad = false;
+    bool bad = false, neg = false;
     const int64_t total = rows * k;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / k;
         const int c = (int)(e - r * k);
-        const T x = X[r * ld + c];
+        const Tin x = X[r * ld + c];
         if (!isfinite((double)x)) bad = true;
-        Xt[(int64_t)c * ldx + r] = x > T(0) ? x : T(0);
+        if (x < Tin(0)) neg = true;
+        const T v = (T)x;
+        Xt[(int64_t)c * ldx + r] = v > T(0) ? v : T(0);
     }
     if (bad) atomicOr(status, ST_NONFINITE);
+    if (neg && reject_negative) atomicOr(status, ST_BADINPUT);
 }
 
-template <typename T>
-cudaError_t launch_dense_to_colmajor(const T* X, int64_t rows, int k,
+template <typename Tin, typename T>
+cudaError_t launch_dense_to_colmajor(const Tin* X, int64_t rows, int k,
                                      int64_t ld, T* Xt, int64_t ldx,
-                                     unsigned* status, cudaStream_t st)
+                                     unsigned* status, bool reject_negative,
+                                     cudaStream_t st)
 {
     if (rows == 0) return cudaSuccess;
     int64_t grid = (rows * k + 255) / 256;
     if (grid > 65535) grid = 65535;
-    dense_to_colmajor_kernel<T><<<(unsigned)grid, 256, 0, st>>>(X, rows, k, ld, Xt, ldx, status);
+    dense_to_colmajor_kernel<Tin, T><<<(unsigned)grid, 256, 0, st>>>(X, rows, k, ld, Xt, ldx,
+                                                                      status, reject_negative);
     return cudaGetLastError();
 }
 
@@ -704,9 +788,9 @@ cudaError_t launch_ell_to_dense(int64_t rows, int k, EllDev F, T* X,
 cudaError_t setup_factor()
 {
     cudaError_t e;
-    e = cudaFuncSetAttribute(finalize_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    e = cudaFuncSetAttribute(emit_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(finalize_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    e = cudaFuncSetAttribute(emit_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(cholesky_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     if (e != cudaSuccess) return e;
@@ -714,8 +798,9 @@ cudaError_t setup_factor()
 }
 
 #define ESPNMF_INST(T)                                                                         \
-    template cudaError_t launch_finalize<T>(int64_t, int, EllDev, EllDev, bool, bool, const T*, \
-                                            int64_t, double*, double*, int, cudaStream_t);     \
+    template cudaError_t launch_emit<T>(const T*, int64_t, int64_t, int, int, const void*,       \
+                                        const uint32_t*, EllDev, EllDev, bool, const T*,       \
+                                        int64_t, double*, double*, int, cudaStream_t);          \
     template cudaError_t launch_cholesky<T>(const double*, int, double*, T*, unsigned*,         \
                                             cudaStream_t);                                      \
     template cudaError_t launch_norm2<T>(const T*, int64_t, double*, int, double*, cudaStream_t); \
@@ -723,16 +808,14 @@ cudaError_t setup_factor()
                                            int, double*, cudaStream_t);                         \
     template cudaError_t launch_ell_to_colmajor<T>(int64_t, int, EllDev, T*, int64_t,          \
                                                    cudaStream_t);                               \
-    template cudaError_t launch_dense_to_colmajor<T>(const T*, int64_t, int, int64_t, T*,      \
-                                                     int64_t, unsigned*, cudaStream_t);         \
     template cudaError_t launch_ell_to_dense<T>(int64_t, int, EllDev, T*, int64_t, cudaStream_t);
 ESPNMF_INST(float)
 ESPNMF_INST(double)
 #undef ESPNMF_INST
 
-template cudaError_t launch_dense_to_ell<double, double>(const double*, int64_t, int, EllDev, unsigned*, cudaStream_t);
-template cudaError_t launch_dense_to_ell<double, float>(const double*, int64_t, int, EllDev, unsigned*, cudaStream_t);
-template cudaError_t launch_dense_to_ell<float, double>(const float*, int64_t, int, EllDev, unsigned*, cudaStream_t);
-template cudaError_t launch_dense_to_ell<float, float>(const float*, int64_t, int, EllDev, unsigned*, cudaStream_t);
+template cudaError_t launch_dense_to_colmajor<double, double>(const double*, int64_t, int, int64_t, double*, int64_t, unsigned*, bool, cudaStream_t);
+template cudaError_t launch_dense_to_colmajor<double, float>(const double*, int64_t, int, int64_t, float*, int64_t, unsigned*, bool, cudaStream_t);
+template cudaError_t launch_dense_to_colmajor<float, double>(const float*, int64_t, int, int64_t, double*, int64_t, unsigned*, bool, cudaStream_t);
+template cudaError_t launch_dense_to_colmajor<float, float>(const float*, int64_t, int, int64_t, float*, int64_t, unsigned*, bool, cudaStream_t);
 
 }  // namespace espnmf

@@ -1,23 +1,29 @@
-// k_select.cu -- the enforcement step of Alg. 2 (steps 2 and 4): keep only
-// the t largest positive entries of every column (Sec. 4) or of the whole
-// factor (Alg. 2 as printed), ties to the lower index.
+// k_select.cu -- the enforcement step of Alg. 2 (steps 2 and 4): find, per
+// column (Sec. 4) or over the whole factor (Alg. 2 as printed), the value of
+// the t-th largest positive entry, with ties to the lower index.  The
+// survivors are written afterwards, row by row and in column order, by the
+// emit kernel (or, for a caller's dense buffer, by apply_thresholds).
 //
-// Input is the projected candidate X in column-major order (Xt[c*ldx+i],
-// rows i < rows, every entry >= +0).  For non-negative IEEE numbers the bit pattern read
-// as an unsigned integer orders exactly like the value, so the t-th largest
-// value is found by an MSB-first radix select over the bit patterns: 8 bits
-// per round, 4 rounds for FP32 and 8 for FP64.
-//
+// Input: the projected candidate X in column-major order (Xt[c*ldx+i],
+// rows i < rows, every entry >= +0).  For non-negative IEEE numbers the bit
+// pattern read as an unsigned integer orders exactly like the value, so the
+// threshold is found by radix selection on the bit patterns:
+//   pass 1  an 11-bit histogram of the top bits (FP32: exponent and the
+//           first 3 mantissa bits, 8 buckets per binade; FP64: exponent),
+//   pass 2  the entries of the bucket holding the t-th largest value are
+//           copied to a candidate list in shared memory,
+//   then    the remaining bits are resolved by radix rounds over the
+//           candidates only, and ties by a radix select over their indices.
 // One thread-block cluster (up to 8 CTAs) owns a column (or the whole
-// matrix).  Each CTA owns a contiguous slice of it, kept in shared memory
-// when it fits, and builds a 256-bin histogram per round with warp-
-// aggregated shared-memory atomics; the cluster adds its CTAs' histograms
-// through distributed shared memory, and every CTA then picks the same
-// digit.  When more entries equal the threshold than may be kept, a second
-// radix select over their indices finds the cut-off index, so exactly
-// min(t, #positive) entries survive.  Survivors are appended to their row of
-// the row-packed factor (row counter atomics; pair order inside a row is
-// irrelevant to every consumer).
+// matrix); each CTA keeps its slice of the data in shared memory when it
+// fits, and the CTAs add their histograms through distributed shared memory.
+// If any CTA's candidates overflow its list, the cluster resolves the bucket
+// with passes over the data instead (same result, slower).
+//
+// Output per segment s (column, or 0 in matrix mode): tau[s] (bit pattern)
+// and cut[s]: an entry survives iff it is positive and its bits are > tau,
+// or == tau and its index (row, or row-major i*k+c in matrix mode) is
+// <= cut.  tau = 0 keeps every positive entry; tau = all ones keeps none.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -27,130 +33,123 @@ namespace cg = cooperative_groups;
 namespace espnmf {
 
 constexpr int kSelThreads = 512;
-constexpr int kSelWarps = kSelThreads / 32;
-constexpr size_t kSelFixedSmem = (size_t)(kSelWarps * 256 + 2 * 256 + 256) * 4 + 64;
-constexpr size_t kSelSmemMax = 200 * 1024;
 
-template <typename T> struct Bits;
-template <> struct Bits<float> {
-    using K = uint32_t;
-    static constexpr int nbits = 32;
-    __device__ static K of(float x) { return __float_as_uint(x); }
-};
-template <> struct Bits<double> {
-    using K = unsigned long long;
-    static constexpr int nbits = 64;
-    __device__ static K of(double x) { return (K)__double_as_longlong(x); }
-};
+template <typename T> struct Vec4Of;
+template <> struct Vec4Of<float> { using type = float4; };
+struct alignas(16) Double4x { double2 a, b; };
+template <> struct Vec4Of<double> { using type = Double4x; };
+constexpr int kHist = 2048;
+constexpr int kCandCap = 6144;   // candidates per CTA
+constexpr size_t kSelSmemMax = 210 * 1024;
 
-struct SelShared {
-    unsigned* whist;   // [kSelWarps][256]
-    unsigned* bhist;   // [2][256], read by the other CTAs of the cluster
-    unsigned* hsum;    // [256] cluster totals
-    unsigned long long* bcast;  // [4] results of the digit scan
+template <typename T>
+struct SelSmem {
+    using K = typename KeyBits<T>::K;
+    static constexpr size_t hist = 0;
+    static constexpr size_t misc = hist + kHist * 4;   // 512 B of scan scratch
+    static constexpr size_t ckey = misc + 512;
+    static constexpr size_t cidx = ckey + (size_t)kCandCap * sizeof(K);
+    static constexpr size_t data = (cidx + (size_t)kCandCap * 4 + 15) & ~(size_t)15;
 };
 
-// All 32 lanes call this with the same trip count.
-__device__ __forceinline__ void hist_add(unsigned* wh, unsigned digit, bool valid)
+struct ScanOut {
+    int bin;
+    unsigned long long before;   // count in the bins scanned before `bin`
+    unsigned long long total;
+};
+
+// Adds the cluster's histograms (first nb bins, 4 per thread) and finds the
+// bin where the running count -- from the top when `descending` -- reaches
+// `need`.  Every CTA computes the same result.
+__device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int nb,
+                                unsigned long long need, bool descending,
+                                unsigned long long* wsum, unsigned long long* res)
 {
-    const unsigned key = valid ? digit : 0x100u;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int lane = threadIdx.x & 31;
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(&wh[digit], (unsigned)__popc(peers));
-}
-
-// Sums the warp histograms into bhist[buf], adds the cluster's CTAs into
-// hsum.  Ends with hsum visible to the whole CTA.
-__device__ void cluster_hist_total(cg::cluster_group& cluster, SelShared& S, int buf)
-{
-    __syncthreads();
-    for (int b = threadIdx.x; b < 256; b += blockDim.x) {
-        unsigned s = 0;
-        for (int w = 0; w < kSelWarps; ++w) s += S.whist[w * 256 + b];
-        S.bhist[buf * 256 + b] = s;
-    }
-    cluster.sync();
+    cluster.sync();   // every CTA's histogram is complete
     const int C = (int)cluster.num_blocks();
-    for (int b = threadIdx.x; b < 256; b += blockDim.x) {
-        unsigned s = 0;
-        for (int r = 0; r < C; ++r) {
-            const unsigned* rem = cluster.map_shared_rank(S.bhist + buf * 256, r);
-            s += rem[b];
+    const int tid = threadIdx.x;
+    unsigned long long v[4] = {0, 0, 0, 0};
+    for (int u = 0; u < 4; ++u) {
+        const int o = tid * 4 + u;
+        if (o < nb) {
+            const int b = descending ? nb - 1 - o : o;
+            for (int r = 0; r < C; ++r) v[u] += cluster.map_shared_rank(hist, r)[b];
         }
-        S.hsum[b] = s;
     }
-    for (int e = threadIdx.x; e < kSelWarps * 256; e += blockDim.x) S.whist[e] = 0;
+    cluster.sync();   // remote reads done: histograms may be reused
+    const unsigned long long local = v[0] + v[1] + v[2] + v[3];
+    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    unsigned long long incl = local;
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long x = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += x;
+    }
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-}
-
-// Finds, walking the bins from the top (descending) or the bottom, the bin
-// where the running count reaches `need`.  Writes bcast[0] = bin,
-// bcast[1] = count before that bin, bcast[2] = total of all bins.
-__device__ void scan_bins(SelShared& S, unsigned long long need, bool descending)
-{
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        unsigned long long local = 0;
-        for (int j = 0; j < 8; ++j) {
-            const int o = lane * 8 + j;
-            const int b = descending ? 255 - o : o;
-            local += S.hsum[b];
-        }
-        unsigned long long incl = local;
+    if (warp == 0) {
+        unsigned long long w = lane < nw ? wsum[lane] : 0;
         for (int off = 1; off < 32; off <<= 1) {
-            unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += v;
+            const unsigned long long x = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += x;
         }
-        const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
-        const unsigned hit = __ballot_sync(0xffffffffu, incl >= need);
-        if (lane == 0) S.bcast[2] = total;
-        if (hit != 0 && lane == __ffs(hit) - 1) {
-            unsigned long long cum = incl - local;
-            for (int j = 0; j < 8; ++j) {
-                const int o = lane * 8 + j;
-                const int b = descending ? 255 - o : o;
-                if (cum + S.hsum[b] >= need) {
-                    S.bcast[0] = (unsigned long long)b;
-                    S.bcast[1] = cum;
-                    break;
-                }
-                cum += S.hsum[b];
+        if (lane < nw) wsum[lane] = w;
+    }
+    if (tid == 0) {
+        res[0] = ~0ull;
+        res[1] = 0;
+    }
+    __syncthreads();
+    const unsigned long long start = (warp > 0 ? wsum[warp - 1] : 0) + incl - local;
+    const unsigned long long total = wsum[nw - 1];
+    if (start < need && start + local >= need) {
+        unsigned long long cum = start;
+        for (int u = 0; u < 4; ++u) {
+            if (cum + v[u] >= need) {
+                const int o = tid * 4 + u;
+                res[0] = (unsigned long long)(descending ? nb - 1 - o : o);
+                res[1] = cum;
+                break;
             }
+            cum += v[u];
         }
     }
     __syncthreads();
+    ScanOut r;
+    r.bin = (int)res[0];
+    r.before = res[1];
+    r.total = total;
+    __syncthreads();
+    return r;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kSelThreads)
 select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
-              int64_t t, int mode, int32_t* __restrict__ cnt,
-              int32_t* __restrict__ colo, T* __restrict__ valo,
-              int64_t cache_elems, unsigned* status, int ld)
+              int64_t t, int mode, typename KeyBits<T>::K* __restrict__ tau_out,
+              uint32_t* __restrict__ cut_out, int64_t cache_elems)
 {
-    using K = typename Bits<T>::K;
-    constexpr int NB = Bits<T>::nbits;
+    using K = typename KeyBits<T>::K;
+    constexpr int TS = KeyBits<T>::top_shift;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SelShared S;
-    S.whist = reinterpret_cast<unsigned*>(smem_raw);
-    S.bhist = S.whist + kSelWarps * 256;
-    S.hsum = S.bhist + 2 * 256;
-    S.bcast = reinterpret_cast<unsigned long long*>(S.hsum + 256);
-    T* cache = reinterpret_cast<T*>(smem_raw + kSelFixedSmem);
+    unsigned* hist = reinterpret_cast<unsigned*>(smem_raw + SelSmem<T>::hist);
+    unsigned long long* wsum = reinterpret_cast<unsigned long long*>(smem_raw + SelSmem<T>::misc);
+    unsigned long long* res = wsum + 32;
+    unsigned* ccount = reinterpret_cast<unsigned*>(res + 2);
+    K* ckey = reinterpret_cast<K*>(smem_raw + SelSmem<T>::ckey);
+    uint32_t* cidx = reinterpret_cast<uint32_t*>(smem_raw + SelSmem<T>::cidx);
+    T* cache = reinterpret_cast<T*>(smem_raw + SelSmem<T>::data);
 
     const int C = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
     const int seg = blockIdx.y;
     const bool matrix = mode == TOPT_MATRIX;
-    // Segment positions g in [0, seg_len): column mode g = row of column
-    // `seg`; matrix mode g = c * rows + i over all columns.
     const int64_t seg_len = matrix ? (int64_t)k * rows : rows;
     int64_t per = (seg_len + C - 1) / C;
     per = (per + 3) & ~(int64_t)3;
     const int64_t lo = (int64_t)crank * per < seg_len ? (int64_t)crank * per : seg_len;
     const int64_t hi = lo + per < seg_len ? lo + per : seg_len;
-    const int64_t nloc = hi - lo;
+    const int nloc = (int)(hi - lo);
     const bool cached = nloc <= cache_elems;
     const int tid = threadIdx.x;
     auto addr = [&](int64_t g) -> int64_t {
@@ -158,120 +157,169 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
         const int64_t c = g / rows;
         return c * ldx + (g - c * rows);
     };
-
-    for (int e = tid; e < kSelWarps * 256; e += blockDim.x) S.whist[e] = 0;
-    if (cached)
-        for (int64_t e = tid; e < nloc; e += blockDim.x) cache[e] = Xt[addr(lo + e)];
-    __syncthreads();
-
-    auto value = [&](int64_t e) -> T { return cached ? cache[e] : Xt[addr(lo + e)]; };
-    // index used for ties: the row (column mode) or the row-major i*k+c
-    auto tie_index = [&](int64_t e) -> uint32_t {
+    auto index_of = [&](int e) -> uint32_t {
         const int64_t g = lo + e;
         if (!matrix) return (uint32_t)g;
         const int64_t c = g / rows, i = g - c * rows;
         return (uint32_t)(i * k + c);
     };
-    unsigned* wh = S.whist + (tid >> 5) * 256;
-    const int64_t trip = (nloc + blockDim.x - 1) / blockDim.x * blockDim.x;
 
-    K tau = 0;                      // keep key > tau, or key == tau and index <= cut
-    uint32_t cut = 0xffffffffu;
-    bool keep_none = t <= 0 && mode != TOPT_NONE;
-    int buf = 0;
-
-    if (!keep_none && mode != TOPT_NONE) {
-        // Round 0 also counts the positive entries.
-        unsigned long long need = (unsigned long long)t;
-        K prefix = 0;
-        bool all = false;
-        unsigned long long last_bin_count = 0;
-        for (int shift = NB - 8; shift >= 0; shift -= 8) {
-            for (int64_t e0 = 0; e0 < trip; e0 += blockDim.x) {
-                const int64_t e = e0 + tid;
-                bool ok = false;
-                unsigned d = 0;
-                if (e < nloc) {
-                    const K key = Bits<T>::of(value(e));
-                    const bool match = shift == NB - 8 ? true : ((key ^ prefix) >> (shift + 8)) == 0;
-                    ok = key != 0 && match;
-                    d = (unsigned)(key >> shift) & 255u;
-                }
-                hist_add(wh, d, ok);
-            }
-            cluster_hist_total(cluster, S, buf);
-            buf ^= 1;
-            if (shift == NB - 8) {
-                unsigned long long tot = 0;
-                for (int b = 0; b < 256; ++b) tot += S.hsum[b];
-                if (tot <= need) { all = true; break; }
-            }
-            scan_bins(S, need, true);
-            const unsigned long long bin = S.bcast[0];
-            const unsigned long long before = S.bcast[1];
-            last_bin_count = S.hsum[bin];
-            need -= before;
-            prefix |= (K)bin << shift;
-            __syncthreads();
+    // t = 0 keeps nothing; mode NONE keeps every positive entry
+    if (mode == TOPT_NONE || t <= 0) {
+        if (crank == 0 && tid == 0) {
+            tau_out[seg] = mode == TOPT_NONE ? (K)0 : ~(K)0;
+            cut_out[seg] = 0xffffffffu;
         }
-        if (!all) {
-            tau = prefix;
-            if (need < last_bin_count) {
-                // more entries equal tau than may be kept: keep the `need`
-                // smallest indices among them
-                uint32_t ipre = 0;
-                for (int shift = 24; shift >= 0; shift -= 8) {
-                    for (int64_t e0 = 0; e0 < trip; e0 += blockDim.x) {
-                        const int64_t e = e0 + tid;
-                        bool ok = false;
-                        unsigned d = 0;
-                        if (e < nloc && Bits<T>::of(value(e)) == tau) {
-                            const uint32_t ix = tie_index(e);
-                            ok = shift == 24 ? true : ((ix ^ ipre) >> (shift + 8)) == 0;
-                            d = (ix >> shift) & 255u;
-                        }
-                        hist_add(wh, d, ok);
-                    }
-                    cluster_hist_total(cluster, S, buf);
-                    buf ^= 1;
-                    scan_bins(S, need, false);
-                    const unsigned long long bin = S.bcast[0];
-                    need -= S.bcast[1];
-                    ipre |= (uint32_t)bin << shift;
-                    __syncthreads();
-                }
-                cut = ipre;
+        return;
+    }
+    if (cached) {
+        if (!matrix) {
+            // contiguous, 16-byte aligned slice (lo and ldx are multiples of
+            // 4): 128-bit loads, four in flight per thread
+            const T* src = Xt + (int64_t)seg * ldx + lo;
+            const int nv = nloc / 4;
+            using V4 = typename Vec4Of<T>::type;
+            const V4* s4 = reinterpret_cast<const V4*>(src);
+            V4* d4 = reinterpret_cast<V4*>(cache);
+            int q = tid;
+            for (; q + 3 * (int)blockDim.x < nv; q += 4 * blockDim.x) {
+                const V4 a0 = s4[q], a1 = s4[q + blockDim.x], a2 = s4[q + 2 * blockDim.x],
+                         a3 = s4[q + 3 * blockDim.x];
+                d4[q] = a0;
+                d4[q + blockDim.x] = a1;
+                d4[q + 2 * blockDim.x] = a2;
+                d4[q + 3 * blockDim.x] = a3;
+            }
+            for (; q < nv; q += blockDim.x) d4[q] = s4[q];
+            for (int e = nv * 4 + tid; e < nloc; e += blockDim.x) cache[e] = src[e];
+        } else {
+            for (int e = tid; e < nloc; e += blockDim.x) cache[e] = Xt[addr(lo + e)];
+        }
+    }
+    auto key_at = [&](int e) -> K { return KeyBits<T>::of(cached ? cache[e] : Xt[addr(lo + e)]); };
+
+    // ---- pass 1: histogram of the top 11 bits of the positive entries
+    for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (int e = tid; e < nloc; e += blockDim.x) {
+        const K key = key_at(e);
+        if (key != 0) atomicAdd(&hist[(unsigned)(key >> TS) & (kHist - 1)], 1u);
+    }
+    __syncthreads();
+    unsigned long long need = (unsigned long long)t;
+    const ScanOut s1 = cluster_scan(cluster, hist, kHist, need, true, wsum, res);
+    if (s1.total <= need) {   // at most t positive entries: keep them all
+        if (crank == 0 && tid == 0) {
+            tau_out[seg] = 0;
+            cut_out[seg] = 0xffffffffu;
+        }
+        return;
+    }
+    need -= s1.before;
+    K prefix = (K)s1.bin << TS;
+    int shift = TS;   // bits below `shift` are still open
+
+    // ---- pass 2: the bucket's entries into the candidate list
+    if (tid == 0) *ccount = 0;
+    __syncthreads();
+    for (int e = tid; e < nloc; e += blockDim.x) {
+        const K key = key_at(e);
+        if (key != 0 && (key >> shift) == (prefix >> shift)) {
+            const unsigned pos = atomicAdd(ccount, 1u);
+            if (pos < (unsigned)kCandCap) {
+                ckey[pos] = key;
+                cidx[pos] = index_of(e);
             }
         }
     }
-    // the last totals read other CTAs' shared memory: no CTA may leave
-    // before every CTA is done with them
-    cluster.sync();
-    if (keep_none) return;
+    __syncthreads();
+    const unsigned ncand = *ccount;
+    __syncthreads();
+    if (tid == 0) hist[0] = ncand > (unsigned)kCandCap ? 1u : 0u;
+    __syncthreads();
+    const ScanOut ov = cluster_scan(cluster, hist, 1, 1, false, wsum, res);
+    const bool use_list = ov.total == 0;   // no CTA overflowed
+    const int nc = use_list ? (int)ncand : 0;
 
-    for (int64_t e = tid; e < nloc; e += blockDim.x) {
-        const T x = value(e);
-        const K key = Bits<T>::of(x);
-        if (key == 0) continue;
-        if (key < tau) continue;
-        if (key == tau && tau != 0 && tie_index(e) > cut) continue;
-        const int64_t g = lo + e;
-        const int64_t c = matrix ? g / rows : (int64_t)seg;
-        const int64_t i = matrix ? g - c * rows : g;
-        const int pos = atomicAdd(&cnt[i], 1);
-        if (pos >= k) {
-            atomicOr(status, ST_OVERFLOW);
-            continue;
+    // ---- the remaining bits: radix rounds of up to 11 bits
+    while (shift > 0) {
+        const int bits = shift >= 11 ? 11 : shift;
+        const int sh = shift - bits;
+        const unsigned mask = (1u << bits) - 1u;
+        for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        if (use_list) {
+            for (int q = tid; q < nc; q += blockDim.x) {
+                const K key = ckey[q];
+                if ((key >> shift) == (prefix >> shift)) atomicAdd(&hist[(unsigned)(key >> sh) & mask], 1u);
+            }
+        } else {
+            for (int e = tid; e < nloc; e += blockDim.x) {
+                const K key = key_at(e);
+                if (key != 0 && (key >> shift) == (prefix >> shift))
+                    atomicAdd(&hist[(unsigned)(key >> sh) & mask], 1u);
+            }
         }
-        colo[i * ld + pos] = (int32_t)c;
-        valo[i * ld + pos] = x;
+        __syncthreads();
+        const ScanOut sr = cluster_scan(cluster, hist, 1 << bits, need, true, wsum, res);
+        need -= sr.before;
+        prefix |= (K)sr.bin << sh;
+        shift = sh;
+    }
+    const K tau = prefix;
+    // how many entries equal tau (at least `need` of them)
+    for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    {
+        unsigned cnt = 0;
+        if (use_list) {
+            for (int q = tid; q < nc; q += blockDim.x) cnt += ckey[q] == tau;
+        } else {
+            for (int e = tid; e < nloc; e += blockDim.x) cnt += key_at(e) == tau;
+        }
+        if (cnt) atomicAdd(&hist[0], cnt);
+    }
+    __syncthreads();
+    const ScanOut se = cluster_scan(cluster, hist, 1, 1, false, wsum, res);
+    uint32_t cut = 0xffffffffu;
+    if (need < se.total) {
+        // keep the `need` smallest indices among the ties: radix select on
+        // the index, ascending, 11 bits at a time
+        uint32_t ipre = 0;
+        int ish = 32;
+        while (ish > 0) {
+            const int bits = ish >= 11 ? 11 : ish;
+            const int sh = ish - bits;
+            const unsigned mask = (1u << bits) - 1u;
+            for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
+            __syncthreads();
+            auto consider = [&](K key, uint32_t ix) {
+                if (key == tau && (ish >= 32 || (ix >> ish) == (ipre >> ish)))
+                    atomicAdd(&hist[(ix >> sh) & mask], 1u);
+            };
+            if (use_list) {
+                for (int q = tid; q < nc; q += blockDim.x) consider(ckey[q], cidx[q]);
+            } else {
+                for (int e = tid; e < nloc; e += blockDim.x) consider(key_at(e), index_of(e));
+            }
+            __syncthreads();
+            const ScanOut si = cluster_scan(cluster, hist, 1 << bits, need, false, wsum, res);
+            need -= si.before;
+            ipre |= (uint32_t)si.bin << sh;
+            ish = sh;
+        }
+        cut = ipre;
+    }
+    if (crank == 0 && tid == 0) {
+        tau_out[seg] = tau;
+        cut_out[seg] = cut;
     }
 }
 
 template <typename T>
 cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
-                          int64_t t, int mode, EllDev out, unsigned* status,
-                          cudaStream_t st, int sm_count, int64_t* smem_need_out)
+                          int64_t t, int mode, void* tau, uint32_t* cut,
+                          cudaStream_t st, int sm_count)
 {
     if (rows == 0) return cudaSuccess;
     const int nseg = mode == TOPT_MATRIX ? 1 : k;
@@ -281,15 +329,15 @@ cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
     const int64_t seg_len = mode == TOPT_MATRIX ? (int64_t)k * rows : rows;
     int64_t per = (seg_len + C - 1) / C;
     per = (per + 3) & ~(int64_t)3;
-    int64_t cache_elems = (int64_t)((kSelSmemMax - kSelFixedSmem) / sizeof(T));
-    size_t smem = kSelFixedSmem;
+    const size_t fixed = SelSmem<T>::data;
+    int64_t cache_elems = (int64_t)((kSelSmemMax - fixed) / sizeof(T));
+    size_t smem = fixed;
     if (per <= cache_elems) {
         smem += (size_t)per * sizeof(T);
         cache_elems = per;
     } else {
         cache_elems = 0;
     }
-    if (smem_need_out) *smem_need_out = (int64_t)smem;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)C, (unsigned)nseg, 1);
     cfg.blockDim = dim3(kSelThreads, 1, 1);
@@ -302,9 +350,46 @@ cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    using K = typename KeyBits<T>::K;
     return cudaLaunchKernelEx(&cfg, select_kernel<T>, Xt, ldx, rows, k, t, mode,
-                              out.cnt, out.col, static_cast<T*>(out.val),
-                              cache_elems, status, out.ld);
+                              static_cast<K*>(tau), cut, cache_elems);
+}
+
+// In-place projection + enforcement of a caller's dense rows x k buffer
+// (leading dimension ld) with thresholds from select_kernel.
+template <typename T>
+__global__ void apply_thresholds_kernel(T* X, int64_t rows, int k, int64_t ld, int mode,
+                                        const typename KeyBits<T>::K* __restrict__ tau,
+                                        const uint32_t* __restrict__ cut, unsigned* status)
+{
+    bool bad = false;
+    const int64_t total = rows * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / k;
+        const int c = (int)(e - r * k);
+        const T x = X[r * ld + c];
+        if (!isfinite((double)x)) bad = true;
+        const T v = x > T(0) ? x : T(0);
+        const int s = mode == TOPT_MATRIX ? 0 : c;
+        const uint32_t ix = mode == TOPT_MATRIX ? (uint32_t)(r * k + c) : (uint32_t)r;
+        X[r * ld + c] = keep_entry<T>(v, tau[s], cut[s], ix) ? v : T(0);
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+template <typename T>
+cudaError_t launch_apply_thresholds(T* X, int64_t rows, int k, int64_t ld, int mode,
+                                    const void* tau, const uint32_t* cut, unsigned* status,
+                                    cudaStream_t st)
+{
+    if (rows == 0) return cudaSuccess;
+    int64_t grid = (rows * k + 255) / 256;
+    if (grid > 65535) grid = 65535;
+    using K = typename KeyBits<T>::K;
+    apply_thresholds_kernel<T><<<(unsigned)grid, 256, 0, st>>>(
+        X, rows, k, ld, mode, static_cast<const K*>(tau), cut, status);
+    return cudaGetLastError();
 }
 
 cudaError_t setup_select()
@@ -318,7 +403,9 @@ cudaError_t setup_select()
                                 (int)kSelSmemMax);
 }
 
-template cudaError_t launch_select<float>(const float*, int64_t, int64_t, int, int64_t, int, EllDev, unsigned*, cudaStream_t, int, int64_t*);
-template cudaError_t launch_select<double>(const double*, int64_t, int64_t, int, int64_t, int, EllDev, unsigned*, cudaStream_t, int, int64_t*);
+template cudaError_t launch_select<float>(const float*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int);
+template cudaError_t launch_select<double>(const double*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int);
+template cudaError_t launch_apply_thresholds<float>(float*, int64_t, int, int64_t, int, const void*, const uint32_t*, unsigned*, cudaStream_t);
+template cudaError_t launch_apply_thresholds<double>(double*, int64_t, int, int64_t, int, const void*, const uint32_t*, unsigned*, cudaStream_t);
 
 }  // namespace espnmf
