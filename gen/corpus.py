@@ -48,6 +48,20 @@ class Corpus:
         v = self.val.astype(dtype).astype(np.float64)
         return dataclasses.replace(self, val=v)
 
+    def first_docs(self, m2: int) -> "Corpus":
+        """The sub-corpus of documents 0..m2-1 (all terms kept)."""
+        m2 = max(1, min(int(m2), self.m))
+        keep = self.colidx < m2
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        counts = np.bincount(rows[keep], minlength=self.n)
+        rowptr = np.zeros(self.n + 1, dtype=np.int64)
+        np.cumsum(counts, out=rowptr[1:])
+        labels = None if self.labels is None else self.labels[:m2].copy()
+        return dataclasses.replace(self, m=m2, rowptr=rowptr,
+                                   colidx=self.colidx[keep].copy(),
+                                   val=self.val[keep].copy(),
+                                   name=f"{self.name}[:{m2} docs]", labels=labels)
+
 
 def _zipf_cdf(n: int, s: float) -> np.ndarray:
     w = 1.0 / np.arange(1, n + 1, dtype=np.float64) ** s

@@ -51,8 +51,8 @@ typedef enum {
 /* Arithmetic of a context (or the element type of a buffer).
  * ESPNMF_F64: everything in FP64 (the plain form).
  * ESPNMF_F32: A's values, the factors, the sparse products and the k x k
- *   solve applied to each row in FP32; the Gram matrices, their Cholesky
- *   factorisation and inverse, and the residual/error reductions in FP64. */
+ *   solve applied to each row in FP32; the Gram matrices, their inverses
+ *   and the residual/error reductions in FP64. */
 typedef enum { ESPNMF_F64 = 0, ESPNMF_F32 = 1, ESPNMF_BF16 = 2 } espnmf_dtype;
 
 /* Enforcement step of Alg. 2 (steps 2 and 4).
@@ -116,7 +116,7 @@ typedef struct espnmf_ctx espnmf_ctx;
  *            the context create its own.
  * The context builds on the device: A in two sliced-ELLPACK layouts (rows
  * of A and rows of A^T), U0 in the row-packed sparse factor layout, and
- * the FP64 Gram U0^T U0 with its Cholesky factorisation. */
+ * the FP64 Gram U0^T U0. */
 espnmf_status espnmf_init(espnmf_ctx **out, const espnmf_csr *A, int32_t k,
                           int64_t t_u, int64_t t_v, espnmf_topt_mode mode,
                           espnmf_dtype compute, const void *U0,
@@ -141,7 +141,8 @@ const char *espnmf_status_string(espnmf_status st);
 /* espnmf_als_update_V -- Alg. 2 steps 1-2:
  *   V = A^T U (U^T U)^-1, negative entries set to zero, then only the t_v
  *   largest nonzeros kept (mode of the context).
- * Also forms V^T V and its Cholesky factorisation for the next U update.
+ * Also forms V^T V in FP64; its inverse is taken at the start of the next
+ * U update, beside that update's sparse product.
  * Asynchronous.  Errors found on the device (a non-finite value, a singular
  * V^T V) are reported by the next synchronising call. */
 espnmf_status espnmf_als_update_V(espnmf_ctx *ctx);
@@ -151,8 +152,8 @@ espnmf_status espnmf_als_update_V(espnmf_ctx *ctx);
  *   largest nonzeros kept.
  * Also computes, on the device and without forming U V^T, the relative
  * residual R = ||U_new - U_old||_F / ||U_new||_F and the relative error
- * E = ||A - U V^T||_F / ||A||_F (Sec. 3.1), and U^T U with its Cholesky
- * factorisation for the next V update.  Asynchronous. */
+ * E = ||A - U V^T||_F / ||A||_F (Sec. 3.1), and U^T U in FP64 for the next
+ * V update.  Asynchronous. */
 espnmf_status espnmf_als_update_U(espnmf_ctx *ctx);
 
 /* espnmf_iterate -- `iters` sweeps of Alg. 2 (each: update_V then
@@ -196,6 +197,42 @@ espnmf_status espnmf_residual(espnmf_ctx *ctx, double *R);
 espnmf_status espnmf_error(espnmf_ctx *ctx, double *E);
 
 /* ------------------------------------------------------------------------ */
+/* Squared objective, its gradient, projected-gradient polish               */
+
+/* espnmf_loss -- f = ||A - U V^T||_F^2 (the squared objective of Sec. 4,
+ * Eq. 6) for the current U and V, through the same identity as
+ * espnmf_error: f = ||A||^2 - 2 <U, A V> + <U^T U, V^T V> (FP64 sums; U V^T
+ * is never formed).  Not clamped at 0, so rounding may leave it slightly
+ * negative when the factorisation is exact.  Synchronises. */
+espnmf_status espnmf_loss(espnmf_ctx *ctx, double *f);
+
+/* espnmf_grad -- the dense gradient of f with respect to one factor at the
+ * current U and V:
+ *   which = ESPNMF_U:  grad_U = 2 (U V^T V - A V)    (n x k)
+ *   which = ESPNMF_V:  grad_V = 2 (V U^T U - A^T U)  (m x k)
+ * out: row-major rows x k (leading dimension k), element type `dtype`
+ * (ESPNMF_F64 or ESPNMF_F32), device memory when on_device != 0, else host
+ * memory (the call then allocates a device staging buffer for the copy).
+ * The product F G_O runs in FP64 over F's nonzeros; A V or A^T U comes
+ * from the context's SpMM in its arithmetic.  Synchronises when out is on
+ * the host; ESPNMF_ERR_INVALID_ARG when U or V has no value. */
+espnmf_status espnmf_grad(espnmf_ctx *ctx, espnmf_which which, void *out,
+                          espnmf_dtype dtype, int32_t on_device);
+
+/* espnmf_pg_step -- one projected-gradient step on a factor's current
+ * support S (an optional polish between sweeps; the paper has no such
+ * step):  F <- P_S(F - eta grad_F f), where P_S clamps to >= 0 and keeps
+ * only the entries of S (entries that reach 0 leave the support).
+ * eta > 0 is used as given; eta <= 0 takes eta = 1 / (2 lambda_max(G_O)),
+ * G_O the other factor's Gram, lambda_max from 20 FP64 power-iteration
+ * steps from the normalised all-ones vector (eta = 0, no change, when
+ * G_O = 0).  eta_used (host, may be NULL) receives the step.  The factor's
+ * Gram is refreshed; R and E are not (espnmf_error recomputes E).
+ * Synchronises. */
+espnmf_status espnmf_pg_step(espnmf_ctx *ctx, espnmf_which which, double eta,
+                             double *eta_used);
+
+/* ------------------------------------------------------------------------ */
 /* Factors out                                                              */
 
 /* espnmf_factor_nnz -- number of nonzeros of U or V.  Synchronises. */
@@ -220,7 +257,20 @@ espnmf_status espnmf_get_factor(espnmf_ctx *ctx, espnmf_which which,
 typedef enum {
     ESPNMF_OPT_USE_GRAPH = 0,     /* 1 (default): espnmf_iterate replays a CUDA graph */
     ESPNMF_OPT_PROFILE = 1,       /* 1: time every kernel launch with CUDA events (eager launches) */
-    ESPNMF_OPT_WAIT_LIMIT = 2     /* iteration limit of bounded device waits (default 1<<26) */
+    ESPNMF_OPT_WAIT_LIMIT = 2,    /* iteration limit of bounded device waits (default 1<<26) */
+    /* Launch shape of the FP32 sparse products (results are bitwise the same
+     * for every shape):
+     *   ESPNMF_OPT_SPMM_TUNE 1 (default): before its first captured sweep,
+     *     espnmf_iterate times the candidate shapes on the current factors
+     *     and keeps the fastest for each product (A V and A^T U); 0: fixed.
+     *   ESPNMF_OPT_SPMM_GROUP: 1 gathers nearly dense factor rows with
+     *     8-lane groups (k <= 64), 0 lane by lane; sets the shape of both
+     *     products and turns tuning off.
+     *   ESPNMF_OPT_SPMM_CARVEOUT: preferred shared-memory carveout in percent
+     *     (-1: the driver's choice); also turns tuning off. */
+    ESPNMF_OPT_SPMM_TUNE = 3,
+    ESPNMF_OPT_SPMM_GROUP = 4,
+    ESPNMF_OPT_SPMM_CARVEOUT = 5
 } espnmf_option;
 
 espnmf_status espnmf_set_option(espnmf_ctx *ctx, espnmf_option opt,
@@ -292,6 +342,53 @@ espnmf_status espnmf_enforce_topt_buffer_noalloc(void *X, int64_t rows,
                                                  espnmf_dtype dtype, int64_t t,
                                                  espnmf_topt_mode mode,
                                                  void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched sweeps of independent problems                                   */
+
+/* Many independent factorisations (uneven n, m, k, t), each a full context,
+ * advanced together: espnmf_batch_iterate runs Alg. 2 sweeps of every
+ * problem, and from the second sweep on replays one captured CUDA graph per
+ * sweep that holds all problems' kernels, spread over a pool of streams so
+ * that small problems overlap.  The paper factorises one matrix at a time;
+ * batching adds no arithmetic (every problem's results are bitwise those of
+ * its own context run alone). */
+typedef struct espnmf_batch espnmf_batch;
+
+/* espnmf_batch_init -- one context per problem, as espnmf_init would make
+ * it: As[i], ks[i], t_us[i], t_vs[i] and U0s[i] (n_i x k_i row-major,
+ * U0_dtype, all on the device or all on the host) for i < nprob; mode and
+ * compute are shared.  streams: size of the stream pool (<= 0: 16).  On
+ * failure nothing is kept and espnmf_last_error(NULL) names the problem. */
+espnmf_status espnmf_batch_init(espnmf_batch **out, int32_t nprob,
+                                const espnmf_csr *As, const int32_t *ks,
+                                const int64_t *t_us, const int64_t *t_vs,
+                                espnmf_topt_mode mode, espnmf_dtype compute,
+                                const void *const *U0s, espnmf_dtype U0_dtype,
+                                int32_t U0_on_device, int32_t streams);
+
+/* espnmf_batch_destroy -- destroys every problem's context (NULL: no-op). */
+espnmf_status espnmf_batch_destroy(espnmf_batch *b);
+
+/* espnmf_batch_ctx -- the context of problem i, owned by the batch (use it
+ * for espnmf_get_factor, espnmf_error, ...; do not destroy it).  A call that
+ * changes one problem's factors (set_factor, enforce_topt, single updates)
+ * makes the next batch sweep run without the graph until the problems are
+ * back in step. */
+espnmf_status espnmf_batch_ctx(espnmf_batch *b, int32_t i, espnmf_ctx **out);
+
+/* espnmf_batch_set_option -- ESPNMF_OPT_USE_GRAPH only (1: default). */
+espnmf_status espnmf_batch_set_option(espnmf_batch *b, espnmf_option opt,
+                                      int64_t value);
+
+/* espnmf_batch_iterate -- `iters` sweeps of every problem.  status_out
+ * (nprob entries, may be NULL) receives each problem's status (a singular
+ * or non-finite problem does not stop the others); R_out and E_out (host,
+ * nprob x iters row-major, may be NULL) the per-sweep measures.  Returns the
+ * first failing problem's status, or ESPNMF_OK.  Synchronises. */
+espnmf_status espnmf_batch_iterate(espnmf_batch *b, int32_t iters,
+                                   espnmf_status *status_out, double *R_out,
+                                   double *E_out);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,7 @@ TOPT_COLUMN, TOPT_MATRIX, TOPT_NONE = 0, 1, 2
 U, V = 0, 1
 DENSE_ROWMAJOR, CSC, CSR = 0, 1, 2
 OPT_USE_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT = 0, 1, 2
+OPT_SPMM_TUNE, OPT_SPMM_GROUP, OPT_SPMM_CARVEOUT = 3, 4, 5
 
 
 class EspnmfError(RuntimeError):
@@ -84,6 +85,14 @@ def load():
             "espnmf_sync": [P],
             "espnmf_enforce_topt_buffer": [P, i64, i32, i64, st, i64, st, P],
             "espnmf_enforce_topt_buffer_noalloc": [P, i64, i32, i64, st, i64, st, P],
+            "espnmf_loss": [P, ctypes.POINTER(d)],
+            "espnmf_grad": [P, st, P, st, i32],
+            "espnmf_pg_step": [P, st, d, ctypes.POINTER(d)],
+            "espnmf_batch_init": [ctypes.POINTER(P), i32, P, P, P, P, st, st, P, st, i32, i32],
+            "espnmf_batch_destroy": [P],
+            "espnmf_batch_ctx": [P, i32, ctypes.POINTER(P)],
+            "espnmf_batch_set_option": [P, st, i64],
+            "espnmf_batch_iterate": [P, i32, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -106,7 +115,9 @@ def exported_symbols():
              "espnmf_factor_nnz", "espnmf_get_factor", "espnmf_set_option",
              "espnmf_kernel_stat_count", "espnmf_kernel_stat", "espnmf_kernel_stats_reset",
              "espnmf_launches_per_sweep", "espnmf_sync", "espnmf_enforce_topt_buffer",
-             "espnmf_enforce_topt_buffer_noalloc"]
+             "espnmf_enforce_topt_buffer_noalloc", "espnmf_loss", "espnmf_grad",
+             "espnmf_pg_step", "espnmf_batch_init", "espnmf_batch_destroy",
+             "espnmf_batch_ctx", "espnmf_batch_set_option", "espnmf_batch_iterate"]
     return {n: hasattr(lib, n) for n in names}
 
 
@@ -158,7 +169,7 @@ class Context:
 
     def __del__(self):
         try:
-            if self.handle:
+            if self.handle and getattr(self, "_owned", True):
                 load().espnmf_destroy(self.handle)
                 self.handle = None
         except Exception:
@@ -188,6 +199,8 @@ def espnmf_init(rowptr, colidx, values, n: int, m: int, k: int, t_u: int, t_v: i
 
 
 def espnmf_destroy(ctx: Context):
+    if not getattr(ctx, "_owned", True):
+        raise ValueError("a batch problem's context is destroyed with its batch")
     if ctx.handle:
         _check(load().espnmf_destroy(ctx.handle))
         ctx.handle = None
@@ -231,6 +244,46 @@ def espnmf_residual(ctx: Context) -> float:
 def espnmf_error(ctx: Context) -> float:
     e = ctypes.c_double()
     _check(load().espnmf_error(ctx.handle, ctypes.byref(e)), ctx.handle)
+    return e.value
+
+
+def espnmf_loss(ctx: Context) -> float:
+    """f = ||A - U V^T||_F^2 at the current U, V (FP64 identity on the device)."""
+    f = ctypes.c_double()
+    _check(load().espnmf_loss(ctx.handle, ctypes.byref(f)), ctx.handle)
+    return f.value
+
+
+def espnmf_grad(ctx: Context, which: int, out=None, dtype=np.float64):
+    """Dense gradient of f with respect to U (which=U) or V (which=V).
+
+    ``out`` may be a contiguous rows x k float32/float64 numpy array or torch
+    tensor (host or CUDA); by default a new numpy array of ``dtype``.  For a
+    CUDA ``out`` the call synchronises the context's stream before it returns.
+    """
+    rows = ctx.n if which == U else ctx.m
+    if out is None:
+        out = np.zeros((rows, ctx.k), dtype=dtype)
+    if tuple(out.shape) != (rows, ctx.k):
+        raise ValueError(f"out must be {rows} x {ctx.k}")
+    if _is_torch(out) and not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    p, dev, keep = _ptr(out)
+    if not _is_torch(out) and keep is not out:
+        raise ValueError("out must be a contiguous numpy array")
+    lib = load()
+    _check(lib.espnmf_grad(ctx.handle, int(which), p, _dtype_code(out), dev), ctx.handle)
+    if dev:
+        _check(lib.espnmf_sync(ctx.handle), ctx.handle)
+    return out
+
+
+def espnmf_pg_step(ctx: Context, which: int, eta: float = 0.0) -> float:
+    """One projected-gradient step on the factor's support; returns the step
+    used (eta <= 0: 1 / (2 lambda_max) of the other factor's Gram)."""
+    e = ctypes.c_double()
+    _check(load().espnmf_pg_step(ctx.handle, int(which), float(eta), ctypes.byref(e)),
+           ctx.handle)
     return e.value
 
 
@@ -323,3 +376,92 @@ def espnmf_enforce_topt_buffer_noalloc(X, t: int, mode: int = TOPT_COLUMN, strea
     _check(load().espnmf_enforce_topt_buffer_noalloc(ctypes.c_void_p(X.data_ptr()), X.shape[0],
                                                      X.shape[1], X.stride(0), _dtype_code(X),
                                                      int(t), int(mode), _stream_handle(stream)))
+
+
+# --- batched problems --------------------------------------------------------------
+
+class Batch:
+    """Owns an espnmf_batch handle (and, through it, one context per problem)."""
+
+    def __init__(self, handle, shapes, compute, keep):
+        self.handle = handle
+        self.shapes = shapes          # [(n, m, k)]
+        self.compute = compute
+        self._keep = keep
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def ctx(self, i: int) -> Context:
+        """Problem i's context (owned by the batch: not destroyed by the view)."""
+        h = ctypes.c_void_p()
+        _check(load().espnmf_batch_ctx(self.handle, int(i), ctypes.byref(h)))
+        n, m, k = self.shapes[i]
+        view = Context.__new__(Context)
+        view.handle, view.n, view.m, view.k, view.compute = h, n, m, k, self.compute
+        view._owned = False
+        view._batch = self
+        return view
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().espnmf_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def espnmf_batch_init(problems, mode: int = TOPT_COLUMN, compute: int = F32,
+                      streams: int = 0) -> Batch:
+    """problems: a list of (rowptr, colidx, values, n, m, k, t_u, t_v, U0);
+    arrays as for espnmf_init, all on the host or all on the device."""
+    count = len(problems)
+    csrs = (_CSR * count)()
+    ks = (ctypes.c_int32 * count)()
+    tus = (ctypes.c_int64 * count)()
+    tvs = (ctypes.c_int64 * count)()
+    u0s = (ctypes.c_void_p * count)()
+    keep, shapes = [], []
+    u0_dev, u0_dtype = None, None
+    for i, (rowptr, colidx, values, n, m, k, t_u, t_v, U0) in enumerate(problems):
+        rp, rdev, rk = _ptr(rowptr)
+        ci, _, ck = _ptr(colidx)
+        va, _, vk = _ptr(values)
+        up, udev, uk = _ptr(U0)
+        keep += [rk, ck, vk, uk]
+        csrs[i] = _CSR(n, m, int(len(colidx)), rp, ci, va, _dtype_code(values), rdev)
+        ks[i], tus[i], tvs[i] = k, t_u, t_v
+        u0s[i] = up
+        if u0_dev is None:
+            u0_dev, u0_dtype = udev, _dtype_code(U0)
+        elif (udev, _dtype_code(U0)) != (u0_dev, u0_dtype):
+            raise ValueError("all U0 must share one dtype and one location")
+        shapes.append((n, m, k))
+    h = ctypes.c_void_p()
+    _check(load().espnmf_batch_init(ctypes.byref(h), count, csrs, ks, tus, tvs, int(mode),
+                                    int(compute), u0s, u0_dtype, u0_dev, int(streams)))
+    return Batch(h, shapes, compute, None)
+
+
+def espnmf_batch_set_option(b: Batch, opt: int, value: int):
+    _check(load().espnmf_batch_set_option(b.handle, int(opt), int(value)))
+
+
+def espnmf_batch_iterate(b: Batch, iters: int, want_measures: bool = True):
+    """Returns (status array, R [nprob x iters] or None, E or None); raises
+    only for failures of the batch itself (per-problem failures are in the
+    status array)."""
+    count = len(b)
+    status = np.zeros(count, dtype=np.int32)
+    R = np.zeros((count, max(iters, 1))) if want_measures else None
+    E = np.zeros((count, max(iters, 1))) if want_measures else None
+    st = load().espnmf_batch_iterate(
+        b.handle, int(iters), status.ctypes.data_as(ctypes.c_void_p),
+        R.ctypes.data_as(ctypes.c_void_p) if want_measures else None,
+        E.ctypes.data_as(ctypes.c_void_p) if want_measures else None)
+    if st != OK and not status.any():
+        _check(st)
+    if want_measures:
+        R, E = R[:, :iters], E[:, :iters]
+    return status, R, E

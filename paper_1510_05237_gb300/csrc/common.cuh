@@ -14,7 +14,7 @@ namespace espnmf {
 // Bits of the device status word every kernel may raise (atomicOr).
 enum : unsigned {
     ST_NONFINITE = 1u,   // a NaN/Inf met in an iterate
-    ST_SINGULAR = 2u,    // Cholesky pivot below the singularity threshold
+    ST_SINGULAR = 2u,    // Gram pivot (LDL^T d_j) below the singularity threshold
     ST_TIMEOUT = 4u,     // a bounded wait gave up
     ST_BADINPUT = 8u,    // negative entry in a factor given by the caller
     ST_OVERFLOW = 16u,   // a factor row received more than k entries (internal)
@@ -92,10 +92,21 @@ struct EllDev {
     int32_t* cnt = nullptr;
     int32_t* col = nullptr;
     void* val = nullptr;
-    void* dense = nullptr;
+    void* dense = nullptr;   // dense copies of heavy rows, row stride dld
+    uint4* rec = nullptr;    // FP32 factors: per-row record, see row_record
     int ld = 0;
+    int dld = 0;
     int heavy = 1 << 30;
 };
+
+// Per-row record of an FP32 factor (16 bytes, one load): x = cnt | c0 << 8 |
+// c1 << 16 | c2 << 24, y/z/w = the bits of the first three values (columns
+// c0 < c1 < c2).  A light row of up to three nonzeros is complete in it.
+__host__ __device__ inline int record_cnt(unsigned x) { return (int)(x & 0xffu); }
+
+// Row stride of the dense heavy-row copies: 32 or 64 floats (whole 128-byte
+// lines) up to k = 64, else the factor stride.
+inline __host__ __device__ int dense_ld(int ld) { return ld <= 32 ? 32 : (ld <= 64 ? 64 : ld); }
 
 // Row stride of factors, Y and the dense heavy rows: k rounded up to 4
 // (k <= 64) or to 16.
@@ -107,9 +118,17 @@ inline __host__ __device__ int heavy_threshold(int ld) { return ld / 4 > 4 ? ld 
 // Launchers.  Every launcher enqueues on `st` and returns the CUDA error of
 // the launch.  T is float or double.
 
+// Launch shape of the FP32 sparse product: heavy rows by lane groups (k <=
+// 64) or lane-private, and the preferred shared-memory carveout in percent
+// (-1: the driver's choice).  Every shape computes bitwise the same Y.
+struct SpmmConfig {
+    int group = 1;
+    int carveout = -1;
+};
+
 template <typename T>
 cudaError_t launch_spmm(const SellDev& S, const EllDev& F, int k, T* Y,
-                        int64_t ldy, cudaStream_t st, int sm_count);
+                        int64_t ldy, SpmmConfig cfg, cudaStream_t st, int sm_count);
 template <typename T>
 cudaError_t launch_spmm_combine(const SellDev& S, int k, T* Y, int64_t ldy,
                                 cudaStream_t st);
@@ -164,8 +183,18 @@ cudaError_t launch_error_metrics(const double* GU, const double* GV, int k,
                                  const double* A2, const double* cross,
                                  double* out, cudaStream_t st);
 
+// Loss gradient and projected-gradient polish (k_grad.cu).
+template <typename T, typename OutT>
+cudaError_t launch_grad(int64_t rows, int k, const EllDev& F, const double* Go, const T* Y,
+                        int64_t ldy, OutT* out, cudaStream_t st);
+cudaError_t launch_lambda_max(const double* G, int k, double* eta_out, double* lam_out,
+                              cudaStream_t st);
 template <typename T>
-cudaError_t launch_cholesky(const double* G, int k, double* Ginv64, T* GinvT,
+cudaError_t launch_pg_apply(int64_t rows, int k, const EllDev& F, const double* Go, const T* Y,
+                            int64_t ldy, const double* eta, T* Xt, int64_t ldx, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_gram_inverse(const double* G, int k, double* Ginv64, T* GinvT,
                             unsigned* status, cudaStream_t st);
 
 template <typename T>
@@ -207,7 +236,7 @@ void set_thread_error(const char* msg);
 // Kernel kinds the profiler keeps statistics for.
 enum KernelKind : int {
     K_SPMM = 0, K_COMBINE, K_SOLVE, K_SELECT, K_EMIT, K_GRAM_REDUCE,
-    K_CHOLESKY, K_TO_COLMAJOR, K_NORM2, K_DOT, K_SCATTER, K_COUNT
+    K_INVERSE, K_TO_COLMAJOR, K_NORM2, K_DOT, K_SCATTER, K_GRAD, K_LAMBDA, K_PG, K_COUNT
 };
 const char* kernel_name(int kind);
 

@@ -3,10 +3,10 @@
 // options, profiling and CUDA-graph replay of whole sweeps.
 //
 // One sweep (update_V then update_U) enqueues, per half:
-//   cholesky(other factor's Gram)  on the auxiliary stream, concurrently with
+//   gram_inverse(other factor's Gram) on the auxiliary stream, concurrently with
 //   spmm (+ combine for split rows) on the main stream, then
-//   solve+project -> select -> finalize -> gram_reduce (+ measures for U).
-// The Cholesky of a factor's Gram only feeds the *next* half-step's solve,
+//   solve+project -> select -> emit -> gram_reduce (+ measures for U).
+// The inverse of a factor's Gram only feeds the *next* half-step's solve,
 // so it is deferred to the start of that half and runs beside its SpMM.
 #include <cuda_runtime.h>
 
@@ -28,8 +28,8 @@ const char* kernel_name(int kind)
 {
     static const char* names[K_COUNT] = {"spmm_sell", "spmm_combine", "solve_project",
                                          "select_topt", "emit", "gram_reduce",
-                                         "cholesky", "to_colmajor", "norm2", "ell_dot",
-                                         "scatter"};
+                                         "gram_inverse", "to_colmajor", "norm2", "ell_dot",
+                                         "scatter", "grad", "lambda_max", "pg_apply"};
     return kind >= 0 && kind < K_COUNT ? names[kind] : "?";
 }
 }  // namespace espnmf
@@ -102,6 +102,7 @@ struct espnmf_ctx {
     double* norm_part = nullptr;
     double* met = nullptr;      // [0] R, [1] E, [2] f, [3] trace
     double* dot = nullptr;      // scratch scalar
+    double* pg = nullptr;       // [0] projected-gradient step eta, [1] lambda_max
     void* tau = nullptr;        // selector thresholds (k keys of 8 bytes)
     uint32_t* cut = nullptr;    // selector tie cut-offs (k)
     double* hist_R = nullptr;
@@ -116,6 +117,10 @@ struct espnmf_ctx {
     bool met_valid = false;
 
     bool use_graph = true;
+    // FP32 sparse-product launch shapes, [0] A V (rows of A), [1] A^T U
+    SpmmConfig spmm_cfg[2];
+    bool spmm_tune = true;
+    bool spmm_tuned = false;
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 
     bool profile = false;
@@ -402,10 +407,11 @@ espnmf_status do_spmm(espnmf_ctx* ctx, bool transA, const EllDev& F)
     const double bytes = (double)S.nnz * (4.0 + ctx->esz) + (double)(S.rows + 1) * 8.0 +
                          (double)S.rows * ctx->k * ctx->esz;
     TRY(run(ctx, K_SPMM, bytes, ctx->st, [&] {
-        return is_f64(ctx) ? launch_spmm<double>(S, F, ctx->k, (double*)ctx->Y, ctx->ldy, ctx->st,
-                                                 ctx->sm_count)
-                           : launch_spmm<float>(S, F, ctx->k, (float*)ctx->Y, ctx->ldy, ctx->st,
-                                                ctx->sm_count);
+        const SpmmConfig cfg = ctx->spmm_cfg[transA ? 1 : 0];
+        return is_f64(ctx) ? launch_spmm<double>(S, F, ctx->k, (double*)ctx->Y, ctx->ldy, cfg,
+                                                 ctx->st, ctx->sm_count)
+                           : launch_spmm<float>(S, F, ctx->k, (float*)ctx->Y, ctx->ldy, cfg,
+                                                ctx->st, ctx->sm_count);
     }));
     if (S.nsplit > 0) {
         const double cb = (double)S.npart * ctx->ldy * ctx->esz;
@@ -417,13 +423,72 @@ espnmf_status do_spmm(espnmf_ctx* ctx, bool transA, const EllDev& F)
     return ESPNMF_OK;
 }
 
-espnmf_status do_cholesky(espnmf_ctx* ctx, Factor& F, cudaStream_t s)
+void drop_graphs(espnmf_ctx* ctx);
+
+// Times every FP32 launch shape of both sparse products on the current
+// factors (each shape gives bitwise the same Y) and keeps the fastest.
+// Leaves Y = A V, as the last U update did.
+espnmf_status tune_spmm(espnmf_ctx* ctx)
+{
+    ctx->spmm_tuned = true;
+    if (is_f64(ctx)) return ESPNMF_OK;
+    std::vector<SpmmConfig> cands;
+    for (int g : {1, 0}) {
+        if (g == 1 && ctx->ldy > 64) continue;
+        for (int cv : {-1, 25, 50, 100}) {
+            SpmmConfig c;
+            c.group = g;
+            c.carveout = cv;
+            cands.push_back(c);
+        }
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    espnmf_status st = ESPNMF_OK;
+    for (int o = 1; o >= 0 && st == ESPNMF_OK; --o) {
+        const SellDev& S = o ? ctx->sAt : ctx->sA;
+        const EllDev& F = o ? ctx->U.buf[ctx->U.cur] : ctx->V.buf[ctx->V.cur];
+        float best = 1e30f;
+        SpmmConfig pick = ctx->spmm_cfg[o];
+        for (const SpmmConfig& c : cands) {
+            cudaError_t e = launch_spmm<float>(S, F, ctx->k, (float*)ctx->Y, ctx->ldy, c, ctx->st,
+                                               ctx->sm_count);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->st);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+                e = launch_spmm<float>(S, F, ctx->k, (float*)ctx->Y, ctx->ldy, c, ctx->st,
+                                       ctx->sm_count);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                st = set_err(ctx, ESPNMF_ERR_CUDA, "spmm tuning: %s", cudaGetErrorString(e));
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                pick = c;
+            }
+        }
+        ctx->spmm_cfg[o] = pick;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TRY(st);
+    drop_graphs(ctx);
+    TRY(do_spmm(ctx, false, ctx->V.buf[ctx->V.cur]));
+    ctx->Y_is_AV = true;
+    return ESPNMF_OK;
+}
+
+espnmf_status do_gram_inverse(espnmf_ctx* ctx, Factor& F, cudaStream_t s)
 {
     const double bytes = (double)ctx->k * ctx->k * (8.0 + 8.0 + ctx->esz);
-    return run(ctx, K_CHOLESKY, bytes, s, [&] {
-        return is_f64(ctx) ? launch_cholesky<double>(F.G, ctx->k, F.Ginv64, (double*)F.GinvT,
+    return run(ctx, K_INVERSE, bytes, s, [&] {
+        return is_f64(ctx) ? launch_gram_inverse<double>(F.G, ctx->k, F.Ginv64, (double*)F.GinvT,
                                                      ctx->status_d, s)
-                           : launch_cholesky<float>(F.G, ctx->k, F.Ginv64, (float*)F.GinvT,
+                           : launch_gram_inverse<float>(F.G, ctx->k, F.Ginv64, (float*)F.GinvT,
                                                     ctx->status_d, s);
     });
 }
@@ -489,10 +554,10 @@ espnmf_status half_update(espnmf_ctx* ctx, bool updV)
     Factor& F = updV ? ctx->V : ctx->U;
     Factor& O = updV ? ctx->U : ctx->V;
     const int64_t rows = F.rows;
-    // The other factor's Cholesky runs beside the SpMM.
+    // The other factor's Gram inverse runs beside the SpMM.
     CU(cudaEventRecord(ctx->ev_fork, ctx->st));
     CU(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-    TRY(do_cholesky(ctx, O, ctx->aux));
+    TRY(do_gram_inverse(ctx, O, ctx->aux));
     CU(cudaEventRecord(ctx->ev_join, ctx->aux));
     O.chol_pending = false;
 
@@ -666,6 +731,45 @@ espnmf_status fail_init(espnmf_ctx* ctx, espnmf_status s)
     return s;
 }
 
+// R/E/f of the current U, V: ||A||^2 - 2 <U, A V> + <U^T U, V^T V>, with
+// A V from the last U update when it is still current.
+espnmf_status ensure_metrics(espnmf_ctx* ctx)
+{
+    if (ctx->met_valid) return ESPNMF_OK;
+    if (!ctx->Y_is_AV) {
+        TRY(do_spmm(ctx, false, ctx->V.buf[ctx->V.cur]));
+        ctx->Y_is_AV = true;
+    }
+    EllDev& u = ctx->U.buf[ctx->U.cur];
+    TRY(run(ctx, K_DOT, (double)ctx->n * 4, ctx->st, [&] {
+        return is_f64(ctx) ? launch_ell_dot<double>(ctx->n, ctx->k, u, (const double*)ctx->Y, ctx->ldy,
+                                                    ctx->norm_part, ctx->sm_count, ctx->dot, ctx->st)
+                           : launch_ell_dot<float>(ctx->n, ctx->k, u, (const float*)ctx->Y, ctx->ldy,
+                                                   ctx->norm_part, ctx->sm_count, ctx->dot, ctx->st);
+    }));
+    TRY(run(ctx, K_DOT, 0.0, ctx->st, [&] {
+        return launch_error_metrics(ctx->U.G, ctx->V.G, ctx->k, ctx->A2, ctx->dot, ctx->met,
+                                    ctx->st);
+    }));
+    ctx->met_valid = true;
+    return ESPNMF_OK;
+}
+
+// Y = A V (for U) or A^T U (for V), the sparse product a gradient needs.
+espnmf_status ensure_product_for(espnmf_ctx* ctx, espnmf_which which)
+{
+    if (which == ESPNMF_U) {
+        if (!ctx->Y_is_AV) {
+            TRY(do_spmm(ctx, false, ctx->V.buf[ctx->V.cur]));
+            ctx->Y_is_AV = true;
+        }
+    } else {
+        TRY(do_spmm(ctx, true, ctx->U.buf[ctx->U.cur]));
+        ctx->Y_is_AV = false;
+    }
+    return ESPNMF_OK;
+}
+
 }  // namespace
 
 // =================================================================================
@@ -754,7 +858,11 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             CU(cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking));
             ctx->own_stream = true;
         }
-        CU(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        // the Gram inverse on the auxiliary stream must not queue behind the
+        // concurrent SpMM's blocks: give the stream the highest priority
+        int prio_lo = 0, prio_hi = 0;
+        CU(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        CU(cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_hi));
         CU(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
         CU(setup_spmm());
@@ -855,6 +963,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         TRY(dmalloc(ctx, &ctx->met, sizeof(double) * 4));
         CU(cudaMemsetAsync(ctx->met, 0, sizeof(double) * 4, ctx->st));
         TRY(dmalloc(ctx, &ctx->dot, sizeof(double)));
+        TRY(dmalloc(ctx, &ctx->pg, 2 * sizeof(double)));
         TRY(dmalloc(ctx, &ctx->tau, 8 * (size_t)k));
         TRY(dmalloc(ctx, &ctx->cut, 4 * (size_t)k));
         TRY(dmalloc(ctx, &ctx->hist_counter, sizeof(int)));
@@ -867,15 +976,25 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         for (Factor* F : {&ctx->U, &ctx->V}) {
             F->rows = F == &ctx->U ? n : m;
             const int ld = factor_ld(k);
+            const int dld = dense_ld(ld);
             void* dense = nullptr;
-            TRY(dmalloc(ctx, &dense, ctx->esz * F->rows * ld));
+            TRY(dmalloc(ctx, &dense, ctx->esz * F->rows * dld));
+            // one dense copy and one record array per factor, rewritten by
+            // each emit (the emit writes every row's record)
+            uint4* rec = nullptr;
+            if (!is_f64(ctx)) {
+                TRY(dmalloc(ctx, &rec, sizeof(uint4) * F->rows));
+                CU(cudaMemsetAsync(rec, 0, sizeof(uint4) * F->rows, ctx->st));
+            }
             for (int b = 0; b < 2; ++b) {
                 TRY(dmalloc(ctx, &F->buf[b].cnt, sizeof(int32_t) * F->rows));
                 TRY(dmalloc(ctx, &F->buf[b].col, sizeof(int32_t) * F->rows * ld));
                 TRY(dmalloc(ctx, &F->buf[b].val, ctx->esz * F->rows * ld));
                 CU(cudaMemsetAsync(F->buf[b].cnt, 0, sizeof(int32_t) * F->rows, ctx->st));
-                F->buf[b].dense = dense;   // one dense copy, rewritten by each finalize
+                F->buf[b].dense = dense;
+                F->buf[b].rec = rec;
                 F->buf[b].ld = ld;
+                F->buf[b].dld = dld;
                 F->buf[b].heavy = heavy_threshold(ld);
             }
             TRY(dmalloc(ctx, &F->G, sizeof(double) * k * k));
@@ -959,6 +1078,7 @@ espnmf_status espnmf_iterate(espnmf_ctx* ctx, int32_t iters, double* R_out, doub
         ++it;
     }
     if (ctx->use_graph && !ctx->profile) {
+        if (it < iters && ctx->spmm_tune && !ctx->spmm_tuned) TRY(tune_spmm(ctx));
         for (; it < iters; ++it) {
             cudaGraphExec_t& g = ctx->gexec[ctx->U.cur][ctx->V.cur];
             if (!g) TRY(sweep_graph(ctx, &g));
@@ -1023,28 +1143,108 @@ espnmf_status espnmf_error(espnmf_ctx* ctx, double* E)
     TRY(enter(ctx));
     if (!E) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "E is NULL");
     if (!ctx->V.valid) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "V has no value yet");
-    if (!ctx->met_valid) {
-        if (!ctx->Y_is_AV) {
-            TRY(do_spmm(ctx, false, ctx->V.buf[ctx->V.cur]));
-            ctx->Y_is_AV = true;
-        }
-        EllDev& u = ctx->U.buf[ctx->U.cur];
-        TRY(run(ctx, K_DOT, (double)ctx->n * 4, ctx->st, [&] {
-            return is_f64(ctx) ? launch_ell_dot<double>(ctx->n, ctx->k, u, (const double*)ctx->Y, ctx->ldy,
-                                                        ctx->norm_part, ctx->sm_count, ctx->dot, ctx->st)
-                               : launch_ell_dot<float>(ctx->n, ctx->k, u, (const float*)ctx->Y, ctx->ldy,
-                                                       ctx->norm_part, ctx->sm_count, ctx->dot, ctx->st);
-        }));
-        // E from ||A||^2, <U, AV> and <U^T U, V^T V>
-        TRY(run(ctx, K_DOT, 0.0, ctx->st, [&] {
-            return launch_error_metrics(ctx->U.G, ctx->V.G, ctx->k, ctx->A2, ctx->dot, ctx->met,
-                                        ctx->st);
-        }));
-        ctx->met_valid = true;
-    }
+    TRY(ensure_metrics(ctx));
     TRY(check_status(ctx));
     CU(cudaMemcpy(E, ctx->met + 1, sizeof(double), cudaMemcpyDeviceToHost));
     return ESPNMF_OK;
+}
+
+espnmf_status espnmf_loss(espnmf_ctx* ctx, double* f)
+{
+    TRY(enter(ctx));
+    if (!f) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "f is NULL");
+    if (!ctx->V.valid) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "V has no value yet");
+    TRY(ensure_metrics(ctx));
+    TRY(check_status(ctx));
+    CU(cudaMemcpy(f, ctx->met + 2, sizeof(double), cudaMemcpyDeviceToHost));
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_grad(espnmf_ctx* ctx, espnmf_which which, void* out, espnmf_dtype dtype,
+                          int32_t on_device)
+{
+    TRY(enter(ctx));
+    if (which != ESPNMF_U && which != ESPNMF_V) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "which");
+    if (!out) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "out is NULL");
+    if (dtype != ESPNMF_F64 && dtype != ESPNMF_F32)
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "dtype must be F64 or F32");
+    if (!ctx->U.valid || !ctx->V.valid)
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "U and V need values");
+    Factor& F = which == ESPNMF_U ? ctx->U : ctx->V;
+    Factor& O = which == ESPNMF_U ? ctx->V : ctx->U;
+    TRY(ensure_product_for(ctx, which));
+    const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
+    const size_t bytes = (size_t)F.rows * ctx->k * es;
+    void* dst = out;
+    if (!on_device) CU(cudaMallocAsync(&dst, bytes ? bytes : 16, ctx->st));
+    const EllDev& fe = F.buf[F.cur];
+    const espnmf_status s = run(ctx, K_GRAD, (double)bytes + (double)F.rows * ctx->ldy * ctx->esz,
+                                ctx->st, [&]() -> cudaError_t {
+        if (is_f64(ctx))
+            return dtype == ESPNMF_F64
+                       ? launch_grad<double, double>(F.rows, ctx->k, fe, O.G, (const double*)ctx->Y,
+                                                     ctx->ldy, (double*)dst, ctx->st)
+                       : launch_grad<double, float>(F.rows, ctx->k, fe, O.G, (const double*)ctx->Y,
+                                                    ctx->ldy, (float*)dst, ctx->st);
+        return dtype == ESPNMF_F64
+                   ? launch_grad<float, double>(F.rows, ctx->k, fe, O.G, (const float*)ctx->Y,
+                                                ctx->ldy, (double*)dst, ctx->st)
+                   : launch_grad<float, float>(F.rows, ctx->k, fe, O.G, (const float*)ctx->Y,
+                                               ctx->ldy, (float*)dst, ctx->st);
+    });
+    if (!on_device) {
+        cudaError_t e = s == ESPNMF_OK ? cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, ctx->st)
+                                       : cudaSuccess;
+        cudaError_t e2 = cudaFreeAsync(dst, ctx->st);
+        TRY(s);
+        CU(e);
+        CU(e2);
+    }
+    TRY(s);
+    return check_status(ctx);
+}
+
+espnmf_status espnmf_pg_step(espnmf_ctx* ctx, espnmf_which which, double eta, double* eta_used)
+{
+    TRY(enter(ctx));
+    if (which != ESPNMF_U && which != ESPNMF_V) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "which");
+    if (!(eta <= 0.0 || std::isfinite(eta))) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "eta");
+    if (!ctx->U.valid || !ctx->V.valid)
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "U and V need values");
+    Factor& F = which == ESPNMF_U ? ctx->U : ctx->V;
+    Factor& O = which == ESPNMF_U ? ctx->V : ctx->U;
+    TRY(ensure_product_for(ctx, which));
+    if (eta > 0.0) {
+        CU(cudaMemcpyAsync(ctx->pg, &eta, sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    } else {
+        TRY(run(ctx, K_LAMBDA, (double)ctx->k * ctx->k * 8, ctx->st, [&] {
+            return launch_lambda_max(O.G, ctx->k, ctx->pg, ctx->pg + 1, ctx->st);
+        }));
+    }
+    const EllDev& fe = F.buf[F.cur];
+    TRY(run(ctx, K_PG, (double)F.rows * ctx->k * ctx->esz * 2, ctx->st, [&] {
+        return is_f64(ctx) ? launch_pg_apply<double>(F.rows, ctx->k, fe, O.G, (const double*)ctx->Y,
+                                                     ctx->ldy, ctx->pg, (double*)ctx->Xt, ctx->ldx,
+                                                     ctx->st)
+                           : launch_pg_apply<float>(F.rows, ctx->k, fe, O.G, (const float*)ctx->Y,
+                                                    ctx->ldy, ctx->pg, (float*)ctx->Xt, ctx->ldx,
+                                                    ctx->st);
+    }));
+    // keep every positive entry of the candidate (the support only shrinks)
+    CU(cudaMemsetAsync(ctx->tau, 0, 8 * (size_t)ctx->k, ctx->st));
+    CU(cudaMemsetAsync(ctx->cut, 0xff, 4 * (size_t)ctx->k, ctx->st));
+    if (which == ESPNMF_U) {
+        // Y = A V is current: the emit also forms R (old vs new U) and E
+        TRY(do_emit(ctx, F, true, ctx->Y, false, TOPT_COLUMN));
+        ctx->met_valid = false;
+        ctx->have_R = false;
+    } else {
+        TRY(do_emit(ctx, F, false, nullptr, false, TOPT_COLUMN));
+        ctx->met_valid = false;
+    }
+    if (eta_used) CU(cudaMemcpyAsync(eta_used, ctx->pg, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    return check_status(ctx);
 }
 
 espnmf_status espnmf_factor_nnz(espnmf_ctx* ctx, espnmf_which which, int64_t* nnz)
@@ -1158,6 +1358,22 @@ espnmf_status espnmf_set_option(espnmf_ctx* ctx, espnmf_option opt, int64_t valu
         if (value < 1) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "wait limit must be >= 1");
         ctx->wait_limit = value;
         return ESPNMF_OK;
+    case ESPNMF_OPT_SPMM_TUNE:
+        ctx->spmm_tune = value != 0;
+        if (ctx->spmm_tune) ctx->spmm_tuned = false;
+        return ESPNMF_OK;
+    case ESPNMF_OPT_SPMM_GROUP:
+        if (value != 0 && value != 1) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "group is 0 or 1");
+        ctx->spmm_cfg[0].group = ctx->spmm_cfg[1].group = (int)value;
+        ctx->spmm_tune = false;
+        drop_graphs(ctx);
+        return ESPNMF_OK;
+    case ESPNMF_OPT_SPMM_CARVEOUT:
+        if (value < -1 || value > 100) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "carveout in -1..100");
+        ctx->spmm_cfg[0].carveout = ctx->spmm_cfg[1].carveout = (int)value;
+        ctx->spmm_tune = false;
+        drop_graphs(ctx);
+        return ESPNMF_OK;
     }
     return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "unknown option");
 }
@@ -1197,7 +1413,7 @@ espnmf_status espnmf_launches_per_sweep(espnmf_ctx* ctx, int32_t* count)
     if (!count) return ESPNMF_ERR_INVALID_ARG;
     int per_half_A = 5 + (ctx->sA.nsplit > 0 ? 1 : 0);
     int per_half_At = 5 + (ctx->sAt.nsplit > 0 ? 1 : 0);
-    *count = per_half_A + per_half_At + 2;   // + the two Cholesky launches
+    *count = per_half_A + per_half_At + 2;   // + the two Gram inverse launches
     return ESPNMF_OK;
 }
 
@@ -1265,6 +1481,216 @@ espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64
     if (e != cudaSuccess) return cuerr(e, "enforce_topt_buffer");
     if (hstat & ST_NONFINITE) return set_err(nullptr, ESPNMF_ERR_NONFINITE, "non-finite value in X");
     return ESPNMF_OK;
+}
+
+}  // extern "C"
+
+// =================================================================================
+// Batched sweeps: many independent problems, one captured CUDA graph per sweep
+
+struct espnmf_batch {
+    int device = 0;
+    std::vector<espnmf_ctx*> ctxs;
+    std::vector<cudaStream_t> pool;   // problem i runs on pool[i % pool.size()]
+    cudaStream_t st = nullptr;        // graph launches
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;    // one per pool stream
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    bool use_graph = true;
+};
+
+namespace {
+
+espnmf_status batch_fail(espnmf_status s, const std::string& msg)
+{
+    espnmf::set_thread_error(msg.c_str());
+    return s;
+}
+
+// st waits for everything enqueued on the pool streams so far
+cudaError_t pool_to_main(espnmf_batch* b)
+{
+    for (size_t s = 0; s < b->pool.size(); ++s) {
+        cudaError_t e = cudaEventRecord(b->join[s], b->pool[s]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->join[s], 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// every pool stream waits for everything enqueued on st so far
+cudaError_t main_to_pool(espnmf_batch* b)
+{
+    cudaError_t e = cudaEventRecord(b->fork, b->st);
+    for (size_t s = 0; e == cudaSuccess && s < b->pool.size(); ++s)
+        e = cudaStreamWaitEvent(b->pool[s], b->fork, 0);
+    return e;
+}
+
+// One sweep of every problem, captured from the pool streams into one graph.
+espnmf_status batch_graph(espnmf_batch* b, cudaGraphExec_t* out)
+{
+    std::vector<HostState> saved;
+    for (auto* c : b->ctxs) saved.push_back(save_state(c));
+    cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(ESPNMF_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    e = main_to_pool(b);
+    espnmf_status st = e == cudaSuccess ? ESPNMF_OK : ESPNMF_ERR_CUDA;
+    for (size_t i = 0; st == ESPNMF_OK && i < b->ctxs.size(); ++i) st = enqueue_sweep(b->ctxs[i]);
+    if (st == ESPNMF_OK && pool_to_main(b) != cudaSuccess) st = ESPNMF_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->st, &g);
+    for (size_t i = 0; i < b->ctxs.size(); ++i) restore_state(b->ctxs[i], saved[i]);
+    if (st != ESPNMF_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return batch_fail(ESPNMF_ERR_CUDA, "batch capture failed");
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return batch_fail(ESPNMF_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    return ESPNMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+espnmf_status espnmf_batch_init(espnmf_batch** out, int32_t nprob, const espnmf_csr* As,
+                                const int32_t* ks, const int64_t* t_us, const int64_t* t_vs,
+                                espnmf_topt_mode mode, espnmf_dtype compute,
+                                const void* const* U0s, espnmf_dtype U0_dtype,
+                                int32_t U0_on_device, int32_t streams)
+{
+    espnmf::set_thread_error("");
+    if (!out) return batch_fail(ESPNMF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nprob < 1 || !As || !ks || !t_us || !t_vs || !U0s)
+        return batch_fail(ESPNMF_ERR_INVALID_ARG, "need nprob >= 1 and non-NULL arrays");
+    auto* b = new espnmf_batch();
+    auto fail = [&](espnmf_status s, const std::string& m) {
+        espnmf_batch_destroy(b);
+        return batch_fail(s, m);
+    };
+    cudaError_t e = cudaGetDevice(&b->device);
+    const int S = std::max(1, std::min<int>(nprob, streams > 0 ? streams : 16));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int s = 0; e == cudaSuccess && s < S; ++s) {
+        cudaStream_t ps = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->pool.push_back(ps);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->join.push_back(ev);
+    }
+    if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, std::string("batch streams: ") + cudaGetErrorString(e));
+    for (int i = 0; i < nprob; ++i) {
+        espnmf_ctx* c = nullptr;
+        const espnmf_status s = espnmf_init(&c, &As[i], ks[i], t_us[i], t_vs[i], mode, compute,
+                                            U0s[i], U0_dtype, U0_on_device, b->pool[i % S]);
+        if (s != ESPNMF_OK) {
+            const std::string why = espnmf_last_error(nullptr);
+            return fail(s, "problem " + std::to_string(i) + ": " + why);
+        }
+        b->ctxs.push_back(c);
+    }
+    *out = b;
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_batch_destroy(espnmf_batch* b)
+{
+    if (!b) return ESPNMF_OK;
+    cudaSetDevice(b->device);
+    if (b->st) cudaStreamSynchronize(b->st);
+    for (auto& row : b->gexec)
+        for (auto& g : row)
+            if (g) cudaGraphExecDestroy(g);
+    for (auto* c : b->ctxs) espnmf_destroy(c);
+    for (auto s : b->pool) cudaStreamDestroy(s);
+    for (auto ev : b->join) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->st) cudaStreamDestroy(b->st);
+    delete b;
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_batch_ctx(espnmf_batch* b, int32_t i, espnmf_ctx** out)
+{
+    if (!b || !out || i < 0 || i >= (int32_t)b->ctxs.size())
+        return batch_fail(ESPNMF_ERR_INVALID_ARG, "bad batch, index or out");
+    *out = b->ctxs[i];
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_batch_set_option(espnmf_batch* b, espnmf_option opt, int64_t value)
+{
+    if (!b) return batch_fail(ESPNMF_ERR_INVALID_ARG, "batch is NULL");
+    if (opt != ESPNMF_OPT_USE_GRAPH) return batch_fail(ESPNMF_ERR_INVALID_ARG, "unsupported batch option");
+    b->use_graph = value != 0;
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_batch_iterate(espnmf_batch* b, int32_t iters, espnmf_status* status_out,
+                                   double* R_out, double* E_out)
+{
+    espnmf::set_thread_error("");
+    if (!b) return batch_fail(ESPNMF_ERR_INVALID_ARG, "batch is NULL");
+    if (iters < 0) return batch_fail(ESPNMF_ERR_INVALID_ARG, "iters must be >= 0");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return batch_fail(ESPNMF_ERR_CUDA, cudaGetErrorString(e));
+    const int n = (int)b->ctxs.size();
+    for (auto* c : b->ctxs) {
+        c->err.clear();
+        espnmf_status s = ensure_hist(c, std::max(iters, 1));
+        if (s == ESPNMF_OK && cudaMemsetAsync(c->hist_counter, 0, sizeof(int), c->st) != cudaSuccess)
+            s = ESPNMF_ERR_CUDA;
+        if (s != ESPNMF_OK) return batch_fail(s, "batch history buffers");
+    }
+    int it = 0;
+    // the problems sweep in lockstep; a graph needs them all in one state
+    auto lockstep = [&]() {
+        for (auto* c : b->ctxs)
+            if (!c->V.valid || c->U.cur != b->ctxs[0]->U.cur || c->V.cur != b->ctxs[0]->V.cur)
+                return false;
+        return true;
+    };
+    espnmf_status st = ESPNMF_OK;
+    for (; st == ESPNMF_OK && it < iters; ++it) {
+        if (!b->use_graph || !lockstep()) {
+            for (int i = 0; st == ESPNMF_OK && i < n; ++i) st = enqueue_sweep(b->ctxs[i]);
+            continue;
+        }
+        cudaGraphExec_t& g = b->gexec[b->ctxs[0]->U.cur][b->ctxs[0]->V.cur];
+        if (!g) st = batch_graph(b, &g);
+        if (st != ESPNMF_OK) break;
+        if (pool_to_main(b) != cudaSuccess || cudaGraphLaunch(g, b->st) != cudaSuccess ||
+            main_to_pool(b) != cudaSuccess) {
+            st = batch_fail(ESPNMF_ERR_CUDA, "batch graph launch");
+            break;
+        }
+        for (auto* c : b->ctxs) after_sweep_state(c);
+    }
+    if (st != ESPNMF_OK) return st;
+    // per-problem status and measures
+    espnmf_status worst = ESPNMF_OK;
+    for (int i = 0; i < n; ++i) {
+        espnmf_ctx* c = b->ctxs[i];
+        espnmf_status s = check_status(c);
+        if (s == ESPNMF_OK && iters > 0) {
+            if (R_out && cudaMemcpy(R_out + (size_t)i * iters, c->hist_R, sizeof(double) * iters,
+                                    cudaMemcpyDeviceToHost) != cudaSuccess)
+                s = ESPNMF_ERR_CUDA;
+            if (E_out && cudaMemcpy(E_out + (size_t)i * iters, c->hist_E, sizeof(double) * iters,
+                                    cudaMemcpyDeviceToHost) != cudaSuccess)
+                s = ESPNMF_ERR_CUDA;
+        }
+        if (status_out) status_out[i] = s;
+        if (s != ESPNMF_OK && worst == ESPNMF_OK) worst = s;
+    }
+    if (worst != ESPNMF_OK)
+        espnmf::set_thread_error("one or more problems failed: see the status array");
+    return worst;
 }
 
 }  // extern "C"

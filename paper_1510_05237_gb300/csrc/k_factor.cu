@@ -11,14 +11,16 @@
 //   gram_reduce   adds the block partials in a fixed order; its last block
 //                 also forms R and E (Sec. 3.1) without ever forming U V^T:
 //                 E^2 ||A||^2 = ||A||^2 - 2 <U, A V> + <U^T U, V^T V>.
-//   cholesky      FP64 Cholesky factorisation of the Gram matrix and its
-//                 inverse (one CTA), used by the k x k solve.
+//   gram_inverse  FP64 inverse of the Gram matrix by the symmetric sweep
+//                 operator (one CTA), used by the k x k solve.
 //   conversions   dense -> row-packed, row-packed -> dense / column-major,
 //                 ||A||^2 and the stand-alone <U, Y> reduction.
 //
 // Every reduction adds in a fixed order (per warp, then per block in warp
 // order, then over blocks in block order), so all results are reproducible.
 #include <float.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -47,7 +49,8 @@ struct EmitArgs {
     int32_t* col;
     T* val;
     T* dense;
-    int ld, heavy, SL;   // SL: staged pairs per lane (light rows)
+    uint4* rec;          // FP32: per-row records (cnt and the first pairs)
+    int ld, dld, heavy, SL;   // SL: staged pairs per lane (light rows)
     bool heavy_gram;     // heavy rows' Gram by register slots
     int32_t* cnt_old;
     const int32_t* col_old;
@@ -170,11 +173,23 @@ emit_kernel(EmitArgs<T> a)
             const bool hv = pos >= a.heavy && a.dense != nullptr;
             if (hv) {
                 // dense copy of a heavy row, from the pairs just written
-                T* dr = a.dense + r * ld;
+                T* dr = a.dense + r * a.dld;
                 for (int c = 0; c < ld; ++c) dr[c] = T(0);
                 for (int j = 0; j < pos; ++j) dr[wc[j]] = wv[j];
             }
             a.cnt[r] = pos;
+            if constexpr (sizeof(T) == 4) {
+                if (a.rec) {
+                    // the first min(pos, 3) pairs are in this lane's staging
+                    unsigned x = (unsigned)pos;
+                    unsigned v[3] = {0u, 0u, 0u};
+                    for (int q = 0; q < pos && q < 3; ++q) {
+                        x |= (unsigned)stc[lane * SL + q] << (8 * (q + 1));
+                        v[q] = __float_as_uint((float)stv[lane * SL + q]);
+                    }
+                    a.rec[r] = make_uint4(x, v[0], v[1], v[2]);
+                }
+            }
             if (a.zero_old) a.cnt_old[r] = 0;
             nl = (hv && a.heavy_gram) ? 0 : pos;
         }
@@ -240,7 +255,7 @@ emit_kernel(EmitArgs<T> a)
             __syncthreads();
             for (int h = 0; h < nh; ++h) {
                 const int64_t rr = hlist[h];
-                for (int c = tid; c < k; c += blockDim.x) drow[c] = (double)a.dense[rr * ld + c];
+                for (int c = tid; c < k; c += blockDim.x) drow[c] = (double)a.dense[rr * a.dld + c];
                 __syncthreads();
 #pragma unroll
                 for (int s = 0; s < kSlots; ++s)
@@ -312,7 +327,9 @@ cudaError_t launch_emit(const T* Xt, int64_t ldx, int64_t rows, int k, int mode,
     a.col = cur.col;
     a.val = static_cast<T*>(cur.val);
     a.dense = static_cast<T*>(cur.dense);
+    a.rec = cur.rec;
     a.ld = cur.ld;
+    a.dld = cur.dld;
     a.heavy = cur.heavy;
     const int ntri = k * (k + 1) / 2;
     a.cnt_old = old.cnt;
@@ -455,17 +472,34 @@ cudaError_t launch_error_metrics(const double* GU, const double* GV, int k,
 }
 
 // ---------------------------------------------------------------------------
-// FP64 inverse of the Gram matrix through its square-root-free Cholesky
-// factorisation G = L D L^T (L unit lower triangular), in one CTA:
-//   G^-1 = L^-T D^-1 L^-1.
-// An index whose diagonal is exactly 0 belongs to an all-zero factor column:
-// it is taken out (identity row/column during the factorisation, zero
-// row/column in the inverse), which gives the minimum-norm solution.  A pivot
-// d_j <= 64 eps max_j G_jj elsewhere raises ST_SINGULAR (d_j is the square
-// of the Cholesky diagonal, so this is the LL^T pivot test).
-// FP64 on this GPU has a long latency, so the column loop has one barrier
-// per column and takes pivot reciprocals from an FP32 seed refined by two
-// FP64 Newton steps.
+// FP64 inverse of the Gram matrix G = F^T F in one CTA, by the symmetric
+// sweep operator (Gauss-Jordan elimination with diagonal pivots, in place on
+// the upper triangle).  Sweeping pivot p with d = a_pp maps
+//   a_ij -> a_ij - a_ip a_pj / d   (i, j != p),
+//   a_ip -> a_ip / d,   a_pp -> -1 / d,
+// and after every index has been swept the array holds -G^-1.  The pivot d
+// at step p is the p-th Schur complement pivot, i.e. the d_p of G = L D L^T
+// (the square of the Cholesky diagonal), so the Cholesky pivot test applies:
+// d_p <= 64 eps max_j G_jj raises ST_SINGULAR.  An index whose diagonal is
+// exactly 0 belongs to an all-zero factor column; it is never swept and its
+// row and column stay 0, which gives the minimum-norm solution.
+//
+// FP64 is slow on this GPU (a warp-wide FMA holds a sub-partition's FP64
+// pipe for tens of cycles), so the kernel does the minimum k^3 / 2 FMAs and
+// keeps the pipe busy:
+//   * every thread owns a segment of one row of the upper triangle (row i,
+//     up to E consecutive columns, segments cut at multiples of E) for the
+//     whole factorisation, in registers: per step it reads pv[i] once and
+//     does E independent FMAs;
+//   * a step has two phases between barriers: the pivot row is scaled by
+//     1/d (prs), then every entry is updated; the owners of the next pivot's
+//     row publish it (pv, double-buffered) and the owners of diagonal
+//     entries publish the diagonal (double-buffered);
+//   * the next pivot's reciprocal is computed during the update phase by a
+//     warp of its own (the last one), from the published diagonal and the
+//     same FMA the entry's owner performs, so its FP64 latency chain is off
+//     the critical path.
+// The reciprocal comes from an FP32 seed refined by two FP64 Newton steps.
 
 __device__ __forceinline__ double recip_fp64(double d)
 {
@@ -478,116 +512,164 @@ __device__ __forceinline__ double recip_fp64(double d)
     return fma(x, e, x);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256)
-cholesky_kernel(const double* __restrict__ G, int k, double* Ginv64,
-                T* GinvT, unsigned* status, int w_in_smem)
+constexpr int kInvMaxWork = 512 - 32;    // threads that own entries
+
+// Segments of the upper triangle with segment length E: row i holds columns
+// [i, k), cut at multiples of E.
+__host__ __device__ inline int inv_row_segments(int i, int k, int E)
+{
+    return (k - 1) / E - i / E + 1;
+}
+
+__host__ __device__ inline int inv_segments(int k, int E)
+{
+    int n = 0;
+    for (int i = 0; i < k; ++i) n += inv_row_segments(i, k, E);
+    return n;
+}
+
+struct InvSmem {
+    size_t pv, prs, diag, alist, total;
+};
+
+__host__ __device__ inline InvSmem inv_smem(int k)
+{
+    InvSmem s;
+    s.pv = 0;                                                   // 2 x k doubles
+    s.prs = align16(s.pv + 2 * (size_t)k * sizeof(double));    // k doubles
+    s.diag = align16(s.prs + (size_t)k * sizeof(double));      // 2 x k doubles
+    s.alist = align16(s.diag + 2 * (size_t)k * sizeof(double)); // k + 1 ints
+    s.total = align16(s.alist + ((size_t)k + 1) * sizeof(int));
+    return s;
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(512)
+gram_inverse_kernel(const double* __restrict__ G, int k, double* Ginv64,
+                    T* GinvT, unsigned* status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* A = reinterpret_cast<double*>(smem_raw);                 // k*k
-    double* W = w_in_smem ? A + (size_t)k * k : Ginv64;               // k*k: L^-1
-    double* dinv = A + (size_t)k * k * (w_in_smem ? 2 : 1);          // k
-    int* act = reinterpret_cast<int*>(dinv + k);
+    const InvSmem lay = inv_smem(k);
+    double* pvb = reinterpret_cast<double*>(smem_raw + lay.pv);     // [2][k]
+    double* prs = reinterpret_cast<double*>(smem_raw + lay.prs);    // [k]
+    double* diagb = reinterpret_cast<double*>(smem_raw + lay.diag); // [2][k]
+    int* alist = reinterpret_cast<int*>(smem_raw + lay.alist);      // active indices
+    __shared__ double rbuf[2];
     __shared__ double maxdiag;
-    __shared__ int sing, nonfin;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int kk = k * k;
-    for (int e = tid; e < kk; e += nt) A[e] = G[e];
-    __syncthreads();
+    __shared__ int na, sing, nonfin;
+    const int tid = threadIdx.x;
+    const int nt = blockDim.x;
+    const int nwork = nt - 32;               // the last warp computes reciprocals
+    const bool recip_warp = tid >= nwork;
+
+    // this thread's segment: row si, columns [sj, sj + sn)
+    int si = -1, sj = 0, sn = 0;
+    if (!recip_warp) {
+        int base = 0;
+        for (int i = 0; i < k; ++i) {
+            const int ns = inv_row_segments(i, k, E);
+            if (tid < base + ns) {
+                const int s = tid - base;
+                si = i;
+                sj = s == 0 ? i : (i / E + s) * E;
+                const int end = min(k, (sj / E + 1) * E);
+                sn = end - sj;
+                break;
+            }
+            base += ns;
+        }
+    }
     if (tid == 0) {
         double md = 0.0;
-        int nf = 0;
+        int nf = 0, cnt = 0;
         for (int j = 0; j < k; ++j) {
-            const double d = A[j * k + j];
+            const double d = G[(size_t)j * k + j];
             if (!isfinite(d)) nf = 1;
-            act[j] = d != 0.0 && isfinite(d);
-            if (act[j] && d > md) md = d;
+            if (d != 0.0 && isfinite(d)) {
+                alist[cnt++] = j;
+                if (d > md) md = d;
+            }
         }
+        alist[cnt] = -1;
+        na = cnt;
         maxdiag = md;
         sing = 0;
         nonfin = nf;
     }
-    __syncthreads();
-    for (int e = tid; e < kk; e += nt) {
-        const int i = e / k, j = e - i * k;
-        if (!act[i] || !act[j]) A[e] = i == j ? 1.0 : 0.0;
-    }
+    double a[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) a[e] = (si >= 0 && e < sn) ? G[(size_t)si * k + sj + e] : 0.0;
     __syncthreads();
     const double tol = 64.0 * DBL_EPSILON * maxdiag;
-    // L D L^T, lower triangle of A: after step j, A[i][j] (i > j) = l_ij
-    for (int j = 0; j < k; ++j) {
-        const double d0 = A[j * k + j];
-        const bool bad = act[j] && !(d0 > tol);
-        const double r = recip_fp64(bad ? 1.0 : d0);
-        // trailing update with the unscaled column: a_il -= a_ij a_lj / d_j
-        const int nrem = k - j - 1;
-        for (int e = tid; e < nrem * nrem; e += nt) {
-            const int ii = e / nrem, ll = e - ii * nrem;
-            if (ll <= ii) {
-                const int i = j + 1 + ii, l = j + 1 + ll;
-                A[i * k + l] -= A[i * k + j] * (A[l * k + j] * r);
-            }
-        }
-        __syncthreads();   // column j is read by everyone; scale it now
-        if (tid == 0) {
-            if (bad) sing = 1;
-            dinv[j] = r;
-            A[j * k + j] = 1.0;
-        }
-        for (int i = j + 1 + tid; i < k; i += nt) A[i * k + j] *= r;
+
+    // step 0 inputs: the first pivot's row, the diagonal, its reciprocal
+    const int p0 = na > 0 ? alist[0] : 0;
+    for (int x = tid; x < k; x += nt) {
+        pvb[x] = na > 0 ? G[(size_t)(x < p0 ? x : p0) * k + (x < p0 ? p0 : x)] : 0.0;
+        diagb[x] = G[(size_t)x * k + x];
+    }
+    if (tid == 0 && na > 0) {
+        const double d = G[(size_t)p0 * k + p0];
+        const bool bad = !(d > tol);
+        if (bad) sing = 1;
+        rbuf[0] = recip_fp64(bad ? 1.0 : d);
     }
     __syncthreads();
-    // W = L^-1 (unit lower), row by row; dot products over four accumulators
-    for (int i = 0; i < k; ++i) {
-        for (int c = tid; c < k; c += nt) {
-            double v;
-            if (c > i) v = 0.0;
-            else if (c == i) v = 1.0;
-            else {
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                int e = c;
-                for (; e + 3 < i; e += 4) {
-                    s0 += A[i * k + e] * W[e * k + c];
-                    s1 += A[i * k + e + 1] * W[(e + 1) * k + c];
-                    s2 += A[i * k + e + 2] * W[(e + 2) * k + c];
-                    s3 += A[i * k + e + 3] * W[(e + 3) * k + c];
-                }
-                for (; e < i; ++e) s0 += A[i * k + e] * W[e * k + c];
-                v = -((s0 + s1) + (s2 + s3));
+
+    for (int s = 0; s < na; ++s) {
+        const int p = alist[s];
+        const int qn = alist[s + 1];            // next pivot, -1 after the last
+        const double* pv = pvb + (s & 1) * k;
+        double* pvn = pvb + ((s + 1) & 1) * k;
+        const double* dg = diagb + (s & 1) * k;
+        double* dgn = diagb + ((s + 1) & 1) * k;
+        const double r = rbuf[s & 1];
+        for (int x = tid; x < k; x += nt) prs[x] = pv[x] * r;
+        __syncthreads();
+        if (si >= 0) {
+            if (si == p) {
+                // the pivot's own row: a_pj -> a_pj / d, a_pp -> -1 / d
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (e < sn) a[e] = sj + e == p ? -r : prs[sj + e];
+            } else {
+                const double pvi = pv[si];
+                const double pri = prs[si];
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (e < sn) a[e] = sj + e == p ? pri : fma(-pvi, prs[sj + e], a[e]);
             }
-            W[i * k + c] = v;
+            if (si == qn) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (e < sn) pvn[sj + e] = a[e];
+            } else if (qn >= sj && qn < sj + sn) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (sj + e == qn) pvn[si] = a[e];
+            }
+            if (sj == si) dgn[si] = a[0];
+        } else if (tid == nwork && qn >= 0) {
+            // same FMA as the owner of (qn, qn): bitwise the same pivot
+            const double d = fma(-pv[qn], prs[qn], dg[qn]);
+            const bool bad = !(d > tol);
+            if (bad) sing = 1;
+            rbuf[(s + 1) & 1] = recip_fp64(bad ? 1.0 : d);
         }
         __syncthreads();
     }
-    // G^-1 = W^T D^-1 W on the upper triangle, mirrored into A
-    const int ntri = k * (k + 1) / 2;
-    for (int e = tid; e < ntri; e += nt) {
-        int c = 0, start = 0, rowlen = k;
-        while (e >= start + rowlen) {
-            start += rowlen;
-            ++c;
-            --rowlen;
+    // the array holds -G^-1 on the active indices and 0 elsewhere
+    if (si >= 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if (e >= sn) continue;
+            const int i = si, j = sj + e;
+            const double v = -a[e];
+            Ginv64[(size_t)i * k + j] = v;
+            Ginv64[(size_t)j * k + i] = v;
+            GinvT[(size_t)i * k + j] = (T)v;
+            GinvT[(size_t)j * k + i] = (T)v;
         }
-        const int d = c + (e - start);
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        if (act[c] && act[d]) {
-            int q = d;
-            for (; q + 3 < k; q += 4) {
-                s0 += W[q * k + c] * dinv[q] * W[q * k + d];
-                s1 += W[(q + 1) * k + c] * dinv[q + 1] * W[(q + 1) * k + d];
-                s2 += W[(q + 2) * k + c] * dinv[q + 2] * W[(q + 2) * k + d];
-                s3 += W[(q + 3) * k + c] * dinv[q + 3] * W[(q + 3) * k + d];
-            }
-            for (; q < k; ++q) s0 += W[q * k + c] * dinv[q] * W[q * k + d];
-        }
-        const double v = (s0 + s1) + (s2 + s3);
-        A[c * k + d] = v;
-        A[d * k + c] = v;
-    }
-    __syncthreads();
-    for (int e = tid; e < kk; e += nt) {
-        Ginv64[e] = A[e];
-        GinvT[e] = (T)A[e];
     }
     if (tid == 0) {
         if (sing) atomicOr(status, ST_SINGULAR);
@@ -595,18 +677,41 @@ cholesky_kernel(const double* __restrict__ G, int k, double* Ginv64,
     }
 }
 
-template <typename T>
-cudaError_t launch_cholesky(const double* G, int k, double* Ginv64, T* GinvT,
-                            unsigned* status, cudaStream_t st)
+template <typename T, int E>
+static cudaError_t launch_inverse_e(const double* G, int k, double* Ginv64, T* GinvT,
+                                    unsigned* status, cudaStream_t st, int nseg)
 {
-    const size_t kk8 = (size_t)k * k * sizeof(double);
-    const size_t extra = (size_t)k * (sizeof(double) + sizeof(int)) + 16;
-    const int w_smem = 2 * kk8 + extra <= 210 * 1024;
-    const size_t smem = kk8 * (w_smem ? 2 : 1) + extra;
-    int threads = k * k >= 256 ? 256 : ((k * k + 31) / 32) * 32;
-    if (threads < 32) threads = 32;
-    cholesky_kernel<T><<<1, threads, smem, st>>>(G, k, Ginv64, GinvT, status, w_smem);
-    return cudaGetLastError();
+    const int threads = (nseg + 31) / 32 * 32 + 32;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = inv_smem(k).total;
+    cfg.stream = st;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = hi;   // ahead of the concurrent SpMM's pending blocks
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gram_inverse_kernel<T, E>, G, k, Ginv64, GinvT, status);
+}
+
+template <typename T>
+cudaError_t launch_gram_inverse(const double* G, int k, double* Ginv64, T* GinvT,
+                                unsigned* status, cudaStream_t st)
+{
+    // the shortest segments that fit the block
+    int n = inv_segments(k, 4);
+    if (n <= kInvMaxWork) return launch_inverse_e<T, 4>(G, k, Ginv64, GinvT, status, st, n);
+    n = inv_segments(k, 8);
+    if (n <= kInvMaxWork) return launch_inverse_e<T, 8>(G, k, Ginv64, GinvT, status, st, n);
+    n = inv_segments(k, 16);
+    if (n <= kInvMaxWork) return launch_inverse_e<T, 16>(G, k, Ginv64, GinvT, status, st, n);
+    n = inv_segments(k, 32);
+    if (n <= kInvMaxWork) return launch_inverse_e<T, 32>(G, k, Ginv64, GinvT, status, st, n);
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -791,17 +896,14 @@ cudaError_t setup_factor()
     e = cudaFuncSetAttribute(emit_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(emit_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(cholesky_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(cholesky_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    return e;
 }
 
 #define ESPNMF_INST(T)                                                                         \
     template cudaError_t launch_emit<T>(const T*, int64_t, int64_t, int, int, const void*,       \
                                         const uint32_t*, EllDev, EllDev, bool, const T*,       \
                                         int64_t, double*, double*, int, cudaStream_t);          \
-    template cudaError_t launch_cholesky<T>(const double*, int, double*, T*, unsigned*,         \
+    template cudaError_t launch_gram_inverse<T>(const double*, int, double*, T*, unsigned*,         \
                                             cudaStream_t);                                      \
     template cudaError_t launch_norm2<T>(const T*, int64_t, double*, int, double*, cudaStream_t); \
     template cudaError_t launch_ell_dot<T>(int64_t, int, EllDev, const T*, int64_t, double*,    \

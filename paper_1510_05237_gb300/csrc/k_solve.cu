@@ -2,7 +2,7 @@
 //   X = Y (F^T F)^-1, then every entry that is not > 0 becomes +0,
 // written column-major (Xt[c * ldx + row]) for the per-column selection.
 //
-// (F^T F)^-1 comes from the FP64 Cholesky kernel, rounded to T, and stays in
+// (F^T F)^-1 comes from the FP64 Gram inverse kernel, rounded to T, and stays in
 // shared memory for all of a block's row tiles.  A tile of BM rows of Y is
 // staged transposed (Ys[d][r]); each thread owns a 4-row x 8-column block of
 // X, so per step d it loads 4 values of Y and 8 of the inverse (128-bit

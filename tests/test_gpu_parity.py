@@ -89,6 +89,28 @@ def test_step_parity_planted_scaled(compute):
     assert abs(E.espnmf_residual(ctx) - oracle.residual(U2, Ug)) < 1e-9
 
 
+@pytest.mark.parametrize("compute", [E.F64, E.F32])
+@pytest.mark.parametrize("k", [1, 3, 33, 64, 72])
+def test_step_parity_factor_widths(compute, k):
+    """Every factor row width: one 16-byte chunk (k <= 4), a partial second
+    chunk (k = 33), two full chunks (k = 64) and the per-lane gathers of
+    k > 64, each from a dense start (all rows heavy) and then from the
+    enforced iterate (light and heavy rows mixed)."""
+    A = planted_50k_100k(seed=7, scale=0.02)
+    U0 = uniform_init(A.n, k, 7)
+    t_u, t_v = max(1, A.n // 12), max(1, A.m // 15)
+    ctx, Ug, Vg = step_parity(A, k, t_u, t_v, U0, E.TOPT_COLUMN, compute, f"k={k}")
+    Ao, _ = as_used(A, U0, compute)
+    E.espnmf_als_update_V(ctx)
+    V2 = E.espnmf_get_factor(ctx, E.V)
+    Vo, Vpre = oracle.update_V(Ao, Ug, t_v, oracle.COLUMN, return_pre=True)
+    compare_factor(V2, Vo, Vpre, t_v, E.TOPT_COLUMN, TOL[compute], f"k={k} V2")
+    E.espnmf_als_update_U(ctx)
+    U2 = E.espnmf_get_factor(ctx, E.U)
+    Uo, Upre = oracle.update_U(Ao, V2, t_u, oracle.COLUMN, return_pre=True)
+    compare_factor(U2, Uo, Upre, t_u, E.TOPT_COLUMN, TOL[compute], f"k={k} U2")
+
+
 def test_full_size_planted_50k_100k_fp32():
     """The benchmarked workload (~10M nnz, k=50, t=1000) in FP32, launched as
     the benchmark launches it, both half-steps compared in full."""
@@ -288,3 +310,25 @@ def test_sweep_measures_on_gpu_iterates():
     U5, V5 = E.espnmf_get_factor(ctx, E.U), E.espnmf_get_factor(ctx, E.V)
     assert abs(R[0] - oracle.residual(U5, U4)) < 1e-12
     assert abs(Es[0] - oracle.error_direct(A, U5, V5)) < 1e-11
+
+
+def test_spmm_launch_shapes_give_identical_results():
+    """Every FP32 sparse-product shape (lane groups or lane-private heavy
+    gathers, any shared-memory carveout, or the tuner's choice) adds the same
+    products in the same order: the sweeps agree bitwise."""
+    A = planted_50k_100k(seed=2, scale=0.05)
+    U0 = uniform_init(A.n, 50, 2)
+    runs = []
+    for opts in [{}, {E.OPT_SPMM_GROUP: 1}, {E.OPT_SPMM_GROUP: 0},
+                 {E.OPT_SPMM_GROUP: 1, E.OPT_SPMM_CARVEOUT: 25},
+                 {E.OPT_SPMM_GROUP: 0, E.OPT_SPMM_CARVEOUT: 100}]:
+        ctx = make_ctx(A, 50, 120, 150, U0, E.TOPT_COLUMN, E.F32)
+        for o, v in opts.items():
+            E.espnmf_set_option(ctx, o, v)
+        R1, E1 = E.espnmf_iterate(ctx, 1)
+        R2, E2 = E.espnmf_iterate(ctx, 3)
+        runs.append((np.concatenate([R1, R2]), np.concatenate([E1, E2]),
+                     E.espnmf_get_factor(ctx, E.U), E.espnmf_get_factor(ctx, E.V)))
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            np.testing.assert_array_equal(a, b)
