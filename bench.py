@@ -292,7 +292,10 @@ def main():
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     dname, (dl, dms, dbytes) = dom
     hbm, src = peaks()
-    spmm = stats["spmm_sell"]
+    # both sparse products run the same kernel (spmm_sell_f32): one roofline
+    spmm = tuple(stats["spmm_AV"][i] + stats["spmm_AtU"][i] for i in range(3))
+    shapes = {name: dict(zip(("split", "carveout"), E.espnmf_spmm_config(ctx, prod)))
+              for name, prod in (("spmm_AV", 0), ("spmm_AtU", 1))}
     achieved = (spmm[2] / spmm[0]) / ((spmm[1] / spmm[0]) / 1000.0) / 1e9
     kstats = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1),
                   "share": v[1] / max(sum(x[1] for x in stats.values()), 1e-12)}
@@ -302,7 +305,7 @@ def main():
                 if src == "measured" else "fallback 6800 GB/s",
                 "bytes_per_launch": spmm[2] / spmm[0], "ms_per_launch": spmm[1] / spmm[0],
                 "traffic": kernel_traffic("spmm_sell"),
-                "dominant_by_time": dname}
+                "dominant_by_time": dname, "spmm_shapes": shapes}
     E.espnmf_destroy(ctx)
 
     # ---------------- FP64 form and the equal-error comparison ---------------

@@ -263,18 +263,25 @@ typedef enum {
      *   ESPNMF_OPT_SPMM_TUNE 1 (default): before its first captured sweep,
      *     espnmf_iterate times the candidate shapes on the current factors
      *     and keeps the fastest for each product (A V and A^T U); 0: fixed.
-     *   ESPNMF_OPT_SPMM_GROUP: 1 gathers nearly dense factor rows with
-     *     8-lane groups (k <= 64), 0 lane by lane; sets the shape of both
-     *     products and turns tuning off.
+     *   ESPNMF_OPT_SPMM_SPLIT: 1, 2 or 4 warps share a slice's output
+     *     columns (k >= 13 for more than 1); sets both products and turns
+     *     tuning off.
      *   ESPNMF_OPT_SPMM_CARVEOUT: preferred shared-memory carveout in percent
      *     (-1: the driver's choice); also turns tuning off. */
     ESPNMF_OPT_SPMM_TUNE = 3,
-    ESPNMF_OPT_SPMM_GROUP = 4,
+    ESPNMF_OPT_SPMM_SPLIT = 4,
     ESPNMF_OPT_SPMM_CARVEOUT = 5
 } espnmf_option;
 
 espnmf_status espnmf_set_option(espnmf_ctx *ctx, espnmf_option opt,
                                 int64_t value);
+
+/* espnmf_spmm_config -- the launch shape in use for a sparse product
+ * (product 0: A V of the U update, 1: A^T U of the V update): split = warps
+ * per slice, carveout in percent (-1: the driver's choice).  Reflects the
+ * tuner's pick once espnmf_iterate ran. */
+espnmf_status espnmf_spmm_config(espnmf_ctx *ctx, int32_t product, int32_t *split,
+                                 int32_t *carveout);
 
 /* Kernel statistics gathered while ESPNMF_OPT_PROFILE is on.
  * espnmf_kernel_stat_count gives the number of kernel kinds; for index i,

@@ -27,7 +27,7 @@ TOPT_COLUMN, TOPT_MATRIX, TOPT_NONE = 0, 1, 2
 U, V = 0, 1
 DENSE_ROWMAJOR, CSC, CSR = 0, 1, 2
 OPT_USE_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT = 0, 1, 2
-OPT_SPMM_TUNE, OPT_SPMM_GROUP, OPT_SPMM_CARVEOUT = 3, 4, 5
+OPT_SPMM_TUNE, OPT_SPMM_SPLIT, OPT_SPMM_CARVEOUT = 3, 4, 5
 
 
 class EspnmfError(RuntimeError):
@@ -93,6 +93,7 @@ def load():
             "espnmf_batch_ctx": [P, i32, ctypes.POINTER(P)],
             "espnmf_batch_set_option": [P, st, i64],
             "espnmf_batch_iterate": [P, i32, P, P, P],
+            "espnmf_spmm_config": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -117,7 +118,8 @@ def exported_symbols():
              "espnmf_launches_per_sweep", "espnmf_sync", "espnmf_enforce_topt_buffer",
              "espnmf_enforce_topt_buffer_noalloc", "espnmf_loss", "espnmf_grad",
              "espnmf_pg_step", "espnmf_batch_init", "espnmf_batch_destroy",
-             "espnmf_batch_ctx", "espnmf_batch_set_option", "espnmf_batch_iterate"]
+             "espnmf_batch_ctx", "espnmf_batch_set_option", "espnmf_batch_iterate",
+             "espnmf_spmm_config"]
     return {n: hasattr(lib, n) for n in names}
 
 
@@ -314,6 +316,14 @@ def espnmf_get_factor(ctx: Context, which: int, layout: int = DENSE_ROWMAJOR,
                                  idx.ctypes.data_as(ctypes.c_void_p),
                                  val.ctypes.data_as(ctypes.c_void_p), code, 0), ctx.handle)
     return ptr, idx[:nnz], val[:nnz]
+
+
+def espnmf_spmm_config(ctx: Context, product: int):
+    """(split, carveout) of product 0 (A V) or 1 (A^T U)."""
+    g, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().espnmf_spmm_config(ctx.handle, int(product), ctypes.byref(g), ctypes.byref(c)),
+           ctx.handle)
+    return g.value, c.value
 
 
 def espnmf_set_option(ctx: Context, opt: int, value: int):

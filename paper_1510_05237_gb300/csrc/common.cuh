@@ -118,11 +118,12 @@ inline __host__ __device__ int heavy_threshold(int ld) { return ld / 4 > 4 ? ld 
 // Launchers.  Every launcher enqueues on `st` and returns the CUDA error of
 // the launch.  T is float or double.
 
-// Launch shape of the FP32 sparse product: heavy rows by lane groups (k <=
-// 64) or lane-private, and the preferred shared-memory carveout in percent
-// (-1: the driver's choice).  Every shape computes bitwise the same Y.
+// Launch shape of the FP32 sparse product: the number of warps that share a
+// slice's output columns (1, 2 or 4; k >= 13 for more than one) and the
+// preferred shared-memory carveout in percent (-1: the driver's choice).
+// Every shape computes bitwise the same Y.
 struct SpmmConfig {
-    int group = 1;
+    int split = 1;
     int carveout = -1;
 };
 
@@ -235,7 +236,7 @@ void set_thread_error(const char* msg);
 
 // Kernel kinds the profiler keeps statistics for.
 enum KernelKind : int {
-    K_SPMM = 0, K_COMBINE, K_SOLVE, K_SELECT, K_EMIT, K_GRAM_REDUCE,
+    K_SPMM = 0, K_SPMM_T, K_COMBINE, K_SOLVE, K_SELECT, K_EMIT, K_GRAM_REDUCE,
     K_INVERSE, K_TO_COLMAJOR, K_NORM2, K_DOT, K_SCATTER, K_GRAD, K_LAMBDA, K_PG, K_COUNT
 };
 const char* kernel_name(int kind);

@@ -26,7 +26,7 @@ using namespace espnmf;
 namespace espnmf {
 const char* kernel_name(int kind)
 {
-    static const char* names[K_COUNT] = {"spmm_sell", "spmm_combine", "solve_project",
+    static const char* names[K_COUNT] = {"spmm_AV", "spmm_AtU", "spmm_combine", "solve_project",
                                          "select_topt", "emit", "gram_reduce",
                                          "gram_inverse", "to_colmajor", "norm2", "ell_dot",
                                          "scatter", "grad", "lambda_max", "pg_apply"};
@@ -406,7 +406,7 @@ espnmf_status do_spmm(espnmf_ctx* ctx, bool transA, const EllDev& F)
     const SellDev& S = transA ? ctx->sAt : ctx->sA;
     const double bytes = (double)S.nnz * (4.0 + ctx->esz) + (double)(S.rows + 1) * 8.0 +
                          (double)S.rows * ctx->k * ctx->esz;
-    TRY(run(ctx, K_SPMM, bytes, ctx->st, [&] {
+    TRY(run(ctx, transA ? K_SPMM_T : K_SPMM, bytes, ctx->st, [&] {
         const SpmmConfig cfg = ctx->spmm_cfg[transA ? 1 : 0];
         return is_f64(ctx) ? launch_spmm<double>(S, F, ctx->k, (double*)ctx->Y, ctx->ldy, cfg,
                                                  ctx->st, ctx->sm_count)
@@ -433,11 +433,11 @@ espnmf_status tune_spmm(espnmf_ctx* ctx)
     ctx->spmm_tuned = true;
     if (is_f64(ctx)) return ESPNMF_OK;
     std::vector<SpmmConfig> cands;
-    for (int g : {1, 0}) {
-        if (g == 1 && ctx->ldy > 64) continue;
-        for (int cv : {-1, 25, 50, 100}) {
+    for (int sp : {1, 2, 4}) {
+        if (sp > 1 && ctx->ldy < 16) continue;
+        for (int cv : {-1, 25, 50}) {
             SpmmConfig c;
-            c.group = g;
+            c.split = sp;
             c.carveout = cv;
             cands.push_back(c);
         }
@@ -1362,9 +1362,10 @@ espnmf_status espnmf_set_option(espnmf_ctx* ctx, espnmf_option opt, int64_t valu
         ctx->spmm_tune = value != 0;
         if (ctx->spmm_tune) ctx->spmm_tuned = false;
         return ESPNMF_OK;
-    case ESPNMF_OPT_SPMM_GROUP:
-        if (value != 0 && value != 1) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "group is 0 or 1");
-        ctx->spmm_cfg[0].group = ctx->spmm_cfg[1].group = (int)value;
+    case ESPNMF_OPT_SPMM_SPLIT:
+        if (value != 1 && value != 2 && value != 4)
+            return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "split is 1, 2 or 4");
+        ctx->spmm_cfg[0].split = ctx->spmm_cfg[1].split = (int)value;
         ctx->spmm_tune = false;
         drop_graphs(ctx);
         return ESPNMF_OK;
@@ -1484,6 +1485,17 @@ espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64
 }
 
 }  // extern "C"
+
+extern "C" espnmf_status espnmf_spmm_config(espnmf_ctx* ctx, int32_t product, int32_t* split,
+                                            int32_t* carveout)
+{
+    TRY(enter(ctx));
+    if (product != 0 && product != 1) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "product is 0 or 1");
+    const SpmmConfig& c = ctx->spmm_cfg[product];
+    if (split) *split = (is_f64(ctx) || ctx->ldy < 16) ? 1 : c.split;
+    if (carveout) *carveout = c.carveout;
+    return ESPNMF_OK;
+}
 
 // =================================================================================
 // Batched sweeps: many independent problems, one captured CUDA graph per sweep

@@ -34,8 +34,11 @@ __device__ inline double warp_sum(double v)
     return v;
 }
 
-constexpr int kEmitThreads = 128;   // 4 warps
-constexpr int kSlots = 40;          // heavy-Gram register slots per thread
+constexpr int kEmitThreads = 256;   // 8 warps
+constexpr int kSlots = 20;          // heavy-Gram register slots per thread
+
+// Upper-triangle index of (c, d), c <= d, row by row.
+__host__ __device__ inline int tri_index(int c, int d, int k) { return c * k - c * (c - 1) / 2 + (d - c); }
 
 template <typename T>
 struct EmitArgs {
@@ -67,7 +70,7 @@ static size_t emit_smem(int k, int ld, int nseg, int SL, int W)
 {
     using K = typename KeyBits<T>::K;
     return align16((size_t)nseg * sizeof(K)) + align16((size_t)nseg * 4) +
-           (size_t)W * align16((size_t)k * k * 8) +
+           (size_t)W * align16((size_t)k * (k + 1) / 2 * 8) +
            (size_t)W * (align16((size_t)32 * SL * 4) + align16((size_t)32 * SL * sizeof(T))) +
            align16((size_t)kEmitThreads * 4) + align16((size_t)ld * 8) + 64;
 }
@@ -78,8 +81,8 @@ emit_kernel(EmitArgs<T> a)
 {
     using K = typename KeyBits<T>::K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[4][4];
-    __shared__ int wcnt[4];
+    __shared__ double red[kEmitThreads / 32][4];
+    __shared__ int wcnt[kEmitThreads / 32];
     const int k = a.k, ld = a.ld, SL = a.SL;
     const int W = blockDim.x >> 5;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -89,7 +92,7 @@ emit_kernel(EmitArgs<T> a)
     uint32_t* scut = reinterpret_cast<uint32_t*>(p);
     p += align16((size_t)a.nseg * 4);
     double* Gall = reinterpret_cast<double*>(p);
-    p += (size_t)W * align16((size_t)k * k * 8);
+    p += (size_t)W * align16((size_t)k * (k + 1) / 2 * 8);
     int* stc_all = reinterpret_cast<int*>(p);
     p += (size_t)W * align16((size_t)32 * SL * 4);
     T* stv_all = reinterpret_cast<T*>(p);
@@ -98,7 +101,7 @@ emit_kernel(EmitArgs<T> a)
     p += align16((size_t)kEmitThreads * 4);
     double* drow = reinterpret_cast<double*>(p);
 
-    const size_t gstride = align16((size_t)k * k * 8) / 8;
+    const size_t gstride = align16((size_t)k * (k + 1) / 2 * 8) / 8;
     double* G = Gall + (size_t)warp * gstride;
     int* stc = stc_all + (size_t)warp * (align16((size_t)32 * SL * 4) / 4);
     T* stv = stv_all + (size_t)warp * (align16((size_t)32 * SL * sizeof(T)) / sizeof(T));
@@ -106,7 +109,7 @@ emit_kernel(EmitArgs<T> a)
         stau[c] = a.tau[c];
         scut[c] = a.cut[c];
     }
-    for (int e = lane; e < k * k; e += 32) G[e] = 0.0;
+    for (int e = lane; e < k * (k + 1) / 2; e += 32) G[e] = 0.0;
     __syncthreads();
 
     const bool matrix = a.mode == TOPT_MATRIX;
@@ -206,7 +209,7 @@ emit_kernel(EmitArgs<T> a)
                 const double va = (double)jv[ia];
                 for (int ib = ia + lane; ib < Lj; ib += 32) {
                     const int cb = jc[ib];
-                    G[ca < cb ? ca * k + cb : cb * k + ca] += va * (double)jv[ib];
+                    G[ca < cb ? tri_index(ca, cb, k) : tri_index(cb, ca, k)] += va * (double)jv[ib];
                 }
             }
             __syncwarp();
@@ -271,7 +274,7 @@ emit_kernel(EmitArgs<T> a)
         if (cd[s] < 0) continue;
         const int c = cd[s] >> 16, d = cd[s] & 0xffff;
         double v = acc[s];
-        for (int w = 0; w < W; ++w) v += Gall[(size_t)w * gstride + c * k + d];
+        for (int w = 0; w < W; ++w) v += Gall[(size_t)w * gstride + tri_index(c, d, k)];
         a.gram_part[(size_t)(c * k + d) * P + blockIdx.x] = v;
         if (c != d) a.gram_part[(size_t)(d * k + c) * P + blockIdx.x] = v;
     }
@@ -285,7 +288,7 @@ emit_kernel(EmitArgs<T> a)
         }
         const int d = c + (e - start);
         double v = 0.0;
-        for (int w = 0; w < W; ++w) v += Gall[(size_t)w * gstride + c * k + d];
+        for (int w = 0; w < W; ++w) v += Gall[(size_t)w * gstride + tri_index(c, d, k)];
         a.gram_part[(size_t)(c * k + d) * P + blockIdx.x] = v;
         if (c != d) a.gram_part[(size_t)(d * k + c) * P + blockIdx.x] = v;
     }
@@ -341,16 +344,16 @@ cudaError_t launch_emit(const T* Xt, int64_t ldx, int64_t rows, int k, int mode,
     a.ldy = ldy;
     a.gram_part = gram_part;
     a.scal_part = scal_part;
-    // 4 warps unless shared memory says otherwise; the heavy rows' Gram
-    // uses register slots when they cover the triangle, else every row is
-    // staged for the pair loop
-    int W = 4;
+    // 8 warps unless shared memory says otherwise (two blocks per SM need
+    // at most ~110 KB each); the heavy rows' Gram uses register slots when
+    // they cover the triangle, else every row is staged for the pair loop
+    int W = kEmitThreads / 32;
     size_t smem = 0;
     for (;;) {
         a.heavy_gram = cur.dense != nullptr && ntri <= kSlots * W * 32;
         a.SL = a.heavy_gram ? (cur.heavy - 1 > 0 ? cur.heavy - 1 : 1) : k;
         smem = emit_smem<T>(k, cur.ld, a.nseg, a.SL, W);
-        if (smem <= 200 * 1024 || W == 1) break;
+        if (smem <= 110 * 1024 || W == 1) break;
         --W;
     }
     emit_kernel<T><<<nblocks, W * 32, smem, st>>>(a);

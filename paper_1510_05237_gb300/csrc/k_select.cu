@@ -15,10 +15,15 @@
 //   then    the remaining bits are resolved by radix rounds over the
 //           candidates only, and ties by a radix select over their indices.
 // One thread-block cluster (up to 8 CTAs) owns a column (or the whole
-// matrix); each CTA keeps its slice of the data in shared memory when it
-// fits, and the CTAs add their histograms through distributed shared memory.
-// If any CTA's candidates overflow its list, the cluster resolves the bucket
-// with passes over the data instead (same result, slower).
+// matrix); each CTA reads its slice of the column straight from global
+// memory (the candidate was just written, so it is in the L2) with 16-byte
+// loads, and the CTAs add their histograms through distributed shared
+// memory.  Shared memory holds only the histogram and the candidate list, so
+// several clusters share an SM.  Histogram updates are aggregated per warp
+// (lanes with the same bucket add once), which matters because the positive
+// entries of a column crowd into a few buckets.  If any CTA's candidates
+// overflow its list, the cluster resolves the bucket with passes over the
+// data instead (same result, slower).
 //
 // Output per segment s (column, or 0 in matrix mode): tau[s] (bit pattern)
 // and cut[s]: an entry survives iff it is positive and its bits are > tau,
@@ -33,13 +38,14 @@ namespace cg = cooperative_groups;
 namespace espnmf {
 
 constexpr int kSelThreads = 512;
+constexpr int kSelMaxCluster = 2;
 
 template <typename T> struct Vec4Of;
 template <> struct Vec4Of<float> { using type = float4; };
 struct alignas(16) Double4x { double2 a, b; };
 template <> struct Vec4Of<double> { using type = Double4x; };
 constexpr int kHist = 2048;
-constexpr int kCandCap = 6144;   // candidates per CTA
+constexpr int kCandCap = 3072;   // candidates per CTA
 constexpr size_t kSelSmemMax = 210 * 1024;
 
 template <typename T>
@@ -58,9 +64,11 @@ struct ScanOut {
     unsigned long long total;
 };
 
-// Adds the cluster's histograms (first nb bins, 4 per thread) and finds the
-// bin where the running count -- from the top when `descending` -- reaches
-// `need`.  Every CTA computes the same result.
+// Adds the cluster's histograms (first nb bins, kBinsPerThread per thread)
+// and finds the bin where the running count -- from the top when
+// `descending` -- reaches `need`.  Every CTA computes the same result.
+constexpr int kBinsPerThread = kHist / kSelThreads;
+
 __device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int nb,
                                 unsigned long long need, bool descending,
                                 unsigned long long* wsum, unsigned long long* res)
@@ -68,16 +76,20 @@ __device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int 
     cluster.sync();   // every CTA's histogram is complete
     const int C = (int)cluster.num_blocks();
     const int tid = threadIdx.x;
-    unsigned long long v[4] = {0, 0, 0, 0};
-    for (int u = 0; u < 4; ++u) {
-        const int o = tid * 4 + u;
+    unsigned long long v[kBinsPerThread];
+#pragma unroll
+    for (int u = 0; u < kBinsPerThread; ++u) {
+        v[u] = 0;
+        const int o = tid * kBinsPerThread + u;
         if (o < nb) {
             const int b = descending ? nb - 1 - o : o;
             for (int r = 0; r < C; ++r) v[u] += cluster.map_shared_rank(hist, r)[b];
         }
     }
     cluster.sync();   // remote reads done: histograms may be reused
-    const unsigned long long local = v[0] + v[1] + v[2] + v[3];
+    unsigned long long local = 0;
+#pragma unroll
+    for (int u = 0; u < kBinsPerThread; ++u) local += v[u];
     const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     unsigned long long incl = local;
     for (int off = 1; off < 32; off <<= 1) {
@@ -103,9 +115,10 @@ __device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int 
     const unsigned long long total = wsum[nw - 1];
     if (start < need && start + local >= need) {
         unsigned long long cum = start;
-        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int u = 0; u < kBinsPerThread; ++u) {
             if (cum + v[u] >= need) {
-                const int o = tid * 4 + u;
+                const int o = tid * kBinsPerThread + u;
                 res[0] = (unsigned long long)(descending ? nb - 1 - o : o);
                 res[1] = cum;
                 break;
@@ -126,7 +139,7 @@ template <typename T>
 __global__ void __launch_bounds__(kSelThreads)
 select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
               int64_t t, int mode, typename KeyBits<T>::K* __restrict__ tau_out,
-              uint32_t* __restrict__ cut_out, int64_t cache_elems)
+              uint32_t* __restrict__ cut_out)
 {
     using K = typename KeyBits<T>::K;
     constexpr int TS = KeyBits<T>::top_shift;
@@ -138,7 +151,6 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
     unsigned* ccount = reinterpret_cast<unsigned*>(res + 2);
     K* ckey = reinterpret_cast<K*>(smem_raw + SelSmem<T>::ckey);
     uint32_t* cidx = reinterpret_cast<uint32_t*>(smem_raw + SelSmem<T>::cidx);
-    T* cache = reinterpret_cast<T*>(smem_raw + SelSmem<T>::data);
 
     const int C = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
@@ -150,7 +162,6 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
     const int64_t lo = (int64_t)crank * per < seg_len ? (int64_t)crank * per : seg_len;
     const int64_t hi = lo + per < seg_len ? lo + per : seg_len;
     const int nloc = (int)(hi - lo);
-    const bool cached = nloc <= cache_elems;
     const int tid = threadIdx.x;
     auto addr = [&](int64_t g) -> int64_t {
         if (!matrix) return (int64_t)seg * ldx + g;
@@ -172,39 +183,60 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
         }
         return;
     }
-    if (cached) {
+    // visits this CTA's entries with their keys: 16-byte loads (four in
+    // flight per thread) of the contiguous slice of a column; strided
+    // addressing in matrix mode.  The loop bound is uniform across a warp,
+    // so fn may use warp collectives; `ok` marks lanes holding an entry.
+    using V4 = typename Vec4Of<T>::type;
+    auto for_each = [&](auto&& fn) {
         if (!matrix) {
-            // contiguous, 16-byte aligned slice (lo and ldx are multiples of
-            // 4): 128-bit loads, four in flight per thread
             const T* src = Xt + (int64_t)seg * ldx + lo;
-            const int nv = nloc / 4;
-            using V4 = typename Vec4Of<T>::type;
             const V4* s4 = reinterpret_cast<const V4*>(src);
-            V4* d4 = reinterpret_cast<V4*>(cache);
-            int q = tid;
-            for (; q + 3 * (int)blockDim.x < nv; q += 4 * blockDim.x) {
-                const V4 a0 = s4[q], a1 = s4[q + blockDim.x], a2 = s4[q + 2 * blockDim.x],
-                         a3 = s4[q + 3 * blockDim.x];
-                d4[q] = a0;
-                d4[q + blockDim.x] = a1;
-                d4[q + 2 * blockDim.x] = a2;
-                d4[q + 3 * blockDim.x] = a3;
+            const int nv = nloc / 4;
+            const int span = (int)blockDim.x * 4;
+            const int nround = (nv + span - 1) / span * span;
+            for (int q0 = tid; q0 < nround; q0 += span) {
+                V4 v[4];
+                bool in[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * (int)blockDim.x;
+                    in[u] = q < nv;
+                    if (in[u]) v[u] = s4[q];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * (int)blockDim.x;
+                    const T* x = reinterpret_cast<const T*>(&v[u]);
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) fn(in[u] ? KeyBits<T>::of(x[w]) : (K)0, 4 * q + w, in[u]);
+                }
             }
-            for (; q < nv; q += blockDim.x) d4[q] = s4[q];
-            for (int e = nv * 4 + tid; e < nloc; e += blockDim.x) cache[e] = src[e];
+            // tail (fewer than 4 entries), the same for every warp's lanes
+            const int tail = nloc - nv * 4;
+            if (tail > 0) {
+                const bool in = tid < tail;
+                const int e = nv * 4 + (in ? tid : 0);
+                fn(in ? KeyBits<T>::of(src[e]) : (K)0, e, in);
+            }
         } else {
-            for (int e = tid; e < nloc; e += blockDim.x) cache[e] = Xt[addr(lo + e)];
+            const int nround = (nloc + (int)blockDim.x - 1) / (int)blockDim.x * (int)blockDim.x;
+            for (int e0 = 0; e0 < nround; e0 += blockDim.x) {
+                const int e = e0 + tid;
+                const bool in = e < nloc;
+                fn(in ? KeyBits<T>::of(Xt[addr(lo + e)]) : (K)0, e, in);
+            }
         }
-    }
-    auto key_at = [&](int e) -> K { return KeyBits<T>::of(cached ? cache[e] : Xt[addr(lo + e)]); };
+    };
+    auto key_at = [&](int e) -> K { return KeyBits<T>::of(Xt[addr(lo + e)]); };
 
     // ---- pass 1: histogram of the top 11 bits of the positive entries
     for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    for (int e = tid; e < nloc; e += blockDim.x) {
-        const K key = key_at(e);
-        if (key != 0) atomicAdd(&hist[(unsigned)(key >> TS) & (kHist - 1)], 1u);
-    }
+    const int lane = tid & 31;
+    for_each([&](K key, int, bool in) {
+        if (in && key != 0) atomicAdd(&hist[(unsigned)(key >> TS) & (kHist - 1)], 1u);
+    });
     __syncthreads();
     unsigned long long need = (unsigned long long)t;
     const ScanOut s1 = cluster_scan(cluster, hist, kHist, need, true, wsum, res);
@@ -222,16 +254,21 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
     // ---- pass 2: the bucket's entries into the candidate list
     if (tid == 0) *ccount = 0;
     __syncthreads();
-    for (int e = tid; e < nloc; e += blockDim.x) {
-        const K key = key_at(e);
-        if (key != 0 && (key >> shift) == (prefix >> shift)) {
-            const unsigned pos = atomicAdd(ccount, 1u);
+    for_each([&](K key, int e, bool in) {
+        const bool hit = in && key != 0 && (key >> shift) == (prefix >> shift);
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m == 0u) return;
+        unsigned base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(ccount, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (hit) {
+            const unsigned pos = base + (unsigned)__popc(m & ((1u << lane) - 1u));
             if (pos < (unsigned)kCandCap) {
                 ckey[pos] = key;
                 cidx[pos] = index_of(e);
             }
         }
-    }
+    });
     __syncthreads();
     const unsigned ncand = *ccount;
     __syncthreads();
@@ -323,21 +360,15 @@ cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
 {
     if (rows == 0) return cudaSuccess;
     const int nseg = mode == TOPT_MATRIX ? 1 : k;
-    int C = sm_count / nseg;
-    if (C > 8) C = 8;
-    if (C < 1) C = 1;
     const int64_t seg_len = mode == TOPT_MATRIX ? (int64_t)k * rows : rows;
-    int64_t per = (seg_len + C - 1) / C;
-    per = (per + 3) & ~(int64_t)3;
-    const size_t fixed = SelSmem<T>::data;
-    int64_t cache_elems = (int64_t)((kSelSmemMax - fixed) / sizeof(T));
-    size_t smem = fixed;
-    if (per <= cache_elems) {
-        smem += (size_t)per * sizeof(T);
-        cache_elems = per;
-    } else {
-        cache_elems = 0;
-    }
+    // about two clusters' CTAs per SM over all segments, at most 8 per
+    // cluster, at least 2048 entries per CTA
+    int C = (int)((2 * (int64_t)sm_count + nseg - 1) / nseg);
+    if (C > kSelMaxCluster) C = kSelMaxCluster;
+    const int64_t by_len = (seg_len + 2047) / 2048;
+    if (C > by_len) C = (int)by_len;
+    if (C < 1) C = 1;
+    const size_t smem = SelSmem<T>::data;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)C, (unsigned)nseg, 1);
     cfg.blockDim = dim3(kSelThreads, 1, 1);
@@ -352,7 +383,7 @@ cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
     cfg.numAttrs = 1;
     using K = typename KeyBits<T>::K;
     return cudaLaunchKernelEx(&cfg, select_kernel<T>, Xt, ldx, rows, k, t, mode,
-                              static_cast<K*>(tau), cut, cache_elems);
+                              static_cast<K*>(tau), cut);
 }
 
 // In-place projection + enforcement of a caller's dense rows x k buffer

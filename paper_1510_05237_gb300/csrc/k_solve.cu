@@ -2,14 +2,15 @@
 //   X = Y (F^T F)^-1, then every entry that is not > 0 becomes +0,
 // written column-major (Xt[c * ldx + row]) for the per-column selection.
 //
-// (F^T F)^-1 comes from the FP64 Gram inverse kernel, rounded to T, and stays in
-// shared memory for all of a block's row tiles.  A tile of BM rows of Y is
-// staged transposed (Ys[d][r]); each thread owns a 4-row x 8-column block of
-// X, so per step d it loads 4 values of Y and 8 of the inverse (128-bit
-// shared loads) for 32 FMAs.  Columns are split over G = ceil(k/8) thread
-// groups and rows over 256/G, so BM = 4 * (256 / G).  The four rows of a
-// thread are consecutive, so each output column is written with one 128-bit
-// store.  A NaN or Inf raises ST_NONFINITE (and is stored as +0).
+// (F^T F)^-1 comes from the FP64 Gram inverse kernel, rounded to T, and
+// stays in shared memory for all of a block's row tiles.  A tile of BM rows
+// of Y is staged transposed (Ys[d][r]); each thread owns a TR-row x
+// 8-column block of X (TR = 8 in FP32, 4 in FP64), so per step d it loads TR
+// values of Y and 8 of the inverse (128-bit shared loads) for 8 TR FMAs.
+// Columns are split over G = ceil(k/8) thread groups and rows over 256/G, so
+// BM = TR * (256 / G).  A thread's rows are consecutive, so each output
+// column is written with 128-bit stores.  A NaN or Inf raises ST_NONFINITE
+// (and is stored as +0).
 #include "common.cuh"
 
 namespace espnmf {
@@ -40,6 +41,11 @@ template <> struct Vec4<double> {
     }
 };
 
+// Rows of the output tile per thread: 8 in FP32 (8 x 8 accumulators), 4 in
+// FP64 (its 8-byte registers would otherwise crowd out occupancy).
+template <typename T> struct SolveTile { static constexpr int TR = 8; };
+template <> struct SolveTile<double> { static constexpr int TR = 4; };
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 solve_project_kernel(const T* __restrict__ Y, int64_t ldy, int64_t rows,
@@ -47,6 +53,7 @@ solve_project_kernel(const T* __restrict__ Y, int64_t ldy, int64_t rows,
                      const T* __restrict__ Ginv, T* __restrict__ Xt,
                      int64_t ldx, unsigned* status)
 {
+    constexpr int TR = SolveTile<T>::TR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Gs = reinterpret_cast<T*>(smem_raw);   // [k][kp8]
     T* Ys = Gs + (size_t)k * kp8;             // [k][BM]
@@ -57,7 +64,7 @@ solve_project_kernel(const T* __restrict__ Y, int64_t ldy, int64_t rows,
     }
     const int g = tid % G;
     const int rg = tid / G;
-    const bool active = rg < BM / 4;
+    const bool active = rg < BM / TR;
     bool bad = false;
     for (int64_t r0 = (int64_t)blockIdx.x * BM; r0 < rows; r0 += (int64_t)gridDim.x * BM) {
         __syncthreads();
@@ -77,18 +84,19 @@ solve_project_kernel(const T* __restrict__ Y, int64_t ldy, int64_t rows,
         }
         __syncthreads();
         if (active) {
-            T acc[4][8];
+            T acc[TR][8];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < TR; ++r)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[r][j] = T(0);
             for (int d = 0; d < k; ++d) {
-                T y[4], ga[4], gb[4];
-                Vec4<T>::load(Ys + d * BM + rg * 4, y);
+                T y[TR], ga[4], gb[4];
+#pragma unroll
+                for (int h = 0; h < TR; h += 4) Vec4<T>::load(Ys + d * BM + rg * TR + h, y + h);
                 Vec4<T>::load(Gs + d * kp8 + g * 8, ga);
                 Vec4<T>::load(Gs + d * kp8 + g * 8 + 4, gb);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
+                for (int r = 0; r < TR; ++r) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         acc[r][j] += y[r] * ga[j];
@@ -96,23 +104,24 @@ solve_project_kernel(const T* __restrict__ Y, int64_t ldy, int64_t rows,
                     }
                 }
             }
-            const int row0 = rg * 4;
+            const int row0 = rg * TR;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int c = g * 8 + j;
                 if (c >= k) continue;
-                T x[4];
+                T x[TR];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
+                for (int r = 0; r < TR; ++r) {
                     const T v = acc[r][j];
                     if (!isfinite(v)) bad = true;
                     x[r] = v > T(0) ? v : T(0);
                 }
                 T* dst = Xt + (int64_t)c * ldx + r0 + row0;
-                if (row0 + 4 <= nr) {
-                    Vec4<T>::store(dst, x);
+                if (row0 + TR <= nr) {
+#pragma unroll
+                    for (int h = 0; h < TR; h += 4) Vec4<T>::store(dst + h, x + h);
                 } else {
-                    for (int r = 0; r < 4; ++r)
+                    for (int r = 0; r < TR; ++r)
                         if (row0 + r < nr) dst[r] = x[r];
                 }
             }
@@ -126,13 +135,14 @@ cudaError_t launch_solve(const T* Y, int64_t ldy, int64_t rows, int k,
                          const T* Ginv, T* Xt, int64_t ldx, unsigned* status,
                          cudaStream_t st, int sm_count)
 {
+    constexpr int TR = SolveTile<T>::TR;
     if (rows == 0) return cudaSuccess;
     const int kp8 = (k + 7) / 8 * 8;
     const int G = kp8 / 8;
-    int R = 256 / G;                          // row groups of 4
+    int R = 256 / G;                          // row groups of TR rows
     // keep the staged tile within budget
-    while (R > 1 && ((size_t)k * kp8 + (size_t)k * 4 * R) * sizeof(T) > 200 * 1024) R /= 2;
-    const int BM = 4 * R;
+    while (R > 1 && ((size_t)k * kp8 + (size_t)k * TR * R) * sizeof(T) > 200 * 1024) R /= 2;
+    const int BM = TR * R;
     const size_t smem = ((size_t)k * kp8 + (size_t)k * BM) * sizeof(T);
     int64_t tiles = (rows + BM - 1) / BM;
     int64_t grid = (int64_t)sm_count * 2;

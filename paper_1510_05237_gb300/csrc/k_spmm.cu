@@ -15,24 +15,19 @@
 //     memory, slot c of thread tid at acc[c * blockDim + tid] -- a warp's
 //     lanes always touch 32 distinct banks whatever columns they update;
 //   heavy rows (nearly dense: the rows of the most frequent terms end up in
-//     almost every column's top-t) from the row's dense copy, in one of two
-//     shapes:
-//       lane-private: each lane reads its own entry's whole row (16-byte
-//         loads) into KP register accumulators;
-//       lane groups (k <= 64): the eight lanes of a group read each of the
-//         group's heavy rows together, lane j taking chunks j and j + 8, so
-//         a load instruction reads whole 128-byte lines; the group keeps the
-//         heavy sums of its eight segments spread over its lanes by column
-//         and moves them to their own lanes through shared memory once,
-//         after the loop.
-//     Lanes that each read 16 bytes of a different row are served at about
-//     one line per cycle by the L1, lane groups at up to a line per cycle
-//     per group; which shape wins depends on how many heavy rows stay in
-//     the L1 (its share of the SM's memory is the launch's carveout), so the
-//     host times both (SpmmConfig).  The shapes add the same products in the
-//     same order: the result does not depend on the choice.
-// The loop is software-pipelined: while a step's gathers run, the next
-// step's records and the step after's entries of A are already in flight.
+//     almost every column's top-t): each lane reads its own entry's row
+//     from the row's dense copy (16-byte loads) into register accumulators.
+// The number of warps that share a slice's columns (1, 2 or 4: fewer
+// registers and slots per thread, so more warps in flight) and the launch's
+// shared-memory carveout (the rest of the SM's memory is L1, which holds the
+// heavy rows) are a launch shape (SpmmConfig) timed by the host; all shapes
+// add the same products in the same order, so the result does not depend
+// on the choice.
+// The loop is software-pipelined: while a step's gathers run, the records
+// of the next step and the entries of A of the next two are in flight, and
+// the slice's whole run of A is prefetched into the L2 when the warp starts
+// (deeper register pipelines measured slower: they cost registers the heavy
+// gathers need).
 // Sums are taken in a fixed order (storage order per lane, a fixed tree
 // across lanes, chunk order for very long rows), so the product is bitwise
 // reproducible.
@@ -63,199 +58,160 @@ struct SpmmParams {
     T* partials; // npart x KP
 };
 
-// FP32.  Light rows by their records into shared-memory slots (both modes);
-// heavy rows either lane-private into KP register accumulators (GROUP =
-// false) or by lane groups into column-distributed registers (GROUP = true,
-// k <= 64).  The two modes add the same products in the same order, so they
-// give bitwise the same Y.
-template <int KP>
-struct V4Shape {
-    static constexpr int NCH = KP / 4;                 // 16-byte chunks of a row
-    static constexpr int NC2 = NCH > 8 ? NCH - 8 : 0;  // lanes j < NC2 take a second chunk
-    // heavy staging row stride: an odd number of chunks keeps the 128-bit
-    // reads of eight consecutive segments' rows on distinct banks
-    static constexpr int KPH = (NCH % 2 == 0) ? KP + 4 : KP;
+// FP32.  NS warps share a slice: warp h of the NS owns the output columns
+// [h * CW, min(KP, (h + 1) * CW)), CW = KP / NS rounded up to 4, for all 32
+// segments of the slice.  Each warp streams the slice's entries of A (the
+// NS warps read the same lines, mostly from L1), adds its columns of light
+// rows' values into its shared-memory slots and gathers its CW columns of
+// heavy rows (CW / 4 16-byte loads) into CW register accumulators.  A larger
+// NS means fewer registers and slots per thread, so more warps in flight
+// for the same shared memory, at the price of re-reading A and the records.
+// Every NS adds the same products in the same order.
+template <int KP, int NS>
+struct SplitShape {
+    static constexpr int CW = ((KP + NS - 1) / NS + 3) / 4 * 4;
 };
 
-template <int KP, bool GROUP>
-__global__ void __launch_bounds__(256, KP <= 64 ? 2 : 1)
+template <int KP, int NS>
+__global__ void __launch_bounds__(256, KP > 64 ? 1 : 2)
 spmm_sell_f32_kernel(SpmmParams<float> p)
 {
-    using S = V4Shape<KP>;
-    static_assert(!GROUP || KP <= 64, "lane groups cover at most 16 chunks");
+    constexpr int CW = SplitShape<KP, NS>::CW;
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int NL = GROUP ? 8 : 1;      // heavy accumulator rows per lane
-    constexpr int NA = GROUP ? 8 : KP;     // heavy accumulators per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int B = blockDim.x;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    float* slots = reinterpret_cast<float*>(smem_raw);                   // KP x B
-    const int64_t s = (int64_t)blockIdx.x * (B >> 5) + warp;
-    if (s >= p.nslices) return;
+    const int h = warp % NS;                  // column block of this warp
+    const int c0 = h * CW;
+    const int cw = KP - c0 < CW ? KP - c0 : CW;   // columns owned (> 0, multiple of 4)
+    float* slots = reinterpret_cast<float*>(smem_raw);                   // CW x B
+    const int64_t s = (int64_t)blockIdx.x * (B >> 5) / NS + warp / NS;
+    if (s >= p.nslices || cw <= 0) return;
     const int64_t seg = s * 32 + lane;
-    const int j = lane & 7;           // position in the lane group
-    const int gb = lane & 24;         // first lane of the group
 
-    float hacc[NL][NA];
+    float acc[CW];
 #pragma unroll
-    for (int L = 0; L < NL; ++L)
-#pragma unroll
-        for (int e = 0; e < NA; ++e) hacc[L][e] = 0.f;
+    for (int c = 0; c < CW; ++c) acc[c] = 0.f;
     float* my = slots + tid;
 #pragma unroll 4
-    for (int c = 0; c < KP; ++c) my[c * B] = 0.f;
+    for (int c = 0; c < CW; ++c) my[c * B] = 0.f;
 
     const int len = p.slice_len[s];
     const int64_t base = p.slice_ptr[s] + lane;
     const int32_t* __restrict__ idx = p.idx + base;
     const float* __restrict__ val = p.val + base;
     const uint4* __restrict__ rec = p.frec;
-    const float4* __restrict__ dense4 = reinterpret_cast<const float4*>(p.fdense);
+    const float4* __restrict__ dense4 = reinterpret_cast<const float4*>(p.fdense) + c0 / 4;
     const int dld4 = p.dld / 4;
     const int heavy = p.heavy;
     const int fld = p.fld;
-    bool any_heavy = false;
+    const unsigned ucw = (unsigned)cw;
 
+    // one value of a light row: column c (absolute) if this warp owns it
+    auto add = [&](unsigned c, float x) {
+        const unsigned r = c - (unsigned)c0;
+        if (r < ucw) my[r * B] += x;
+    };
     auto light = [&](int i, float a, const uint4& r) {
         const int cnt = record_cnt(r.x);
         if (cnt == 0 || cnt >= heavy) return;
-        my[((r.x >> 8) & 0xffu) * B] += a * __uint_as_float(r.y);
-        if (cnt > 1) my[((r.x >> 16) & 0xffu) * B] += a * __uint_as_float(r.z);
-        if (cnt > 2) my[(r.x >> 24) * B] += a * __uint_as_float(r.w);
+        add((r.x >> 8) & 0xffu, a * __uint_as_float(r.y));
+        if (cnt > 1) add((r.x >> 16) & 0xffu, a * __uint_as_float(r.z));
+        if (cnt > 2) add(r.x >> 24, a * __uint_as_float(r.w));
         if (cnt > 3) {
             const int32_t* cr = p.fcol + (int64_t)i * fld;
             const float* vr = p.fval + (int64_t)i * fld;
-            my[__ldg(cr + 3) * B] += a * __ldg(vr + 3);
+            add((unsigned)__ldg(cr + 3), a * __ldg(vr + 3));
             for (int q = 4; q < cnt; q += 4) {
                 const int4 cc = __ldg(reinterpret_cast<const int4*>(cr + q));
                 const float4 vv = __ldg(reinterpret_cast<const float4*>(vr + q));
-                my[cc.x * B] += a * vv.x;
-                if (q + 1 < cnt) my[cc.y * B] += a * vv.y;
-                if (q + 2 < cnt) my[cc.z * B] += a * vv.z;
-                if (q + 3 < cnt) my[cc.w * B] += a * vv.w;
+                add((unsigned)cc.x, a * vv.x);
+                if (q + 1 < cnt) add((unsigned)cc.y, a * vv.y);
+                if (q + 2 < cnt) add((unsigned)cc.z, a * vv.z);
+                if (q + 3 < cnt) add((unsigned)cc.w, a * vv.w);
             }
         }
     };
-    // lane-private: this lane's heavy entry, its whole dense row
-    auto heavy_lane = [&](int i, float a, bool h) {
-        if (!h) return;
+    // this lane's heavy entry: its CW columns of the dense row
+    auto heavy_row = [&](int i, float a) {
         const float4* r = dense4 + (int64_t)i * dld4;
 #pragma unroll
-        for (int q = 0; q < KP / 4; ++q) {
+        for (int q = 0; q < CW / 4; ++q) {
+            if (4 * q >= cw) break;
             const float4 v = __ldg(r + q);
-            hacc[0][(4 * q + 0) % NA] = fmaf(a, v.x, hacc[0][(4 * q + 0) % NA]);
-            hacc[0][(4 * q + 1) % NA] = fmaf(a, v.y, hacc[0][(4 * q + 1) % NA]);
-            hacc[0][(4 * q + 2) % NA] = fmaf(a, v.z, hacc[0][(4 * q + 2) % NA]);
-            hacc[0][(4 * q + 3) % NA] = fmaf(a, v.w, hacc[0][(4 * q + 3) % NA]);
+            acc[4 * q + 0] = fmaf(a, v.x, acc[4 * q + 0]);
+            acc[4 * q + 1] = fmaf(a, v.y, acc[4 * q + 1]);
+            acc[4 * q + 2] = fmaf(a, v.z, acc[4 * q + 2]);
+            acc[4 * q + 3] = fmaf(a, v.w, acc[4 * q + 3]);
         }
     };
-    // lane groups: the heavy entries of two steps; group g gathers, for each
-    // of its eight segments L, the dense rows of that segment's entries
-    auto heavy_group = [&](int i0, float a0, bool h0, int i1, float a1, bool h1) {
-        const unsigned m0 = __ballot_sync(FULL, h0);
-        const unsigned m1 = __ballot_sync(FULL, h1);
-        if ((m0 | m1) == 0u) return;
-        any_heavy = true;
-#pragma unroll
-        for (int L = 0; L < NL; ++L) {
-            const unsigned any0 = (m0 >> L) & 0x01010101u, any1 = (m1 >> L) & 0x01010101u;
-            if ((any0 | any1) == 0u) continue;
-            const int src = gb | L;
-            const int r0 = __shfl_sync(FULL, i0, src);
-            const float c0 = __shfl_sync(FULL, a0, src);
-            const int r1 = __shfl_sync(FULL, i1, src);
-            const float c1 = __shfl_sync(FULL, a1, src);
-            const bool g0 = (m0 >> src) & 1u, g1 = (m1 >> src) & 1u;
-            float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), y0 = x0, x1 = x0, y1 = x0;
-            if (g0 && j < S::NCH) x0 = __ldg(dense4 + (int64_t)r0 * dld4 + j);
-            if (g0 && j < S::NC2) y0 = __ldg(dense4 + (int64_t)r0 * dld4 + 8 + j);
-            if (g1 && j < S::NCH) x1 = __ldg(dense4 + (int64_t)r1 * dld4 + j);
-            if (g1 && j < S::NC2) y1 = __ldg(dense4 + (int64_t)r1 * dld4 + 8 + j);
-            const float f0 = g0 ? c0 : 0.f, f1 = g1 ? c1 : 0.f;
-            float* h = hacc[L];
-            h[0 % NA] = fmaf(f1, x1.x, fmaf(f0, x0.x, h[0 % NA]));
-            h[1 % NA] = fmaf(f1, x1.y, fmaf(f0, x0.y, h[1 % NA]));
-            h[2 % NA] = fmaf(f1, x1.z, fmaf(f0, x0.z, h[2 % NA]));
-            h[3 % NA] = fmaf(f1, x1.w, fmaf(f0, x0.w, h[3 % NA]));
-            if (S::NC2 > 0) {
-                h[4 % NA] = fmaf(f1, y1.x, fmaf(f0, y0.x, h[4 % NA]));
-                h[5 % NA] = fmaf(f1, y1.y, fmaf(f0, y0.y, h[5 % NA]));
-                h[6 % NA] = fmaf(f1, y1.z, fmaf(f0, y0.z, h[6 % NA]));
-                h[7 % NA] = fmaf(f1, y1.w, fmaf(f0, y0.w, h[7 % NA]));
-            }
-        }
-    };
-    auto load2 = [&](int pp, int& i0, float& a0, int& i1, float& a1) {
-        i0 = pp < len ? __ldcs(idx + (int64_t)pp * 32) : -1;
-        a0 = pp < len ? __ldcs(val + (int64_t)pp * 32) : 0.f;
-        i1 = pp + 1 < len ? __ldcs(idx + (int64_t)(pp + 1) * 32) : -1;
-        a1 = pp + 1 < len ? __ldcs(val + (int64_t)(pp + 1) * 32) : 0.f;
+    auto load2 = [&](int pp, int* ii, float* aa) {
+        ii[0] = pp < len ? __ldcs(idx + (int64_t)pp * 32) : -1;
+        aa[0] = pp < len ? __ldcs(val + (int64_t)pp * 32) : 0.f;
+        ii[1] = pp + 1 < len ? __ldcs(idx + (int64_t)(pp + 1) * 32) : -1;
+        aa[1] = pp + 1 < len ? __ldcs(val + (int64_t)(pp + 1) * 32) : 0.f;
     };
     const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    auto rec2 = [&](const int* ii, uint4* rr) {
+        rr[0] = ii[0] >= 0 ? __ldg(rec + ii[0]) : zero4;
+        rr[1] = ii[1] >= 0 ? __ldg(rec + ii[1]) : zero4;
+    };
 
-    // stage j: entries (j, j+1) gathered; stage j+2's records and j+4's
-    // entries are loaded meanwhile
-    int i0, i1, n0, n1;
-    float a0, a1, b0, b1;
-    load2(0, i0, a0, i1, a1);
-    load2(2, n0, b0, n1, b1);
-    uint4 r0 = i0 >= 0 ? __ldg(rec + i0) : zero4;
-    uint4 r1 = i1 >= 0 ? __ldg(rec + i1) : zero4;
+    // The slice's entries of A are one contiguous run per array: ask the
+    // L2 for all of it now, so that the loads below wait on the L2 rather
+    // than on HBM.
+    if (lane == 0 && len > 0) {
+        const unsigned bytes = (unsigned)len * 128u;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                     :: "l"(p.idx + p.slice_ptr[s]), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                     :: "l"(p.val + p.slice_ptr[s]), "r"(bytes) : "memory");
+    }
+
+    // Step pairs in flight: entries of A for the next DA pairs, records
+    // (which need the entries' row index) for the next DR pairs.
+    constexpr int DA = 2, DR = 1;
+    int I[DA][2];
+    float Av[DA][2];
+    uint4 Rc[DR][2];
+#pragma unroll
+    for (int q = 0; q < DA; ++q) load2(2 * q, I[q], Av[q]);
+#pragma unroll
+    for (int q = 0; q < DR; ++q) rec2(I[q], Rc[q]);
     for (int p0 = 0; p0 < len; p0 += 2) {
-        const uint4 q0 = n0 >= 0 ? __ldg(rec + n0) : zero4;
-        const uint4 q1 = n1 >= 0 ? __ldg(rec + n1) : zero4;
-        int m0, m1;
-        float e0, e1;
-        load2(p0 + 4, m0, e0, m1, e1);
-        const bool h0 = record_cnt(r0.x) >= heavy, h1 = record_cnt(r1.x) >= heavy;
-        light(i0, a0, r0);
-        light(i1, a1, r1);
-        if constexpr (GROUP) {
-            heavy_group(i0, a0, h0, i1, a1, h1);
-        } else {
-            heavy_lane(i0, a0, h0);
-            heavy_lane(i1, a1, h1);
+        int ni[2];
+        float na[2];
+        uint4 nr[2];
+        load2(p0 + 2 * DA, ni, na);
+        rec2(I[DR], nr);
+        light(I[0][0], Av[0][0], Rc[0][0]);
+        light(I[0][1], Av[0][1], Rc[0][1]);
+        if (record_cnt(Rc[0][0].x) >= heavy) heavy_row(I[0][0], Av[0][0]);
+        if (record_cnt(Rc[0][1].x) >= heavy) heavy_row(I[0][1], Av[0][1]);
+#pragma unroll
+        for (int q = 0; q < DA - 1; ++q) {
+            I[q][0] = I[q + 1][0];
+            I[q][1] = I[q + 1][1];
+            Av[q][0] = Av[q + 1][0];
+            Av[q][1] = Av[q + 1][1];
         }
-        i0 = n0; i1 = n1; a0 = b0; a1 = b1; r0 = q0; r1 = q1;
-        n0 = m0; n1 = m1; b0 = e0; b1 = e1;
+        I[DA - 1][0] = ni[0];
+        I[DA - 1][1] = ni[1];
+        Av[DA - 1][0] = na[0];
+        Av[DA - 1][1] = na[1];
+#pragma unroll
+        for (int q = 0; q < DR - 1; ++q) {
+            Rc[q][0] = Rc[q + 1][0];
+            Rc[q][1] = Rc[q + 1][1];
+        }
+        Rc[DR - 1][0] = nr[0];
+        Rc[DR - 1][1] = nr[1];
     }
 
-    float acc[KP];
-    if constexpr (GROUP) {
-        if (__any_sync(FULL, any_heavy)) {
-            // group g's column-distributed sums -> H[segment][column]; each
-            // group writes whole 128-byte runs of one segment's row
-            float* H = slots + (size_t)KP * B + (size_t)warp * 32 * S::KPH;
 #pragma unroll
-            for (int L = 0; L < NL; ++L) {
-                float* hr = H + (gb | L) * S::KPH;
-                if (j < S::NCH)
-                    *reinterpret_cast<float4*>(hr + 4 * j) =
-                        make_float4(hacc[L][0], hacc[L][1 % NA], hacc[L][2 % NA], hacc[L][3 % NA]);
-                if (j < S::NC2)
-                    *reinterpret_cast<float4*>(hr + 32 + 4 * j) =
-                        make_float4(hacc[L][4 % NA], hacc[L][5 % NA], hacc[L][6 % NA], hacc[L][7 % NA]);
-            }
-            __syncwarp();
-            const float* mine = H + lane * S::KPH;
-#pragma unroll
-            for (int q = 0; q < S::NCH; ++q) {
-                const float4 h = *reinterpret_cast<const float4*>(mine + 4 * q);
-                acc[4 * q + 0] = h.x + my[(4 * q + 0) * B];
-                acc[4 * q + 1] = h.y + my[(4 * q + 1) * B];
-                acc[4 * q + 2] = h.z + my[(4 * q + 2) * B];
-                acc[4 * q + 3] = h.w + my[(4 * q + 3) * B];
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < KP; ++c) acc[c] = my[c * B];
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < KP; ++c) acc[c] = hacc[0][c % NA] + my[c * B];
-    }
+    for (int c = 0; c < CW; ++c) acc[c] += c < cw ? my[c * B] : 0.f;
     // combine the lanes [head, end) of each row: fixed tree, lane head
     // ends with the row's sum
     const int grp = p.seg_grp[seg];
@@ -264,7 +220,7 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
     for (int off = 1; off < maxg; off <<= 1) {
         const bool take = lane + off < end;
 #pragma unroll
-        for (int c = 0; c < KP; ++c) {
+        for (int c = 0; c < CW; ++c) {
             const float v = __shfl_down_sync(FULL, acc[c], off);
             if (take) acc[c] += v;
         }
@@ -272,11 +228,12 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
     const int row = p.seg_row[seg];
     if (row < 0 || lane != head) return;
     const int part = p.seg_part[seg];
-    float* out = part < 0 ? p.Y + (int64_t)row * KP : p.partials + (int64_t)part * KP;
+    float* out = (part < 0 ? p.Y + (int64_t)row * KP : p.partials + (int64_t)part * KP) + c0;
     float4* o4 = reinterpret_cast<float4*>(out);
 #pragma unroll
-    for (int q = 0; q < KP / 4; ++q)
-        o4[q] = make_float4(acc[4 * q + 0], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    for (int q = 0; q < CW / 4; ++q)
+        if (4 * q < cw)
+            o4[q] = make_float4(acc[4 * q + 0], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
 }
 
 // FP64 (the plain form): every gather into shared-memory accumulators.
@@ -370,19 +327,21 @@ static int spmm_block(int KP, size_t esz, size_t limit)
     return b;
 }
 
-template <int KP, bool GROUP>
-static cudaError_t launch_f32_mode(const SpmmParams<float>& p, int64_t nslices, int carveout,
-                                   cudaStream_t st)
+template <int KP, int NS>
+static cudaError_t launch_f32_split(const SpmmParams<float>& p, int64_t nslices, int carveout,
+                                    cudaStream_t st)
 {
-    const int B = spmm_block(KP, 4, 48 * 1024);
-    const int64_t wpb = B / 32;
-    const int64_t grid = (nslices + wpb - 1) / wpb;
-    // slots (plus, for lane groups, the per-warp heavy staging rows)
-    const size_t smem = (size_t)KP * B * 4 + (GROUP ? (size_t)B * V4Shape<KP>::KPH * 4 : 0);
+    constexpr int CW = SplitShape<KP, NS>::CW;
+    // NS warps per slice; about 48 KB of slots per block
+    int B = spmm_block(CW, 4, 48 * 1024);
+    B = B / (32 * NS) * (32 * NS);
+    if (B < 32 * NS) B = 32 * NS;
+    const int64_t spb = B / (32 * NS);   // slices per block
+    const int64_t grid = (nslices + spb - 1) / spb;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(B);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = (size_t)CW * B * 4;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     if (carveout >= 0) {
@@ -391,17 +350,18 @@ static cudaError_t launch_f32_mode(const SpmmParams<float>& p, int64_t nslices, 
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    return cudaLaunchKernelEx(&cfg, spmm_sell_f32_kernel<KP, GROUP>, p);
+    return cudaLaunchKernelEx(&cfg, spmm_sell_f32_kernel<KP, NS>, p);
 }
 
 template <int KP>
 static cudaError_t launch_f32(const SpmmParams<float>& p, int64_t nslices, SpmmConfig c,
                               cudaStream_t st)
 {
-    if constexpr (KP <= 64) {
-        if (c.group) return launch_f32_mode<KP, true>(p, nslices, c.carveout, st);
+    if constexpr (KP >= 16) {
+        if (c.split == 4) return launch_f32_split<KP, 4>(p, nslices, c.carveout, st);
+        if (c.split == 2) return launch_f32_split<KP, 2>(p, nslices, c.carveout, st);
     }
-    return launch_f32_mode<KP, false>(p, nslices, c.carveout, st);
+    return launch_f32_split<KP, 1>(p, nslices, c.carveout, st);
 }
 
 template <typename T>
@@ -469,11 +429,14 @@ cudaError_t launch_spmm_combine(const SellDev& S, int KP, T* Y, int64_t ldy,
 template <int KP>
 static cudaError_t setup_f32()
 {
-    cudaError_t e = cudaFuncSetAttribute(spmm_sell_f32_kernel<KP, false>,
+    cudaError_t e = cudaFuncSetAttribute(spmm_sell_f32_kernel<KP, 1>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
-    if constexpr (KP <= 64) {
+    if constexpr (KP >= 16) {
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(spmm_sell_f32_kernel<KP, true>,
+            e = cudaFuncSetAttribute(spmm_sell_f32_kernel<KP, 2>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(spmm_sell_f32_kernel<KP, 4>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
     }
     return e;

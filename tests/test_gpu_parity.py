@@ -313,15 +313,15 @@ def test_sweep_measures_on_gpu_iterates():
 
 
 def test_spmm_launch_shapes_give_identical_results():
-    """Every FP32 sparse-product shape (lane groups or lane-private heavy
-    gathers, any shared-memory carveout, or the tuner's choice) adds the same
-    products in the same order: the sweeps agree bitwise."""
+    """Every FP32 sparse-product shape (1, 2 or 4 warps per slice, any
+    shared-memory carveout, or the tuner's choice) adds the same products in
+    the same order: the sweeps agree bitwise."""
     A = planted_50k_100k(seed=2, scale=0.05)
     U0 = uniform_init(A.n, 50, 2)
     runs = []
-    for opts in [{}, {E.OPT_SPMM_GROUP: 1}, {E.OPT_SPMM_GROUP: 0},
-                 {E.OPT_SPMM_GROUP: 1, E.OPT_SPMM_CARVEOUT: 25},
-                 {E.OPT_SPMM_GROUP: 0, E.OPT_SPMM_CARVEOUT: 100}]:
+    for opts in [{}, {E.OPT_SPMM_SPLIT: 1}, {E.OPT_SPMM_SPLIT: 2}, {E.OPT_SPMM_SPLIT: 4},
+                 {E.OPT_SPMM_SPLIT: 2, E.OPT_SPMM_CARVEOUT: 25},
+                 {E.OPT_SPMM_SPLIT: 4, E.OPT_SPMM_CARVEOUT: 100}]:
         ctx = make_ctx(A, 50, 120, 150, U0, E.TOPT_COLUMN, E.F32)
         for o, v in opts.items():
             E.espnmf_set_option(ctx, o, v)
