@@ -125,8 +125,9 @@ class Clocks:
 
 
 def kernel_traffic(kernel: str):
-    """dram bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel's file; else None."""
+    """DRAM bytes per sparse product (mean of A V and A^T U, all of its
+    kernels) from the committed ncu summary, if it was taken on the current
+    source of the kernels' file; else None."""
     src = os.path.join(ROOT, "paper_1510_05237_gb300", "csrc", "k_spmm.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", f"ncu_{kernel}_{WORKLOAD}.md")
@@ -135,7 +136,7 @@ def kernel_traffic(kernel: str):
     except OSError:
         return None
     m1 = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
-    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m2 = re.search(r"dram_bytes_per_product:\s*([0-9.eE+]+)", txt)
     if m1 and m2 and m1.group(1) == sha:
         return float(m2.group(1))
     return None
@@ -292,19 +293,31 @@ def main():
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     dname, (dl, dms, dbytes) = dom
     hbm, src = peaks()
-    # both sparse products run the same kernel (spmm_sell_f32): one roofline
-    spmm = tuple(stats["spmm_AV"][i] + stats["spmm_AtU"][i] for i in range(3))
+    # The dominant step is the sparse product (A^T U and A V): its SELL
+    # kernel, its frequent-row kernel and the combine of split rows.  Its
+    # algorithmic bytes per product: A in CSR once (int32 index + f32 value
+    # per nonzero, int64 row pointers) and Y (rows x k f32) written once.
+    get = lambda name: stats.get(name, (0, 0.0, 0.0))
+    t_prod = sum(get(nm)[1] for nm in ("spmm_AV", "spmm_AtU", "spmm_freq_AV",
+                                       "spmm_freq_AtU", "spmm_combine")) / prof_steps
+    b_av = A.nnz * 8 + (A.n + 1) * 8 + A.n * K_TOPICS * 4
+    b_atu = A.nnz * 8 + (A.m + 1) * 8 + A.m * K_TOPICS * 4
+    ms_per_product = t_prod / 2.0
+    bytes_per_product = (b_av + b_atu) / 2.0
+    achieved = bytes_per_product / (ms_per_product / 1000.0) / 1e9
     shapes = {name: dict(zip(("split", "carveout"), E.espnmf_spmm_config(ctx, prod)))
               for name, prod in (("spmm_AV", 0), ("spmm_AtU", 1))}
-    achieved = (spmm[2] / spmm[0]) / ((spmm[1] / spmm[0]) / 1000.0) / 1e9
     kstats = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1),
                   "share": v[1] / max(sum(x[1] for x in stats.values()), 1e-12)}
               for k, v in stats.items() if v[0] > 0}
-    roofline = {"bound": "hbm", "kernel": "spmm_sell", "achieved": achieved, "peak": hbm,
+    roofline = {"bound": "hbm",
+                "kernel": "sparse product A^T U / A V (spmm_sell + spmm_freq + spmm_combine)",
+                "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"
                 if src == "measured" else "fallback 6800 GB/s",
-                "bytes_per_launch": spmm[2] / spmm[0], "ms_per_launch": spmm[1] / spmm[0],
-                "traffic": kernel_traffic("spmm_sell"),
+                "bytes_per_launch": bytes_per_product, "ms_per_launch": ms_per_product,
+                "per_launch": "one sparse product (mean of A V and A^T U)",
+                "traffic": kernel_traffic("spmm"),
                 "dominant_by_time": dname, "spmm_shapes": shapes}
     E.espnmf_destroy(ctx)
 

@@ -283,6 +283,17 @@ espnmf_status espnmf_set_option(espnmf_ctx *ctx, espnmf_option opt,
 espnmf_status espnmf_spmm_config(espnmf_ctx *ctx, int32_t product, int32_t *split,
                                  int32_t *carveout);
 
+/* espnmf_spmm_frequent -- the frequent part of a sparse product (product 0:
+ * A V, 1: A^T U; FP32 contexts only): h = number of gathered factor rows
+ * staged densely in shared memory (0: the product has no frequent part)
+ * and hnnz = the entries of A routed to them.  The rows are chosen once by
+ * espnmf_init: the gathered rows referenced by the most entries of A (the
+ * frequent terms, for A^T U), as many as fit a 200 KB table, kept when they
+ * carry at least a tenth of the entries.  The paper has no counterpart:
+ * this is a layout choice of the sparse product of Alg. 2 steps 1 and 3. */
+espnmf_status espnmf_spmm_frequent(espnmf_ctx *ctx, int32_t product, int32_t *h,
+                                   int64_t *hnnz);
+
 /* Kernel statistics gathered while ESPNMF_OPT_PROFILE is on.
  * espnmf_kernel_stat_count gives the number of kernel kinds; for index i,
  * espnmf_kernel_stat returns its name, launch count, summed event time (ms)

@@ -94,6 +94,7 @@ def load():
             "espnmf_batch_set_option": [P, st, i64],
             "espnmf_batch_iterate": [P, i32, P, P, P],
             "espnmf_spmm_config": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+            "espnmf_spmm_frequent": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -119,7 +120,7 @@ def exported_symbols():
              "espnmf_enforce_topt_buffer_noalloc", "espnmf_loss", "espnmf_grad",
              "espnmf_pg_step", "espnmf_batch_init", "espnmf_batch_destroy",
              "espnmf_batch_ctx", "espnmf_batch_set_option", "espnmf_batch_iterate",
-             "espnmf_spmm_config"]
+             "espnmf_spmm_config", "espnmf_spmm_frequent"]
     return {n: hasattr(lib, n) for n in names}
 
 
@@ -324,6 +325,14 @@ def espnmf_spmm_config(ctx: Context, product: int):
     _check(load().espnmf_spmm_config(ctx.handle, int(product), ctypes.byref(g), ctypes.byref(c)),
            ctx.handle)
     return g.value, c.value
+
+
+def espnmf_spmm_frequent(ctx: Context, product: int):
+    """(h, hnnz) of the frequent part of product 0 (A V) or 1 (A^T U)."""
+    h, e = ctypes.c_int32(), ctypes.c_int64()
+    _check(load().espnmf_spmm_frequent(ctx.handle, int(product), ctypes.byref(h), ctypes.byref(e)),
+           ctx.handle)
+    return h.value, e.value
 
 
 def espnmf_set_option(ctx: Context, opt: int, value: int):

@@ -29,11 +29,13 @@ template <> struct KeyBits<float> {
     using K = uint32_t;
     static constexpr int top_shift = 20;   // first histogram: bits 30..20
     __device__ static K of(float x) { return __float_as_uint(x); }
+    __device__ static float value(K k) { return __uint_as_float(k); }
 };
 template <> struct KeyBits<double> {
     using K = unsigned long long;
     static constexpr int top_shift = 52;   // first histogram: the exponent
     __device__ static K of(double x) { return (K)__double_as_longlong(x); }
+    __device__ static double value(K k) { return __longlong_as_double((long long)k); }
 };
 
 // Survival rule of the enforcement step, given the selector's threshold
@@ -57,9 +59,10 @@ constexpr int kMaxK = 256;
 // in adjacent lanes [head, end) of one slice (seg_grp = head << 8 | end);
 // the lanes' sums are combined inside the warp.  Rows too long for 32
 // segments are cut into chunks that write partial rows (seg_part >= 0),
-// added by spmm_combine.  Lane s%32 of slice s/32 owns segment s; its entry
-// p is at slice_ptr[s/32] + p*32 + s%32, so a warp reads 32 consecutive
-// entries per step.  Padding entries have idx = -1.
+// added by spmm_combine.  Lane l = s%32 of slice s/32 owns segment s; its
+// entry p is at slice_ptr[s/32] + (p/4)*128 + 4*l + p%4 (slice lengths are
+// multiples of 4), so a lane reads four entries with one 16-byte load and a
+// warp 512 consecutive bytes.  Padding entries have idx = -1.
 struct SellDev {
     int64_t rows = 0;        // output rows
     int64_t nseg = 0;
@@ -79,6 +82,23 @@ struct SellDev {
     int32_t* split_count = nullptr;// [nsplit]
     int64_t npart = 0;             // partial slots
     void* partials = nullptr;      // [npart * k] of T
+    // Frequent part (FP32 form only; h = 0: none).  The h gathered rows that
+    // the most entries reference (the frequent terms of A^T U) are staged
+    // densely in shared memory by spmm_h; their entries are kept out of the
+    // SELL arrays above and stored per output row instead: entries
+    // [hptr[r], hptr[r+1]) of row r, hidx = slot of the gathered row in the
+    // dense table, hval = the value.  The output rows are cut into chunks
+    // [hwarp[c], hwarp[c+1]) of about equal cost, which the warps of spmm_h
+    // take in turn.  slot_of[g] is the slot of gathered row g or -1.
+    int h = 0;
+    int64_t hnnz = 0;
+    int64_t* hptr = nullptr;       // [rows+1]
+    uint16_t* hidx = nullptr;      // [hnnz]
+    void* hval = nullptr;          // [hnnz] of T
+    int32_t* hwarp = nullptr;      // [hwarps+1] row ranges (work chunks)
+    int hwarps = 0;                // number of chunks
+    int* hcounter = nullptr;       // next chunk to take (reset before each launch)
+    int32_t* slot_of = nullptr;    // [rows of the gathered factor]
 };
 
 // A factor (U: n x k, V: m x k) in row-packed sparse form: row i holds
@@ -88,12 +108,24 @@ struct SellDev {
 // least `heavy` nonzeros also have a dense copy dense[i*ld + c] (zeros and
 // the padding columns included), which the sparse product reads instead of
 // the pairs.
+//
+// FP32 factors also keep, rewritten by every emit: a bitmask of the rows
+// that hold a nonzero (bit r % 32 of word r / 32), and, when the sparse
+// product that gathers this factor has a frequent part, the dense copy of
+// each frequent row (htab[slot * ld + c], zeros and padding included) with
+// a flag per slot telling whether the row is nonzero.
 struct EllDev {
     int32_t* cnt = nullptr;
     int32_t* col = nullptr;
     void* val = nullptr;
     void* dense = nullptr;   // dense copies of heavy rows, row stride dld
     uint4* rec = nullptr;    // FP32 factors: per-row record, see row_record
+    int64_t rows = 0;        // rows of the factor
+    uint32_t* nzmask = nullptr;      // FP32 factors: nonzero-row bitmask
+    const int32_t* hslot = nullptr;  // [rows] slot in htab or -1 (nullptr: no table)
+    void* htab = nullptr;            // [h][ld]
+    uint8_t* hnz = nullptr;          // [h]
+    int h = 0;
     int ld = 0;
     int dld = 0;
     int heavy = 1 << 30;
@@ -119,13 +151,17 @@ inline __host__ __device__ int heavy_threshold(int ld) { return ld / 4 > 4 ? ld 
 // the launch.  T is float or double.
 
 // Launch shape of the FP32 sparse product: the number of warps that share a
-// slice's output columns (1, 2 or 4; k >= 13 for more than one) and the
-// preferred shared-memory carveout in percent (-1: the driver's choice).
-// Every shape computes bitwise the same Y.
+// slice's output columns (1, 2 or 4; k >= 13 for more than one), the
+// preferred shared-memory carveout in percent (-1: the driver's choice) and
+// whether zero factor rows are skipped by the bitmask.  Every shape computes
+// bitwise the same Y.
 struct SpmmConfig {
     int split = 1;
     int carveout = -1;
+    int mask = 1;   // skip zero factor rows by the bitmask: 0 no, 1 from global, 2 from shared
 };
+// Largest bitmask (32-bit words, i.e. factor rows / 32) that mask = 2 stages.
+constexpr int kSellSmemMaskWords = 4096;
 
 template <typename T>
 cudaError_t launch_spmm(const SellDev& S, const EllDev& F, int k, T* Y,
@@ -133,6 +169,14 @@ cudaError_t launch_spmm(const SellDev& S, const EllDev& F, int k, T* Y,
 template <typename T>
 cudaError_t launch_spmm_combine(const SellDev& S, int k, T* Y, int64_t ldy,
                                 cudaStream_t st);
+// Frequent part of an FP32 product (S.h > 0): Y += the products of the
+// entries whose gathered row is one of the h frequent rows, from F.htab
+// staged in shared memory.  Runs after launch_spmm (and the combine), one
+// CTA per SM; `wait_limit` bounds the wait for the staging copy.
+constexpr int kHThreads = 1024;
+constexpr size_t kHTableBytes = 200 * 1024;   // largest dense table staged
+cudaError_t launch_spmm_h(const SellDev& S, const EllDev& F, float* Y, int sm_count,
+                          unsigned* status, long long wait_limit, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_solve(const T* Y, int64_t ldy, int64_t rows, int k,
@@ -142,10 +186,16 @@ cudaError_t launch_solve(const T* Y, int64_t ldy, int64_t rows, int k,
 // Threshold of the enforcement step per column (or one for the whole matrix)
 // from the column-major projected candidate Xt (k columns of length rows,
 // leading dimension ldx, entries >= +0): tau[s] (key) and cut[s] (tie index).
+// With rowbits (COLUMN mode), the survivors are also marked, bit c % 32 of
+// word rowbits[i * ceil(k/32) + c / 32] (the words must be zero), and the
+// FP64 sum of squares of each column's survivors is written to
+// diag_part[c * select_cluster(...) + r], r < select_cluster(...).
 template <typename T>
 cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
                           int64_t t, int mode, void* tau, uint32_t* cut,
-                          cudaStream_t st, int sm_count);
+                          cudaStream_t st, int sm_count, uint32_t* rowbits,
+                          double* diag_part);
+int select_cluster(int64_t rows, int k, int mode, int sm_count);
 
 // Projects and enforces a caller's dense rows x k buffer in place.
 template <typename T>
@@ -175,10 +225,29 @@ struct MetricsArgs {
     int hist_cap = 0;
 };
 
-cudaError_t launch_gram_reduce(const double* gram_part,
-                               const double* scal_part, int nparts, int k,
-                               double* G, double* scal, unsigned* counter,
-                               MetricsArgs m, cudaStream_t st);
+// Adds the Gram partials (upper triangle, entry-major: gram_part[e * nparts
+// + b] for e = tri(c, d), c <= d), the scalar partials (scal_part[j *
+// nscal_parts + b]) and, for diagonal entries, diag_parts per-column partials
+// (diag_part[c * diag_parts + j], or NULL) in a fixed order; writes the
+// symmetric G and, with m.enabled, R and E.
+cudaError_t launch_gram_reduce(const double* gram_part, const double* scal_part, int nparts,
+                               int nscal_parts, int k, const double* diag_part, int diag_parts,
+                               double* G, double* scal, unsigned* counter, MetricsArgs m,
+                               cudaStream_t st);
+
+// Survivor-driven emit (FP32, column mode): rowbits from launch_select's
+// marking (cleared here); nblocks blocks write partial columns [0, nblocks)
+// of gram_part (P columns in all: the off-diagonal products of the rows
+// with two or more nonzeros outside the frequent table) and of scal_part
+// (nblocks columns).
+cudaError_t launch_emit_s(const float* Xt, int64_t ldx, int64_t rows, int k, uint32_t* rowbits,
+                          EllDev cur, EllDev old, bool residual, const float* Y, int64_t ldy,
+                          double* gram_part, double* scal_part, int nblocks, int P,
+                          cudaStream_t st);
+// Off-diagonal Gram products of the frequent rows (F.htab), partial columns
+// [pcol0, pcol0 + nblocks) of gram_part.
+cudaError_t launch_gram_table(const EllDev& F, int k, double* gram_part, int P, int pcol0,
+                              int nblocks, cudaStream_t st);
 
 cudaError_t launch_error_metrics(const double* GU, const double* GV, int k,
                                  const double* A2, const double* cross,
@@ -198,9 +267,22 @@ template <typename T>
 cudaError_t launch_gram_inverse(const double* G, int k, double* Ginv64, T* GinvT,
                             unsigned* status, cudaStream_t st);
 
+// FP32 form, KP = factor_ld(k) <= 64 (k_chol.cu): the FP64 Cholesky factor
+// of G rounded to FP32 (strictly lower L and its transpose, KP x KP each,
+// then the reciprocal diagonal, KP) and the row solves X = Y G^-1 by
+// substitution, projected and written column-major.
+cudaError_t launch_cholesky(const double* G, int k, int KP, float* Ls, float* LTs, float* rd,
+                            unsigned* status, cudaStream_t st);
+cudaError_t launch_solve_chol(const float* Y, int64_t ldy, int64_t rows, int k, int KP,
+                              const float* L, const float* LT, const float* rd, float* Xt,
+                              int64_t ldx, unsigned* status, cudaStream_t st, int sm_count);
+cudaError_t setup_chol();
+
+// out = sum of squares of val[0, count) and val2[0, count2) (val2 may be
+// NULL), in a fixed order.
 template <typename T>
-cudaError_t launch_norm2(const T* val, int64_t count, double* part,
-                         int nparts, double* out, cudaStream_t st);
+cudaError_t launch_norm2(const T* val, int64_t count, const T* val2, int64_t count2,
+                         double* part, int nparts, double* out, cudaStream_t st);
 
 // E for arbitrary U, V: cross term <U, Y> with Y = A V given.
 template <typename T>
@@ -237,7 +319,8 @@ void set_thread_error(const char* msg);
 // Kernel kinds the profiler keeps statistics for.
 enum KernelKind : int {
     K_SPMM = 0, K_SPMM_T, K_COMBINE, K_SOLVE, K_SELECT, K_EMIT, K_GRAM_REDUCE,
-    K_INVERSE, K_TO_COLMAJOR, K_NORM2, K_DOT, K_SCATTER, K_GRAD, K_LAMBDA, K_PG, K_COUNT
+    K_INVERSE, K_TO_COLMAJOR, K_NORM2, K_DOT, K_SCATTER, K_GRAD, K_LAMBDA, K_PG,
+    K_SPMM_H, K_SPMM_H_T, K_GRAM_TABLE, K_COUNT
 };
 const char* kernel_name(int kind);
 

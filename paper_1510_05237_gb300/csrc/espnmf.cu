@@ -29,7 +29,8 @@ const char* kernel_name(int kind)
     static const char* names[K_COUNT] = {"spmm_AV", "spmm_AtU", "spmm_combine", "solve_project",
                                          "select_topt", "emit", "gram_reduce",
                                          "gram_inverse", "to_colmajor", "norm2", "ell_dot",
-                                         "scatter", "grad", "lambda_max", "pg_apply"};
+                                         "scatter", "grad", "lambda_max", "pg_apply",
+                                         "spmm_freq_AV", "spmm_freq_AtU", "gram_table"};
     return kind >= 0 && kind < K_COUNT ? names[kind] : "?";
 }
 }  // namespace espnmf
@@ -51,6 +52,7 @@ struct Factor {
     double* G = nullptr;       // k x k FP64 Gram of the current factor
     double* Ginv64 = nullptr;  // k x k FP64 inverse
     void* GinvT = nullptr;     // k x k inverse in T
+    float* Lf = nullptr;       // FP32 form, k <= 64: Cholesky factor (L, L^T, 1/diag)
     bool chol_pending = true;
     bool valid = false;        // holds a value (V is empty until the first update)
 };
@@ -111,6 +113,11 @@ struct espnmf_ctx {
     int hist_cap = 0;
     unsigned* status_d = nullptr;
     unsigned* status_h = nullptr;
+    // FP32 form, column mode: the selector marks the survivors (rowbits,
+    // ceil(k/32) words per row of the larger factor, kept zero between
+    // updates) and writes the Gram diagonal (diag_part, k x cluster size)
+    uint32_t* rowbits = nullptr;
+    double* diag_part = nullptr;
 
     bool have_R = false;
     bool Y_is_AV = false;
@@ -277,7 +284,10 @@ struct SellHost {
 // is cut into chunks of up to 32 segments; each chunk writes a partial row
 // that spmm_combine adds in chunk order.  Groups are sorted by segment
 // length (longest first) and packed greedily, so the lanes of a slice walk
-// segments of about the same length.
+// segments of about the same length.  Entry p of lane l of slice s is
+// stored at slice_ptr[s] + (p / 4) * 128 + 4 l + p % 4 (SELL-32 with groups
+// of four), so each lane reads four entries with one 16-byte load and a
+// warp reads 512 consecutive bytes.
 template <typename T>
 void build_sell(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
                 SellHost<T>& S)
@@ -346,9 +356,12 @@ void build_sell(int64_t rows, const int64_t* ptr, const int32_t* ind, const doub
     S.nslices = S.nseg / 32;
     S.slice_ptr.assign(S.nslices + 1, 0);
     S.slice_len.assign(S.nslices, 0);
+    // a slice's length is its longest segment rounded up to 4: each lane's
+    // entries are stored in groups of four, so a 16-byte load brings four
     for (int64_t s = 0; s < S.nslices; ++s) {
         int mx = 0;
         for (int l = 0; l < 32; ++l) mx = std::max(mx, lanes[s * 32 + l].len);
+        mx = (mx + 3) / 4 * 4;
         S.slice_len[s] = mx;
         S.slice_ptr[s + 1] = S.slice_ptr[s] + (int64_t)mx * 32;
     }
@@ -363,12 +376,117 @@ void build_sell(int64_t rows, const int64_t* ptr, const int32_t* ind, const doub
         S.seg_row[g] = ln.row;
         S.seg_part[g] = ln.part;
         S.seg_grp[g] = ln.grp;
-        int64_t o = S.slice_ptr[g / 32] + g % 32;
-        for (int p = 0; p < ln.len; ++p, o += 32) {
-            S.idx[o] = ind[ln.start + p];
-            S.val[o] = (T)vals[ln.start + p];
+        const int64_t o = S.slice_ptr[g / 32] + (g % 32) * 4;
+        for (int p = 0; p < ln.len; ++p) {
+            const int64_t at = o + (int64_t)(p / 4) * 128 + p % 4;
+            S.idx[at] = ind[ln.start + p];
+            S.val[at] = (T)vals[ln.start + p];
         }
     }
+}
+
+// The frequent part of an FP32 product.  The gathered rows that the most
+// entries reference (weight = entries per gathered row) are candidates when
+// they are referenced at least 4x as often as the average row (and at least
+// 16 times); up to kHTableBytes / (ld * 4) of them (and < 2^16) form the
+// table, in decreasing weight (ties: lower index first).  The part is kept
+// only if its entries are at least a tenth of all.  Returns h (0: none) and
+// fills slot_of.
+int choose_frequent(const std::vector<int64_t>& weight, int64_t nnz, int ld,
+                    std::vector<int32_t>& slot_of)
+{
+    const int64_t ng = (int64_t)weight.size();
+    slot_of.assign(ng, -1);
+    if (ng == 0 || nnz == 0) return 0;
+    const int64_t cap = std::min<int64_t>((int64_t)(kHTableBytes / ((size_t)ld * 4)), 65535);
+    const double floor_w = std::max(16.0, 4.0 * (double)nnz / (double)ng);
+    std::vector<int32_t> order;
+    for (int64_t g = 0; g < ng; ++g)
+        if ((double)weight[g] >= floor_w) order.push_back((int32_t)g);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return weight[a] > weight[b]; });
+    if ((int64_t)order.size() > cap) order.resize(cap);
+    int64_t covered = 0;
+    for (int32_t g : order) covered += weight[g];
+    if (order.empty() || covered * 10 < nnz) return 0;
+    for (size_t q = 0; q < order.size(); ++q) slot_of[order[q]] = (int32_t)q;
+    return (int)order.size();
+}
+
+// Splits a CSR matrix into the entries of frequent gathered rows (per
+// output row: slot and value) and the rest (a CSR matrix for build_sell).
+struct FreqHost {
+    int h = 0;
+    std::vector<int32_t> slot_of;
+    std::vector<int64_t> hptr;
+    std::vector<uint16_t> hidx;
+    std::vector<float> hval;
+    std::vector<int32_t> hwarp;
+};
+
+void split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
+                    FreqHost& F, std::vector<int64_t>& lptr, std::vector<int32_t>& lind,
+                    std::vector<double>& lval)
+{
+    F.hptr.assign(rows + 1, 0);
+    lptr.assign(rows + 1, 0);
+    for (int64_t r = 0; r < rows; ++r) {
+        int64_t nh = 0;
+        for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) nh += F.slot_of[ind[q]] >= 0;
+        F.hptr[r + 1] = F.hptr[r] + nh;
+        lptr[r + 1] = lptr[r] + (ptr[r + 1] - ptr[r] - nh);
+    }
+    F.hidx.resize(F.hptr[rows]);
+    F.hval.resize(F.hptr[rows]);
+    lind.resize(lptr[rows]);
+    lval.resize(lptr[rows]);
+    for (int64_t r = 0; r < rows; ++r) {
+        int64_t a = F.hptr[r], b = lptr[r];
+        for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) {
+            const int32_t sl = F.slot_of[ind[q]];
+            if (sl >= 0) {
+                F.hidx[a] = (uint16_t)sl;
+                F.hval[a++] = (float)vals[q];
+            } else {
+                lind[b] = ind[q];
+                lval[b++] = vals[q];
+            }
+        }
+    }
+}
+
+// Chunks of output rows for the warps of spmm_freq: contiguous ranges of
+// about equal cost (entries, plus a fixed cost per row that has any).
+void balance_frequent(int64_t rows, int nwarps, FreqHost& F)
+{
+    std::vector<int64_t> cost(rows + 1, 0);
+    for (int64_t r = 0; r < rows; ++r) {
+        const int64_t e = F.hptr[r + 1] - F.hptr[r];
+        cost[r + 1] = cost[r] + (e > 0 ? e + 8 : 0);
+    }
+    F.hwarp.assign(nwarps + 1, 0);
+    int64_t r = 0;
+    for (int w = 1; w < nwarps; ++w) {
+        const double target = (double)cost[rows] * w / nwarps;
+        while (r < rows && (double)cost[r] < target) ++r;
+        F.hwarp[w] = (int32_t)r;
+    }
+    F.hwarp[nwarps] = (int32_t)rows;
+}
+
+espnmf_status upload_frequent(espnmf_ctx* ctx, const FreqHost& H, SellDev& D)
+{
+    D.h = H.h;
+    D.hnnz = (int64_t)H.hidx.size();
+    D.hwarps = (int)H.hwarp.size() - 1;
+    TRY(dupload(ctx, &D.slot_of, H.slot_of.data(), H.slot_of.size() * 4));
+    TRY(dupload(ctx, &D.hptr, H.hptr.data(), H.hptr.size() * 8));
+    TRY(dupload(ctx, &D.hidx, H.hidx.data(), H.hidx.size() * 2));
+    TRY(dupload(ctx, &D.hval, H.hval.data(), H.hval.size() * 4));
+    TRY(dupload(ctx, &D.hwarp, H.hwarp.data(), H.hwarp.size() * 4));
+    TRY(dmalloc(ctx, &D.hcounter, sizeof(int)));
+    CU(cudaStreamSynchronize(ctx->st));
+    return ESPNMF_OK;
 }
 
 template <typename T>
@@ -404,8 +522,9 @@ bool is_f64(const espnmf_ctx* ctx) { return ctx->dt == ESPNMF_F64; }
 espnmf_status do_spmm(espnmf_ctx* ctx, bool transA, const EllDev& F)
 {
     const SellDev& S = transA ? ctx->sAt : ctx->sA;
-    const double bytes = (double)S.nnz * (4.0 + ctx->esz) + (double)(S.rows + 1) * 8.0 +
-                         (double)S.rows * ctx->k * ctx->esz;
+    // the SELL part: its entries (index + value), slice pointers, Y written
+    const double bytes = (double)S.nnz * (4.0 + ctx->esz) +
+                         (double)(S.nslices + 1) * 8.0 + (double)S.rows * ctx->ldy * ctx->esz;
     TRY(run(ctx, transA ? K_SPMM_T : K_SPMM, bytes, ctx->st, [&] {
         const SpmmConfig cfg = ctx->spmm_cfg[transA ? 1 : 0];
         return is_f64(ctx) ? launch_spmm<double>(S, F, ctx->k, (double*)ctx->Y, ctx->ldy, cfg,
@@ -418,6 +537,15 @@ espnmf_status do_spmm(espnmf_ctx* ctx, bool transA, const EllDev& F)
         TRY(run(ctx, K_COMBINE, cb, ctx->st, [&] {
             return is_f64(ctx) ? launch_spmm_combine<double>(S, (int)ctx->ldy, (double*)ctx->Y, ctx->ldy, ctx->st)
                                : launch_spmm_combine<float>(S, (int)ctx->ldy, (float*)ctx->Y, ctx->ldy, ctx->st);
+        }));
+    }
+    if (S.h > 0 && S.hnnz > 0) {
+        // entries (slot + value), row pointers, Y read and written back
+        const double hb = (double)S.hnnz * 6.0 + (double)(S.rows + 1) * 8.0 +
+                          2.0 * (double)S.rows * ctx->ldy * 4.0;
+        TRY(run(ctx, transA ? K_SPMM_H_T : K_SPMM_H, hb, ctx->st, [&] {
+            return launch_spmm_h(S, F, (float*)ctx->Y, ctx->sm_count, ctx->status_d,
+                                 ctx->wait_limit, ctx->st);
         }));
     }
     return ESPNMF_OK;
@@ -435,12 +563,15 @@ espnmf_status tune_spmm(espnmf_ctx* ctx)
     std::vector<SpmmConfig> cands;
     for (int sp : {1, 2, 4}) {
         if (sp > 1 && ctx->ldy < 16) continue;
-        for (int cv : {-1, 25, 50}) {
-            SpmmConfig c;
-            c.split = sp;
-            c.carveout = cv;
-            cands.push_back(c);
-        }
+        for (int cv : {-1, 25, 50})
+            for (int mk : {0, 1, 2}) {
+                if (mk == 2 && std::max(ctx->n, ctx->m) > 32ll * kSellSmemMaskWords) continue;
+                SpmmConfig c;
+                c.split = sp;
+                c.carveout = cv;
+                c.mask = mk;
+                cands.push_back(c);
+            }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CU(cudaEventCreate(&e0));
@@ -482,8 +613,17 @@ espnmf_status tune_spmm(espnmf_ctx* ctx)
     return ESPNMF_OK;
 }
 
+bool use_cholesky(const espnmf_ctx* ctx) { return !is_f64(ctx) && ctx->ldy <= 64; }
+
 espnmf_status do_gram_inverse(espnmf_ctx* ctx, Factor& F, cudaStream_t s)
 {
+    if (use_cholesky(ctx)) {
+        const int KP = (int)ctx->ldy;
+        return run(ctx, K_INVERSE, (double)ctx->k * ctx->k * 8.0 + 2.0 * KP * KP * 4.0, s, [&] {
+            return launch_cholesky(F.G, ctx->k, KP, F.Lf, F.Lf + KP * KP, F.Lf + 2 * KP * KP,
+                                   ctx->status_d, s);
+        });
+    }
     const double bytes = (double)ctx->k * ctx->k * (8.0 + 8.0 + ctx->esz);
     return run(ctx, K_INVERSE, bytes, s, [&] {
         return is_f64(ctx) ? launch_gram_inverse<double>(F.G, ctx->k, F.Ginv64, (double*)F.GinvT,
@@ -526,27 +666,76 @@ espnmf_status do_emit(espnmf_ctx* ctx, Factor& F, bool residual, const void* Y, 
         ma.hist_counter = ctx->hist_counter;
         ma.hist_cap = ctx->hist_cap;
     }
-    const double rb = (double)ctx->fin_blocks * ctx->k * ctx->k * 8.0;
+    const double rb = (double)ctx->fin_blocks * ctx->k * (ctx->k + 1) / 2 * 8.0;
     TRY(run(ctx, K_GRAM_REDUCE, rb, ctx->st, [&] {
-        return launch_gram_reduce(ctx->gram_part, ctx->scal_part, ctx->fin_blocks, ctx->k, F.G,
-                                  ctx->scal, ctx->gram_counter, ma, ctx->st);
+        return launch_gram_reduce(ctx->gram_part, ctx->scal_part, ctx->fin_blocks,
+                                  ctx->fin_blocks, ctx->k, nullptr, 0, F.G, ctx->scal,
+                                  ctx->gram_counter, ma, ctx->st);
     }));
     F.cur ^= 1;
     F.chol_pending = true;
     return ESPNMF_OK;
 }
 
-espnmf_status do_select(espnmf_ctx* ctx, int64_t rows, int64_t t)
+espnmf_status do_select(espnmf_ctx* ctx, int64_t rows, int64_t t, bool mark)
 {
     return run(ctx, K_SELECT, (double)rows * ctx->k * ctx->esz, ctx->st, [&] {
         return is_f64(ctx) ? launch_select<double>((const double*)ctx->Xt, ctx->ldx, rows, ctx->k,
                                                    t, ctx->mode, ctx->tau, ctx->cut, ctx->st,
-                                                   ctx->sm_count)
+                                                   ctx->sm_count, nullptr, nullptr)
                            : launch_select<float>((const float*)ctx->Xt, ctx->ldx, rows, ctx->k,
                                                   t, ctx->mode, ctx->tau, ctx->cut, ctx->st,
-                                                  ctx->sm_count);
+                                                  ctx->sm_count, mark ? ctx->rowbits : nullptr,
+                                                  mark ? ctx->diag_part : nullptr);
     });
 }
+
+// The half-step's survivors were marked by the selector (FP32 form, column
+// mode): writes factor F's next buffer from them, the Gram of the frequent
+// rows from the table, and reduces the Gram (and R, E with `metrics`).
+espnmf_status do_emit_survivors(espnmf_ctx* ctx, Factor& F, bool residual, const void* Y,
+                                bool metrics)
+{
+    EllDev& nxt = F.buf[F.cur ^ 1];
+    EllDev& cur = F.buf[F.cur];
+    const int Pe = ctx->fin_blocks;
+    const bool tab = nxt.h > 0;
+    const int P = Pe + (tab ? ctx->sm_count : 0);
+    const int ntri = ctx->k * (ctx->k + 1) / 2;
+    // the rows' survivor bits and counts, the survivors' values and pairs
+    const double bytes = (double)F.rows * (4.0 * ((ctx->k + 31) / 32) + 4.0 + 16.0) +
+                         (double)Pe * ntri * 8.0;
+    TRY(run(ctx, K_EMIT, bytes, ctx->st, [&] {
+        return launch_emit_s((const float*)ctx->Xt, ctx->ldx, F.rows, ctx->k, ctx->rowbits, nxt,
+                             cur, residual, (const float*)Y, ctx->ldy, ctx->gram_part,
+                             ctx->scal_part, Pe, P, ctx->st);
+    }));
+    if (tab)
+        TRY(run(ctx, K_GRAM_TABLE, (double)nxt.h * nxt.ld * 4.0, ctx->st, [&] {
+            return launch_gram_table(nxt, ctx->k, ctx->gram_part, P, Pe, ctx->sm_count, ctx->st);
+        }));
+    MetricsArgs ma;
+    if (metrics) {
+        ma.enabled = true;
+        ma.G_other = ctx->V.G;
+        ma.A2 = ctx->A2;
+        ma.out = ctx->met;
+        ma.hist_R = ctx->hist_R;
+        ma.hist_E = ctx->hist_E;
+        ma.hist_counter = ctx->hist_counter;
+        ma.hist_cap = ctx->hist_cap;
+    }
+    const int Cd = select_cluster(F.rows, ctx->k, TOPT_COLUMN, ctx->sm_count);
+    TRY(run(ctx, K_GRAM_REDUCE, (double)P * ntri * 8.0, ctx->st, [&] {
+        return launch_gram_reduce(ctx->gram_part, ctx->scal_part, P, Pe, ctx->k, ctx->diag_part,
+                                  Cd, F.G, ctx->scal, ctx->gram_counter, ma, ctx->st);
+    }));
+    F.cur ^= 1;
+    F.chol_pending = true;
+    return ESPNMF_OK;
+}
+
+bool survivor_path(const espnmf_ctx* ctx) { return ctx->rowbits != nullptr && ctx->mode == TOPT_COLUMN; }
 
 // Alg. 2 steps 1-2 (updV) or 3-4.
 espnmf_status half_update(espnmf_ctx* ctx, bool updV)
@@ -566,6 +755,12 @@ espnmf_status half_update(espnmf_ctx* ctx, bool updV)
 
     const double sb = (double)rows * ctx->k * ctx->esz * 2.0;
     TRY(run(ctx, K_SOLVE, sb, ctx->st, [&] {
+        if (use_cholesky(ctx)) {
+            const int KP = (int)ctx->ldy;
+            return launch_solve_chol((const float*)ctx->Y, ctx->ldy, rows, ctx->k, KP, O.Lf,
+                                     O.Lf + KP * KP, O.Lf + 2 * KP * KP, (float*)ctx->Xt,
+                                     ctx->ldx, ctx->status_d, ctx->st, ctx->sm_count);
+        }
         return is_f64(ctx) ? launch_solve<double>((const double*)ctx->Y, ctx->ldy, rows, ctx->k,
                                                   (const double*)O.GinvT, (double*)ctx->Xt,
                                                   ctx->ldx, ctx->status_d, ctx->st, ctx->sm_count)
@@ -574,8 +769,13 @@ espnmf_status half_update(espnmf_ctx* ctx, bool updV)
                                                  ctx->status_d, ctx->st, ctx->sm_count);
     }));
     const int64_t t = updV ? ctx->t_v : ctx->t_u;
-    TRY(do_select(ctx, rows, t));
-    TRY(do_emit(ctx, F, !updV && F.valid, updV ? nullptr : ctx->Y, !updV, ctx->mode));
+    if (survivor_path(ctx)) {
+        TRY(do_select(ctx, rows, t, true));
+        TRY(do_emit_survivors(ctx, F, !updV && F.valid, updV ? nullptr : ctx->Y, !updV));
+    } else {
+        TRY(do_select(ctx, rows, t, false));
+        TRY(do_emit(ctx, F, !updV && F.valid, updV ? nullptr : ctx->Y, !updV, ctx->mode));
+    }
     F.valid = true;
     if (updV) {
         ctx->Y_is_AV = false;
@@ -869,6 +1069,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         CU(setup_solve());
         CU(setup_select());
         CU(setup_factor());
+        CU(setup_chol());
 
         // ---- A: bring to the host, validate, build both layouts
         const int64_t n = A->n, m = A->m, nnz = A->nnz;
@@ -938,11 +1139,37 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             build_sell(m, cp.data(), ri.data(), cv.data(), h2);
             TRY(upload_sell(ctx, h2, ctx->sAt));
         } else {
-            SellHost<float> h1, h2;
-            build_sell(n, rp.data(), ci.data(), vv.data(), h1);
-            TRY(upload_sell(ctx, h1, ctx->sA));
-            build_sell(m, cp.data(), ri.data(), cv.data(), h2);
-            TRY(upload_sell(ctx, h2, ctx->sAt));
+            // rows of A gather rows of V (documents), rows of A^T rows of U
+            // (terms); each product gets a frequent part when its gathered
+            // rows are skewed enough (the frequent terms of a corpus)
+            const int ld = factor_ld(k);
+            // chunks of the frequent part's rows: four per warp of spmm_h
+            const int hwarps = 4 * ctx->sm_count * (kHThreads / 32);
+            auto build_f32 = [&](int64_t rows, const int64_t* ptr, const int32_t* ind,
+                                 const double* vals, int64_t ngather,
+                                 SellDev& D) -> espnmf_status {
+                std::vector<int64_t> w(ngather, 0);
+                for (int64_t q = 0; q < ptr[rows]; ++q) w[ind[q]]++;
+                FreqHost F;
+                F.h = choose_frequent(w, ptr[rows], ld, F.slot_of);
+                SellHost<float> h;
+                if (F.h > 0) {
+                    std::vector<int64_t> lp;
+                    std::vector<int32_t> li;
+                    std::vector<double> lv;
+                    split_frequent(rows, ptr, ind, vals, F, lp, li, lv);
+                    balance_frequent(rows, hwarps, F);
+                    build_sell(rows, lp.data(), li.data(), lv.data(), h);
+                    TRY(upload_sell(ctx, h, D));
+                    TRY(upload_frequent(ctx, F, D));
+                } else {
+                    build_sell(rows, ptr, ind, vals, h);
+                    TRY(upload_sell(ctx, h, D));
+                }
+                return ESPNMF_OK;
+            };
+            TRY(build_f32(n, rp.data(), ci.data(), vv.data(), m, ctx->sA));
+            TRY(build_f32(m, cp.data(), ri.data(), cv.data(), n, ctx->sAt));
         }
 
         // ---- work buffers
@@ -953,7 +1180,19 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         TRY(dmalloc(ctx, &ctx->Xt, (size_t)k * ctx->ldx * ctx->esz));
         CU(cudaMemsetAsync(ctx->Xt, 0, (size_t)k * ctx->ldx * ctx->esz, ctx->st));
         ctx->fin_blocks = 2 * ctx->sm_count;
-        TRY(dmalloc(ctx, &ctx->gram_part, sizeof(double) * ctx->fin_blocks * k * k));
+        {
+            // partials: emit blocks (and the frequent table's), upper triangle
+            const size_t ntri = (size_t)k * (k + 1) / 2;
+            const size_t parts = std::max((size_t)ctx->fin_blocks * k * k,
+                                          (size_t)(ctx->fin_blocks + ctx->sm_count) * ntri);
+            TRY(dmalloc(ctx, &ctx->gram_part, sizeof(double) * parts));
+        }
+        if (!is_f64(ctx)) {
+            const size_t words = (size_t)rmax * ((k + 31) / 32);
+            TRY(dmalloc(ctx, &ctx->rowbits, 4 * words));
+            CU(cudaMemsetAsync(ctx->rowbits, 0, 4 * words, ctx->st));
+            TRY(dmalloc(ctx, &ctx->diag_part, sizeof(double) * k * 8));
+        }
         TRY(dmalloc(ctx, &ctx->scal_part, sizeof(double) * ctx->fin_blocks * 4));
         TRY(dmalloc(ctx, &ctx->scal, sizeof(double) * 4));
         TRY(dmalloc(ctx, &ctx->gram_counter, sizeof(unsigned)));
@@ -982,9 +1221,23 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             // one dense copy and one record array per factor, rewritten by
             // each emit (the emit writes every row's record)
             uint4* rec = nullptr;
+            uint32_t* nzmask = nullptr;
+            void* htab = nullptr;
+            uint8_t* hnz = nullptr;
+            // the product that gathers this factor: A^T U gathers U, A V gathers V
+            const SellDev& Gp = F == &ctx->U ? ctx->sAt : ctx->sA;
             if (!is_f64(ctx)) {
                 TRY(dmalloc(ctx, &rec, sizeof(uint4) * F->rows));
                 CU(cudaMemsetAsync(rec, 0, sizeof(uint4) * F->rows, ctx->st));
+                const size_t words = (size_t)(F->rows + 31) / 32;
+                TRY(dmalloc(ctx, &nzmask, 4 * words));
+                CU(cudaMemsetAsync(nzmask, 0, 4 * words, ctx->st));
+                if (Gp.h > 0) {
+                    TRY(dmalloc(ctx, &htab, (size_t)Gp.h * ld * 4));
+                    CU(cudaMemsetAsync(htab, 0, (size_t)Gp.h * ld * 4, ctx->st));
+                    TRY(dmalloc(ctx, &hnz, (size_t)Gp.h));
+                    CU(cudaMemsetAsync(hnz, 0, (size_t)Gp.h, ctx->st));
+                }
             }
             for (int b = 0; b < 2; ++b) {
                 TRY(dmalloc(ctx, &F->buf[b].cnt, sizeof(int32_t) * F->rows));
@@ -993,7 +1246,13 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                 CU(cudaMemsetAsync(F->buf[b].cnt, 0, sizeof(int32_t) * F->rows, ctx->st));
                 F->buf[b].dense = dense;
                 F->buf[b].rec = rec;
+                F->buf[b].nzmask = nzmask;
+                F->buf[b].hslot = Gp.h > 0 ? Gp.slot_of : nullptr;
+                F->buf[b].htab = htab;
+                F->buf[b].hnz = hnz;
+                F->buf[b].h = htab ? Gp.h : 0;
                 F->buf[b].ld = ld;
+                F->buf[b].rows = F->rows;
                 F->buf[b].dld = dld;
                 F->buf[b].heavy = heavy_threshold(ld);
             }
@@ -1001,17 +1260,23 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             CU(cudaMemsetAsync(F->G, 0, sizeof(double) * k * k, ctx->st));
             TRY(dmalloc(ctx, &F->Ginv64, sizeof(double) * k * k));
             TRY(dmalloc(ctx, &F->GinvT, ctx->esz * k * k));
+            if (use_cholesky(ctx)) {
+                const size_t lf = (size_t)2 * ctx->ldy * ctx->ldy + ctx->ldy;
+                TRY(dmalloc(ctx, &F->Lf, sizeof(float) * lf));
+                CU(cudaMemsetAsync(F->Lf, 0, sizeof(float) * lf, ctx->st));
+            }
         }
 
         // ---- ||A||^2 from the values the kernels use
         if (is_f64(ctx))
             TRY(run(ctx, K_NORM2, (double)ctx->sA.total * 8, ctx->st, [&] {
-                return launch_norm2<double>((const double*)ctx->sA.val, ctx->sA.total,
+                return launch_norm2<double>((const double*)ctx->sA.val, ctx->sA.total, nullptr, 0,
                                             ctx->norm_part, ctx->sm_count, ctx->A2, ctx->st);
             }));
         else
             TRY(run(ctx, K_NORM2, (double)ctx->sA.total * 4, ctx->st, [&] {
                 return launch_norm2<float>((const float*)ctx->sA.val, ctx->sA.total,
+                                           (const float*)ctx->sA.hval, ctx->sA.hnnz,
                                            ctx->norm_part, ctx->sm_count, ctx->A2, ctx->st);
             }));
 
@@ -1108,7 +1373,7 @@ espnmf_status espnmf_enforce_topt(espnmf_ctx* ctx, espnmf_which which, int64_t t
         return is_f64(ctx) ? launch_ell_to_colmajor<double>(F.rows, ctx->k, cur, (double*)ctx->Xt, ctx->ldx, ctx->st)
                            : launch_ell_to_colmajor<float>(F.rows, ctx->k, cur, (float*)ctx->Xt, ctx->ldx, ctx->st);
     }));
-    TRY(do_select(ctx, F.rows, t));
+    TRY(do_select(ctx, F.rows, t, false));
     TRY(do_emit(ctx, F, false, nullptr, false, ctx->mode));
     ctx->met_valid = false;
     if (which == ESPNMF_V) ctx->Y_is_AV = false;
@@ -1379,6 +1644,17 @@ espnmf_status espnmf_set_option(espnmf_ctx* ctx, espnmf_option opt, int64_t valu
     return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "unknown option");
 }
 
+espnmf_status espnmf_spmm_frequent(espnmf_ctx* ctx, int32_t product, int32_t* h, int64_t* hnnz)
+{
+    TRY(enter(ctx));
+    if (!h || !hnnz || product < 0 || product > 1)
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "product must be 0 or 1, outputs non-NULL");
+    const SellDev& S = product == 0 ? ctx->sA : ctx->sAt;
+    *h = S.h;
+    *hnnz = S.hnnz;
+    return ESPNMF_OK;
+}
+
 espnmf_status espnmf_kernel_stat_count(espnmf_ctx* ctx, int32_t* count)
 {
     TRY(enter(ctx));
@@ -1412,8 +1688,13 @@ espnmf_status espnmf_launches_per_sweep(espnmf_ctx* ctx, int32_t* count)
 {
     TRY(enter(ctx));
     if (!count) return ESPNMF_ERR_INVALID_ARG;
-    int per_half_A = 5 + (ctx->sA.nsplit > 0 ? 1 : 0);
-    int per_half_At = 5 + (ctx->sAt.nsplit > 0 ? 1 : 0);
+    // U update: A V (+ combine, + frequent part), solve, select, emit,
+    // (+ U's table Gram), reduce; the V update likewise with A^T U
+    const bool sv = survivor_path(ctx);
+    int per_half_A = 5 + (ctx->sA.nsplit > 0 ? 1 : 0) + (ctx->sA.h > 0 && ctx->sA.hnnz > 0 ? 1 : 0) +
+                     (sv && ctx->sAt.h > 0 ? 1 : 0);
+    int per_half_At = 5 + (ctx->sAt.nsplit > 0 ? 1 : 0) + (ctx->sAt.h > 0 && ctx->sAt.hnnz > 0 ? 1 : 0) +
+                      (sv && ctx->sA.h > 0 ? 1 : 0);
     *count = per_half_A + per_half_At + 2;   // + the two Gram inverse launches
     return ESPNMF_OK;
 }
@@ -1469,8 +1750,8 @@ espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64
                 : launch_dense_to_colmajor<float, float>((const float*)X, rows, k, ld, (float*)ws, ldx, status, false, st);
     if (e == cudaSuccess)
         e = dtype == ESPNMF_F64
-                ? launch_select<double>((const double*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms)
-                : launch_select<float>((const float*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms);
+                ? launch_select<double>((const double*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms, nullptr, nullptr)
+                : launch_select<float>((const float*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms, nullptr, nullptr);
     if (e == cudaSuccess)
         e = dtype == ESPNMF_F64 ? launch_apply_thresholds<double>((double*)X, rows, k, ld, (int)mode, tau, cut, status, st)
                                 : launch_apply_thresholds<float>((float*)X, rows, k, ld, (int)mode, tau, cut, status, st);

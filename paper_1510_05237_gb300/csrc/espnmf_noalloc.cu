@@ -121,8 +121,8 @@ espnmf_status espnmf_enforce_topt_buffer_noalloc(void* X, int64_t rows, int32_t 
                 : launch_dense_to_colmajor<float, float>((const float*)X, rows, k, ld, (float*)ws, ldx, status, false, st);
     if (e == cudaSuccess)
         e = dtype == ESPNMF_F64
-                ? launch_select<double>((const double*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms)
-                : launch_select<float>((const float*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms);
+                ? launch_select<double>((const double*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms, nullptr, nullptr)
+                : launch_select<float>((const float*)ws, ldx, rows, k, t, (int)mode, tau, cut, st, sms, nullptr, nullptr);
     if (e == cudaSuccess)
         e = dtype == ESPNMF_F64 ? launch_apply_thresholds<double>((double*)X, rows, k, ld, (int)mode, tau, cut, status, st)
                                 : launch_apply_thresholds<float>((float*)X, rows, k, ld, (int)mode, tau, cut, status, st);

@@ -1,0 +1,304 @@
+// k_chol.cu -- the k x k solve of Alg. 2 steps 1 and 3 in the FP32 form
+// (k <= 64), by a Cholesky factor instead of an explicit inverse:
+//
+//   cholesky      G = L L^T of the other factor's Gram matrix, in FP64, one
+//                 CTA (right-looking, k^3 / 6 fused multiply-adds: a third
+//                 of what an explicit inverse costs, which matters because
+//                 FP64 runs at a small fraction of the FP32 rate on this
+//                 GPU).  It writes L rounded to FP32: the strictly lower part
+//                 row-major (Ls), its transpose (LTs) and the reciprocal
+//                 diagonal (rd), each padded with zeros to KP columns.
+//   solve_chol    per row y of Y: L z = y (forward), L^T x = z (backward),
+//                 in FP32, one thread per row with the row in registers; the
+//                 factor is read from shared memory with 128-bit broadcast
+//                 loads.  The projection onto x >= 0 is fused and the result
+//                 written column-major (Xt[c * ldx + row], coalesced across
+//                 the threads of a warp) for the selector.
+//
+// An index j with G_jj = 0 belongs to an all-zero factor column: its row and
+// column of L are zero and rd_j = 0, so x_j = 0 and no other entry depends on
+// it (the minimum-norm solution).  Any other pivot (the j-th Schur
+// complement diagonal, the same quantity the sweep-operator inverse tests)
+// at or below 64 eps max_j G_jj raises ST_SINGULAR; a non-finite entry of G
+// raises ST_NONFINITE.
+#include <float.h>
+
+#include "common.cuh"
+
+namespace espnmf {
+
+constexpr int kCholThreads = 256;
+
+// 1 / sqrt(d) for d > 0: an FP32 seed refined by two FP64 Newton steps
+// x <- x (3 - d x^2) / 2 (each step doubles the correct bits: 23 -> 46 ->
+// full precision); a short dependent chain on this GPU's slow FP64 pipe.
+__device__ __forceinline__ double rsqrt_fp64(double d)
+{
+    if (!(d > 1e-300 && d < 1e300)) return 1.0 / sqrt(d);
+    double x = (double)rsqrtf((float)d);
+    double t = d * x;
+    x = x * fma(-0.5 * t, x, 1.5);
+    t = d * x;
+    return x * fma(-0.5 * t, x, 1.5);
+}
+
+// Right-looking Cholesky on the lower triangle in shared memory.  Step j:
+// (1) the column below the pivot is scaled by 1 / L_jj, (2) the trailing
+// triangle is updated, its entries packed so that every lane of every warp
+// does one FMA per pass (a warp instruction holds the FP64 pipe whatever
+// its active lanes); the thread that updates the next active diagonal entry
+// computes that pivot's reciprocal square root at once, so the FP64 chain
+// of the next pivot runs while the others are still updating.  Two barriers
+// per step.
+__global__ void __launch_bounds__(kCholThreads)
+cholesky_kernel(const double* __restrict__ G, int k, int KP, float* __restrict__ Ls,
+                float* __restrict__ LTs, float* __restrict__ rd, unsigned* status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ks = k + 1;                                   // row stride (odd)
+    double* a = reinterpret_cast<double*>(smem_raw);        // [k][ks], lower part used
+    int* act = reinterpret_cast<int*>(a + (size_t)k * ks);  // [k] 1: active index
+    int* nxt = act + k;                                     // [k] next active index (k: none)
+    // the lower triangle's entries (i, l) packed as i << 8 | l, ordered by
+    // column l, then row i: the trailing triangle of step j is the suffix
+    // that starts at column j + 1, at offset cstart(j + 1)
+    uint16_t* tri = reinterpret_cast<uint16_t*>(nxt + k);
+    auto cstart = [&](int l) { return l * k - l * (l - 1) / 2; };
+    __shared__ double prs[2];                               // 1 / L_jj, double-buffered
+    __shared__ double maxdiag, tol;
+    __shared__ int sing, nonfin;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < k * k; e += blockDim.x) {
+        const int i = e / k, j = e - i * k;
+        if (j <= i) a[i * ks + j] = G[(size_t)i * k + j];
+    }
+    for (int l = tid; l < k; l += blockDim.x)
+        for (int i = l; i < k; ++i) tri[cstart(l) + (i - l)] = (uint16_t)((i << 8) | l);
+    if (tid == 0) {
+        double md = 0.0;
+        int nf = 0;
+        for (int j = 0; j < k; ++j) {
+            const double d = G[(size_t)j * k + j];
+            if (!isfinite(d)) nf = 1;
+            act[j] = (d != 0.0 && isfinite(d)) ? 1 : 0;
+            if (act[j] && d > md) md = d;
+        }
+        int n = k;
+        for (int j = k - 1; j >= 0; --j) {
+            nxt[j] = n;
+            if (act[j]) n = j;
+        }
+        maxdiag = md;
+        tol = 64.0 * DBL_EPSILON * md;
+        sing = 0;
+        nonfin = nf;
+        // the first pivot
+        if (n < k) {
+            const double d = G[(size_t)n * k + n];
+            const bool bad = !(d > tol);
+            if (bad) sing = 1;
+            prs[0] = rsqrt_fp64(bad ? 1.0 : d);
+        }
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int j = 0; j < k; ++j) {
+        if (!act[j]) continue;   // uniform: act is shared
+        const double r = prs[buf];
+        for (int i = j + 1 + tid; i < k; i += blockDim.x)
+            a[i * ks + j] = act[i] ? a[i * ks + j] * r : 0.0;
+        if (tid == 0) a[j * ks + j] = r * a[j * ks + j];   // L_jj = d / sqrt(d)
+        __syncthreads();
+        // trailing update a_il -= L_ij L_lj (j < l <= i), every lane on an
+        // entry of the packed suffix
+        const int jn = nxt[j];
+        const int e0 = j + 1 < k ? cstart(j + 1) : 0, e1 = j + 1 < k ? cstart(k) : 0;
+        for (int e = e0 + tid; e < e1; e += blockDim.x) {
+            const int il = tri[e];
+            const int i = il >> 8, l = il & 0xff;
+            const double v = fma(-a[i * ks + j], a[l * ks + j], a[i * ks + l]);
+            a[i * ks + l] = v;
+            if (i == l && i == jn) {
+                const bool bad = !(v > tol);
+                if (bad) sing = 1;
+                prs[buf ^ 1] = rsqrt_fp64(bad ? 1.0 : v);
+            }
+        }
+        buf ^= 1;
+        __syncthreads();
+    }
+    // FP32 copies, zero-padded to KP x KP
+    for (int e = tid; e < KP * KP; e += blockDim.x) {
+        const int i = e / KP, l = e - i * KP;
+        float v = 0.f;
+        if (i < k && l < i && act[i] && act[l]) v = (float)a[i * ks + l];
+        Ls[e] = v;                      // L[i][l], strictly lower
+        LTs[(size_t)l * KP + i] = v;    // L^T[l][i]
+    }
+    for (int j = tid; j < KP; j += blockDim.x)
+        rd[j] = (j < k && act[j]) ? (float)(1.0 / a[j * ks + j]) : 0.f;
+    if (tid == 0) {
+        if (sing) atomicOr(status, ST_SINGULAR);
+        if (nonfin) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+cudaError_t launch_cholesky(const double* G, int k, int KP, float* Ls, float* LTs, float* rd,
+                            unsigned* status, cudaStream_t st)
+{
+    if (k < 1 || KP < k || KP > 64) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)k * (k + 1) * sizeof(double) + 2 * (size_t)k * sizeof(int) +
+                        (size_t)k * (k + 1) / 2 * sizeof(uint16_t);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(kCholThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = hi;   // ahead of the concurrent SpMM's pending blocks
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cholesky_kernel, G, k, KP, Ls, LTs, rd, status);
+}
+
+// ---------------------------------------------------------------------------
+
+constexpr int kSolveRows = 128;   // rows per tile, one per thread
+constexpr int kSolveStride = kSolveRows + 1;   // staged tile row stride (bank offset)
+
+template <int KP>
+__global__ void __launch_bounds__(kSolveRows, 4)
+solve_chol_kernel(const float* __restrict__ Y, int64_t ldy, int64_t rows, int k,
+                  const float* __restrict__ Lg, const float* __restrict__ LTg,
+                  const float* __restrict__ rdg, float* __restrict__ Xt, int64_t ldx,
+                  unsigned* status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* Ls = reinterpret_cast<float*>(smem_raw);   // [KP][KP]
+    float* LTs = Ls + KP * KP;                          // [KP][KP]
+    float* rds = LTs + KP * KP;                         // [KP]
+    float* Ys = rds + KP;                               // [KP][kSolveStride]
+    const int tid = threadIdx.x;
+    for (int e = tid; e < KP * KP; e += blockDim.x) {
+        Ls[e] = Lg[e];
+        LTs[e] = LTg[e];
+    }
+    for (int e = tid; e < KP; e += blockDim.x) rds[e] = rdg[e];
+    bool bad = false;
+    for (int64_t r0 = (int64_t)blockIdx.x * kSolveRows; r0 < rows;
+         r0 += (int64_t)gridDim.x * kSolveRows) {
+        __syncthreads();
+        const int nr = (int)(rows - r0 < kSolveRows ? rows - r0 : kSolveRows);
+        // stage the tile transposed: four rows per pass, a quarter-warp per
+        // row, so each row is read with consecutive 16-byte loads
+        for (int q = tid; q < kSolveRows * (KP / 4); q += blockDim.x) {
+            const int rr = q / (KP / 4), d4 = q - rr * (KP / 4);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rr < nr) v = *reinterpret_cast<const float4*>(Y + (r0 + rr) * ldy + 4 * d4);
+            Ys[(4 * d4 + 0) * kSolveStride + rr] = v.x;
+            Ys[(4 * d4 + 1) * kSolveStride + rr] = v.y;
+            Ys[(4 * d4 + 2) * kSolveStride + rr] = v.z;
+            Ys[(4 * d4 + 3) * kSolveStride + rr] = v.w;
+        }
+        __syncthreads();
+        float x[KP];
+#pragma unroll
+        for (int d = 0; d < KP; ++d) x[d] = Ys[d * kSolveStride + tid];
+        // L z = y: z_j = (y_j - sum_{i<j} L_ji z_i) / L_jj; the strictly
+        // upper entries of Ls are zero, so whole 4-wide groups can be read
+#pragma unroll
+        for (int j = 0; j < KP; ++j) {
+            float s = x[j];
+#pragma unroll
+            for (int i = 0; i < (j + 3) / 4 * 4; i += 4) {
+                const float4 l = *reinterpret_cast<const float4*>(Ls + j * KP + i);
+                s = fmaf(-l.x, x[i + 0], s);
+                s = fmaf(-l.y, x[i + 1], s);
+                s = fmaf(-l.z, x[i + 2], s);
+                s = fmaf(-l.w, x[i + 3], s);
+            }
+            x[j] = s * rds[j];
+        }
+        // L^T x = z: x_j = (z_j - sum_{i>j} L_ij x_i) / L_jj
+#pragma unroll
+        for (int j = KP - 1; j >= 0; --j) {
+            float s = x[j];
+#pragma unroll
+            for (int i = (j + 1) / 4 * 4; i < KP; i += 4) {
+                const float4 l = *reinterpret_cast<const float4*>(LTs + j * KP + i);
+                s = fmaf(-l.x, x[i + 0], s);
+                s = fmaf(-l.y, x[i + 1], s);
+                s = fmaf(-l.z, x[i + 2], s);
+                s = fmaf(-l.w, x[i + 3], s);
+            }
+            x[j] = s * rds[j];
+        }
+        if (tid < nr) {
+#pragma unroll
+            for (int c = 0; c < KP; ++c) {
+                if (c >= k) break;
+                const float v = x[c];
+                if (!isfinite(v)) bad = true;
+                Xt[(int64_t)c * ldx + r0 + tid] = v > 0.f ? v : 0.f;
+            }
+        }
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+template <int KP>
+static cudaError_t launch_solve_chol_kp(const float* Y, int64_t ldy, int64_t rows, int k,
+                                        const float* L, const float* LT, const float* rd,
+                                        float* Xt, int64_t ldx, unsigned* status,
+                                        cudaStream_t st, int sm_count)
+{
+    const size_t smem = ((size_t)2 * KP * KP + KP + (size_t)KP * kSolveStride) * sizeof(float);
+    const int64_t tiles = (rows + kSolveRows - 1) / kSolveRows;
+    int64_t grid = (int64_t)sm_count * 4;
+    if (grid > tiles) grid = tiles;
+    solve_chol_kernel<KP><<<(unsigned)grid, kSolveRows, smem, st>>>(Y, ldy, rows, k, L, LT, rd,
+                                                                  Xt, ldx, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_chol(const float* Y, int64_t ldy, int64_t rows, int k, int KP,
+                              const float* L, const float* LT, const float* rd, float* Xt,
+                              int64_t ldx, unsigned* status, cudaStream_t st, int sm_count)
+{
+    if (rows == 0) return cudaSuccess;
+    if (ldy != KP) return cudaErrorInvalidValue;
+    switch (KP) {
+#define ESPNMF_KP(v) case v: return launch_solve_chol_kp<v>(Y, ldy, rows, k, L, LT, rd, Xt, ldx, status, st, sm_count);
+        ESPNMF_KP(4) ESPNMF_KP(8) ESPNMF_KP(12) ESPNMF_KP(16) ESPNMF_KP(20) ESPNMF_KP(24)
+        ESPNMF_KP(28) ESPNMF_KP(32) ESPNMF_KP(36) ESPNMF_KP(40) ESPNMF_KP(44) ESPNMF_KP(48)
+        ESPNMF_KP(52) ESPNMF_KP(56) ESPNMF_KP(60) ESPNMF_KP(64)
+#undef ESPNMF_KP
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int KP>
+static cudaError_t setup_solve_kp()
+{
+    const size_t smem = ((size_t)2 * KP * KP + KP + (size_t)KP * kSolveStride) * sizeof(float);
+    return cudaFuncSetAttribute(solve_chol_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+cudaError_t setup_chol()
+{
+    cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         64 * 65 * 8 + 2 * 64 * 4 + 64 * 65);
+#define ESPNMF_KP(v) if (e == cudaSuccess) e = setup_solve_kp<v>();
+    ESPNMF_KP(4) ESPNMF_KP(8) ESPNMF_KP(12) ESPNMF_KP(16) ESPNMF_KP(20) ESPNMF_KP(24)
+    ESPNMF_KP(28) ESPNMF_KP(32) ESPNMF_KP(36) ESPNMF_KP(40) ESPNMF_KP(44) ESPNMF_KP(48)
+    ESPNMF_KP(52) ESPNMF_KP(56) ESPNMF_KP(60) ESPNMF_KP(64)
+#undef ESPNMF_KP
+    return e;
+}
+
+}  // namespace espnmf

@@ -53,6 +53,10 @@ struct EmitArgs {
     T* val;
     T* dense;
     uint4* rec;          // FP32: per-row records (cnt and the first pairs)
+    uint32_t* nzmask;    // FP32: nonzero-row bitmask (or NULL)
+    const int32_t* hslot;   // slot of the row in htab, or -1 (NULL: no table)
+    T* htab;
+    uint8_t* hnz;
     int ld, dld, heavy, SL;   // SL: staged pairs per lane (light rows)
     bool heavy_gram;     // heavy rows' Gram by register slots
     int32_t* cnt_old;
@@ -113,7 +117,8 @@ emit_kernel(EmitArgs<T> a)
     __syncthreads();
 
     const bool matrix = a.mode == TOPT_MATRIX;
-    const int64_t chunk = (a.rows + gridDim.x - 1) / gridDim.x;
+    // blocks own whole 32-row words of the nonzero-row bitmask
+    const int64_t chunk = ((a.rows + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
     const int64_t b0 = (int64_t)blockIdx.x * chunk;
     const int64_t b1 = b0 + chunk < a.rows ? b0 + chunk : a.rows;
     double s_diff = 0.0, s_new = 0.0, s_old = 0.0, s_cross = 0.0;
@@ -127,6 +132,7 @@ emit_kernel(EmitArgs<T> a)
             return keep_entry<T>(x, stau[sg], scut[sg], ix);
         };
         int nl = 0;
+        bool nonzero = false;
         if (valid) {
             int pos = 0, q = 0;
             const int Lo = (a.residual || a.zero_old) ? a.cnt_old[r] : 0;
@@ -180,6 +186,17 @@ emit_kernel(EmitArgs<T> a)
                 for (int c = 0; c < ld; ++c) dr[c] = T(0);
                 for (int j = 0; j < pos; ++j) dr[wc[j]] = wv[j];
             }
+            if (a.hslot) {
+                // a frequent row: its dense copy in the sparse product's table
+                const int sl = a.hslot[r];
+                if (sl >= 0) {
+                    T* tr = a.htab + (int64_t)sl * ld;
+                    for (int c = 0; c < ld; ++c) tr[c] = T(0);
+                    for (int j = 0; j < pos; ++j) tr[wc[j]] = wv[j];
+                    a.hnz[sl] = pos > 0 ? 1 : 0;
+                }
+            }
+            nonzero = pos > 0;
             a.cnt[r] = pos;
             if constexpr (sizeof(T) == 4) {
                 if (a.rec) {
@@ -197,6 +214,10 @@ emit_kernel(EmitArgs<T> a)
             nl = (hv && a.heavy_gram) ? 0 : pos;
         }
         __syncwarp();
+        if (a.nzmask) {
+            const unsigned word = __ballot_sync(0xffffffffu, nonzero);
+            if (lane == 0) a.nzmask[base >> 5] = word;
+        }
         // Gram of the light rows: a row's pairs (ia <= ib) across the lanes,
         // into the upper triangle (slot min*k + max); slots are distinct
         // within a row, rows follow each other.
@@ -275,8 +296,7 @@ emit_kernel(EmitArgs<T> a)
         const int c = cd[s] >> 16, d = cd[s] & 0xffff;
         double v = acc[s];
         for (int w = 0; w < W; ++w) v += Gall[(size_t)w * gstride + tri_index(c, d, k)];
-        a.gram_part[(size_t)(c * k + d) * P + blockIdx.x] = v;
-        if (c != d) a.gram_part[(size_t)(d * k + c) * P + blockIdx.x] = v;
+        a.gram_part[(size_t)tri_index(c, d, k) * P + blockIdx.x] = v;
     }
     // entries beyond the register slots (only for k too large for them)
     for (int e = kSlots * NT + tid; e < ntri; e += NT) {
@@ -289,8 +309,7 @@ emit_kernel(EmitArgs<T> a)
         const int d = c + (e - start);
         double v = 0.0;
         for (int w = 0; w < W; ++w) v += Gall[(size_t)w * gstride + tri_index(c, d, k)];
-        a.gram_part[(size_t)(c * k + d) * P + blockIdx.x] = v;
-        if (c != d) a.gram_part[(size_t)(d * k + c) * P + blockIdx.x] = v;
+        a.gram_part[(size_t)tri_index(c, d, k) * P + blockIdx.x] = v;
     }
     s_diff = warp_sum(s_diff);
     s_new = warp_sum(s_new);
@@ -331,6 +350,10 @@ cudaError_t launch_emit(const T* Xt, int64_t ldx, int64_t rows, int k, int mode,
     a.val = static_cast<T*>(cur.val);
     a.dense = static_cast<T*>(cur.dense);
     a.rec = cur.rec;
+    a.nzmask = cur.nzmask;
+    a.hslot = cur.h > 0 ? cur.hslot : nullptr;
+    a.htab = static_cast<T*>(cur.htab);
+    a.hnz = cur.hnz;
     a.ld = cur.ld;
     a.dld = cur.dld;
     a.heavy = cur.heavy;
@@ -364,28 +387,46 @@ cudaError_t launch_emit(const T* Xt, int64_t ldx, int64_t rows, int k, int mode,
 
 __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
                                    const double* __restrict__ scal_part,
-                                   int P, int k, double* G, double* scal,
+                                   int P, int Ps, int k, const double* __restrict__ diag_part,
+                                   int Cd, double* G, double* scal,
                                    unsigned* counter, MetricsArgs m)
 {
-    // one warp per output: the k*k Gram entries, then the 4 scalars; a lane
-    // adds parts lane, lane+32, ... and the warp adds the lanes in a fixed
-    // tree, so the sum is reproducible
+    // one warp per output: the upper-triangle Gram entries (partials
+    // entry-major, P per entry), then the 4 scalars (Ps partials each); a
+    // lane adds parts lane, lane+32, ... and the warp adds the lanes in a
+    // fixed tree, so the sum is reproducible.  Diagonal entries also get the
+    // Cd per-column partials of diag_part.
+    const int ntri = k * (k + 1) / 2;
     const int kk = k * k;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (w < kk + 4) {
-        const double* src = w < kk ? gram_part + (size_t)w * P : scal_part + (size_t)(w - kk) * P;
+    if (w < ntri + 4) {
+        const int np = w < ntri ? P : Ps;
+        const double* src = w < ntri ? gram_part + (size_t)w * P : scal_part + (size_t)(w - ntri) * Ps;
         double s0 = 0.0, s1 = 0.0;
         int p = lane;
-        for (; p + 32 < P; p += 64) {
+        for (; p + 32 < np; p += 64) {
             s0 += src[p];
             s1 += src[p + 32];
         }
-        if (p < P) s0 += src[p];
-        const double v = warp_sum(s0 + s1);
+        if (p < np) s0 += src[p];
+        double v = warp_sum(s0 + s1);
         if (lane == 0) {
-            if (w < kk) G[w] = v;
-            else scal[w - kk] = v;
+            if (w < ntri) {
+                int c = 0, start = 0, rowlen = k;
+                while (w >= start + rowlen) {
+                    start += rowlen;
+                    ++c;
+                    --rowlen;
+                }
+                const int d = c + (w - start);
+                if (c == d && diag_part)
+                    for (int j = 0; j < Cd; ++j) v += diag_part[(size_t)c * Cd + j];
+                G[c * k + d] = v;
+                G[d * k + c] = v;
+            } else {
+                scal[w - ntri] = v;
+            }
         }
     }
     if (!m.enabled) return;
@@ -430,15 +471,462 @@ __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
     }
 }
 
-cudaError_t launch_gram_reduce(const double* gram_part,
-                               const double* scal_part, int nparts, int k,
-                               double* G, double* scal, unsigned* counter,
-                               MetricsArgs m, cudaStream_t st)
+cudaError_t launch_gram_reduce(const double* gram_part, const double* scal_part, int nparts,
+                               int nscal_parts, int k, const double* diag_part, int diag_parts,
+                               double* G, double* scal, unsigned* counter, MetricsArgs m,
+                               cudaStream_t st)
 {
     const int B = 256;
-    const int grid = ((k * k + 4) * 32 + B - 1) / B;
-    gram_reduce_kernel<<<grid, B, 0, st>>>(gram_part, scal_part, nparts, k, G,
-                                           scal, counter, m);
+    const int ntri = k * (k + 1) / 2;
+    const int grid = ((ntri + 4) * 32 + B - 1) / B;
+    gram_reduce_kernel<<<grid, B, 0, st>>>(gram_part, scal_part, nparts, nscal_parts, k,
+                                           diag_part, diag_parts, G, scal, counter, m);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Survivor-driven emit (FP32 form, column mode).  The selector has marked
+// every survivor in a per-row bitmask (bit c of row i: entry (i, c) is kept)
+// and written the Gram diagonal; this pass reads each row's bits (and
+// clears them for the next selection), writes the row's pairs from the
+// candidate, its record, its nonzero bit, its dense copy (heavy rows) and
+// its row of the frequent table, and accumulates in FP64 the Sec. 3.1 sums
+// (||F_new - F_old||^2 over the union of the two supports, ||F_new||^2,
+// ||F_old||^2, <F_new, Y>).  The off-diagonal Gram products of the rows
+// with two or more nonzeros that are not frequent rows are added by one
+// warp, row after row in row order, into the block's triangle; the frequent
+// rows' products come from gram_table_kernel.  Work is proportional to the
+// rows plus the survivors, not to rows x k.
+
+struct EmitSArgs {
+    const float* Xt;
+    int64_t ldx;
+    int64_t rows;
+    int k;
+    uint32_t* rowbits;
+    int32_t* cnt;
+    int32_t* col;
+    float* val;
+    float* dense;
+    uint4* rec;
+    uint32_t* nzmask;
+    const int32_t* hslot;
+    float* htab;
+    uint8_t* hnz;
+    int ld, dld, heavy;
+    int32_t* cnt_old;
+    const int32_t* col_old;
+    const float* val_old;
+    bool residual, zero_old;
+    const float* Y;
+    int64_t ldy;
+    double* gram_part;   // [ntri][P], this kernel's blocks are columns [0, gridDim.x)
+    double* scal_part;   // [4][gridDim.x]
+    int P;
+};
+
+constexpr int kEmitSThreads = 512;
+constexpr int kEmitSStage = 8;   // pairs per row staged in shared memory
+constexpr int kLaneSurv = 8;     // rows with more survivors are written by a whole warp
+
+template <int WD>
+__global__ void __launch_bounds__(kEmitSThreads)
+emit_s_kernel(EmitSArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* T = reinterpret_cast<double*>(smem_raw);   // [ntri]
+    // the pairs of this round's rows (the first kEmitSStage of each), so
+    // that the warp adding the off-diagonal products reads shared memory
+    int2* stage = reinterpret_cast<int2*>(smem_raw + (((size_t)a.k * (a.k + 1) / 2 * 8 + 15) & ~(size_t)15));
+    __shared__ int wcount[kEmitSThreads / 32];
+    __shared__ int list[kEmitSThreads];
+    __shared__ double red[kEmitSThreads / 32][4];
+    __shared__ float wold[kEmitSThreads / 32][kMaxK];   // a warp's old row, dense
+    const int k = a.k, ld = a.ld;
+    const int ntri = k * (k + 1) / 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int NW = blockDim.x >> 5;
+    for (int e = tid; e < ntri; e += blockDim.x) T[e] = 0.0;
+    // blocks own whole 32-row words of the nonzero-row bitmask
+    const int64_t chunk = ((a.rows + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk < a.rows ? (int64_t)blockIdx.x * chunk : a.rows;
+    const int64_t b1 = b0 + chunk < a.rows ? b0 + chunk : a.rows;
+    double s_diff = 0.0, s_new = 0.0, s_old = 0.0, s_cross = 0.0;
+
+    for (int64_t base = b0; base < b1; base += blockDim.x) {
+        const int64_t r = base + tid;
+        const bool valid = r < b1;
+        bool nonzero = false, offdiag = false;
+        uint32_t bits[WD];
+#pragma unroll
+        for (int w = 0; w < WD; ++w) bits[w] = 0u;
+        bool coop = false;
+        if (valid) {
+            uint32_t* bp = a.rowbits + r * WD;
+#pragma unroll
+            for (int w = 0; w < WD; ++w) bits[w] = bp[w];
+#pragma unroll
+            for (int w = 0; w < WD; ++w)
+                if (bits[w]) bp[w] = 0u;
+            int nb = 0;
+#pragma unroll
+            for (int w = 0; w < WD; ++w) nb += __popc(bits[w]);
+            coop = nb > kLaneSurv;
+            if (coop) {
+                // written below by the whole warp
+                const int sl = a.hslot ? a.hslot[r] : -1;
+                nonzero = true;
+                offdiag = sl < 0;
+            }
+        }
+        if (valid && !coop) {
+            const int Lo = (a.residual || a.zero_old) ? a.cnt_old[r] : 0;
+            const int32_t* co = a.col_old + r * ld;
+            const float* vo = a.val_old + r * ld;
+            int32_t* wc = a.col + r * ld;
+            float* wv = a.val + r * ld;
+            unsigned rx = 0u, rv0 = 0u, rv1 = 0u, rv2 = 0u;
+            int pos = 0, q = 0;
+#pragma unroll
+            for (int w = 0; w < WD; ++w) {
+                uint32_t mb = bits[w];
+                while (mb) {
+                    const int c = 32 * w + __ffs(mb) - 1;
+                    mb &= mb - 1u;
+                    const float x = a.Xt[(int64_t)c * a.ldx + r];
+                    wc[pos] = c;
+                    wv[pos] = x;
+                    if (pos < kEmitSStage) stage[tid * kEmitSStage + pos] = make_int2(c, __float_as_int(x));
+                    if (pos == 0) { rx |= (unsigned)c << 8; rv0 = __float_as_uint(x); }
+                    else if (pos == 1) { rx |= (unsigned)c << 16; rv1 = __float_as_uint(x); }
+                    else if (pos == 2) { rx |= (unsigned)c << 24; rv2 = __float_as_uint(x); }
+                    const double xd = (double)x;
+                    s_new = fma(xd, xd, s_new);
+                    if (a.Y) s_cross = fma(xd, (double)a.Y[r * a.ldy + c], s_cross);
+                    if (a.residual) {
+                        while (q < Lo && co[q] < c) {
+                            const double o = (double)vo[q];
+                            s_old = fma(o, o, s_old);
+                            s_diff = fma(o, o, s_diff);
+                            ++q;
+                        }
+                        double d = xd;
+                        if (q < Lo && co[q] == c) {
+                            const double o = (double)vo[q];
+                            s_old = fma(o, o, s_old);
+                            d = xd - o;
+                            ++q;
+                        }
+                        s_diff = fma(d, d, s_diff);
+                    }
+                    ++pos;
+                }
+            }
+            if (a.residual) {
+                for (; q < Lo; ++q) {
+                    const double o = (double)vo[q];
+                    s_old = fma(o, o, s_old);
+                    s_diff = fma(o, o, s_diff);
+                }
+            }
+            a.cnt[r] = pos;
+            if (a.rec) a.rec[r] = make_uint4(rx | (unsigned)pos, rv0, rv1, rv2);
+            if (a.zero_old) a.cnt_old[r] = 0;
+            if (pos >= a.heavy && a.dense != nullptr) {
+                float* dr = a.dense + r * a.dld;
+                for (int c = 0; c < ld; ++c) dr[c] = 0.f;
+                for (int j = 0; j < pos; ++j) dr[wc[j]] = wv[j];
+            }
+            const int sl = a.hslot ? a.hslot[r] : -1;
+            if (sl >= 0) {
+                float* tr = a.htab + (int64_t)sl * ld;
+                for (int c = 0; c < ld; ++c) tr[c] = 0.f;
+                for (int j = 0; j < pos; ++j) tr[wc[j]] = wv[j];
+                a.hnz[sl] = pos > 0 ? 1 : 0;
+            }
+            nonzero = pos > 0;
+            offdiag = pos >= 2 && sl < 0;
+        }
+        // rows with many survivors, one at a time by the whole warp: lane c
+        // handles column c (and c + 32, ...), positions by prefix counts
+        unsigned cm = __ballot_sync(0xffffffffu, coop);
+        while (cm) {
+            const int j = __ffs(cm) - 1;
+            cm &= cm - 1u;
+            const int64_t rr = base + warp * 32 + j;
+            uint32_t bw[WD];
+#pragma unroll
+            for (int w = 0; w < WD; ++w) bw[w] = __shfl_sync(0xffffffffu, bits[w], j);
+            auto surv = [&](int c) -> bool {
+                uint32_t wd = bw[0];
+#pragma unroll
+                for (int w = 1; w < WD; ++w)
+                    if ((c >> 5) == w) wd = bw[w];
+                return (wd >> (c & 31)) & 1u;
+            };
+            const int Lo = (a.residual || a.zero_old) ? a.cnt_old[rr] : 0;
+            const int32_t* co = a.col_old + rr * ld;
+            const float* vo = a.val_old + rr * ld;
+            float* od = wold[warp];
+            if (a.residual) {
+                for (int c = lane; c < ld; c += 32) od[c] = 0.f;
+                __syncwarp();
+                for (int q = lane; q < Lo; q += 32) {
+                    const int oc = co[q];
+                    const double o = (double)vo[q];
+                    od[oc] = vo[q];
+                    s_old = fma(o, o, s_old);
+                    if (!surv(oc)) s_diff = fma(o, o, s_diff);
+                }
+                __syncwarp();
+            }
+            int32_t* wc = a.col + rr * ld;
+            float* wv = a.val + rr * ld;
+            const int sl = a.hslot ? a.hslot[rr] : -1;
+            int before = 0, nb = 0;
+#pragma unroll
+            for (int w = 0; w < WD; ++w) nb += __popc(bw[w]);
+            float* dr = nb >= a.heavy && a.dense != nullptr ? a.dense + rr * a.dld : nullptr;
+            float* tr = sl >= 0 ? a.htab + (int64_t)sl * ld : nullptr;
+            unsigned rx = (unsigned)nb, rv[3] = {0u, 0u, 0u};
+#pragma unroll
+            for (int w = 0; w < WD; ++w) {
+                const int c = 32 * w + lane;
+                const bool sv = (bw[w] >> lane) & 1u;
+                const int pos = before + __popc(bw[w] & ((1u << lane) - 1u));
+                float x = 0.f;
+                if (sv) {
+                    x = a.Xt[(int64_t)c * a.ldx + rr];
+                    wc[pos] = c;
+                    wv[pos] = x;
+                    const double xd = (double)x;
+                    s_new = fma(xd, xd, s_new);
+                    if (a.Y) s_cross = fma(xd, (double)a.Y[rr * a.ldy + c], s_cross);
+                    if (a.residual) {
+                        const double d = xd - (double)od[c];
+                        s_diff = fma(d, d, s_diff);
+                    }
+                }
+                if (c < ld) {
+                    if (dr) dr[c] = x;
+                    if (tr) tr[c] = x;
+                }
+                // the record's first three pairs
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const unsigned who = __ballot_sync(0xffffffffu, sv && pos == q);
+                    if (who) {
+                        const int src = __ffs(who) - 1;
+                        const unsigned cq = (unsigned)__shfl_sync(0xffffffffu, c, src);
+                        const unsigned xq = __shfl_sync(0xffffffffu, __float_as_uint(x), src);
+                        rx |= cq << (8 * (q + 1));
+                        rv[q] = xq;
+                    }
+                }
+                before += __popc(bw[w]);
+            }
+            if (dr)
+                for (int c = 32 * WD + lane; c < a.dld; c += 32) dr[c] = 0.f;
+            if (lane == 0) {
+                a.cnt[rr] = nb;
+                if (a.rec) a.rec[rr] = make_uint4(rx, rv[0], rv[1], rv[2]);
+                if (a.zero_old) a.cnt_old[rr] = 0;
+                if (tr) a.hnz[sl] = 1;
+            }
+            __syncwarp();
+        }
+        if (a.nzmask) {
+            const unsigned word = __ballot_sync(0xffffffffu, nonzero);
+            const int64_t w0 = base + warp * 32;
+            if (lane == 0 && w0 < b1) a.nzmask[w0 >> 5] = word;
+        }
+        // this round's rows with off-diagonal products, in row order
+        const unsigned ob = __ballot_sync(0xffffffffu, offdiag);
+        if (lane == 0) wcount[warp] = __popc(ob);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int w = 0; w < NW; ++w) {
+            if (w < warp) off += wcount[w];
+            tot += wcount[w];
+        }
+        if (offdiag) list[off + __popc(ob & ((1u << lane) - 1u))] = (int)(r - base);
+        __syncthreads();
+        if (warp == 0) {
+            for (int i = 0; i < tot; ++i) {
+                const int lr = list[i];
+                const int64_t rr = base + lr;
+                const int L = a.cnt[rr];
+                if (L <= kEmitSStage) {
+                    const int2* sp = stage + lr * kEmitSStage;
+                    for (int ia = 0; ia + 1 < L; ++ia) {
+                        const int2 pa = sp[ia];
+                        const double va = (double)__int_as_float(pa.y);
+                        const int ib = ia + 1 + lane;
+                        if (ib < L) {
+                            const int2 pb = sp[ib];
+                            double* tp = T + tri_index(pa.x, pb.x, k);
+                            *tp = fma(va, (double)__int_as_float(pb.y), *tp);
+                        }
+                        __syncwarp();
+                    }
+                } else {
+                    // a long row (rare): its pairs from global memory
+                    const int32_t* cr = a.col + rr * ld;
+                    const float* vr = a.val + rr * ld;
+                    for (int ia = 0; ia + 1 < L; ++ia) {
+                        const int ca = cr[ia];
+                        const double va = (double)vr[ia];
+                        for (int ib = ia + 1 + lane; ib < L; ib += 32) {
+                            double* tp = T + tri_index(ca, cr[ib], k);
+                            *tp = fma(va, (double)vr[ib], *tp);
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+        // the next round's first barrier orders warp 0's reads of `list`
+        // before the list is rewritten
+    }
+    __syncthreads();
+    for (int e = tid; e < ntri; e += blockDim.x) a.gram_part[(size_t)e * a.P + blockIdx.x] = T[e];
+    s_diff = warp_sum(s_diff);
+    s_new = warp_sum(s_new);
+    s_old = warp_sum(s_old);
+    s_cross = warp_sum(s_cross);
+    if (lane == 0) {
+        red[warp][0] = s_diff;
+        red[warp][1] = s_new;
+        red[warp][2] = s_old;
+        red[warp][3] = s_cross;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        double sum = 0.0;
+        for (int w = 0; w < NW; ++w) sum += red[w][tid];
+        a.scal_part[(size_t)tid * gridDim.x + blockIdx.x] = sum;
+    }
+}
+
+cudaError_t launch_emit_s(const float* Xt, int64_t ldx, int64_t rows, int k, uint32_t* rowbits,
+                          EllDev cur, EllDev old, bool residual, const float* Y, int64_t ldy,
+                          double* gram_part, double* scal_part, int nblocks, int P,
+                          cudaStream_t st)
+{
+    EmitSArgs a;
+    a.Xt = Xt;
+    a.ldx = ldx;
+    a.rows = rows;
+    a.k = k;
+    a.rowbits = rowbits;
+    a.cnt = cur.cnt;
+    a.col = cur.col;
+    a.val = static_cast<float*>(cur.val);
+    a.dense = static_cast<float*>(cur.dense);
+    a.rec = cur.rec;
+    a.nzmask = cur.nzmask;
+    a.hslot = cur.h > 0 ? cur.hslot : nullptr;
+    a.htab = static_cast<float*>(cur.htab);
+    a.hnz = cur.hnz;
+    a.ld = cur.ld;
+    a.dld = cur.dld;
+    a.heavy = cur.heavy;
+    a.cnt_old = old.cnt;
+    a.col_old = old.col;
+    a.val_old = static_cast<const float*>(old.val);
+    a.residual = residual && old.cnt != nullptr;
+    a.zero_old = old.cnt != nullptr;
+    a.Y = Y;
+    a.ldy = ldy;
+    a.gram_part = gram_part;
+    a.scal_part = scal_part;
+    a.P = P;
+    const size_t smem = (((size_t)k * (k + 1) / 2 * sizeof(double) + 15) & ~(size_t)15) +
+                        (size_t)kEmitSThreads * kEmitSStage * sizeof(int2);
+    const int wd = (k + 31) / 32;
+    switch (wd) {
+    case 1: emit_s_kernel<1><<<nblocks, kEmitSThreads, smem, st>>>(a); break;
+    case 2: emit_s_kernel<2><<<nblocks, kEmitSThreads, smem, st>>>(a); break;
+    case 3: emit_s_kernel<3><<<nblocks, kEmitSThreads, smem, st>>>(a); break;
+    case 4: emit_s_kernel<4><<<nblocks, kEmitSThreads, smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Off-diagonal Gram products of the frequent rows, from their dense table
+// (h rows of ld floats): block b adds the products of its share of the
+// rows into its partial column pcol0 + b (entry-major, upper triangle,
+// diagonal entries 0: the selector provides the diagonal).  Thread tid owns
+// the entries e = tid + 256 s in FP64 registers.
+constexpr int kTableRows = 16;   // table rows staged per pass
+
+template <int S>
+__global__ void __launch_bounds__(256)
+gram_table_kernel(const float* __restrict__ htab, const uint8_t* __restrict__ hnz, int h,
+                  int k, int ld, double* gram_part, int P, int pcol0)
+{
+    __shared__ double rowd[kTableRows][kMaxK];
+    const int tid = threadIdx.x;
+    const int ntri = k * (k + 1) / 2;
+    int cd[S];
+    double acc[S];
+    {
+        int e0 = tid, c = 0, rowlen = k, start = 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            acc[s] = 0.0;
+            const int e = e0 + s * 256;
+            if (e < ntri) {
+                while (e >= start + rowlen) {
+                    start += rowlen;
+                    ++c;
+                    --rowlen;
+                }
+                const int d = c + (e - start);
+                cd[s] = c < d ? ((c << 16) | d) : -1;
+            } else {
+                cd[s] = -1;
+            }
+        }
+    }
+    const int r0 = (int)((int64_t)h * blockIdx.x / gridDim.x);
+    const int r1 = (int)((int64_t)h * (blockIdx.x + 1) / gridDim.x);
+    // up to kTableRows rows at a time: one load round trip and two barriers
+    // per pass (a zero row contributes zeros)
+    for (int rb = r0; rb < r1; rb += kTableRows) {
+        const int nr = r1 - rb < kTableRows ? r1 - rb : kTableRows;
+        __syncthreads();
+        for (int e = tid; e < nr * k; e += blockDim.x) {
+            const int q = e / k, c = e - q * k;
+            rowd[q][c] = hnz[rb + q] ? (double)htab[(int64_t)(rb + q) * ld + c] : 0.0;
+        }
+        __syncthreads();
+        for (int q = 0; q < nr; ++q) {
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                if (cd[s] >= 0) acc[s] = fma(rowd[q][cd[s] >> 16], rowd[q][cd[s] & 0xffff], acc[s]);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int e = tid + s * 256;
+        if (e < ntri) gram_part[(size_t)e * P + pcol0 + blockIdx.x] = acc[s];
+    }
+}
+
+cudaError_t launch_gram_table(const EllDev& F, int k, double* gram_part, int P, int pcol0,
+                              int nblocks, cudaStream_t st)
+{
+    if (F.h <= 0) return cudaSuccess;
+    const int ntri = k * (k + 1) / 2;
+    const int S = (ntri + 255) / 256;
+    const float* tab = static_cast<const float*>(F.htab);
+    if (S <= 4) gram_table_kernel<4><<<nblocks, 256, 0, st>>>(tab, F.hnz, F.h, k, F.ld, gram_part, P, pcol0);
+    else if (S <= 8) gram_table_kernel<8><<<nblocks, 256, 0, st>>>(tab, F.hnz, F.h, k, F.ld, gram_part, P, pcol0);
+    else if (S <= 16) gram_table_kernel<16><<<nblocks, 256, 0, st>>>(tab, F.hnz, F.h, k, F.ld, gram_part, P, pcol0);
+    else if (S <= 33) gram_table_kernel<33><<<nblocks, 256, 0, st>>>(tab, F.hnz, F.h, k, F.ld, gram_part, P, pcol0);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
@@ -722,15 +1210,17 @@ cudaError_t launch_gram_inverse(const double* G, int k, double* Ginv64, T* GinvT
 
 template <typename T>
 __global__ void norm2_part_kernel(const T* __restrict__ v, int64_t count,
+                                  const T* __restrict__ v2, int64_t count2,
                                   double* part)
 {
     __shared__ double red[32];
-    const int64_t chunk = (count + gridDim.x - 1) / gridDim.x;
+    const int64_t total = count + count2;
+    const int64_t chunk = (total + gridDim.x - 1) / gridDim.x;
     const int64_t b0 = (int64_t)blockIdx.x * chunk;
-    const int64_t b1 = b0 + chunk < count ? b0 + chunk : count;
+    const int64_t b1 = b0 + chunk < total ? b0 + chunk : total;
     double s = 0.0;
     for (int64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
-        const double x = (double)v[e];
+        const double x = e < count ? (double)v[e] : (double)v2[e - count];
         s += x * x;
     }
     s = warp_sum(s);
@@ -753,10 +1243,11 @@ __global__ void sum_parts_kernel(const double* part, int n, double* out)
 }
 
 template <typename T>
-cudaError_t launch_norm2(const T* val, int64_t count, double* part,
-                         int nparts, double* out, cudaStream_t st)
+cudaError_t launch_norm2(const T* val, int64_t count, const T* val2, int64_t count2,
+                         double* part, int nparts, double* out, cudaStream_t st)
 {
-    norm2_part_kernel<T><<<nparts, 256, 0, st>>>(val, count, part);
+    if (val2 == nullptr) count2 = 0;
+    norm2_part_kernel<T><<<nparts, 256, 0, st>>>(val, count, val2, count2, part);
     sum_parts_kernel<<<1, 32, 0, st>>>(part, nparts, out);
     return cudaGetLastError();
 }
@@ -899,6 +1390,14 @@ cudaError_t setup_factor()
     e = cudaFuncSetAttribute(emit_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(emit_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(emit_s_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(emit_s_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(emit_s_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(emit_s_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     return e;
 }
 
@@ -908,7 +1407,8 @@ cudaError_t setup_factor()
                                         int64_t, double*, double*, int, cudaStream_t);          \
     template cudaError_t launch_gram_inverse<T>(const double*, int, double*, T*, unsigned*,         \
                                             cudaStream_t);                                      \
-    template cudaError_t launch_norm2<T>(const T*, int64_t, double*, int, double*, cudaStream_t); \
+    template cudaError_t launch_norm2<T>(const T*, int64_t, const T*, int64_t, double*, int,      \
+                                         double*, cudaStream_t);                                 \
     template cudaError_t launch_ell_dot<T>(int64_t, int, EllDev, const T*, int64_t, double*,    \
                                            int, double*, cudaStream_t);                         \
     template cudaError_t launch_ell_to_colmajor<T>(int64_t, int, EllDev, T*, int64_t,          \

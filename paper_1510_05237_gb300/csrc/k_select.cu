@@ -135,16 +135,28 @@ __device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int 
     return r;
 }
 
+// Optional survivor marking (COLUMN mode): once a column's threshold is
+// known, each CTA walks its slice again, sets bit (c % 32) of word c / 32 of
+// row i in rowbits ([rows][mark_words]) for every survivor and writes the
+// sum of the survivors' squares (the column's diagonal entry of F^T F, in
+// FP64, fixed order) to diag_part[c * clusterDim + rank].
+struct SelMark {
+    uint32_t* rowbits = nullptr;
+    int words = 0;
+    double* diag_part = nullptr;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kSelThreads)
 select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
               int64_t t, int mode, typename KeyBits<T>::K* __restrict__ tau_out,
-              uint32_t* __restrict__ cut_out)
+              uint32_t* __restrict__ cut_out, SelMark mark)
 {
     using K = typename KeyBits<T>::K;
     constexpr int TS = KeyBits<T>::top_shift;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double wsq[kSelThreads / 32];
     unsigned* hist = reinterpret_cast<unsigned*>(smem_raw + SelSmem<T>::hist);
     unsigned long long* wsum = reinterpret_cast<unsigned long long*>(smem_raw + SelSmem<T>::misc);
     unsigned long long* res = wsum + 32;
@@ -181,6 +193,7 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
             tau_out[seg] = mode == TOPT_NONE ? (K)0 : ~(K)0;
             cut_out[seg] = 0xffffffffu;
         }
+        if (mark.rowbits && tid == 0) mark.diag_part[(size_t)seg * C + crank] = 0.0;
         return;
     }
     // visits this CTA's entries with their keys: 16-byte loads (four in
@@ -229,6 +242,28 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
         }
     };
     auto key_at = [&](int e) -> K { return KeyBits<T>::of(Xt[addr(lo + e)]); };
+    // the survivors of this CTA's slice (column mode): row bits and the
+    // FP64 sum of squares, reduced in a fixed order
+    auto mark_survivors = [&](K tau_m, uint32_t cut_m) {
+        double sq = 0.0;
+        const uint32_t bit = 1u << (seg & 31);
+        uint32_t* word = mark.rowbits + (seg >> 5);
+        for_each([&](K key, int e, bool in) {
+            if (in && keep_entry<T>(KeyBits<T>::value(key), tau_m, cut_m, (uint32_t)(lo + e))) {
+                atomicOr(word + (size_t)(lo + e) * mark.words, bit);
+                const double x = (double)KeyBits<T>::value(key);
+                sq = fma(x, x, sq);
+            }
+        });
+        for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+        if ((tid & 31) == 0) wsq[tid >> 5] = sq;
+        __syncthreads();
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsq[w];
+            mark.diag_part[(size_t)seg * C + crank] = tot;
+        }
+    };
 
     // ---- pass 1: histogram of the top 11 bits of the positive entries
     for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
@@ -245,6 +280,7 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
             tau_out[seg] = 0;
             cut_out[seg] = 0xffffffffu;
         }
+        if (mark.rowbits) mark_survivors((K)0, 0xffffffffu);
         return;
     }
     need -= s1.before;
@@ -351,18 +387,20 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
         tau_out[seg] = tau;
         cut_out[seg] = cut;
     }
+    if (mark.rowbits) mark_survivors(tau, cut);
 }
 
 template <typename T>
 cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
                           int64_t t, int mode, void* tau, uint32_t* cut,
-                          cudaStream_t st, int sm_count)
+                          cudaStream_t st, int sm_count, uint32_t* rowbits,
+                          double* diag_part)
 {
     if (rows == 0) return cudaSuccess;
     const int nseg = mode == TOPT_MATRIX ? 1 : k;
     const int64_t seg_len = mode == TOPT_MATRIX ? (int64_t)k * rows : rows;
-    // about two clusters' CTAs per SM over all segments, at most 8 per
-    // cluster, at least 2048 entries per CTA
+    // about two CTAs per SM over all segments, at most kSelMaxCluster per
+    // cluster (larger clusters measured slower), at least 2048 entries per CTA
     int C = (int)((2 * (int64_t)sm_count + nseg - 1) / nseg);
     if (C > kSelMaxCluster) C = kSelMaxCluster;
     const int64_t by_len = (seg_len + 2047) / 2048;
@@ -382,8 +420,28 @@ cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     using K = typename KeyBits<T>::K;
+    SelMark mark;
+    if (rowbits && mode == TOPT_COLUMN) {
+        mark.rowbits = rowbits;
+        mark.words = (k + 31) / 32;
+        mark.diag_part = diag_part;
+    }
     return cudaLaunchKernelEx(&cfg, select_kernel<T>, Xt, ldx, rows, k, t, mode,
-                              static_cast<K*>(tau), cut);
+                              static_cast<K*>(tau), cut, mark);
+}
+
+// Cluster size launch_select uses for k columns of `rows` entries (the
+// number of diagonal partials per column it writes when marking).
+int select_cluster(int64_t rows, int k, int mode, int sm_count)
+{
+    const int nseg = mode == TOPT_MATRIX ? 1 : k;
+    const int64_t seg_len = mode == TOPT_MATRIX ? (int64_t)k * rows : rows;
+    int C = (int)((2 * (int64_t)sm_count + nseg - 1) / nseg);
+    if (C > kSelMaxCluster) C = kSelMaxCluster;
+    const int64_t by_len = (seg_len + 2047) / 2048;
+    if (C > by_len) C = (int)by_len;
+    if (C < 1) C = 1;
+    return C;
 }
 
 // In-place projection + enforcement of a caller's dense rows x k buffer
@@ -434,8 +492,8 @@ cudaError_t setup_select()
                                 (int)kSelSmemMax);
 }
 
-template cudaError_t launch_select<float>(const float*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int);
-template cudaError_t launch_select<double>(const double*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int);
+template cudaError_t launch_select<float>(const float*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int, uint32_t*, double*);
+template cudaError_t launch_select<double>(const double*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int, uint32_t*, double*);
 template cudaError_t launch_apply_thresholds<float>(float*, int64_t, int, int64_t, int, const void*, const uint32_t*, unsigned*, cudaStream_t);
 template cudaError_t launch_apply_thresholds<double>(double*, int64_t, int, int64_t, int, const void*, const uint32_t*, unsigned*, cudaStream_t);
 

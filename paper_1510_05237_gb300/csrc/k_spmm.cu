@@ -1,35 +1,38 @@
 // k_spmm.cu -- the sparse products of Alg. 2 steps 1 and 3:
 //   Y = A^T U (V half)   and   Y = A V (U half).
 //
-// A is streamed once per product from a sliced-ELLPACK layout (SELL-32):
-// a warp's 32 lanes walk 32 segments of about the same length, so every
-// load of A is a coalesced 128-byte transaction.  A row is cut into 1..32
-// segments of at most 64 entries held by adjacent lanes; each lane sums its
-// segment and the lanes of a row are combined by a fixed shuffle tree.
+// Each product has up to two parts, run one after the other on the stream.
 //
-// The factor F is gathered two ways, chosen per factor row:
-//   light rows (fewer than `heavy` nonzeros, most rows of an enforced-sparse
-//     factor): one 16-byte record holds the row's count and its first three
-//     (column, value) pairs, so a row of up to three nonzeros costs a single
-//     load; each value is added into a per-thread accumulator in shared
-//     memory, slot c of thread tid at acc[c * blockDim + tid] -- a warp's
-//     lanes always touch 32 distinct banks whatever columns they update;
-//   heavy rows (nearly dense: the rows of the most frequent terms end up in
-//     almost every column's top-t): each lane reads its own entry's row
-//     from the row's dense copy (16-byte loads) into register accumulators.
-// The number of warps that share a slice's columns (1, 2 or 4: fewer
-// registers and slots per thread, so more warps in flight) and the launch's
-// shared-memory carveout (the rest of the SM's memory is L1, which holds the
-// heavy rows) are a launch shape (SpmmConfig) timed by the host; all shapes
-// add the same products in the same order, so the result does not depend
-// on the choice.
-// The loop is software-pipelined: while a step's gathers run, the records
-// of the next step and the entries of A of the next two are in flight, and
-// the slice's whole run of A is prefetched into the L2 when the warp starts
-// (deeper register pipelines measured slower: they cost registers the heavy
-// gathers need).
-// Sums are taken in a fixed order (storage order per lane, a fixed tree
-// across lanes, chunk order for very long rows), so the product is bitwise
+// SELL part (spmm_sell_*): A's entries are streamed once from a
+// sliced-ELLPACK layout (SELL-32): a warp's 32 lanes walk 32 segments of
+// about the same length, so every load of A is a coalesced 128-byte
+// transaction.  A row is cut into 1..32 segments of at most 64 entries held
+// by adjacent lanes; each lane sums its segment and the lanes of a row are
+// combined by a fixed shuffle tree.  The factor row an entry gathers is read
+// sparsely: a bitmask (L1-resident) skips rows that are zero; otherwise one
+// 16-byte record holds the row's count and its first three (column, value)
+// pairs, longer rows continue in the row-packed pairs, and the rare dense
+// row is read from its dense copy.  Every product is added into per-thread
+// accumulators in shared memory, slot c of thread tid at acc[c * B + tid]
+// (a warp's lanes always touch 32 distinct banks, whatever columns they
+// update), so a thread needs few registers and many warps stay resident to
+// hide the latency of the gathers.
+//
+// Frequent part (spmm_freq_f32, FP32 form): on text corpora the factor rows
+// of the most frequent terms end up in nearly every column's top t, so the
+// entries that gather them (a large share of A's nonzeros) would each cost
+// a dense row of scattered loads.  These h rows are chosen once, when the
+// context is built (the gathered rows that the most entries of A reference,
+// as many as fit a 200 KB table); their entries are stored apart from the
+// SELL arrays, per output row.  One persistent CTA per SM stages the dense
+// copies of the h rows in shared memory with a TMA bulk copy; each warp walks
+// its output rows, a group of lanes per entry reading the entry's table row
+// with 128-bit shared loads (lanes over columns, conflict-free), and adds
+// its sum into the row of Y that the SELL part wrote.
+//
+// All sums are taken in a fixed order (storage order per lane, a fixed tree
+// across lanes, chunk order for very long rows, a fixed entry order per
+// group of lanes and a fixed tree across groups), so the product is bitwise
 // reproducible.
 #include "common.cuh"
 
@@ -50,6 +53,8 @@ struct SpmmParams {
     const T* fval;
     const T* fdense;
     const uint4* frec;
+    const uint32_t* fmask;
+    int mask_words;   // words of fmask (staged in shared memory when MASK == 2)
     int dld;
     int fld;
     int heavy;
@@ -60,20 +65,21 @@ struct SpmmParams {
 
 // FP32.  NS warps share a slice: warp h of the NS owns the output columns
 // [h * CW, min(KP, (h + 1) * CW)), CW = KP / NS rounded up to 4, for all 32
-// segments of the slice.  Each warp streams the slice's entries of A (the
-// NS warps read the same lines, mostly from L1), adds its columns of light
-// rows' values into its shared-memory slots and gathers its CW columns of
-// heavy rows (CW / 4 16-byte loads) into CW register accumulators.  A larger
-// NS means fewer registers and slots per thread, so more warps in flight
-// for the same shared memory, at the price of re-reading A and the records.
-// Every NS adds the same products in the same order.
+// segments of the slice.  Each of them streams the slice's entries (the NS
+// warps read the same lines, mostly from L1) and adds the products for its
+// columns into its slots.  A larger NS means fewer slots per thread, so more
+// warps in flight for the same shared memory, at the price of re-reading A
+// and the records.  Every NS adds the same products in the same order.
 template <int KP, int NS>
 struct SplitShape {
     static constexpr int CW = ((KP + NS - 1) / NS + 3) / 4 * 4;
 };
 
-template <int KP, int NS>
-__global__ void __launch_bounds__(256, KP > 64 ? 1 : 2)
+// MASK: 0 -- every entry loads its row's record; 1 -- zero rows are skipped
+// by the bitmask in global memory (the L1/L2); 2 -- the bitmask is first
+// copied into shared memory (after the slots).
+template <int KP, int NS, int MASK>
+__global__ void __launch_bounds__(256, 4)
 spmm_sell_f32_kernel(SpmmParams<float> p)
 {
     constexpr int CW = SplitShape<KP, NS>::CW;
@@ -87,21 +93,15 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
     const int c0 = h * CW;
     const int cw = KP - c0 < CW ? KP - c0 : CW;   // columns owned (> 0, multiple of 4)
     float* slots = reinterpret_cast<float*>(smem_raw);                   // CW x B
-    const int64_t s = (int64_t)blockIdx.x * (B >> 5) / NS + warp / NS;
-    if (s >= p.nslices || cw <= 0) return;
-    const int64_t seg = s * 32 + lane;
-
-    float acc[CW];
-#pragma unroll
-    for (int c = 0; c < CW; ++c) acc[c] = 0.f;
+    const uint32_t* __restrict__ fmask = p.fmask;
+    if constexpr (MASK == 2) {
+        uint32_t* sm = reinterpret_cast<uint32_t*>(slots + (size_t)CW * B);
+        for (int w = tid; w < p.mask_words; w += B) sm[w] = __ldg(p.fmask + w);
+        __syncthreads();
+        fmask = sm;
+    }
+    if (cw <= 0) return;
     float* my = slots + tid;
-#pragma unroll 4
-    for (int c = 0; c < CW; ++c) my[c * B] = 0.f;
-
-    const int len = p.slice_len[s];
-    const int64_t base = p.slice_ptr[s] + lane;
-    const int32_t* __restrict__ idx = p.idx + base;
-    const float* __restrict__ val = p.val + base;
     const uint4* __restrict__ rec = p.frec;
     const float4* __restrict__ dense4 = reinterpret_cast<const float4*>(p.fdense) + c0 / 4;
     const int dld4 = p.dld / 4;
@@ -109,131 +109,371 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
     const int fld = p.fld;
     const unsigned ucw = (unsigned)cw;
 
-    // one value of a light row: column c (absolute) if this warp owns it
-    auto add = [&](unsigned c, float x) {
+    // one product of a row's pair: column c (absolute) if this warp owns it.
+    // Every accumulation is an explicit fused multiply-add, so that all
+    // launch shapes (different instantiations) round the same way.
+    auto add = [&](unsigned c, float a, float v) {
         const unsigned r = c - (unsigned)c0;
-        if (r < ucw) my[r * B] += x;
+        if (r < ucw) my[r * B] = __fmaf_rn(a, v, my[r * B]);
     };
-    auto light = [&](int i, float a, const uint4& r) {
-        const int cnt = record_cnt(r.x);
-        if (cnt == 0 || cnt >= heavy) return;
-        add((r.x >> 8) & 0xffu, a * __uint_as_float(r.y));
-        if (cnt > 1) add((r.x >> 16) & 0xffu, a * __uint_as_float(r.z));
-        if (cnt > 2) add(r.x >> 24, a * __uint_as_float(r.w));
-        if (cnt > 3) {
-            const int32_t* cr = p.fcol + (int64_t)i * fld;
-            const float* vr = p.fval + (int64_t)i * fld;
-            add((unsigned)__ldg(cr + 3), a * __ldg(vr + 3));
-            for (int q = 4; q < cnt; q += 4) {
-                const int4 cc = __ldg(reinterpret_cast<const int4*>(cr + q));
-                const float4 vv = __ldg(reinterpret_cast<const float4*>(vr + q));
-                add((unsigned)cc.x, a * vv.x);
-                if (q + 1 < cnt) add((unsigned)cc.y, a * vv.y);
-                if (q + 2 < cnt) add((unsigned)cc.z, a * vv.z);
-                if (q + 3 < cnt) add((unsigned)cc.w, a * vv.w);
+    // the pairs of row i beyond the record's three, or the whole dense copy
+    // of a heavy row
+    auto gather_long = [&](int i, float a, int cnt) {
+        if (cnt >= heavy) {
+            const float4* d = dense4 + (int64_t)i * dld4;
+            for (int q = 0; 4 * q < cw; ++q) {
+                const float4 v = __ldg(d + q);
+                my[(4 * q + 0) * B] = __fmaf_rn(a, v.x, my[(4 * q + 0) * B]);
+                my[(4 * q + 1) * B] = __fmaf_rn(a, v.y, my[(4 * q + 1) * B]);
+                my[(4 * q + 2) * B] = __fmaf_rn(a, v.z, my[(4 * q + 2) * B]);
+                my[(4 * q + 3) * B] = __fmaf_rn(a, v.w, my[(4 * q + 3) * B]);
+            }
+            return;
+        }
+        const int32_t* cr = p.fcol + (int64_t)i * fld;
+        const float* vr = p.fval + (int64_t)i * fld;
+        add((unsigned)__ldg(cr + 3), a, __ldg(vr + 3));
+        for (int q = 4; q < cnt; q += 4) {
+            const int4 cc = __ldg(reinterpret_cast<const int4*>(cr + q));
+            const float4 vv = __ldg(reinterpret_cast<const float4*>(vr + q));
+            add((unsigned)cc.x, a, vv.x);
+            if (q + 1 < cnt) add((unsigned)cc.y, a, vv.y);
+            if (q + 2 < cnt) add((unsigned)cc.z, a, vv.z);
+            if (q + 3 < cnt) add((unsigned)cc.w, a, vv.w);
+        }
+    };
+    // Slices are sorted longest first; the warps (groups of NS) take them
+    // round-robin, so every warp gets about the same work.
+    const int64_t stride = (int64_t)gridDim.x * (B >> 5) / NS;
+    for (int64_t s = (int64_t)blockIdx.x * (B >> 5) / NS + warp / NS; s < p.nslices; s += stride) {
+        const int64_t seg = s * 32 + lane;
+#pragma unroll 4
+        for (int c = 0; c < CW; ++c) my[c * B] = 0.f;
+        const int len = p.slice_len[s];   // a multiple of 4
+        const int nq = len >> 2;
+        const int64_t base = p.slice_ptr[s] + lane * 4;
+        const int4* __restrict__ idx4 = reinterpret_cast<const int4*>(p.idx + base);
+        const float4* __restrict__ val4 = reinterpret_cast<const float4*>(p.val + base);
+
+        // The slice's entries of A are one contiguous run per array: ask the
+        // L2 for all of it now, so that the loads below wait on the L2 rather
+        // than on HBM.
+        if (lane == 0 && len > 0) {
+            const unsigned bytes = (unsigned)len * 128u;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                         :: "l"(p.idx + p.slice_ptr[s]), "r"(bytes) : "memory");
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                         :: "l"(p.val + p.slice_ptr[s]), "r"(bytes) : "memory");
+        }
+
+        // Quads of four entries per lane (one 16-byte load of indices and
+        // one of values), two quads ahead.  A quad's bitmask words (MASK),
+        // then its records, are loaded together (four independent loads per
+        // stage).  Its products: the record's pairs (up to three per entry)
+        // as twelve pair slots, visited in order and only where some lane
+        // of the warp has a pair, so the warp does not diverge; rows with
+        // more nonzeros (rare in an enforced-sparse factor) afterwards.
+        const int4 none_i = make_int4(-1, -1, -1, -1);
+        const float4 none_a = make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+        int4 i0 = nq > 0 ? __ldcs(idx4) : none_i;
+        float4 a0 = nq > 0 ? __ldcs(val4) : none_a;
+        int4 i1 = nq > 1 ? __ldcs(idx4 + 32) : none_i;
+        float4 a1 = nq > 1 ? __ldcs(val4 + 32) : none_a;
+        for (int q = 0; q < nq; ++q) {
+            int4 i2 = none_i;
+            float4 a2 = none_a;
+            if (q + 2 < nq) {
+                i2 = __ldcs(idx4 + (int64_t)(q + 2) * 32);
+                a2 = __ldcs(val4 + (int64_t)(q + 2) * 32);
+            }
+            const int ii[4] = {i0.x, i0.y, i0.z, i0.w};
+            const float aa[4] = {a0.x, a0.y, a0.z, a0.w};
+            uint4 rc[4];
+            if constexpr (MASK > 0) {
+                // skip the records of zero rows (one more dependent load)
+                uint32_t mw[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) mw[u] = ii[u] >= 0 ? fmask[ii[u] >> 5] : 0u;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    rc[u] = (ii[u] >= 0 && ((mw[u] >> (ii[u] & 31)) & 1u)) ? __ldg(rec + ii[u]) : zero4;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) rc[u] = ii[u] >= 0 ? __ldg(rec + ii[u]) : zero4;
+            }
+            // this lane's pair slots (bit 3u + j: pair j of entry u) and its
+            // longer rows (bit 12 + u)
+            unsigned mine = 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = record_cnt(rc[u].x);
+                const int light = c >= heavy ? 0 : (c < 3 ? c : 3);
+                mine |= ((1u << light) - 1u) << (3 * u);
+                if (c > 3) mine |= 1u << (12 + u);
+            }
+            const unsigned need = __reduce_or_sync(FULL, mine);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const unsigned bit = 1u << (3 * u + j);
+                    if (need & bit) {
+                        if (mine & bit) {
+                            const unsigned col = (rc[u].x >> (8 * (j + 1))) & 0xffu;
+                            const unsigned vb = j == 0 ? rc[u].y : (j == 1 ? rc[u].z : rc[u].w);
+                            add(col, aa[u], __uint_as_float(vb));
+                        }
+                    }
+                }
+            }
+            if (need >> 12) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (mine & (1u << (12 + u))) gather_long(ii[u], aa[u], record_cnt(rc[u].x));
+            }
+            i0 = i1;
+            a0 = a1;
+            i1 = i2;
+            a1 = a2;
+        }
+
+        // combine the lanes [head, end) of each row, four columns at a time:
+        // fixed tree, lane head ends with the row's sum
+        const int grp = p.seg_grp[seg];
+        const int head = grp >> 8, end = grp & 0xff;
+        const int maxg = __reduce_max_sync(FULL, (unsigned)(end - head));
+        const int row = p.seg_row[seg];
+        const int part = p.seg_part[seg];
+        float* out = (part < 0 ? p.Y + (int64_t)(row < 0 ? 0 : row) * KP
+                               : p.partials + (int64_t)part * KP) + c0;
+        float4* o4 = reinterpret_cast<float4*>(out);
+        const bool writer = row >= 0 && lane == head;
+#pragma unroll 1
+        for (int q = 0; 4 * q < cw; ++q) {
+            float v0 = my[(4 * q + 0) * B], v1 = my[(4 * q + 1) * B];
+            float v2 = my[(4 * q + 2) * B], v3 = my[(4 * q + 3) * B];
+            for (int off = 1; off < maxg; off <<= 1) {
+                const bool take = lane + off < end;
+                const float t0 = __shfl_down_sync(FULL, v0, off);
+                const float t1 = __shfl_down_sync(FULL, v1, off);
+                const float t2 = __shfl_down_sync(FULL, v2, off);
+                const float t3 = __shfl_down_sync(FULL, v3, off);
+                if (take) {
+                    v0 += t0;
+                    v1 += t1;
+                    v2 += t2;
+                    v3 += t3;
+                }
+            }
+            if (writer) o4[q] = make_float4(v0, v1, v2, v3);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Frequent part (FP32).
+
+// A group of LPG lanes (a power of two, >= KP / 4) handles one entry: lane
+// ql of the group holds the float4 of columns [4 ql, 4 ql + 4).  A warp step
+// processes G = 32 / LPG entries.
+template <int KP>
+struct FreqShape {
+    static constexpr int Q = KP / 4;
+    static constexpr int LPG = Q <= 1 ? 1 : Q <= 2 ? 2 : Q <= 4 ? 4 : Q <= 8 ? 8 : Q <= 16 ? 16 : 32;
+    static constexpr int G = 32 / LPG;
+};
+
+struct FreqParams {
+    const int64_t* hptr;
+    const uint16_t* hidx;
+    const float* hval;
+    const int32_t* hwarp;
+    int nchunks;
+    int* counter;
+    const float* htab;     // [h][KP]
+    const uint8_t* hnz;    // [h]
+    int h;
+    float* Y;              // rows x KP: holds the SELL part, receives the sum
+    unsigned* status;
+    long long wait_limit;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Two FP32 lanes in one 64-bit register: (x, y) = (low, high) word.
+__device__ __forceinline__ unsigned long long pack2(float a)
+{
+    const unsigned long long u = __float_as_uint(a);
+    return u | (u << 32);
+}
+// acc = a * v + acc on both lanes (IEEE round-to-nearest fused multiply-add
+// per lane, the same rounding as fmaf).
+__device__ __forceinline__ void fma2(unsigned long long& acc, unsigned long long a,
+                                     unsigned long long v)
+{
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(v));
+}
+__device__ __forceinline__ float4 unpack4(unsigned long long xy, unsigned long long zw)
+{
+    return make_float4(__uint_as_float((unsigned)xy), __uint_as_float((unsigned)(xy >> 32)),
+                       __uint_as_float((unsigned)zw), __uint_as_float((unsigned)(zw >> 32)));
+}
+
+// Waits (bounded) for phase 0 of the mbarrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_phase0(uint32_t mbar, long long limit)
+{
+    for (long long it = 0; it < limit; ++it) {
+        uint32_t done = 0;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(mbar), "r"(0u) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int KP>
+__global__ void __launch_bounds__(kHThreads, 1)
+spmm_freq_f32_kernel(FreqParams p)
+{
+    using S = FreqShape<KP>;
+    constexpr int Q = S::Q, LPG = S::LPG, G = S::G;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(16) int2 wstage[kHThreads];
+    float* tab = reinterpret_cast<float*>(smem_raw);                       // [h][KP]
+    uint8_t* nz = smem_raw + (size_t)p.h * KP * 4;                          // [h]
+    const int tid = threadIdx.x;
+    const uint32_t bar = smem_addr(&mbar);
+    const uint32_t bytes = (uint32_t)p.h * KP * 4u;   // a multiple of 16
+
+    // stage the dense table: TMA bulk copies (32 KB each) completing on one
+    // mbarrier; the nonzero flags by plain loads meanwhile
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(1u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     :: "r"(bar), "r"(bytes) : "memory");
+        for (uint32_t off = 0; off < bytes; off += 32768u) {
+            const uint32_t n = bytes - off < 32768u ? bytes - off : 32768u;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                :: "r"(smem_addr(smem_raw + off)), "l"(reinterpret_cast<const unsigned char*>(p.htab) + off),
+                   "r"(n), "r"(bar) : "memory");
+        }
+    }
+    for (int i = tid; i < p.h; i += blockDim.x) nz[i] = p.hnz[i];
+    __syncthreads();
+    if (!mbar_wait_phase0(bar, p.wait_limit)) {
+        // the copy did not land: report, give it one more bounded wait so
+        // that it does not write into a later CTA's memory, and stop
+        if (tid == 0) atomicOr(p.status, ST_TIMEOUT);
+        mbar_wait_phase0(bar, p.wait_limit);
+        return;
+    }
+
+    const int lane = tid & 31;
+    const int grp = lane / LPG, ql = lane % LPG;
+    const bool colact = ql < Q;
+    // A chunk of up to 32 of a row's entries is staged per warp as (slot,
+    // value) pairs, slot -1 for a zero table row; group g takes the entry
+    // pairs (2j, 2j + 1) for j = g, g + G, ... (one 128-bit shared load per
+    // pair) and adds them with packed two-lane FMAs (each lane rounds as
+    // fmaf does) into two accumulators.
+    int2* stage = wstage + (tid >> 5) * 32;
+    // The warps take chunks of rows in turn (a CTA that starts late, e.g.
+    // on an SM shared with another kernel, does not hold the others up);
+    // every row is summed by one warp in a fixed order, so the result does
+    // not depend on which warp takes it.
+    for (;;) {
+        int ch = 0;
+        if (lane == 0) ch = atomicAdd(p.counter, 1);
+        ch = __shfl_sync(FULL, ch, 0);
+        if (ch >= p.nchunks) break;
+        const int r0 = p.hwarp[ch], r1 = p.hwarp[ch + 1];
+        if (r0 >= r1) continue;
+        // this chunk's entries are one contiguous run: ask the L2 for it
+        if (lane == 0) {
+            const int64_t e0 = p.hptr[r0], e1 = p.hptr[r1];
+            if (e1 > e0) {
+                const uintptr_t ia = reinterpret_cast<uintptr_t>(p.hidx + e0) & ~(uintptr_t)15;
+                const uintptr_t ib = (reinterpret_cast<uintptr_t>(p.hidx + e1) + 15) & ~(uintptr_t)15;
+                const uintptr_t va = reinterpret_cast<uintptr_t>(p.hval + e0) & ~(uintptr_t)15;
+                const uintptr_t vb = (reinterpret_cast<uintptr_t>(p.hval + e1) + 15) & ~(uintptr_t)15;
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                             :: "l"(ia), "r"((unsigned)(ib - ia)) : "memory");
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                             :: "l"(va), "r"((unsigned)(vb - va)) : "memory");
             }
         }
-    };
-    // this lane's heavy entry: its CW columns of the dense row
-    auto heavy_row = [&](int i, float a) {
-        const float4* r = dense4 + (int64_t)i * dld4;
+        int64_t q0 = p.hptr[r0];
+        for (int r = r0; r < r1; ++r) {
+            const int64_t q1 = p.hptr[r + 1];
+            if (q1 == q0) continue;
+            // the row's SELL part, loaded early
+            float4* yr = reinterpret_cast<float4*>(p.Y + (int64_t)r * KP) + ql;
+            float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (grp == 0 && colact) yv = *yr;
+            unsigned long long a0xy = 0ull, a0zw = 0ull, a1xy = 0ull, a1zw = 0ull;
+            for (int64_t qb = q0; qb < q1; qb += 32) {
+                const int64_t e = qb + lane;
+                int sl = -1;
+                float a = 0.f;
+                if (e < q1) {
+                    sl = p.hidx[e];
+                    a = p.hval[e];
+                    if (nz[sl] == 0) sl = -1;
+                }
+                stage[lane] = make_int2(sl, __float_as_int(a));
+                __syncwarp();
+                const int n = q1 - qb < 32 ? (int)(q1 - qb) : 32;
+                for (int j = 2 * grp; j < n; j += 2 * G) {
+                    const int4 ee = *reinterpret_cast<const int4*>(stage + j);   // entries j, j + 1
+                    const int s1 = j + 1 < n ? ee.z : -1;
+                    if (colact) {
+                        if (ee.x >= 0) {
+                            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(
+                                tab + (size_t)ee.x * KP + 4 * ql);
+                            const unsigned long long a2 = pack2(__int_as_float(ee.y));
+                            fma2(a0xy, a2, v.x);
+                            fma2(a0zw, a2, v.y);
+                        }
+                        if (s1 >= 0) {
+                            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(
+                                tab + (size_t)s1 * KP + 4 * ql);
+                            const unsigned long long a2 = pack2(__int_as_float(ee.w));
+                            fma2(a1xy, a2, v.x);
+                            fma2(a1zw, a2, v.y);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            const float4 acc0 = unpack4(a0xy, a0zw), acc1 = unpack4(a1xy, a1zw);
+            float4 acc = make_float4(acc0.x + acc1.x, acc0.y + acc1.y, acc0.z + acc1.z, acc0.w + acc1.w);
+            // the groups' sums in a fixed tree; group 0 adds to the SELL part
 #pragma unroll
-        for (int q = 0; q < CW / 4; ++q) {
-            if (4 * q >= cw) break;
-            const float4 v = __ldg(r + q);
-            acc[4 * q + 0] = fmaf(a, v.x, acc[4 * q + 0]);
-            acc[4 * q + 1] = fmaf(a, v.y, acc[4 * q + 1]);
-            acc[4 * q + 2] = fmaf(a, v.z, acc[4 * q + 2]);
-            acc[4 * q + 3] = fmaf(a, v.w, acc[4 * q + 3]);
-        }
-    };
-    auto load2 = [&](int pp, int* ii, float* aa) {
-        ii[0] = pp < len ? __ldcs(idx + (int64_t)pp * 32) : -1;
-        aa[0] = pp < len ? __ldcs(val + (int64_t)pp * 32) : 0.f;
-        ii[1] = pp + 1 < len ? __ldcs(idx + (int64_t)(pp + 1) * 32) : -1;
-        aa[1] = pp + 1 < len ? __ldcs(val + (int64_t)(pp + 1) * 32) : 0.f;
-    };
-    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-    auto rec2 = [&](const int* ii, uint4* rr) {
-        rr[0] = ii[0] >= 0 ? __ldg(rec + ii[0]) : zero4;
-        rr[1] = ii[1] >= 0 ? __ldg(rec + ii[1]) : zero4;
-    };
-
-    // The slice's entries of A are one contiguous run per array: ask the
-    // L2 for all of it now, so that the loads below wait on the L2 rather
-    // than on HBM.
-    if (lane == 0 && len > 0) {
-        const unsigned bytes = (unsigned)len * 128u;
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
-                     :: "l"(p.idx + p.slice_ptr[s]), "r"(bytes) : "memory");
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
-                     :: "l"(p.val + p.slice_ptr[s]), "r"(bytes) : "memory");
-    }
-
-    // Step pairs in flight: entries of A for the next DA pairs, records
-    // (which need the entries' row index) for the next DR pairs.
-    constexpr int DA = 2, DR = 1;
-    int I[DA][2];
-    float Av[DA][2];
-    uint4 Rc[DR][2];
-#pragma unroll
-    for (int q = 0; q < DA; ++q) load2(2 * q, I[q], Av[q]);
-#pragma unroll
-    for (int q = 0; q < DR; ++q) rec2(I[q], Rc[q]);
-    for (int p0 = 0; p0 < len; p0 += 2) {
-        int ni[2];
-        float na[2];
-        uint4 nr[2];
-        load2(p0 + 2 * DA, ni, na);
-        rec2(I[DR], nr);
-        light(I[0][0], Av[0][0], Rc[0][0]);
-        light(I[0][1], Av[0][1], Rc[0][1]);
-        if (record_cnt(Rc[0][0].x) >= heavy) heavy_row(I[0][0], Av[0][0]);
-        if (record_cnt(Rc[0][1].x) >= heavy) heavy_row(I[0][1], Av[0][1]);
-#pragma unroll
-        for (int q = 0; q < DA - 1; ++q) {
-            I[q][0] = I[q + 1][0];
-            I[q][1] = I[q + 1][1];
-            Av[q][0] = Av[q + 1][0];
-            Av[q][1] = Av[q + 1][1];
-        }
-        I[DA - 1][0] = ni[0];
-        I[DA - 1][1] = ni[1];
-        Av[DA - 1][0] = na[0];
-        Av[DA - 1][1] = na[1];
-#pragma unroll
-        for (int q = 0; q < DR - 1; ++q) {
-            Rc[q][0] = Rc[q + 1][0];
-            Rc[q][1] = Rc[q + 1][1];
-        }
-        Rc[DR - 1][0] = nr[0];
-        Rc[DR - 1][1] = nr[1];
-    }
-
-#pragma unroll
-    for (int c = 0; c < CW; ++c) acc[c] += c < cw ? my[c * B] : 0.f;
-    // combine the lanes [head, end) of each row: fixed tree, lane head
-    // ends with the row's sum
-    const int grp = p.seg_grp[seg];
-    const int head = grp >> 8, end = grp & 0xff;
-    const int maxg = __reduce_max_sync(FULL, (unsigned)(end - head));
-    for (int off = 1; off < maxg; off <<= 1) {
-        const bool take = lane + off < end;
-#pragma unroll
-        for (int c = 0; c < CW; ++c) {
-            const float v = __shfl_down_sync(FULL, acc[c], off);
-            if (take) acc[c] += v;
+            for (int off = LPG; off < 32; off <<= 1) {
+                acc.x += __shfl_xor_sync(FULL, acc.x, off);
+                acc.y += __shfl_xor_sync(FULL, acc.y, off);
+                acc.z += __shfl_xor_sync(FULL, acc.z, off);
+                acc.w += __shfl_xor_sync(FULL, acc.w, off);
+            }
+            if (grp == 0 && colact)
+                *yr = make_float4(yv.x + acc.x, yv.y + acc.y, yv.z + acc.z, yv.w + acc.w);
+            q0 = q1;
         }
     }
-    const int row = p.seg_row[seg];
-    if (row < 0 || lane != head) return;
-    const int part = p.seg_part[seg];
-    float* out = (part < 0 ? p.Y + (int64_t)row * KP : p.partials + (int64_t)part * KP) + c0;
-    float4* o4 = reinterpret_cast<float4*>(out);
-#pragma unroll
-    for (int q = 0; q < CW / 4; ++q)
-        if (4 * q < cw)
-            o4[q] = make_float4(acc[4 * q + 0], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
 }
 
 // FP64 (the plain form): every gather into shared-memory accumulators.
@@ -251,11 +491,12 @@ spmm_sell_f64_kernel(SpmmParams<double> p, int KP)
     double* my = slots + tid;
     for (int c = 0; c < KP; ++c) my[c * B] = 0.0;
     const int len = p.slice_len[s];
-    const int64_t base = p.slice_ptr[s] + lane;
+    const int64_t base = p.slice_ptr[s] + lane * 4;
     const int heavy = p.heavy;
     for (int p0 = 0; p0 < len; ++p0) {
-        const int i = __ldcs(p.idx + base + (int64_t)p0 * 32);
-        const double a = __ldcs(p.val + base + (int64_t)p0 * 32);
+        const int64_t at = base + (int64_t)(p0 >> 2) * 128 + (p0 & 3);
+        const int i = __ldcs(p.idx + at);
+        const double a = __ldcs(p.val + at);
         const int cnt = i >= 0 ? __ldg(p.fcnt + i) : 0;
         if (cnt >= heavy) {
             const double2* r = reinterpret_cast<const double2*>(p.fdense + (int64_t)i * p.dld);
@@ -327,21 +568,39 @@ static int spmm_block(int KP, size_t esz, size_t limit)
     return b;
 }
 
+// Resident blocks per SM of each FP32 SELL instantiation, found by the
+// per-device set-up (before any capture) and read by the launches.
+static int g_sell_per_sm[129][5][3];
+
 template <int KP, int NS>
-static cudaError_t launch_f32_split(const SpmmParams<float>& p, int64_t nslices, int carveout,
-                                    cudaStream_t st)
+static int sell_block(int& B)
 {
     constexpr int CW = SplitShape<KP, NS>::CW;
-    // NS warps per slice; about 48 KB of slots per block
-    int B = spmm_block(CW, 4, 48 * 1024);
+    // NS warps per slice; at most 56 KB of slots per block (four blocks of
+    // 256 threads per SM at k = 50)
+    B = spmm_block(CW, 4, 56 * 1024);
     B = B / (32 * NS) * (32 * NS);
     if (B < 32 * NS) B = 32 * NS;
+    return CW * B * 4;
+}
+
+template <int KP, int NS, int MASK>
+static cudaError_t launch_f32_split(const SpmmParams<float>& p, int64_t nslices, int carveout,
+                                    cudaStream_t st, int sm_count)
+{
+    int B = 0;
+    int smem = sell_block<KP, NS>(B);
+    if (MASK == 2) smem += p.mask_words * 4;
     const int64_t spb = B / (32 * NS);   // slices per block
-    const int64_t grid = (nslices + spb - 1) / spb;
+    int64_t grid = (nslices + spb - 1) / spb;
+    // no more blocks than fit at once: the warps loop over the slices
+    const int occ = g_sell_per_sm[KP][NS][MASK];
+    const int per_sm = occ > 0 ? occ : 1;
+    if (grid > (int64_t)per_sm * sm_count) grid = (int64_t)per_sm * sm_count;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(B);
-    cfg.dynamicSmemBytes = (size_t)CW * B * 4;
+    cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     if (carveout >= 0) {
@@ -350,25 +609,36 @@ static cudaError_t launch_f32_split(const SpmmParams<float>& p, int64_t nslices,
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    return cudaLaunchKernelEx(&cfg, spmm_sell_f32_kernel<KP, NS>, p);
+    return cudaLaunchKernelEx(&cfg, spmm_sell_f32_kernel<KP, NS, MASK>, p);
+}
+
+template <int KP, int MASK>
+static cudaError_t launch_f32_m(const SpmmParams<float>& p, int64_t nslices, SpmmConfig c,
+                                cudaStream_t st, int sm_count)
+{
+    if constexpr (KP >= 16) {
+        if (c.split == 4) return launch_f32_split<KP, 4, MASK>(p, nslices, c.carveout, st, sm_count);
+        if (c.split == 2) return launch_f32_split<KP, 2, MASK>(p, nslices, c.carveout, st, sm_count);
+    }
+    return launch_f32_split<KP, 1, MASK>(p, nslices, c.carveout, st, sm_count);
 }
 
 template <int KP>
 static cudaError_t launch_f32(const SpmmParams<float>& p, int64_t nslices, SpmmConfig c,
-                              cudaStream_t st)
+                              cudaStream_t st, int sm_count)
 {
-    if constexpr (KP >= 16) {
-        if (c.split == 4) return launch_f32_split<KP, 4>(p, nslices, c.carveout, st);
-        if (c.split == 2) return launch_f32_split<KP, 2>(p, nslices, c.carveout, st);
+    if (c.mask == 2) {
+        if (p.mask_words > kSellSmemMaskWords) return cudaErrorInvalidValue;
+        return launch_f32_m<KP, 2>(p, nslices, c, st, sm_count);
     }
-    return launch_f32_split<KP, 1>(p, nslices, c.carveout, st);
+    return c.mask ? launch_f32_m<KP, 1>(p, nslices, c, st, sm_count)
+                  : launch_f32_m<KP, 0>(p, nslices, c, st, sm_count);
 }
 
 template <typename T>
 cudaError_t launch_spmm(const SellDev& S, const EllDev& F, int k, T* Y,
                         int64_t ldy, SpmmConfig cfg, cudaStream_t st, int sm_count)
 {
-    (void)sm_count;
     (void)ldy;
     if (S.nslices == 0) return cudaSuccess;
     SpmmParams<T> p;
@@ -385,6 +655,8 @@ cudaError_t launch_spmm(const SellDev& S, const EllDev& F, int k, T* Y,
     p.fval = static_cast<const T*>(F.val);
     p.fdense = static_cast<const T*>(F.dense);
     p.frec = F.rec;
+    p.fmask = F.nzmask;
+    p.mask_words = (int)((F.rows + 31) / 32);
     p.dld = F.dld;
     p.fld = F.ld;
     p.heavy = F.heavy;
@@ -394,7 +666,7 @@ cudaError_t launch_spmm(const SellDev& S, const EllDev& F, int k, T* Y,
     const int KP = F.ld;
     if constexpr (sizeof(T) == 4) {
         switch (KP) {
-#define ESPNMF_KP(v) case v: return launch_f32<v>(p, S.nslices, cfg, st);
+#define ESPNMF_KP(v) case v: return launch_f32<v>(p, S.nslices, cfg, st, sm_count);
             ESPNMF_KP(4) ESPNMF_KP(8) ESPNMF_KP(12) ESPNMF_KP(16) ESPNMF_KP(20) ESPNMF_KP(24)
             ESPNMF_KP(28) ESPNMF_KP(32) ESPNMF_KP(36) ESPNMF_KP(40) ESPNMF_KP(44) ESPNMF_KP(48)
             ESPNMF_KP(52) ESPNMF_KP(56) ESPNMF_KP(60) ESPNMF_KP(64) ESPNMF_KP(80) ESPNMF_KP(96)
@@ -427,18 +699,81 @@ cudaError_t launch_spmm_combine(const SellDev& S, int KP, T* Y, int64_t ldy,
 }
 
 template <int KP>
+static cudaError_t launch_freq(const FreqParams& p, int grid, cudaStream_t st)
+{
+    const size_t smem = (size_t)p.h * KP * 4 + (size_t)p.h;
+    spmm_freq_f32_kernel<KP><<<grid, kHThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmm_h(const SellDev& S, const EllDev& F, float* Y, int sm_count,
+                          unsigned* status, long long wait_limit, cudaStream_t st)
+{
+    if (S.h <= 0 || S.hnnz == 0) return cudaSuccess;
+    if (F.htab == nullptr || F.hnz == nullptr || F.h != S.h) return cudaErrorInvalidValue;
+    FreqParams p;
+    p.hptr = S.hptr;
+    p.hidx = S.hidx;
+    p.hval = static_cast<const float*>(S.hval);
+    p.hwarp = S.hwarp;
+    p.nchunks = S.hwarps;
+    p.counter = S.hcounter;
+    p.htab = static_cast<const float*>(F.htab);
+    p.hnz = F.hnz;
+    p.h = S.h;
+    p.Y = Y;
+    p.status = status;
+    p.wait_limit = wait_limit < (1ll << 20) ? wait_limit : (1ll << 20);
+    const int grid = sm_count;
+    if ((size_t)S.h * F.ld * 4 > kHTableBytes) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(S.hcounter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    switch (F.ld) {
+#define ESPNMF_KP(v) case v: return launch_freq<v>(p, grid, st);
+        ESPNMF_KP(4) ESPNMF_KP(8) ESPNMF_KP(12) ESPNMF_KP(16) ESPNMF_KP(20) ESPNMF_KP(24)
+        ESPNMF_KP(28) ESPNMF_KP(32) ESPNMF_KP(36) ESPNMF_KP(40) ESPNMF_KP(44) ESPNMF_KP(48)
+        ESPNMF_KP(52) ESPNMF_KP(56) ESPNMF_KP(60) ESPNMF_KP(64) ESPNMF_KP(80) ESPNMF_KP(96)
+        ESPNMF_KP(112) ESPNMF_KP(128)
+#undef ESPNMF_KP
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int KP, int NS, int MASK>
+static cudaError_t setup_sell_one()
+{
+    cudaError_t e = cudaFuncSetAttribute(spmm_sell_f32_kernel<KP, NS, MASK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+    if (e != cudaSuccess) return e;
+    int B = 0;
+    const int smem = sell_block<KP, NS>(B);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, spmm_sell_f32_kernel<KP, NS, MASK>, B, (size_t)smem);
+    g_sell_per_sm[KP][NS][MASK] = per_sm;
+    return e;
+}
+
+template <int KP, int NS>
+static cudaError_t setup_sell_occupancy()
+{
+    cudaError_t e = setup_sell_one<KP, NS, 0>();
+    if (e == cudaSuccess) e = setup_sell_one<KP, NS, 1>();
+    if (e == cudaSuccess) e = setup_sell_one<KP, NS, 2>();
+    return e;
+}
+
+template <int KP>
 static cudaError_t setup_f32()
 {
-    cudaError_t e = cudaFuncSetAttribute(spmm_sell_f32_kernel<KP, 1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(spmm_freq_f32_kernel<KP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kHTableBytes + kHTableBytes / 16));
     if constexpr (KP >= 16) {
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(spmm_sell_f32_kernel<KP, 2>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(spmm_sell_f32_kernel<KP, 4>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+        if (e == cudaSuccess) e = setup_sell_occupancy<KP, 2>();
+        if (e == cudaSuccess) e = setup_sell_occupancy<KP, 4>();
     }
+    if (e == cudaSuccess) e = setup_sell_occupancy<KP, 1>();
     return e;
 }
 

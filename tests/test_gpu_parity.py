@@ -332,3 +332,57 @@ def test_spmm_launch_shapes_give_identical_results():
     for r in runs[1:]:
         for a, b in zip(runs[0], r):
             np.testing.assert_array_equal(a, b)
+
+
+def _transpose(A: Corpus) -> Corpus:
+    """The corpus with terms and documents exchanged (CSR of A^T)."""
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    order = np.lexsort((rows, A.colidx))
+    rowptr = np.zeros(A.m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(A.colidx, minlength=A.m), out=rowptr[1:])
+    return Corpus(A.m, A.n, rowptr, rows[order].astype(np.int32), A.val[order].copy())
+
+
+@pytest.mark.parametrize("transposed", [False, True])
+@pytest.mark.parametrize("sparse_start", [False, True])
+def test_frequent_part_matches_oracle(transposed, sparse_start):
+    """The frequent terms' entries go through the dense-table kernel: A^T U on
+    the Zipf corpus, A V on its transpose (whose documents are Zipf); from a
+    dense start, and from a sparse one whose frequent rows are partly zero;
+    two sweeps, each half-step from the GPU's own iterate."""
+    from gen import sparse_init
+    A = small_zipf(3)
+    if transposed:
+        A = _transpose(A)
+    k, t = 12, 40
+    U0 = sparse_init(A.n, k, 6, 3) if sparse_start else uniform_init(A.n, k, 3)
+    ctx = make_ctx(A, k, t, t, U0, E.TOPT_COLUMN, E.F32)
+    h, hnnz = E.espnmf_spmm_frequent(ctx, 0 if transposed else 1)
+    assert h > 0 and hnnz * 10 >= A.nnz, (h, hnnz)
+    Ao = A.astype(np.float32)
+    Ucur = U0.astype(np.float32).astype(np.float64)
+    for sweep in range(2):
+        E.espnmf_als_update_V(ctx)
+        Vg = E.espnmf_get_factor(ctx, E.V)
+        Vo, Vpre = oracle.update_V(Ao, Ucur, t, oracle.COLUMN, return_pre=True)
+        compare_factor(Vg, Vo, Vpre, t, E.TOPT_COLUMN, 2e-5, f"freq V{sweep}")
+        E.espnmf_als_update_U(ctx)
+        Ug = E.espnmf_get_factor(ctx, E.U)
+        Uo, Upre = oracle.update_U(Ao, Vg, t, oracle.COLUMN, return_pre=True)
+        compare_factor(Ug, Uo, Upre, t, E.TOPT_COLUMN, 2e-5, f"freq U{sweep}")
+        assert abs(E.espnmf_error(ctx) - oracle.error_identity(Ao, Ug, Vg)) < ETOL[E.F32]
+        assert abs(E.espnmf_residual(ctx) - oracle.residual(Ug, Ucur)) < 1e-9
+        Ucur = Ug
+
+
+def test_benchmark_corpus_uses_the_frequent_part():
+    """The planted corpus routes its frequent terms through the dense table
+    (A^T U) and leaves A V, whose documents are not skewed, to the SELL part."""
+    A = planted_50k_100k(seed=2, scale=0.05)
+    ctx = make_ctx(A, 50, 120, 150, uniform_init(A.n, 50, 2), E.TOPT_COLUMN, E.F32)
+    h_atu, e_atu = E.espnmf_spmm_frequent(ctx, 1)
+    h_av, e_av = E.espnmf_spmm_frequent(ctx, 0)
+    assert h_atu > 0 and e_atu * 10 >= A.nnz
+    assert h_av == 0 and e_av == 0
+    ctx64 = make_ctx(A, 50, 120, 150, uniform_init(A.n, 50, 2), E.TOPT_COLUMN, E.F64)
+    assert E.espnmf_spmm_frequent(ctx64, 1) == (0, 0)
