@@ -48,6 +48,56 @@ __device__ __forceinline__ bool keep_entry(T v, typename KeyBits<T>::K tau, uint
     return key != 0 && (key > tau || (key == tau && ix <= cut));
 }
 
+// ---------------------------------------------------------------------------
+// Compensated FP32 accumulation ("double-float": an unevaluated sum hi + lo
+// of two floats).  The product of two floats is split exactly into p + e
+// with one FMA (e = fma(a, b, -p)), and sums use Knuth's branch-free
+// two-sum, so a running sum of products keeps about 48 significant bits --
+// FP64-like accuracy -- on the FP32 pipes.  Used for per-lane sums in
+// divergent code, where every FP64 warp instruction would hold the GPU's
+// low-rate FP64 pipe whatever its active lanes; the sums are widened to
+// FP64 (hi + lo) before they are reduced.
+struct DFloat {
+    float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void df_add(DFloat& s, float p, float e)
+{
+    const float t = s.hi + p;
+    const float bp = t - s.hi;
+    const float err = (s.hi - (t - bp)) + (p - bp);
+    const float lo = s.lo + (err + e);
+    const float h = t + lo;
+    s.lo = lo - (h - t);
+    s.hi = h;
+}
+// s += a * b, the product exactly
+__device__ __forceinline__ void df_add_prod(DFloat& s, float a, float b)
+{
+    const float p = __fmul_rn(a, b);   // never contracted into a neighbouring add
+    df_add(s, p, fmaf(a, b, -p));
+}
+// s += (a - b)^2 with a - b split exactly (two-sum) first
+__device__ __forceinline__ void df_add_sqdiff(DFloat& s, float a, float b)
+{
+    const float d = a - b;
+    const float bb = d - a;
+    const float dl = (a - (d - bb)) + (-b - bb);   // a - b = d + dl exactly
+    const float p = __fmul_rn(d, d);
+    df_add(s, p, fmaf(d, d, -p) + 2.f * d * dl);
+}
+__device__ __forceinline__ double df_value(const DFloat& s) { return (double)s.hi + (double)s.lo; }
+// sum over the warp (every lane gets it), butterfly in a fixed order
+__device__ __forceinline__ DFloat df_warp_sum(DFloat v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, v.hi, off);
+        const float l = __shfl_xor_sync(0xffffffffu, v.lo, off);
+        df_add(v, h, l);
+    }
+    return v;
+}
+
 // Rows are cut into segments of at most this many entries, one per lane.
 constexpr int kSegTarget = 64;
 constexpr int kMaxK = 256;
@@ -157,7 +207,7 @@ inline __host__ __device__ int heavy_threshold(int ld) { return ld / 4 > 4 ? ld 
 // bitwise the same Y.
 struct SpmmConfig {
     int split = 1;
-    int carveout = -1;
+    int carveout = 100;   // the per-thread slots want all of the shared memory
     int mask = 1;   // skip zero factor rows by the bitmask: 0 no, 1 from global, 2 from shared
 };
 // Largest bitmask (32-bit words, i.e. factor rows / 32) that mask = 2 stages.
@@ -229,11 +279,12 @@ struct MetricsArgs {
 // + b] for e = tri(c, d), c <= d), the scalar partials (scal_part[j *
 // nscal_parts + b]) and, for diagonal entries, diag_parts per-column partials
 // (diag_part[c * diag_parts + j], or NULL) in a fixed order; writes the
-// symmetric G and, with m.enabled, R and E.
+// symmetric G and, with m.enabled, R and E.  With `pairs` every partial is a
+// compensated FP32 pair (float2 hi, lo) in its 8-byte slot.
 cudaError_t launch_gram_reduce(const double* gram_part, const double* scal_part, int nparts,
                                int nscal_parts, int k, const double* diag_part, int diag_parts,
-                               double* G, double* scal, unsigned* counter, MetricsArgs m,
-                               cudaStream_t st);
+                               bool pairs, double* G, double* scal, unsigned* counter,
+                               MetricsArgs m, cudaStream_t st);
 
 // Survivor-driven emit (FP32, column mode): rowbits from launch_select's
 // marking (cleared here); nblocks blocks write partial columns [0, nblocks)

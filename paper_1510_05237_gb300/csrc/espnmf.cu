@@ -563,7 +563,7 @@ espnmf_status tune_spmm(espnmf_ctx* ctx)
     std::vector<SpmmConfig> cands;
     for (int sp : {1, 2, 4}) {
         if (sp > 1 && ctx->ldy < 16) continue;
-        for (int cv : {-1, 25, 50})
+        for (int cv : {100, 75, 50})
             for (int mk : {0, 1, 2}) {
                 if (mk == 2 && std::max(ctx->n, ctx->m) > 32ll * kSellSmemMaskWords) continue;
                 SpmmConfig c;
@@ -669,7 +669,7 @@ espnmf_status do_emit(espnmf_ctx* ctx, Factor& F, bool residual, const void* Y, 
     const double rb = (double)ctx->fin_blocks * ctx->k * (ctx->k + 1) / 2 * 8.0;
     TRY(run(ctx, K_GRAM_REDUCE, rb, ctx->st, [&] {
         return launch_gram_reduce(ctx->gram_part, ctx->scal_part, ctx->fin_blocks,
-                                  ctx->fin_blocks, ctx->k, nullptr, 0, F.G, ctx->scal,
+                                  ctx->fin_blocks, ctx->k, nullptr, 0, false, F.G, ctx->scal,
                                   ctx->gram_counter, ma, ctx->st);
     }));
     F.cur ^= 1;
@@ -728,7 +728,7 @@ espnmf_status do_emit_survivors(espnmf_ctx* ctx, Factor& F, bool residual, const
     const int Cd = select_cluster(F.rows, ctx->k, TOPT_COLUMN, ctx->sm_count);
     TRY(run(ctx, K_GRAM_REDUCE, (double)P * ntri * 8.0, ctx->st, [&] {
         return launch_gram_reduce(ctx->gram_part, ctx->scal_part, P, Pe, ctx->k, ctx->diag_part,
-                                  Cd, F.G, ctx->scal, ctx->gram_counter, ma, ctx->st);
+                                  Cd, true, F.G, ctx->scal, ctx->gram_counter, ma, ctx->st);
     }));
     F.cur ^= 1;
     F.chol_pending = true;

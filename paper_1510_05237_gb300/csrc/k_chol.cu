@@ -210,32 +210,34 @@ solve_chol_kernel(const float* __restrict__ Y, int64_t ldy, int64_t rows, int k,
         for (int d = 0; d < KP; ++d) x[d] = Ys[d * kSolveStride + tid];
         // L z = y: z_j = (y_j - sum_{i<j} L_ji z_i) / L_jj; the strictly
         // upper entries of Ls are zero, so whole 4-wide groups can be read
+        // (two interleaved partial sums per unknown: twice the independent
+        // FMAs in flight; they are added in a fixed order)
 #pragma unroll
         for (int j = 0; j < KP; ++j) {
-            float s = x[j];
+            float s0 = x[j], s1 = 0.f;
 #pragma unroll
             for (int i = 0; i < (j + 3) / 4 * 4; i += 4) {
                 const float4 l = *reinterpret_cast<const float4*>(Ls + j * KP + i);
-                s = fmaf(-l.x, x[i + 0], s);
-                s = fmaf(-l.y, x[i + 1], s);
-                s = fmaf(-l.z, x[i + 2], s);
-                s = fmaf(-l.w, x[i + 3], s);
+                s0 = fmaf(-l.x, x[i + 0], s0);
+                s1 = fmaf(-l.y, x[i + 1], s1);
+                s0 = fmaf(-l.z, x[i + 2], s0);
+                s1 = fmaf(-l.w, x[i + 3], s1);
             }
-            x[j] = s * rds[j];
+            x[j] = (s0 + s1) * rds[j];
         }
         // L^T x = z: x_j = (z_j - sum_{i>j} L_ij x_i) / L_jj
 #pragma unroll
         for (int j = KP - 1; j >= 0; --j) {
-            float s = x[j];
+            float s0 = x[j], s1 = 0.f;
 #pragma unroll
             for (int i = (j + 1) / 4 * 4; i < KP; i += 4) {
                 const float4 l = *reinterpret_cast<const float4*>(LTs + j * KP + i);
-                s = fmaf(-l.x, x[i + 0], s);
-                s = fmaf(-l.y, x[i + 1], s);
-                s = fmaf(-l.z, x[i + 2], s);
-                s = fmaf(-l.w, x[i + 3], s);
+                s0 = fmaf(-l.x, x[i + 0], s0);
+                s1 = fmaf(-l.y, x[i + 1], s1);
+                s0 = fmaf(-l.z, x[i + 2], s0);
+                s1 = fmaf(-l.w, x[i + 3], s1);
             }
-            x[j] = s * rds[j];
+            x[j] = (s0 + s1) * rds[j];
         }
         if (tid < nr) {
 #pragma unroll
@@ -285,8 +287,14 @@ template <int KP>
 static cudaError_t setup_solve_kp()
 {
     const size_t smem = ((size_t)2 * KP * KP + KP + (size_t)KP * kSolveStride) * sizeof(float);
-    return cudaFuncSetAttribute(solve_chol_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(solve_chol_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    // four blocks per SM need most of the shared memory: do not let the
+    // driver pick a smaller carveout
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_chol_kernel<KP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 cudaError_t setup_chol()

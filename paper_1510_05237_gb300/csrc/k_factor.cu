@@ -388,7 +388,7 @@ cudaError_t launch_emit(const T* Xt, int64_t ldx, int64_t rows, int k, int mode,
 __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
                                    const double* __restrict__ scal_part,
                                    int P, int Ps, int k, const double* __restrict__ diag_part,
-                                   int Cd, double* G, double* scal,
+                                   int Cd, bool pairs, double* G, double* scal,
                                    unsigned* counter, MetricsArgs m)
 {
     // one warp per output: the upper-triangle Gram entries (partials
@@ -403,14 +403,24 @@ __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
     if (w < ntri + 4) {
         const int np = w < ntri ? P : Ps;
         const double* src = w < ntri ? gram_part + (size_t)w * P : scal_part + (size_t)(w - ntri) * Ps;
-        double s0 = 0.0, s1 = 0.0;
-        int p = lane;
-        for (; p + 32 < np; p += 64) {
-            s0 += src[p];
-            s1 += src[p + 32];
+        double v;
+        if (pairs) {
+            // compensated pairs, added on the FP32 pipes, widened once
+            const float2* sp = reinterpret_cast<const float2*>(src);
+            DFloat acc;
+            for (int p = lane; p < np; p += 32) df_add(acc, sp[p].x, sp[p].y);
+            acc = df_warp_sum(acc);
+            v = df_value(acc);
+        } else {
+            double s0 = 0.0, s1 = 0.0;
+            int p = lane;
+            for (; p + 32 < np; p += 64) {
+                s0 += src[p];
+                s1 += src[p + 32];
+            }
+            if (p < np) s0 += src[p];
+            v = warp_sum(s0 + s1);
         }
-        if (p < np) s0 += src[p];
-        double v = warp_sum(s0 + s1);
         if (lane == 0) {
             if (w < ntri) {
                 int c = 0, start = 0, rowlen = k;
@@ -420,8 +430,16 @@ __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
                     --rowlen;
                 }
                 const int d = c + (w - start);
-                if (c == d && diag_part)
-                    for (int j = 0; j < Cd; ++j) v += diag_part[(size_t)c * Cd + j];
+                if (c == d && diag_part) {
+                    if (pairs) {
+                        const float2* dp = reinterpret_cast<const float2*>(diag_part) + (size_t)c * Cd;
+                        DFloat dg;
+                        for (int j = 0; j < Cd; ++j) df_add(dg, dp[j].x, dp[j].y);
+                        v += df_value(dg);
+                    } else {
+                        for (int j = 0; j < Cd; ++j) v += diag_part[(size_t)c * Cd + j];
+                    }
+                }
                 G[c * k + d] = v;
                 G[d * k + c] = v;
             } else {
@@ -473,14 +491,14 @@ __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
 
 cudaError_t launch_gram_reduce(const double* gram_part, const double* scal_part, int nparts,
                                int nscal_parts, int k, const double* diag_part, int diag_parts,
-                               double* G, double* scal, unsigned* counter, MetricsArgs m,
-                               cudaStream_t st)
+                               bool pairs, double* G, double* scal, unsigned* counter,
+                               MetricsArgs m, cudaStream_t st)
 {
     const int B = 256;
     const int ntri = k * (k + 1) / 2;
     const int grid = ((ntri + 4) * 32 + B - 1) / B;
     gram_reduce_kernel<<<grid, B, 0, st>>>(gram_part, scal_part, nparts, nscal_parts, k,
-                                           diag_part, diag_parts, G, scal, counter, m);
+                                           diag_part, diag_parts, pairs, G, scal, counter, m);
     return cudaGetLastError();
 }
 
@@ -534,24 +552,25 @@ __global__ void __launch_bounds__(kEmitSThreads)
 emit_s_kernel(EmitSArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* T = reinterpret_cast<double*>(smem_raw);   // [ntri]
+    DFloat* T = reinterpret_cast<DFloat*>(smem_raw);   // [ntri] compensated FP32 sums
     // the pairs of this round's rows (the first kEmitSStage of each), so
     // that the warp adding the off-diagonal products reads shared memory
-    int2* stage = reinterpret_cast<int2*>(smem_raw + (((size_t)a.k * (a.k + 1) / 2 * 8 + 15) & ~(size_t)15));
+    int2* stage = reinterpret_cast<int2*>(smem_raw + (((size_t)a.k * (a.k + 1) / 2 * sizeof(DFloat) + 15) & ~(size_t)15));
     __shared__ int wcount[kEmitSThreads / 32];
     __shared__ int list[kEmitSThreads];
-    __shared__ double red[kEmitSThreads / 32][4];
+    __shared__ DFloat red[kEmitSThreads / 32][4];
     __shared__ float wold[kEmitSThreads / 32][kMaxK];   // a warp's old row, dense
     const int k = a.k, ld = a.ld;
     const int ntri = k * (k + 1) / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int NW = blockDim.x >> 5;
-    for (int e = tid; e < ntri; e += blockDim.x) T[e] = 0.0;
+    for (int e = tid; e < ntri; e += blockDim.x) T[e] = DFloat();
     // blocks own whole 32-row words of the nonzero-row bitmask
     const int64_t chunk = ((a.rows + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
     const int64_t b0 = (int64_t)blockIdx.x * chunk < a.rows ? (int64_t)blockIdx.x * chunk : a.rows;
     const int64_t b1 = b0 + chunk < a.rows ? b0 + chunk : a.rows;
-    double s_diff = 0.0, s_new = 0.0, s_old = 0.0, s_cross = 0.0;
+    // per-lane Sec. 3.1 sums in compensated FP32 (widened to FP64 at the end)
+    DFloat s_diff, s_new, s_old, s_cross;
 
     for (int64_t base = b0; base < b1; base += blockDim.x) {
         const int64_t r = base + tid;
@@ -600,33 +619,31 @@ emit_s_kernel(EmitSArgs a)
                     if (pos == 0) { rx |= (unsigned)c << 8; rv0 = __float_as_uint(x); }
                     else if (pos == 1) { rx |= (unsigned)c << 16; rv1 = __float_as_uint(x); }
                     else if (pos == 2) { rx |= (unsigned)c << 24; rv2 = __float_as_uint(x); }
-                    const double xd = (double)x;
-                    s_new = fma(xd, xd, s_new);
-                    if (a.Y) s_cross = fma(xd, (double)a.Y[r * a.ldy + c], s_cross);
+                    df_add_prod(s_new, x, x);
+                    if (a.Y) df_add_prod(s_cross, x, a.Y[r * a.ldy + c]);
                     if (a.residual) {
                         while (q < Lo && co[q] < c) {
-                            const double o = (double)vo[q];
-                            s_old = fma(o, o, s_old);
-                            s_diff = fma(o, o, s_diff);
+                            const float o = vo[q];
+                            df_add_prod(s_old, o, o);
+                            df_add_prod(s_diff, o, o);
                             ++q;
                         }
-                        double d = xd;
+                        float o = 0.f;
                         if (q < Lo && co[q] == c) {
-                            const double o = (double)vo[q];
-                            s_old = fma(o, o, s_old);
-                            d = xd - o;
+                            o = vo[q];
+                            df_add_prod(s_old, o, o);
                             ++q;
                         }
-                        s_diff = fma(d, d, s_diff);
+                        df_add_sqdiff(s_diff, x, o);
                     }
                     ++pos;
                 }
             }
             if (a.residual) {
                 for (; q < Lo; ++q) {
-                    const double o = (double)vo[q];
-                    s_old = fma(o, o, s_old);
-                    s_diff = fma(o, o, s_diff);
+                    const float o = vo[q];
+                    df_add_prod(s_old, o, o);
+                    df_add_prod(s_diff, o, o);
                 }
             }
             a.cnt[r] = pos;
@@ -673,10 +690,10 @@ emit_s_kernel(EmitSArgs a)
                 __syncwarp();
                 for (int q = lane; q < Lo; q += 32) {
                     const int oc = co[q];
-                    const double o = (double)vo[q];
-                    od[oc] = vo[q];
-                    s_old = fma(o, o, s_old);
-                    if (!surv(oc)) s_diff = fma(o, o, s_diff);
+                    const float o = vo[q];
+                    od[oc] = o;
+                    df_add_prod(s_old, o, o);
+                    if (!surv(oc)) df_add_prod(s_diff, o, o);
                 }
                 __syncwarp();
             }
@@ -699,13 +716,9 @@ emit_s_kernel(EmitSArgs a)
                     x = a.Xt[(int64_t)c * a.ldx + rr];
                     wc[pos] = c;
                     wv[pos] = x;
-                    const double xd = (double)x;
-                    s_new = fma(xd, xd, s_new);
-                    if (a.Y) s_cross = fma(xd, (double)a.Y[rr * a.ldy + c], s_cross);
-                    if (a.residual) {
-                        const double d = xd - (double)od[c];
-                        s_diff = fma(d, d, s_diff);
-                    }
+                    df_add_prod(s_new, x, x);
+                    if (a.Y) df_add_prod(s_cross, x, a.Y[rr * a.ldy + c]);
+                    if (a.residual) df_add_sqdiff(s_diff, x, od[c]);
                 }
                 if (c < ld) {
                     if (dr) dr[c] = x;
@@ -760,12 +773,11 @@ emit_s_kernel(EmitSArgs a)
                     const int2* sp = stage + lr * kEmitSStage;
                     for (int ia = 0; ia + 1 < L; ++ia) {
                         const int2 pa = sp[ia];
-                        const double va = (double)__int_as_float(pa.y);
+                        const float va = __int_as_float(pa.y);
                         const int ib = ia + 1 + lane;
                         if (ib < L) {
                             const int2 pb = sp[ib];
-                            double* tp = T + tri_index(pa.x, pb.x, k);
-                            *tp = fma(va, (double)__int_as_float(pb.y), *tp);
+                            df_add_prod(T[tri_index(pa.x, pb.x, k)], va, __int_as_float(pb.y));
                         }
                         __syncwarp();
                     }
@@ -775,11 +787,9 @@ emit_s_kernel(EmitSArgs a)
                     const float* vr = a.val + rr * ld;
                     for (int ia = 0; ia + 1 < L; ++ia) {
                         const int ca = cr[ia];
-                        const double va = (double)vr[ia];
-                        for (int ib = ia + 1 + lane; ib < L; ib += 32) {
-                            double* tp = T + tri_index(ca, cr[ib], k);
-                            *tp = fma(va, (double)vr[ib], *tp);
-                        }
+                        const float va = vr[ia];
+                        for (int ib = ia + 1 + lane; ib < L; ib += 32)
+                            df_add_prod(T[tri_index(ca, cr[ib], k)], va, vr[ib]);
                         __syncwarp();
                     }
                 }
@@ -789,22 +799,23 @@ emit_s_kernel(EmitSArgs a)
         // before the list is rewritten
     }
     __syncthreads();
-    for (int e = tid; e < ntri; e += blockDim.x) a.gram_part[(size_t)e * a.P + blockIdx.x] = T[e];
-    s_diff = warp_sum(s_diff);
-    s_new = warp_sum(s_new);
-    s_old = warp_sum(s_old);
-    s_cross = warp_sum(s_cross);
-    if (lane == 0) {
-        red[warp][0] = s_diff;
-        red[warp][1] = s_new;
-        red[warp][2] = s_old;
-        red[warp][3] = s_cross;
+    // partials as compensated pairs (float2 in the double slots); the
+    // reduction widens them once
+    float2* gp = reinterpret_cast<float2*>(a.gram_part);
+    for (int e = tid; e < ntri; e += blockDim.x)
+        gp[(size_t)e * a.P + blockIdx.x] = make_float2(T[e].hi, T[e].lo);
+    DFloat sc[4] = {s_diff, s_new, s_old, s_cross};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        sc[j] = df_warp_sum(sc[j]);
+        if (lane == 0) red[warp][j] = sc[j];
     }
     __syncthreads();
     if (tid < 4) {
-        double sum = 0.0;
-        for (int w = 0; w < NW; ++w) sum += red[w][tid];
-        a.scal_part[(size_t)tid * gridDim.x + blockIdx.x] = sum;
+        DFloat sum;
+        for (int w = 0; w < NW; ++w) df_add(sum, red[w][tid].hi, red[w][tid].lo);
+        reinterpret_cast<float2*>(a.scal_part)[(size_t)tid * gridDim.x + blockIdx.x] =
+            make_float2(sum.hi, sum.lo);
     }
 }
 
@@ -841,7 +852,7 @@ cudaError_t launch_emit_s(const float* Xt, int64_t ldx, int64_t rows, int k, uin
     a.gram_part = gram_part;
     a.scal_part = scal_part;
     a.P = P;
-    const size_t smem = (((size_t)k * (k + 1) / 2 * sizeof(double) + 15) & ~(size_t)15) +
+    const size_t smem = (((size_t)k * (k + 1) / 2 * sizeof(DFloat) + 15) & ~(size_t)15) +
                         (size_t)kEmitSThreads * kEmitSStage * sizeof(int2);
     const int wd = (k + 31) / 32;
     switch (wd) {
@@ -866,16 +877,15 @@ __global__ void __launch_bounds__(256)
 gram_table_kernel(const float* __restrict__ htab, const uint8_t* __restrict__ hnz, int h,
                   int k, int ld, double* gram_part, int P, int pcol0)
 {
-    __shared__ double rowd[kTableRows][kMaxK];
+    __shared__ float rowd[kTableRows][kMaxK];
     const int tid = threadIdx.x;
     const int ntri = k * (k + 1) / 2;
     int cd[S];
-    double acc[S];
+    DFloat acc[S];
     {
         int e0 = tid, c = 0, rowlen = k, start = 0;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            acc[s] = 0.0;
             const int e = e0 + s * 256;
             if (e < ntri) {
                 while (e >= start + rowlen) {
@@ -899,19 +909,20 @@ gram_table_kernel(const float* __restrict__ htab, const uint8_t* __restrict__ hn
         __syncthreads();
         for (int e = tid; e < nr * k; e += blockDim.x) {
             const int q = e / k, c = e - q * k;
-            rowd[q][c] = hnz[rb + q] ? (double)htab[(int64_t)(rb + q) * ld + c] : 0.0;
+            rowd[q][c] = hnz[rb + q] ? htab[(int64_t)(rb + q) * ld + c] : 0.f;
         }
         __syncthreads();
         for (int q = 0; q < nr; ++q) {
 #pragma unroll
             for (int s = 0; s < S; ++s)
-                if (cd[s] >= 0) acc[s] = fma(rowd[q][cd[s] >> 16], rowd[q][cd[s] & 0xffff], acc[s]);
+                if (cd[s] >= 0) df_add_prod(acc[s], rowd[q][cd[s] >> 16], rowd[q][cd[s] & 0xffff]);
         }
     }
+    float2* gp = reinterpret_cast<float2*>(gram_part);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         const int e = tid + s * 256;
-        if (e < ntri) gram_part[(size_t)e * P + pcol0 + blockIdx.x] = acc[s];
+        if (e < ntri) gp[(size_t)e * P + pcol0 + blockIdx.x] = make_float2(acc[s].hi, acc[s].lo);
     }
 }
 
@@ -1391,13 +1402,17 @@ cudaError_t setup_factor()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(emit_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(emit_s_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(emit_s_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(emit_s_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(emit_s_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    auto es = [&](auto kern) {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+        return r;
+    };
+    e = es(emit_s_kernel<1>);
+    if (e == cudaSuccess) e = es(emit_s_kernel<2>);
+    if (e == cudaSuccess) e = es(emit_s_kernel<3>);
+    if (e == cudaSuccess) e = es(emit_s_kernel<4>);
     return e;
 }
 

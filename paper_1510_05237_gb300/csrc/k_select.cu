@@ -135,11 +135,24 @@ __device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int 
     return r;
 }
 
+// For a positive FP32 bit pattern: the integer mantissa m (implicit bit
+// included) and the exponent s with x = m 2^s.
+__device__ __forceinline__ unsigned long long mantissa24(uint32_t key)
+{
+    const uint32_t e = (key >> 23) & 0xffu;
+    return (unsigned long long)((key & 0x7fffffu) | (e ? 0x800000u : 0u));
+}
+__device__ __forceinline__ int exponent_of(uint32_t key)
+{
+    const int e = (int)((key >> 23) & 0xffu);
+    return e ? e - 150 : -149;
+}
+
 // Optional survivor marking (COLUMN mode): once a column's threshold is
 // known, each CTA walks its slice again, sets bit (c % 32) of word c / 32 of
 // row i in rowbits ([rows][mark_words]) for every survivor and writes the
-// sum of the survivors' squares (the column's diagonal entry of F^T F, in
-// FP64, fixed order) to diag_part[c * clusterDim + rank].
+// sum of the survivors' squares (the column's diagonal entry of F^T F, as a
+// compensated FP32 pair, fixed order) to diag_part[c * clusterDim + rank].
 struct SelMark {
     uint32_t* rowbits = nullptr;
     int words = 0;
@@ -156,7 +169,9 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
     constexpr int TS = KeyBits<T>::top_shift;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double wsq[kSelThreads / 32];
+    __shared__ DFloat wsq[kSelThreads / 32];
+    __shared__ unsigned long long wisq[kSelThreads / 32];
+    __shared__ double bucket_sq;   // the bucket survivors' exact sum of squares
     unsigned* hist = reinterpret_cast<unsigned*>(smem_raw + SelSmem<T>::hist);
     unsigned long long* wsum = reinterpret_cast<unsigned long long*>(smem_raw + SelSmem<T>::misc);
     unsigned long long* res = wsum + 32;
@@ -242,27 +257,37 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
         }
     };
     auto key_at = [&](int e) -> K { return KeyBits<T>::of(Xt[addr(lo + e)]); };
-    // the survivors of this CTA's slice (column mode): row bits and the
-    // FP64 sum of squares, reduced in a fixed order
-    auto mark_survivors = [&](K tau_m, uint32_t cut_m) {
-        double sq = 0.0;
-        const uint32_t bit = 1u << (seg & 31);
-        uint32_t* word = mark.rowbits + (seg >> 5);
-        for_each([&](K key, int e, bool in) {
-            if (in && keep_entry<T>(KeyBits<T>::value(key), tau_m, cut_m, (uint32_t)(lo + e))) {
-                atomicOr(word + (size_t)(lo + e) * mark.words, bit);
-                const double x = (double)KeyBits<T>::value(key);
-                sq = fma(x, x, sq);
-            }
-        });
-        for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    if (tid == 0) bucket_sq = 0.0;   // read by mark_finish after barriers
+    // Survivor marking (column mode): a survivor sets its row's bit and
+    // adds its square to this thread's FP64 sum (msq); mark_finish reduces
+    // the sums in a fixed order into the column's diagonal partial.
+    DFloat msq;   // compensated FP32 (only FP32 contexts mark)
+    const uint32_t mbit = 1u << (seg & 31);
+    auto mark_one = [&](K key, uint32_t row) {
+        atomicOr(mark.rowbits + (seg >> 5) + (size_t)row * mark.words, mbit);
+        const float x = (float)KeyBits<T>::value(key);
+        df_add_prod(msq, x, x);
+    };
+    auto mark_finish = [&]() {
+        const DFloat sq = df_warp_sum(msq);
         if ((tid & 31) == 0) wsq[tid >> 5] = sq;
         __syncthreads();
         if (tid == 0) {
-            double tot = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsq[w];
-            mark.diag_part[(size_t)seg * C + crank] = tot;
+            DFloat tot;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_add(tot, wsq[w].hi, wsq[w].lo);
+            if (bucket_sq != 0.0) {
+                const float bh = (float)bucket_sq;
+                df_add(tot, bh, (float)(bucket_sq - (double)bh));
+            }
+            reinterpret_cast<float2*>(mark.diag_part)[(size_t)seg * C + crank] = make_float2(tot.hi, tot.lo);
         }
+    };
+    // every positive entry survives (at most t of them)
+    auto mark_all = [&]() {
+        for_each([&](K key, int e, bool in) {
+            if (in && key != 0) mark_one(key, (uint32_t)(lo + e));
+        });
+        mark_finish();
     };
 
     // ---- pass 1: histogram of the top 11 bits of the positive entries
@@ -280,7 +305,7 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
             tau_out[seg] = 0;
             cut_out[seg] = 0xffffffffu;
         }
-        if (mark.rowbits) mark_survivors((K)0, 0xffffffffu);
+        if (mark.rowbits) mark_all();
         return;
     }
     need -= s1.before;
@@ -290,8 +315,11 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
     // ---- pass 2: the bucket's entries into the candidate list
     if (tid == 0) *ccount = 0;
     __syncthreads();
+    const bool marking = mark.rowbits != nullptr;
     for_each([&](K key, int e, bool in) {
         const bool hit = in && key != 0 && (key >> shift) == (prefix >> shift);
+        // above the threshold's bucket: a survivor whatever the threshold
+        if (marking && in && (key >> shift) > (prefix >> shift)) mark_one(key, (uint32_t)(lo + e));
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (m == 0u) return;
         unsigned base = 0;
@@ -387,7 +415,40 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
         tau_out[seg] = tau;
         cut_out[seg] = cut;
     }
-    if (mark.rowbits) mark_survivors(tau, cut);
+    if (marking) {
+        // the survivors inside the bucket: from the candidate list, or by a
+        // pass over the slice if a CTA's list overflowed
+        const K bucket = prefix >> TS;   // the first histogram's bin
+        if (use_list) {
+            // The list's order depends on the order of the appends, so its
+            // survivors' squares are added exactly: all of the bucket's
+            // entries share one FP32 exponent, x = m 2^s with an integer
+            // m < 2^24, and sum(m^2) fits 64 bits (at most kCandCap terms).
+            unsigned long long isq = 0;
+            for (int q = tid; q < nc; q += blockDim.x) {
+                if (keep_entry<T>(KeyBits<T>::value(ckey[q]), tau, cut, cidx[q])) {
+                    atomicOr(mark.rowbits + (seg >> 5) + (size_t)cidx[q] * mark.words, mbit);
+                    const unsigned long long m = mantissa24((uint32_t)ckey[q]);
+                    isq += m * m;
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) isq += __shfl_xor_sync(0xffffffffu, isq, off);
+            if ((tid & 31) == 0) wisq[tid >> 5] = isq;
+            __syncthreads();
+            if (tid == 0) {
+                unsigned long long tot = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wisq[w];
+                bucket_sq = ldexp((double)tot, 2 * exponent_of((uint32_t)(bucket << TS)));
+            }
+        } else {
+            for_each([&](K key, int e, bool in) {
+                if (in && key != 0 && (key >> TS) == bucket &&
+                    keep_entry<T>(KeyBits<T>::value(key), tau, cut, (uint32_t)(lo + e)))
+                    mark_one(key, (uint32_t)(lo + e));
+            });
+        }
+        mark_finish();
+    }
 }
 
 template <typename T>
