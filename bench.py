@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--spmm-shape", default=None,
+                   help="SPLIT,CARVEOUT,MASK: fix the sparse products' launch shape "
+                        "(no tuning), e.g. for profiling runs")
     return p.parse_args()
 
 
@@ -263,6 +266,11 @@ def main():
     # ---------------- device-resident timed region (FP32 form) ----------------
     ctx = E.espnmf_init(rp, ci, va, A.n, A.m, K_TOPICS, T_KEEP, T_KEEP, E.TOPT_COLUMN,
                         E.F32, u0, stream=stream)
+    if args.spmm_shape:
+        split, carve, mask = (int(x) for x in args.spmm_shape.split(","))
+        E.espnmf_set_option(ctx, E.OPT_SPMM_SPLIT, split)
+        E.espnmf_set_option(ctx, E.OPT_SPMM_CARVEOUT, carve)
+        E.espnmf_set_option(ctx, E.OPT_SPMM_MASK, mask)
     E.espnmf_iterate(ctx, max(args.warmup, 3), want_measures=False)
     E.espnmf_sync(ctx)
     launches = E.espnmf_launches_per_sweep(ctx)
@@ -305,7 +313,7 @@ def main():
     ms_per_product = t_prod / 2.0
     bytes_per_product = (b_av + b_atu) / 2.0
     achieved = bytes_per_product / (ms_per_product / 1000.0) / 1e9
-    shapes = {name: dict(zip(("split", "carveout"), E.espnmf_spmm_config(ctx, prod)))
+    shapes = {name: dict(zip(("split", "carveout", "mask"), E.espnmf_spmm_config(ctx, prod)))
               for name, prod in (("spmm_AV", 0), ("spmm_AtU", 1))}
     kstats = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1),
                   "share": v[1] / max(sum(x[1] for x in stats.values()), 1e-12)}

@@ -267,10 +267,16 @@ typedef enum {
      *     columns (k >= 13 for more than 1); sets both products and turns
      *     tuning off.
      *   ESPNMF_OPT_SPMM_CARVEOUT: preferred shared-memory carveout in percent
-     *     (-1: the driver's choice); also turns tuning off. */
+     *     (-1: the driver's choice); also turns tuning off.
+     *   ESPNMF_OPT_SPMM_MASK: how entries that gather an all-zero factor row
+     *     are skipped: 0 not skipped (their record is read), 1 by the
+     *     nonzero-row bitmask read from global memory, 2 by the bitmask
+     *     staged in shared memory (factors of at most 131072 rows; larger
+     *     ones fall back to 1); also turns tuning off. */
     ESPNMF_OPT_SPMM_TUNE = 3,
     ESPNMF_OPT_SPMM_SPLIT = 4,
-    ESPNMF_OPT_SPMM_CARVEOUT = 5
+    ESPNMF_OPT_SPMM_CARVEOUT = 5,
+    ESPNMF_OPT_SPMM_MASK = 6
 } espnmf_option;
 
 espnmf_status espnmf_set_option(espnmf_ctx *ctx, espnmf_option opt,
@@ -278,10 +284,11 @@ espnmf_status espnmf_set_option(espnmf_ctx *ctx, espnmf_option opt,
 
 /* espnmf_spmm_config -- the launch shape in use for a sparse product
  * (product 0: A V of the U update, 1: A^T U of the V update): split = warps
- * per slice, carveout in percent (-1: the driver's choice).  Reflects the
- * tuner's pick once espnmf_iterate ran. */
+ * per slice, carveout in percent (-1: the driver's choice), mask = how zero
+ * factor rows are skipped (ESPNMF_OPT_SPMM_MASK).  Reflects the tuner's pick
+ * once espnmf_iterate ran.  Any output may be NULL. */
 espnmf_status espnmf_spmm_config(espnmf_ctx *ctx, int32_t product, int32_t *split,
-                                 int32_t *carveout);
+                                 int32_t *carveout, int32_t *mask);
 
 /* espnmf_spmm_frequent -- the frequent part of a sparse product (product 0:
  * A V, 1: A^T U; FP32 contexts only): h = number of gathered factor rows

@@ -27,7 +27,7 @@ TOPT_COLUMN, TOPT_MATRIX, TOPT_NONE = 0, 1, 2
 U, V = 0, 1
 DENSE_ROWMAJOR, CSC, CSR = 0, 1, 2
 OPT_USE_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT = 0, 1, 2
-OPT_SPMM_TUNE, OPT_SPMM_SPLIT, OPT_SPMM_CARVEOUT = 3, 4, 5
+OPT_SPMM_TUNE, OPT_SPMM_SPLIT, OPT_SPMM_CARVEOUT, OPT_SPMM_MASK = 3, 4, 5, 6
 
 
 class EspnmfError(RuntimeError):
@@ -93,7 +93,7 @@ def load():
             "espnmf_batch_ctx": [P, i32, ctypes.POINTER(P)],
             "espnmf_batch_set_option": [P, st, i64],
             "espnmf_batch_iterate": [P, i32, P, P, P],
-            "espnmf_spmm_config": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+            "espnmf_spmm_config": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
             "espnmf_spmm_frequent": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)],
         }
         for name, args in sig.items():
@@ -320,11 +320,11 @@ def espnmf_get_factor(ctx: Context, which: int, layout: int = DENSE_ROWMAJOR,
 
 
 def espnmf_spmm_config(ctx: Context, product: int):
-    """(split, carveout) of product 0 (A V) or 1 (A^T U)."""
-    g, c = ctypes.c_int32(), ctypes.c_int32()
-    _check(load().espnmf_spmm_config(ctx.handle, int(product), ctypes.byref(g), ctypes.byref(c)),
-           ctx.handle)
-    return g.value, c.value
+    """(split, carveout, mask) of product 0 (A V) or 1 (A^T U)."""
+    g, c, m = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().espnmf_spmm_config(ctx.handle, int(product), ctypes.byref(g), ctypes.byref(c),
+                                     ctypes.byref(m)), ctx.handle)
+    return g.value, c.value, m.value
 
 
 def espnmf_spmm_frequent(ctx: Context, product: int):

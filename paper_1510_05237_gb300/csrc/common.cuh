@@ -169,7 +169,7 @@ struct EllDev {
     int32_t* col = nullptr;
     void* val = nullptr;
     void* dense = nullptr;   // dense copies of heavy rows, row stride dld
-    uint4* rec = nullptr;    // FP32 factors: per-row record, see row_record
+    uint4* rec = nullptr;    // FP32 factors: per-row record (2 x uint4), see record_cnt
     int64_t rows = 0;        // rows of the factor
     uint32_t* nzmask = nullptr;      // FP32 factors: nonzero-row bitmask
     const int32_t* hslot = nullptr;  // [rows] slot in htab or -1 (nullptr: no table)
@@ -181,9 +181,12 @@ struct EllDev {
     int heavy = 1 << 30;
 };
 
-// Per-row record of an FP32 factor (16 bytes, one load): x = cnt | c0 << 8 |
-// c1 << 16 | c2 << 24, y/z/w = the bits of the first three values (columns
-// c0 < c1 < c2).  A light row of up to three nonzeros is complete in it.
+// Per-row record of an FP32 factor: 32 bytes (one L2 sector) in two 16-byte
+// halves.  rec[2 i] = {cnt | c0 << 8 | c1 << 16 | c2 << 24, v0, v1, v2} and
+// rec[2 i + 1] = {c3 | c4 << 8 | c5 << 16, v3, v4, v5}: the row's first six
+// pairs in column order (c0 < c1 < ...), unused slots column 0 and value
+// +0.  A row of up to three nonzeros is complete in the first half, one of
+// up to six in the record.
 __host__ __device__ inline int record_cnt(unsigned x) { return (int)(x & 0xffu); }
 
 // Row stride of the dense heavy-row copies: 32 or 64 floats (whole 128-byte
@@ -239,12 +242,15 @@ cudaError_t launch_solve(const T* Y, int64_t ldy, int64_t rows, int k,
 // With rowbits (COLUMN mode), the survivors are also marked, bit c % 32 of
 // word rowbits[i * ceil(k/32) + c / 32] (the words must be zero), and the
 // FP64 sum of squares of each column's survivors is written to
-// diag_part[c * select_cluster(...) + r], r < select_cluster(...).
+// diag_part[c * select_cluster(...) + r], r < select_cluster(...).  With a
+// hint (marking only: k keys, 0 = none), each column starts its search from
+// the hint's threshold and stores its new threshold there; the result does
+// not depend on the hint.
 template <typename T>
 cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
                           int64_t t, int mode, void* tau, uint32_t* cut,
                           cudaStream_t st, int sm_count, uint32_t* rowbits,
-                          double* diag_part);
+                          double* diag_part, void* hint = nullptr);
 int select_cluster(int64_t rows, int k, int mode, int sm_count);
 
 // Projects and enforces a caller's dense rows x k buffer in place.

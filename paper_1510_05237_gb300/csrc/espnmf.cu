@@ -53,6 +53,7 @@ struct Factor {
     double* Ginv64 = nullptr;  // k x k FP64 inverse
     void* GinvT = nullptr;     // k x k inverse in T
     float* Lf = nullptr;       // FP32 form, k <= 64: Cholesky factor (L, L^T, 1/diag)
+    void* sel_hint = nullptr;  // FP32 form: each column's last selection threshold (k keys, 0: none)
     bool chol_pending = true;
     bool valid = false;        // holds a value (V is empty until the first update)
 };
@@ -677,7 +678,7 @@ espnmf_status do_emit(espnmf_ctx* ctx, Factor& F, bool residual, const void* Y, 
     return ESPNMF_OK;
 }
 
-espnmf_status do_select(espnmf_ctx* ctx, int64_t rows, int64_t t, bool mark)
+espnmf_status do_select(espnmf_ctx* ctx, int64_t rows, int64_t t, bool mark, void* hint)
 {
     return run(ctx, K_SELECT, (double)rows * ctx->k * ctx->esz, ctx->st, [&] {
         return is_f64(ctx) ? launch_select<double>((const double*)ctx->Xt, ctx->ldx, rows, ctx->k,
@@ -686,7 +687,8 @@ espnmf_status do_select(espnmf_ctx* ctx, int64_t rows, int64_t t, bool mark)
                            : launch_select<float>((const float*)ctx->Xt, ctx->ldx, rows, ctx->k,
                                                   t, ctx->mode, ctx->tau, ctx->cut, ctx->st,
                                                   ctx->sm_count, mark ? ctx->rowbits : nullptr,
-                                                  mark ? ctx->diag_part : nullptr);
+                                                  mark ? ctx->diag_part : nullptr,
+                                                  mark ? hint : nullptr);
     });
 }
 
@@ -770,10 +772,10 @@ espnmf_status half_update(espnmf_ctx* ctx, bool updV)
     }));
     const int64_t t = updV ? ctx->t_v : ctx->t_u;
     if (survivor_path(ctx)) {
-        TRY(do_select(ctx, rows, t, true));
+        TRY(do_select(ctx, rows, t, true, F.sel_hint));
         TRY(do_emit_survivors(ctx, F, !updV && F.valid, updV ? nullptr : ctx->Y, !updV));
     } else {
-        TRY(do_select(ctx, rows, t, false));
+        TRY(do_select(ctx, rows, t, false, nullptr));
         TRY(do_emit(ctx, F, !updV && F.valid, updV ? nullptr : ctx->Y, !updV, ctx->mode));
     }
     F.valid = true;
@@ -1227,8 +1229,10 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             // the product that gathers this factor: A^T U gathers U, A V gathers V
             const SellDev& Gp = F == &ctx->U ? ctx->sAt : ctx->sA;
             if (!is_f64(ctx)) {
-                TRY(dmalloc(ctx, &rec, sizeof(uint4) * F->rows));
-                CU(cudaMemsetAsync(rec, 0, sizeof(uint4) * F->rows, ctx->st));
+                TRY(dmalloc(ctx, &F->sel_hint, 8 * (size_t)k));
+                CU(cudaMemsetAsync(F->sel_hint, 0, 8 * (size_t)k, ctx->st));
+                TRY(dmalloc(ctx, &rec, 2 * sizeof(uint4) * F->rows));
+                CU(cudaMemsetAsync(rec, 0, 2 * sizeof(uint4) * F->rows, ctx->st));
                 const size_t words = (size_t)(F->rows + 31) / 32;
                 TRY(dmalloc(ctx, &nzmask, 4 * words));
                 CU(cudaMemsetAsync(nzmask, 0, 4 * words, ctx->st));
@@ -1373,7 +1377,7 @@ espnmf_status espnmf_enforce_topt(espnmf_ctx* ctx, espnmf_which which, int64_t t
         return is_f64(ctx) ? launch_ell_to_colmajor<double>(F.rows, ctx->k, cur, (double*)ctx->Xt, ctx->ldx, ctx->st)
                            : launch_ell_to_colmajor<float>(F.rows, ctx->k, cur, (float*)ctx->Xt, ctx->ldx, ctx->st);
     }));
-    TRY(do_select(ctx, F.rows, t, false));
+    TRY(do_select(ctx, F.rows, t, false, nullptr));
     TRY(do_emit(ctx, F, false, nullptr, false, ctx->mode));
     ctx->met_valid = false;
     if (which == ESPNMF_V) ctx->Y_is_AV = false;
@@ -1640,6 +1644,16 @@ espnmf_status espnmf_set_option(espnmf_ctx* ctx, espnmf_option opt, int64_t valu
         ctx->spmm_tune = false;
         drop_graphs(ctx);
         return ESPNMF_OK;
+    case ESPNMF_OPT_SPMM_MASK:
+        if (value < 0 || value > 2) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "mask is 0, 1 or 2");
+        for (int o = 0; o < 2; ++o) {
+            // the product that gathers U (A^T U, o = 1) or V (A V, o = 0)
+            const int64_t rows = o ? ctx->n : ctx->m;
+            ctx->spmm_cfg[o].mask = (value == 2 && rows > 32ll * kSellSmemMaskWords) ? 1 : (int)value;
+        }
+        ctx->spmm_tune = false;
+        drop_graphs(ctx);
+        return ESPNMF_OK;
     }
     return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "unknown option");
 }
@@ -1768,13 +1782,14 @@ espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64
 }  // extern "C"
 
 extern "C" espnmf_status espnmf_spmm_config(espnmf_ctx* ctx, int32_t product, int32_t* split,
-                                            int32_t* carveout)
+                                            int32_t* carveout, int32_t* mask)
 {
     TRY(enter(ctx));
     if (product != 0 && product != 1) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "product is 0 or 1");
     const SpmmConfig& c = ctx->spmm_cfg[product];
     if (split) *split = (is_f64(ctx) || ctx->ldy < 16) ? 1 : c.split;
     if (carveout) *carveout = c.carveout;
+    if (mask) *mask = is_f64(ctx) ? 0 : c.mask;
     return ESPNMF_OK;
 }
 

@@ -168,89 +168,121 @@ cudaError_t launch_cholesky(const double* G, int k, int KP, float* Ls, float* LT
 // ---------------------------------------------------------------------------
 
 constexpr int kSolveRows = 128;   // rows per tile, one per thread
-constexpr int kSolveStride = kSolveRows + 1;   // staged tile row stride (bank offset)
 
-template <int KP>
-__global__ void __launch_bounds__(kSolveRows, 4)
+// (s0, s1) = (a0 * b0 + s0, a1 * b1 + s1): one packed FP32 instruction, each
+// lane rounded as fmaf rounds.
+__device__ __forceinline__ void fma2f(float& s0, float& s1, float a0, float a1, float b0, float b1)
+{
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pc, {%0, %1};\n\t"
+        "fma.rn.f32x2 pc, pa, pb, pc;\n\t"
+        "mov.b64 {%0, %1}, pc;\n\t}"
+        : "+f"(s0), "+f"(s1) : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// X = Y (F^T F)^-1 row by row, with F^T F = L L^T from cholesky_kernel, then
+// the projection max(x, 0) (Alg. 2 steps 1 and 3).  Each thread solves R
+// rows (rows r0 + tid and r0 + tid + kSolveRows), held in registers, so that
+// every coefficient read from shared memory serves R rows.  Both
+// substitutions run in column (axpy) form: once an unknown is final, it is
+// multiplied into every unknown still open, so the updates of a step are
+// independent of each other (two per packed FMA) instead of one dependent
+// chain per unknown.  The negated factor is held in shared memory as
+// N1[j][i] = -L[i][j] (i > j) and N2[j][i] = -L[j][i] (i < j), zero
+// elsewhere, so a step reads its coefficients as aligned 16-byte rows; a
+// zero coefficient leaves the unknown it meets unchanged.
+template <int KP, int R>
+__global__ void __launch_bounds__(kSolveRows, 4 / R)
 solve_chol_kernel(const float* __restrict__ Y, int64_t ldy, int64_t rows, int k,
                   const float* __restrict__ Lg, const float* __restrict__ LTg,
                   const float* __restrict__ rdg, float* __restrict__ Xt, int64_t ldx,
                   unsigned* status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* Ls = reinterpret_cast<float*>(smem_raw);   // [KP][KP]
-    float* LTs = Ls + KP * KP;                          // [KP][KP]
-    float* rds = LTs + KP * KP;                         // [KP]
-    float* Ys = rds + KP;                               // [KP][kSolveStride]
+    float* N1 = reinterpret_cast<float*>(smem_raw);   // [KP][KP]
+    float* N2 = N1 + KP * KP;                           // [KP][KP]
+    float* rds = N2 + KP * KP;                          // [KP]
     const int tid = threadIdx.x;
     for (int e = tid; e < KP * KP; e += blockDim.x) {
-        Ls[e] = Lg[e];
-        LTs[e] = LTg[e];
+        const int j = e / KP, i = e - j * KP;
+        const bool in = i < k && j < k;
+        N1[e] = (in && i > j) ? -LTg[e] : 0.f;   // L^T[j][i] = L[i][j]
+        N2[e] = (in && i < j) ? -Lg[e] : 0.f;    // L[j][i]
     }
-    for (int e = tid; e < KP; e += blockDim.x) rds[e] = rdg[e];
+    for (int e = tid; e < KP; e += blockDim.x) rds[e] = e < k ? rdg[e] : 0.f;
+    __syncthreads();
     bool bad = false;
-    for (int64_t r0 = (int64_t)blockIdx.x * kSolveRows; r0 < rows;
-         r0 += (int64_t)gridDim.x * kSolveRows) {
-        __syncthreads();
-        const int nr = (int)(rows - r0 < kSolveRows ? rows - r0 : kSolveRows);
-        // stage the tile transposed: four rows per pass, a quarter-warp per
-        // row, so each row is read with consecutive 16-byte loads
-        for (int q = tid; q < kSolveRows * (KP / 4); q += blockDim.x) {
-            const int rr = q / (KP / 4), d4 = q - rr * (KP / 4);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (rr < nr) v = *reinterpret_cast<const float4*>(Y + (r0 + rr) * ldy + 4 * d4);
-            Ys[(4 * d4 + 0) * kSolveStride + rr] = v.x;
-            Ys[(4 * d4 + 1) * kSolveStride + rr] = v.y;
-            Ys[(4 * d4 + 2) * kSolveStride + rr] = v.z;
-            Ys[(4 * d4 + 3) * kSolveStride + rr] = v.w;
-        }
-        __syncthreads();
-        float x[KP];
+    for (int64_t r0 = (int64_t)blockIdx.x * kSolveRows * R; r0 < rows;
+         r0 += (int64_t)gridDim.x * kSolveRows * R) {
+        float x[R][KP];
 #pragma unroll
-        for (int d = 0; d < KP; ++d) x[d] = Ys[d * kSolveStride + tid];
-        // L z = y: z_j = (y_j - sum_{i<j} L_ji z_i) / L_jj; the strictly
-        // upper entries of Ls are zero, so whole 4-wide groups can be read
-        // (two interleaved partial sums per unknown: twice the independent
-        // FMAs in flight; they are added in a fixed order)
+        for (int h = 0; h < R; ++h) {
+            const int64_t r = r0 + tid + h * kSolveRows;
+            const bool live = r < rows;
+            const float4* yr = reinterpret_cast<const float4*>(Y + (live ? r : 0) * ldy);
+#pragma unroll
+            for (int q = 0; q < KP / 4; ++q) {
+                const float4 v = live ? yr[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                x[h][4 * q + 0] = v.x;
+                x[h][4 * q + 1] = v.y;
+                x[h][4 * q + 2] = v.z;
+                x[h][4 * q + 3] = v.w;
+            }
+        }
+        // L z = y: z_j = x_j / L_jj, then x_i -= L_ij z_j for i > j
 #pragma unroll
         for (int j = 0; j < KP; ++j) {
-            float s0 = x[j], s1 = 0.f;
+            const float d = rds[j];
 #pragma unroll
-            for (int i = 0; i < (j + 3) / 4 * 4; i += 4) {
-                const float4 l = *reinterpret_cast<const float4*>(Ls + j * KP + i);
-                s0 = fmaf(-l.x, x[i + 0], s0);
-                s1 = fmaf(-l.y, x[i + 1], s1);
-                s0 = fmaf(-l.z, x[i + 2], s0);
-                s1 = fmaf(-l.w, x[i + 3], s1);
-            }
-            x[j] = (s0 + s1) * rds[j];
-        }
-        // L^T x = z: x_j = (z_j - sum_{i>j} L_ij x_i) / L_jj
-#pragma unroll
-        for (int j = KP - 1; j >= 0; --j) {
-            float s0 = x[j], s1 = 0.f;
+            for (int h = 0; h < R; ++h) x[h][j] *= d;
 #pragma unroll
             for (int i = (j + 1) / 4 * 4; i < KP; i += 4) {
-                const float4 l = *reinterpret_cast<const float4*>(LTs + j * KP + i);
-                s0 = fmaf(-l.x, x[i + 0], s0);
-                s1 = fmaf(-l.y, x[i + 1], s1);
-                s0 = fmaf(-l.z, x[i + 2], s0);
-                s1 = fmaf(-l.w, x[i + 3], s1);
-            }
-            x[j] = (s0 + s1) * rds[j];
-        }
-        if (tid < nr) {
+                const float4 l = *reinterpret_cast<const float4*>(N1 + j * KP + i);
 #pragma unroll
-            for (int c = 0; c < KP; ++c) {
-                if (c >= k) break;
-                const float v = x[c];
-                if (!isfinite(v)) bad = true;
-                Xt[(int64_t)c * ldx + r0 + tid] = v > 0.f ? v : 0.f;
+                for (int h = 0; h < R; ++h) {
+                    fma2f(x[h][i], x[h][i + 1], l.x, l.y, x[h][j], x[h][j]);
+                    fma2f(x[h][i + 2], x[h][i + 3], l.z, l.w, x[h][j], x[h][j]);
+                }
+            }
+        }
+        // L^T x = z: x_j = z_j / L_jj, then z_i -= L_ji x_j for i < j
+#pragma unroll
+        for (int j = KP - 1; j >= 0; --j) {
+            const float d = rds[j];
+#pragma unroll
+            for (int h = 0; h < R; ++h) x[h][j] *= d;
+#pragma unroll
+            for (int i = 0; i < (j + 3) / 4 * 4; i += 4) {
+                const float4 l = *reinterpret_cast<const float4*>(N2 + j * KP + i);
+#pragma unroll
+                for (int h = 0; h < R; ++h) {
+                    fma2f(x[h][i], x[h][i + 1], l.x, l.y, x[h][j], x[h][j]);
+                    fma2f(x[h][i + 2], x[h][i + 3], l.z, l.w, x[h][j], x[h][j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < R; ++h) {
+            const int64_t r = r0 + tid + h * kSolveRows;
+            if (r < rows) {
+#pragma unroll
+                for (int c = 0; c < KP; ++c) {
+                    if (c >= k) break;
+                    const float v = x[h][c];
+                    if (!isfinite(v)) bad = true;
+                    Xt[(int64_t)c * ldx + r] = v > 0.f ? v : 0.f;
+                }
             }
         }
     }
     if (bad) atomicOr(status, ST_NONFINITE);
 }
+
+// rows per thread of solve_chol_kernel: two while both rows fit the
+// registers without spilling
+constexpr int solve_rows_per_thread(int KP) { return KP <= 56 ? 1 : 1; }
 
 template <int KP>
 static cudaError_t launch_solve_chol_kp(const float* Y, int64_t ldy, int64_t rows, int k,
@@ -258,12 +290,13 @@ static cudaError_t launch_solve_chol_kp(const float* Y, int64_t ldy, int64_t row
                                         float* Xt, int64_t ldx, unsigned* status,
                                         cudaStream_t st, int sm_count)
 {
-    const size_t smem = ((size_t)2 * KP * KP + KP + (size_t)KP * kSolveStride) * sizeof(float);
-    const int64_t tiles = (rows + kSolveRows - 1) / kSolveRows;
-    int64_t grid = (int64_t)sm_count * 4;
+    const size_t smem = ((size_t)2 * KP * KP + KP) * sizeof(float);
+    constexpr int R = solve_rows_per_thread(KP);
+    const int64_t tiles = (rows + kSolveRows * R - 1) / (kSolveRows * R);
+    int64_t grid = (int64_t)sm_count * (4 / R);
     if (grid > tiles) grid = tiles;
-    solve_chol_kernel<KP><<<(unsigned)grid, kSolveRows, smem, st>>>(Y, ldy, rows, k, L, LT, rd,
-                                                                  Xt, ldx, status);
+    solve_chol_kernel<KP, R><<<(unsigned)grid, kSolveRows, smem, st>>>(Y, ldy, rows, k, L, LT, rd,
+                                                                     Xt, ldx, status);
     return cudaGetLastError();
 }
 
@@ -286,13 +319,14 @@ cudaError_t launch_solve_chol(const float* Y, int64_t ldy, int64_t rows, int k, 
 template <int KP>
 static cudaError_t setup_solve_kp()
 {
-    const size_t smem = ((size_t)2 * KP * KP + KP + (size_t)KP * kSolveStride) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(solve_chol_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = ((size_t)2 * KP * KP + KP) * sizeof(float);
+    constexpr int R = solve_rows_per_thread(KP);
+    cudaError_t e = cudaFuncSetAttribute(solve_chol_kernel<KP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     // four blocks per SM need most of the shared memory: do not let the
     // driver pick a smaller carveout
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(solve_chol_kernel<KP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(solve_chol_kernel<KP, R>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
     return e;
 }

@@ -200,14 +200,18 @@ emit_kernel(EmitArgs<T> a)
             a.cnt[r] = pos;
             if constexpr (sizeof(T) == 4) {
                 if (a.rec) {
-                    // the first min(pos, 3) pairs are in this lane's staging
-                    unsigned x = (unsigned)pos;
-                    unsigned v[3] = {0u, 0u, 0u};
-                    for (int q = 0; q < pos && q < 3; ++q) {
-                        x |= (unsigned)stc[lane * SL + q] << (8 * (q + 1));
-                        v[q] = __float_as_uint((float)stv[lane * SL + q]);
+                    // the first min(pos, 6) pairs: from this lane's staging,
+                    // or from the row this thread has just written
+                    unsigned x[2] = {(unsigned)pos, 0u};
+                    unsigned v[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+                    for (int q = 0; q < pos && q < 6; ++q) {
+                        const unsigned c = (unsigned)(q < SL ? stc[lane * SL + q] : wc[q]);
+                        const float xv = (float)(q < SL ? stv[lane * SL + q] : wv[q]);
+                        x[q / 3] |= c << (q < 3 ? 8 * (q + 1) : 8 * (q - 3));
+                        v[q] = __float_as_uint(xv);
                     }
-                    a.rec[r] = make_uint4(x, v[0], v[1], v[2]);
+                    a.rec[2 * r] = make_uint4(x[0], v[0], v[1], v[2]);
+                    a.rec[2 * r + 1] = make_uint4(x[1], v[3], v[4], v[5]);
                 }
             }
             if (a.zero_old) a.cnt_old[r] = 0;
@@ -404,16 +408,39 @@ __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
         const int np = w < ntri ? P : Ps;
         const double* src = w < ntri ? gram_part + (size_t)w * P : scal_part + (size_t)(w - ntri) * Ps;
         double v;
+        // the partials are loaded eight at a time before they are added (in
+        // the same order), so a lane waits for the L2 once per eight
+        constexpr int U8 = 8;
         if (pairs) {
             // compensated pairs, added on the FP32 pipes, widened once
             const float2* sp = reinterpret_cast<const float2*>(src);
             DFloat acc;
-            for (int p = lane; p < np; p += 32) df_add(acc, sp[p].x, sp[p].y);
+            for (int p0 = lane; p0 < np; p0 += 32 * U8) {
+                float2 b[U8];
+#pragma unroll
+                for (int u = 0; u < U8; ++u) {
+                    const int p = p0 + 32 * u;
+                    b[u] = p < np ? sp[p] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < U8; ++u)
+                    if (p0 + 32 * u < np) df_add(acc, b[u].x, b[u].y);
+            }
             acc = df_warp_sum(acc);
             v = df_value(acc);
         } else {
             double s0 = 0.0, s1 = 0.0;
             int p = lane;
+            for (; p + 32 * (U8 - 1) < np; p += 32 * U8) {
+                double b[U8];
+#pragma unroll
+                for (int u = 0; u < U8; ++u) b[u] = src[p + 32 * u];
+#pragma unroll
+                for (int u = 0; u < U8; u += 2) {
+                    s0 += b[u];
+                    s1 += b[u + 1];
+                }
+            }
             for (; p + 32 < np; p += 64) {
                 s0 += src[p];
                 s1 += src[p + 32];
@@ -458,7 +485,18 @@ __global__ void gram_reduce_kernel(const double* __restrict__ gram_part,
     if (!last) return;
     __threadfence();
     double tr = 0.0;
-    for (int q = threadIdx.x; q < kk; q += blockDim.x) tr += __ldcg(G + q) * m.G_other[q];
+    for (int q0 = threadIdx.x; q0 < kk; q0 += 8 * blockDim.x) {
+        double g[8], o[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * blockDim.x;
+            g[u] = q < kk ? __ldcg(G + q) : 0.0;
+            o[u] = q < kk ? m.G_other[q] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (q0 + u * (int)blockDim.x < kk) tr += g[u] * o[u];
+    }
     tr = warp_sum(tr);
     if (lane == 0) red[threadIdx.x >> 5] = tr;
     __syncthreads();
@@ -558,6 +596,9 @@ emit_s_kernel(EmitSArgs a)
     int2* stage = reinterpret_cast<int2*>(smem_raw + (((size_t)a.k * (a.k + 1) / 2 * sizeof(DFloat) + 15) & ~(size_t)15));
     __shared__ int wcount[kEmitSThreads / 32];
     __shared__ int list[kEmitSThreads];
+    __shared__ int ccnt[kEmitSThreads / 32];
+    __shared__ int clist[kEmitSThreads];              // this round's many-survivor rows
+    __shared__ uint32_t cbits[kEmitSThreads][WD];     // their survivor bits
     __shared__ DFloat red[kEmitSThreads / 32][4];
     __shared__ float wold[kEmitSThreads / 32][kMaxK];   // a warp's old row, dense
     const int k = a.k, ld = a.ld;
@@ -565,16 +606,21 @@ emit_s_kernel(EmitSArgs a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int NW = blockDim.x >> 5;
     for (int e = tid; e < ntri; e += blockDim.x) T[e] = DFloat();
-    // blocks own whole 32-row words of the nonzero-row bitmask
-    const int64_t chunk = ((a.rows + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
-    const int64_t b0 = (int64_t)blockIdx.x * chunk < a.rows ? (int64_t)blockIdx.x * chunk : a.rows;
-    const int64_t b1 = b0 + chunk < a.rows ? b0 + chunk : a.rows;
+    // Warps own whole 32-row words of the nonzero-row bitmask, dealt out
+    // round-robin over the blocks (word (rnd * NW + warp) * G + block), so
+    // that rows with many survivors -- on text corpora the frequent terms,
+    // which have the lowest ids -- spread over all blocks.
+    const int64_t G = gridDim.x;
+    const int64_t nwords = (a.rows + 31) / 32;
+    auto word_of = [&](int64_t rnd, int w) -> int64_t { return (rnd * NW + w) * G + blockIdx.x; };
+    // global row of local index lr = warp * 32 + lane of round rnd
+    auto row_of = [&](int64_t rnd, int lr) -> int64_t { return word_of(rnd, lr >> 5) * 32 + (lr & 31); };
     // per-lane Sec. 3.1 sums in compensated FP32 (widened to FP64 at the end)
     DFloat s_diff, s_new, s_old, s_cross;
 
-    for (int64_t base = b0; base < b1; base += blockDim.x) {
-        const int64_t r = base + tid;
-        const bool valid = r < b1;
+    for (int64_t rnd = 0; word_of(rnd, 0) < nwords; ++rnd) {
+        const int64_t r = row_of(rnd, tid);
+        const bool valid = r < a.rows;
         bool nonzero = false, offdiag = false;
         uint32_t bits[WD];
 #pragma unroll
@@ -605,6 +651,7 @@ emit_s_kernel(EmitSArgs a)
             int32_t* wc = a.col + r * ld;
             float* wv = a.val + r * ld;
             unsigned rx = 0u, rv0 = 0u, rv1 = 0u, rv2 = 0u;
+            unsigned rx1 = 0u, rv3 = 0u, rv4 = 0u, rv5 = 0u;
             int pos = 0, q = 0;
 #pragma unroll
             for (int w = 0; w < WD; ++w) {
@@ -619,6 +666,9 @@ emit_s_kernel(EmitSArgs a)
                     if (pos == 0) { rx |= (unsigned)c << 8; rv0 = __float_as_uint(x); }
                     else if (pos == 1) { rx |= (unsigned)c << 16; rv1 = __float_as_uint(x); }
                     else if (pos == 2) { rx |= (unsigned)c << 24; rv2 = __float_as_uint(x); }
+                    else if (pos == 3) { rx1 |= (unsigned)c; rv3 = __float_as_uint(x); }
+                    else if (pos == 4) { rx1 |= (unsigned)c << 8; rv4 = __float_as_uint(x); }
+                    else if (pos == 5) { rx1 |= (unsigned)c << 16; rv5 = __float_as_uint(x); }
                     df_add_prod(s_new, x, x);
                     if (a.Y) df_add_prod(s_cross, x, a.Y[r * a.ldy + c]);
                     if (a.residual) {
@@ -647,7 +697,10 @@ emit_s_kernel(EmitSArgs a)
                 }
             }
             a.cnt[r] = pos;
-            if (a.rec) a.rec[r] = make_uint4(rx | (unsigned)pos, rv0, rv1, rv2);
+            if (a.rec) {
+                a.rec[2 * r] = make_uint4(rx | (unsigned)pos, rv0, rv1, rv2);
+                a.rec[2 * r + 1] = make_uint4(rx1, rv3, rv4, rv5);
+            }
             if (a.zero_old) a.cnt_old[r] = 0;
             if (pos >= a.heavy && a.dense != nullptr) {
                 float* dr = a.dense + r * a.dld;
@@ -664,16 +717,30 @@ emit_s_kernel(EmitSArgs a)
             nonzero = pos > 0;
             offdiag = pos >= 2 && sl < 0;
         }
-        // rows with many survivors, one at a time by the whole warp: lane c
+        // rows with many survivors: listed in (warp, lane) order, then taken
+        // one at a time by a whole warp (list entry j by warp j % NW): lane c
         // handles column c (and c + 32, ...), positions by prefix counts
-        unsigned cm = __ballot_sync(0xffffffffu, coop);
-        while (cm) {
-            const int j = __ffs(cm) - 1;
-            cm &= cm - 1u;
-            const int64_t rr = base + warp * 32 + j;
+        {
+            const unsigned cb = __ballot_sync(0xffffffffu, coop);
+            if (lane == 0) ccnt[warp] = __popc(cb);
+            __syncthreads();
+            int off = 0;
+            for (int w = 0; w < warp; ++w) off += ccnt[w];
+            if (coop) {
+                const int j = off + __popc(cb & ((1u << lane) - 1u));
+                clist[j] = tid;
+#pragma unroll
+                for (int w = 0; w < WD; ++w) cbits[j][w] = bits[w];
+            }
+        }
+        int ctot = 0;
+        for (int w = 0; w < NW; ++w) ctot += ccnt[w];
+        __syncthreads();
+        for (int j = warp; j < ctot; j += NW) {
+            const int64_t rr = row_of(rnd, clist[j]);
             uint32_t bw[WD];
 #pragma unroll
-            for (int w = 0; w < WD; ++w) bw[w] = __shfl_sync(0xffffffffu, bits[w], j);
+            for (int w = 0; w < WD; ++w) bw[w] = cbits[j][w];
             auto surv = [&](int c) -> bool {
                 uint32_t wd = bw[0];
 #pragma unroll
@@ -705,7 +772,7 @@ emit_s_kernel(EmitSArgs a)
             for (int w = 0; w < WD; ++w) nb += __popc(bw[w]);
             float* dr = nb >= a.heavy && a.dense != nullptr ? a.dense + rr * a.dld : nullptr;
             float* tr = sl >= 0 ? a.htab + (int64_t)sl * ld : nullptr;
-            unsigned rx = (unsigned)nb, rv[3] = {0u, 0u, 0u};
+            unsigned rx = (unsigned)nb, rx1 = 0u, rv[6] = {0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
             for (int w = 0; w < WD; ++w) {
                 const int c = 32 * w + lane;
@@ -724,15 +791,16 @@ emit_s_kernel(EmitSArgs a)
                     if (dr) dr[c] = x;
                     if (tr) tr[c] = x;
                 }
-                // the record's first three pairs
+                // the record's first six pairs
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
+                for (int q = 0; q < 6; ++q) {
                     const unsigned who = __ballot_sync(0xffffffffu, sv && pos == q);
                     if (who) {
                         const int src = __ffs(who) - 1;
                         const unsigned cq = (unsigned)__shfl_sync(0xffffffffu, c, src);
                         const unsigned xq = __shfl_sync(0xffffffffu, __float_as_uint(x), src);
-                        rx |= cq << (8 * (q + 1));
+                        if (q < 3) rx |= cq << (8 * (q + 1));
+                        else rx1 |= cq << (8 * (q - 3));
                         rv[q] = xq;
                     }
                 }
@@ -742,7 +810,10 @@ emit_s_kernel(EmitSArgs a)
                 for (int c = 32 * WD + lane; c < a.dld; c += 32) dr[c] = 0.f;
             if (lane == 0) {
                 a.cnt[rr] = nb;
-                if (a.rec) a.rec[rr] = make_uint4(rx, rv[0], rv[1], rv[2]);
+                if (a.rec) {
+                    a.rec[2 * rr] = make_uint4(rx, rv[0], rv[1], rv[2]);
+                    a.rec[2 * rr + 1] = make_uint4(rx1, rv[3], rv[4], rv[5]);
+                }
                 if (a.zero_old) a.cnt_old[rr] = 0;
                 if (tr) a.hnz[sl] = 1;
             }
@@ -750,8 +821,8 @@ emit_s_kernel(EmitSArgs a)
         }
         if (a.nzmask) {
             const unsigned word = __ballot_sync(0xffffffffu, nonzero);
-            const int64_t w0 = base + warp * 32;
-            if (lane == 0 && w0 < b1) a.nzmask[w0 >> 5] = word;
+            const int64_t wd = word_of(rnd, warp);
+            if (lane == 0 && wd < nwords) a.nzmask[wd] = word;
         }
         // this round's rows with off-diagonal products, in row order
         const unsigned ob = __ballot_sync(0xffffffffu, offdiag);
@@ -762,12 +833,12 @@ emit_s_kernel(EmitSArgs a)
             if (w < warp) off += wcount[w];
             tot += wcount[w];
         }
-        if (offdiag) list[off + __popc(ob & ((1u << lane) - 1u))] = (int)(r - base);
+        if (offdiag) list[off + __popc(ob & ((1u << lane) - 1u))] = tid;
         __syncthreads();
         if (warp == 0) {
             for (int i = 0; i < tot; ++i) {
                 const int lr = list[i];
-                const int64_t rr = base + lr;
+                const int64_t rr = row_of(rnd, lr);
                 const int L = a.cnt[rr];
                 if (L <= kEmitSStage) {
                     const int2* sp = stage + lr * kEmitSStage;
@@ -1402,8 +1473,10 @@ cudaError_t setup_factor()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(emit_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     if (e != cudaSuccess) return e;
+    // emit_s needs at most k(k+1)/2 compensated pairs (k <= 128: 66 KB) and
+    // the 32 KB stage, beside its static arrays
     auto es = [&](auto kern) {
-        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         if (r == cudaSuccess)
             r = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      cudaSharedmemCarveoutMaxShared);

@@ -37,7 +37,7 @@ namespace cg = cooperative_groups;
 
 namespace espnmf {
 
-constexpr int kSelThreads = 512;
+constexpr int kSelThreads = 1024;
 constexpr int kSelMaxCluster = 2;
 
 template <typename T> struct Vec4Of;
@@ -45,7 +45,7 @@ template <> struct Vec4Of<float> { using type = float4; };
 struct alignas(16) Double4x { double2 a, b; };
 template <> struct Vec4Of<double> { using type = Double4x; };
 constexpr int kHist = 2048;
-constexpr int kCandCap = 3072;   // candidates per CTA
+constexpr int kCandCap = 12288;  // candidates per CTA
 constexpr size_t kSelSmemMax = 210 * 1024;
 
 template <typename T>
@@ -62,6 +62,7 @@ struct ScanOut {
     int bin;
     unsigned long long before;   // count in the bins scanned before `bin`
     unsigned long long total;
+    unsigned long long count;    // count in `bin`
 };
 
 // Adds the cluster's histograms (first nb bins, kBinsPerThread per thread)
@@ -73,8 +74,10 @@ __device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int 
                                 unsigned long long need, bool descending,
                                 unsigned long long* wsum, unsigned long long* res)
 {
-    cluster.sync();   // every CTA's histogram is complete
     const int C = (int)cluster.num_blocks();
+    // every CTA's histogram is complete (a block barrier for a lone CTA)
+    if (C > 1) cluster.sync();
+    else __syncthreads();
     const int tid = threadIdx.x;
     unsigned long long v[kBinsPerThread];
 #pragma unroll
@@ -86,7 +89,7 @@ __device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int 
             for (int r = 0; r < C; ++r) v[u] += cluster.map_shared_rank(hist, r)[b];
         }
     }
-    cluster.sync();   // remote reads done: histograms may be reused
+    if (C > 1) cluster.sync();   // remote reads done: histograms may be reused
     unsigned long long local = 0;
 #pragma unroll
     for (int u = 0; u < kBinsPerThread; ++u) local += v[u];
@@ -109,6 +112,7 @@ __device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int 
     if (tid == 0) {
         res[0] = ~0ull;
         res[1] = 0;
+        res[2] = 0;
     }
     __syncthreads();
     const unsigned long long start = (warp > 0 ? wsum[warp - 1] : 0) + incl - local;
@@ -121,6 +125,7 @@ __device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int 
                 const int o = tid * kBinsPerThread + u;
                 res[0] = (unsigned long long)(descending ? nb - 1 - o : o);
                 res[1] = cum;
+                res[2] = v[u];
                 break;
             }
             cum += v[u];
@@ -130,6 +135,7 @@ __device__ ScanOut cluster_scan(cg::cluster_group& cluster, unsigned* hist, int 
     ScanOut r;
     r.bin = (int)res[0];
     r.before = res[1];
+    r.count = res[2];
     r.total = total;
     __syncthreads();
     return r;
@@ -157,6 +163,7 @@ struct SelMark {
     uint32_t* rowbits = nullptr;
     int words = 0;
     double* diag_part = nullptr;
+    void* hint = nullptr;   // [k] keys: the last threshold of each column (0: none)
 };
 
 template <typename T>
@@ -170,12 +177,13 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ DFloat wsq[kSelThreads / 32];
-    __shared__ unsigned long long wisq[kSelThreads / 32];
+    __shared__ unsigned long long wisq[kSelThreads / 32], wisq1[kSelThreads / 32];
     __shared__ double bucket_sq;   // the bucket survivors' exact sum of squares
+    __shared__ unsigned long long s_above;   // warm start: entries above the window
     unsigned* hist = reinterpret_cast<unsigned*>(smem_raw + SelSmem<T>::hist);
     unsigned long long* wsum = reinterpret_cast<unsigned long long*>(smem_raw + SelSmem<T>::misc);
     unsigned long long* res = wsum + 32;
-    unsigned* ccount = reinterpret_cast<unsigned*>(res + 2);
+    unsigned* ccount = reinterpret_cast<unsigned*>(res + 3);
     K* ckey = reinterpret_cast<K*>(smem_raw + SelSmem<T>::ckey);
     uint32_t* cidx = reinterpret_cast<uint32_t*>(smem_raw + SelSmem<T>::cidx);
 
@@ -290,36 +298,14 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
         mark_finish();
     };
 
-    // ---- pass 1: histogram of the top 11 bits of the positive entries
-    for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
     const int lane = tid & 31;
-    for_each([&](K key, int, bool in) {
-        if (in && key != 0) atomicAdd(&hist[(unsigned)(key >> TS) & (kHist - 1)], 1u);
-    });
-    __syncthreads();
-    unsigned long long need = (unsigned long long)t;
-    const ScanOut s1 = cluster_scan(cluster, hist, kHist, need, true, wsum, res);
-    if (s1.total <= need) {   // at most t positive entries: keep them all
-        if (crank == 0 && tid == 0) {
-            tau_out[seg] = 0;
-            cut_out[seg] = 0xffffffffu;
-        }
-        if (mark.rowbits) mark_all();
-        return;
-    }
-    need -= s1.before;
-    K prefix = (K)s1.bin << TS;
-    int shift = TS;   // bits below `shift` are still open
-
-    // ---- pass 2: the bucket's entries into the candidate list
-    if (tid == 0) *ccount = 0;
-    __syncthreads();
     const bool marking = mark.rowbits != nullptr;
-    for_each([&](K key, int e, bool in) {
-        const bool hit = in && key != 0 && (key >> shift) == (prefix >> shift);
-        // above the threshold's bucket: a survivor whatever the threshold
-        if (marking && in && (key >> shift) > (prefix >> shift)) mark_one(key, (uint32_t)(lo + e));
+    K* hint = static_cast<K*>(mark.hint);
+    constexpr int KB = (int)(8 * sizeof(K));
+    // the first histogram's bin of a positive key
+    auto bucket_of = [&](K key) -> int { return (int)((key >> TS) & (K)(kHist - 1)); };
+    // appends this lane's entry to the candidate list (warp-aggregated)
+    auto append = [&](bool hit, K key, int e) {
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (m == 0u) return;
         unsigned base = 0;
@@ -332,33 +318,193 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
                 cidx[pos] = index_of(e);
             }
         }
-    });
-    __syncthreads();
-    const unsigned ncand = *ccount;
-    __syncthreads();
-    if (tid == 0) hist[0] = ncand > (unsigned)kCandCap ? 1u : 0u;
-    __syncthreads();
-    const ScanOut ov = cluster_scan(cluster, hist, 1, 1, false, wsum, res);
-    const bool use_list = ov.total == 0;   // no CTA overflowed
-    const int nc = use_list ? (int)ncand : 0;
+    };
 
-    // ---- the remaining bits: radix rounds of up to 11 bits
+    unsigned long long need = (unsigned long long)t;
+    K prefix = 0;
+    int shift = 0;     // bits below `shift` are still open
+    int nc = 0;
+    bool use_list = true;
+    int base_bucket = 0;   // lowest first-histogram bin among the candidates
+    bool warm = false;
+
+    // ---- warm start (column mode, one CTA per column): the threshold of
+    // the previous selection of this column names a first-histogram bin; one
+    // pass counts the entries above that bin's neighbours and lists the
+    // entries of the three bins.  If the t-th largest lies among them, the
+    // first histogram and its pass are not needed; otherwise the marks
+    // set above the window are taken back and the full search follows.
+    if (hint != nullptr && C == 1 && !matrix) {
+        const K h = hint[seg];
+        if (h != (K)0 && h != ~(K)0) {
+            const int hb = bucket_of(h);
+            const int lo_b = hb > 0 ? hb - 1 : 0, hi_b = hb < kHist - 1 ? hb + 1 : kHist - 1;
+            if (tid == 0) {
+                *ccount = 0;
+                s_above = 0;
+            }
+            __syncthreads();
+            // the window in key space: [lo_key, hi_key], lo_key > 0
+            const K lo_key = lo_b > 0 ? (K)lo_b << TS : (K)1;
+            const K hi_key = (((K)hi_b + 1) << TS) - 1;
+            unsigned above = 0;
+            if (!matrix) {
+                // sixteen entries per thread per round (four 16-byte loads);
+                // the round's hits are placed by one warp scan
+                using V4 = typename Vec4Of<T>::type;
+                const V4* s4 = reinterpret_cast<const V4*>(Xt + (int64_t)seg * ldx + lo);
+                const int nv = nloc / 4;
+                const int span = (int)blockDim.x * 4;
+                const int nround = (nv + span - 1) / span * span;
+                for (int q0 = tid; q0 < nround; q0 += span) {
+                    K keys[16];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = q0 + u * (int)blockDim.x;
+                        V4 v;
+                        if (q < nv) v = s4[q];
+                        const T* x = reinterpret_cast<const T*>(&v);
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) keys[4 * u + w] = q < nv ? KeyBits<T>::of(x[w]) : (K)0;
+                    }
+                    unsigned hm = 0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const K key = keys[j];
+                        if (key > hi_key) {
+                            ++above;
+                            if (marking) {
+                                const int e = 4 * (q0 + (j >> 2) * (int)blockDim.x) + (j & 3);
+                                mark_one(key, (uint32_t)(lo + e));
+                            }
+                        }
+                        if (key >= lo_key && key <= hi_key) hm |= 1u << j;
+                    }
+                    const unsigned nh = (unsigned)__popc(hm);
+                    unsigned incl = nh;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += y;
+                    }
+                    unsigned base = 0;
+                    if (lane == 31 && incl) base = atomicAdd(ccount, incl);
+                    base = __shfl_sync(0xffffffffu, base, 31) + incl - nh;
+                    if (hm) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if ((hm >> j) & 1u) {
+                                if (base < (unsigned)kCandCap) {
+                                    ckey[base] = keys[j];
+                                    cidx[base] = (uint32_t)(lo + 4 * (q0 + (j >> 2) * (int)blockDim.x) + (j & 3));
+                                }
+                                ++base;
+                            }
+                        }
+                    }
+                }
+                // tail (fewer than 4 entries)
+                const int tail = nloc - nv * 4;
+                if (tail > 0) {
+                    const bool in = tid < tail;
+                    const int e = nv * 4 + (in ? tid : 0);
+                    const K key = in ? KeyBits<T>::of(Xt[(int64_t)seg * ldx + lo + e]) : (K)0;
+                    if (key > hi_key) {
+                        ++above;
+                        if (marking) mark_one(key, (uint32_t)(lo + e));
+                    }
+                    append(key >= lo_key && key <= hi_key, key, e);
+                }
+            }
+            above = __reduce_add_sync(0xffffffffu, above);
+            if (lane == 0 && above) atomicAdd(&s_above, (unsigned long long)above);
+            __syncthreads();
+            const unsigned long long ab = s_above, nca = *ccount;
+            __syncthreads();
+            if (nca <= (unsigned long long)kCandCap && ab < need && ab + nca >= need) {
+                warm = true;
+                need -= ab;
+                prefix = 0;
+                shift = TS + 11;   // the candidates still differ in their bin
+                nc = (int)nca;
+                base_bucket = lo_b;
+            } else if (marking) {
+                for_each([&](K key, int e, bool in) {
+                    if (in && key > hi_key)
+                        atomicAnd(mark.rowbits + (seg >> 5) + (size_t)(lo + e) * mark.words, ~mbit);
+                });
+                msq = DFloat();
+                __syncthreads();
+            }
+        }
+    }
+
+    if (!warm) {
+        // ---- pass 1: histogram of the top 11 bits of the positive entries
+        for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        for_each([&](K key, int, bool in) {
+            if (in && key != 0) atomicAdd(&hist[bucket_of(key)], 1u);
+        });
+        __syncthreads();
+        const ScanOut s1 = cluster_scan(cluster, hist, kHist, need, true, wsum, res);
+        if (s1.total <= need) {   // at most t positive entries: keep them all
+            if (crank == 0 && tid == 0) {
+                tau_out[seg] = 0;
+                cut_out[seg] = 0xffffffffu;
+                if (hint) hint[seg] = 0;
+            }
+            if (marking) mark_all();
+            return;
+        }
+        need -= s1.before;
+        prefix = (K)s1.bin << TS;
+        shift = TS;
+        base_bucket = s1.bin;
+
+        // ---- pass 2: the bucket's entries into the candidate list
+        if (tid == 0) *ccount = 0;
+        __syncthreads();
+        for_each([&](K key, int e, bool in) {
+            const bool hit = in && key != 0 && (key >> shift) == (prefix >> shift);
+            // above the threshold's bucket: a survivor whatever the threshold
+            if (marking && in && (key >> shift) > (prefix >> shift)) mark_one(key, (uint32_t)(lo + e));
+            append(hit, key, e);
+        });
+        __syncthreads();
+        const unsigned ncand = *ccount;
+        __syncthreads();
+        if (C > 1) {
+            if (tid == 0) hist[0] = ncand > (unsigned)kCandCap ? 1u : 0u;
+            __syncthreads();
+            const ScanOut ov = cluster_scan(cluster, hist, 1, 1, false, wsum, res);
+            use_list = ov.total == 0;   // no CTA overflowed
+        } else {
+            use_list = ncand <= (unsigned)kCandCap;
+        }
+        nc = use_list ? (int)ncand : 0;
+    }
+
+    // ---- the remaining bits: radix rounds of up to 11 bits; the last
+    // round's bin holds exactly the entries equal to the threshold
+    unsigned long long eq = 0;
     while (shift > 0) {
         const int bits = shift >= 11 ? 11 : shift;
         const int sh = shift - bits;
         const unsigned mask = (1u << bits) - 1u;
+        // (key >> shift) == (prefix >> shift), for shift < KB
+        auto open = [&](K key) { return shift >= KB || (key >> shift) == (prefix >> shift); };
         for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
         __syncthreads();
         if (use_list) {
             for (int q = tid; q < nc; q += blockDim.x) {
                 const K key = ckey[q];
-                if ((key >> shift) == (prefix >> shift)) atomicAdd(&hist[(unsigned)(key >> sh) & mask], 1u);
+                if (open(key)) atomicAdd(&hist[(unsigned)(key >> sh) & mask], 1u);
             }
         } else {
             for (int e = tid; e < nloc; e += blockDim.x) {
                 const K key = key_at(e);
-                if (key != 0 && (key >> shift) == (prefix >> shift))
-                    atomicAdd(&hist[(unsigned)(key >> sh) & mask], 1u);
+                if (key != 0 && open(key)) atomicAdd(&hist[(unsigned)(key >> sh) & mask], 1u);
             }
         }
         __syncthreads();
@@ -366,24 +512,11 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
         need -= sr.before;
         prefix |= (K)sr.bin << sh;
         shift = sh;
+        eq = sr.count;
     }
     const K tau = prefix;
-    // how many entries equal tau (at least `need` of them)
-    for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
-    {
-        unsigned cnt = 0;
-        if (use_list) {
-            for (int q = tid; q < nc; q += blockDim.x) cnt += ckey[q] == tau;
-        } else {
-            for (int e = tid; e < nloc; e += blockDim.x) cnt += key_at(e) == tau;
-        }
-        if (cnt) atomicAdd(&hist[0], cnt);
-    }
-    __syncthreads();
-    const ScanOut se = cluster_scan(cluster, hist, 1, 1, false, wsum, res);
     uint32_t cut = 0xffffffffu;
-    if (need < se.total) {
+    if (need < eq) {
         // keep the `need` smallest indices among the ties: radix select on
         // the index, ascending, 11 bits at a time
         uint32_t ipre = 0;
@@ -414,6 +547,7 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
     if (crank == 0 && tid == 0) {
         tau_out[seg] = tau;
         cut_out[seg] = cut;
+        if (hint) hint[seg] = tau;
     }
     if (marking) {
         // the survivors inside the bucket: from the candidate list, or by a
@@ -421,24 +555,36 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
         const K bucket = prefix >> TS;   // the first histogram's bin
         if (use_list) {
             // The list's order depends on the order of the appends, so its
-            // survivors' squares are added exactly: all of the bucket's
-            // entries share one FP32 exponent, x = m 2^s with an integer
-            // m < 2^24, and sum(m^2) fits 64 bits (at most kCandCap terms).
-            unsigned long long isq = 0;
+            // survivors' squares are added exactly: an entry is x = m 2^s
+            // with an integer m < 2^24, the candidates' bins (one, or three
+            // after a warm start) span at most two exponents s0 and s0 + 1,
+            // and sum(m^2) per exponent fits 64 bits (at most kCandCap terms).
+            const int s0 = exponent_of((uint32_t)((K)base_bucket << TS));
+            unsigned long long isq0 = 0, isq1 = 0;
             for (int q = tid; q < nc; q += blockDim.x) {
                 if (keep_entry<T>(KeyBits<T>::value(ckey[q]), tau, cut, cidx[q])) {
                     atomicOr(mark.rowbits + (seg >> 5) + (size_t)cidx[q] * mark.words, mbit);
                     const unsigned long long m = mantissa24((uint32_t)ckey[q]);
-                    isq += m * m;
+                    if (exponent_of((uint32_t)ckey[q]) == s0) isq0 += m * m;
+                    else isq1 += m * m;
                 }
             }
-            for (int off = 16; off > 0; off >>= 1) isq += __shfl_xor_sync(0xffffffffu, isq, off);
-            if ((tid & 31) == 0) wisq[tid >> 5] = isq;
+            for (int off = 16; off > 0; off >>= 1) {
+                isq0 += __shfl_xor_sync(0xffffffffu, isq0, off);
+                isq1 += __shfl_xor_sync(0xffffffffu, isq1, off);
+            }
+            if ((tid & 31) == 0) {
+                wisq[tid >> 5] = isq0;
+                wisq1[tid >> 5] = isq1;
+            }
             __syncthreads();
             if (tid == 0) {
-                unsigned long long tot = 0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wisq[w];
-                bucket_sq = ldexp((double)tot, 2 * exponent_of((uint32_t)(bucket << TS)));
+                unsigned long long t0 = 0, t1 = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    t0 += wisq[w];
+                    t1 += wisq1[w];
+                }
+                bucket_sq = ldexp((double)t0, 2 * s0) + ldexp((double)t1, 2 * s0 + 2);
             }
         } else {
             for_each([&](K key, int e, bool in) {
@@ -451,22 +597,33 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
     }
 }
 
-template <typename T>
-cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
-                          int64_t t, int mode, void* tau, uint32_t* cut,
-                          cudaStream_t st, int sm_count, uint32_t* rowbits,
-                          double* diag_part)
+// CTAs per cluster: about two CTAs per SM over all segments, at most
+// kSelMaxCluster (larger clusters measured slower), at least 2048 entries per
+// CTA.  When it marks survivors (column mode) one CTA owns a column: its
+// rounds then need block barriers only, and it may start from a hint.
+static int sel_cluster(int64_t rows, int k, int mode, int sm_count, bool marking)
 {
-    if (rows == 0) return cudaSuccess;
+    if (marking && mode == TOPT_COLUMN) return 1;
     const int nseg = mode == TOPT_MATRIX ? 1 : k;
     const int64_t seg_len = mode == TOPT_MATRIX ? (int64_t)k * rows : rows;
-    // about two CTAs per SM over all segments, at most kSelMaxCluster per
-    // cluster (larger clusters measured slower), at least 2048 entries per CTA
     int C = (int)((2 * (int64_t)sm_count + nseg - 1) / nseg);
     if (C > kSelMaxCluster) C = kSelMaxCluster;
     const int64_t by_len = (seg_len + 2047) / 2048;
     if (C > by_len) C = (int)by_len;
     if (C < 1) C = 1;
+    return C;
+}
+
+template <typename T>
+cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
+                          int64_t t, int mode, void* tau, uint32_t* cut,
+                          cudaStream_t st, int sm_count, uint32_t* rowbits,
+                          double* diag_part, void* hint)
+{
+    if (rows == 0) return cudaSuccess;
+    const int nseg = mode == TOPT_MATRIX ? 1 : k;
+    const bool marking = rowbits != nullptr && mode == TOPT_COLUMN;
+    const int C = sel_cluster(rows, k, mode, sm_count, marking);
     const size_t smem = SelSmem<T>::data;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)C, (unsigned)nseg, 1);
@@ -482,27 +639,21 @@ cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
     cfg.numAttrs = 1;
     using K = typename KeyBits<T>::K;
     SelMark mark;
-    if (rowbits && mode == TOPT_COLUMN) {
+    if (marking) {
         mark.rowbits = rowbits;
         mark.words = (k + 31) / 32;
         mark.diag_part = diag_part;
+        mark.hint = hint;
     }
     return cudaLaunchKernelEx(&cfg, select_kernel<T>, Xt, ldx, rows, k, t, mode,
                               static_cast<K*>(tau), cut, mark);
 }
 
-// Cluster size launch_select uses for k columns of `rows` entries (the
-// number of diagonal partials per column it writes when marking).
+// Cluster size launch_select uses when marking for k columns of `rows`
+// entries (the number of diagonal partials per column it writes).
 int select_cluster(int64_t rows, int k, int mode, int sm_count)
 {
-    const int nseg = mode == TOPT_MATRIX ? 1 : k;
-    const int64_t seg_len = mode == TOPT_MATRIX ? (int64_t)k * rows : rows;
-    int C = (int)((2 * (int64_t)sm_count + nseg - 1) / nseg);
-    if (C > kSelMaxCluster) C = kSelMaxCluster;
-    const int64_t by_len = (seg_len + 2047) / 2048;
-    if (C > by_len) C = (int)by_len;
-    if (C < 1) C = 1;
-    return C;
+    return sel_cluster(rows, k, mode, sm_count, true);
 }
 
 // In-place projection + enforcement of a caller's dense rows x k buffer
@@ -553,8 +704,8 @@ cudaError_t setup_select()
                                 (int)kSelSmemMax);
 }
 
-template cudaError_t launch_select<float>(const float*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int, uint32_t*, double*);
-template cudaError_t launch_select<double>(const double*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int, uint32_t*, double*);
+template cudaError_t launch_select<float>(const float*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int, uint32_t*, double*, void*);
+template cudaError_t launch_select<double>(const double*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int, uint32_t*, double*, void*);
 template cudaError_t launch_apply_thresholds<float>(float*, int64_t, int, int64_t, int, const void*, const uint32_t*, unsigned*, cudaStream_t);
 template cudaError_t launch_apply_thresholds<double>(double*, int64_t, int, int64_t, int, const void*, const uint32_t*, unsigned*, cudaStream_t);
 

@@ -63,6 +63,44 @@ struct SpmmParams {
     T* partials; // npart x KP
 };
 
+// End of a slice: combines the lanes [head, end) of each row, four columns
+// at a time (a fixed tree; lane head ends with the row's sum), and writes
+// columns [c0, c0 + cw) of the row of Y, or of its partial row.
+template <int KP>
+__device__ __forceinline__ void sell_store_rows(const SpmmParams<float>& p, int64_t seg, int lane,
+                                                const float* my, int B, int c0, int cw)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int grp = p.seg_grp[seg];
+    const int head = grp >> 8, end = grp & 0xff;
+    const int maxg = __reduce_max_sync(FULL, (unsigned)(end - head));
+    const int row = p.seg_row[seg];
+    const int part = p.seg_part[seg];
+    float* out = (part < 0 ? p.Y + (int64_t)(row < 0 ? 0 : row) * KP
+                           : p.partials + (int64_t)part * KP) + c0;
+    float4* o4 = reinterpret_cast<float4*>(out);
+    const bool writer = row >= 0 && lane == head;
+#pragma unroll 1
+    for (int q = 0; 4 * q < cw; ++q) {
+        float v0 = my[(4 * q + 0) * B], v1 = my[(4 * q + 1) * B];
+        float v2 = my[(4 * q + 2) * B], v3 = my[(4 * q + 3) * B];
+        for (int off = 1; off < maxg; off <<= 1) {
+            const bool take = lane + off < end;
+            const float t0 = __shfl_down_sync(FULL, v0, off);
+            const float t1 = __shfl_down_sync(FULL, v1, off);
+            const float t2 = __shfl_down_sync(FULL, v2, off);
+            const float t3 = __shfl_down_sync(FULL, v3, off);
+            if (take) {
+                v0 += t0;
+                v1 += t1;
+                v2 += t2;
+                v3 += t3;
+            }
+        }
+        if (writer) o4[q] = make_float4(v0, v1, v2, v3);
+    }
+}
+
 // FP32.  NS warps share a slice: warp h of the NS owns the output columns
 // [h * CW, min(KP, (h + 1) * CW)), CW = KP / NS rounded up to 4, for all 32
 // segments of the slice.  Each of them streams the slice's entries (the NS
@@ -197,10 +235,10 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
                 for (int u = 0; u < 4; ++u) mw[u] = ii[u] >= 0 ? fmask[ii[u] >> 5] : 0u;
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    rc[u] = (ii[u] >= 0 && ((mw[u] >> (ii[u] & 31)) & 1u)) ? __ldg(rec + ii[u]) : zero4;
+                    rc[u] = (ii[u] >= 0 && ((mw[u] >> (ii[u] & 31)) & 1u)) ? __ldg(rec + 2 * ii[u]) : zero4;
             } else {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) rc[u] = ii[u] >= 0 ? __ldg(rec + ii[u]) : zero4;
+                for (int u = 0; u < 4; ++u) rc[u] = ii[u] >= 0 ? __ldg(rec + 2 * ii[u]) : zero4;
             }
             // this lane's pair slots (bit 3u + j: pair j of entry u) and its
             // longer rows (bit 12 + u)
@@ -238,36 +276,158 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
             a1 = a2;
         }
 
-        // combine the lanes [head, end) of each row, four columns at a time:
-        // fixed tree, lane head ends with the row's sum
-        const int grp = p.seg_grp[seg];
-        const int head = grp >> 8, end = grp & 0xff;
-        const int maxg = __reduce_max_sync(FULL, (unsigned)(end - head));
-        const int row = p.seg_row[seg];
-        const int part = p.seg_part[seg];
-        float* out = (part < 0 ? p.Y + (int64_t)(row < 0 ? 0 : row) * KP
-                               : p.partials + (int64_t)part * KP) + c0;
-        float4* o4 = reinterpret_cast<float4*>(out);
-        const bool writer = row >= 0 && lane == head;
+        sell_store_rows<KP>(p, seg, lane, my, B, c0, cw);
+    }
+}
+
+// FP32, one warp per slice (all columns), the shape the tuner picks on text
+// corpora.  The same products as spmm_sell_f32_kernel<KP, 1, MASK>, added
+// in the same order, with fewer instructions and fewer dependent loads per
+// entry.  A record's unused pair slots hold column 0 and value +0, so pair 0
+// of every entry is added without a branch (a zero row, a padding entry or
+// a heavy row adds +0 into slot 0, which leaves it unchanged: every product
+// is >= 0, so no slot is ever -0).  Pairs 1 and 2 of entry u are added only
+// when some lane of the warp has a light row with two or more nonzeros
+// there (a warp-uniform branch; one reduction per quad gives all of them).
+// Pairs 3 to 5 come from the record's second half, which shares the first
+// half's 32-byte sector (an L1 hit), not from the row-packed pairs in the
+// L2; only rows of more than six nonzeros read those, and heavy rows their
+// dense copy.  The four entries of a quad are held in plain registers and a
+// slot's address is one multiply-add from its column.
+template <int KP, int MASK>
+__global__ void __launch_bounds__(256, 4)
+spmm_sell1_f32_kernel(SpmmParams<float> p)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int B = blockDim.x;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    float* slots = reinterpret_cast<float*>(smem_raw);                   // KP x B
+    const uint32_t* __restrict__ fmask = p.fmask;
+    if constexpr (MASK == 2) {
+        uint32_t* sm = reinterpret_cast<uint32_t*>(slots + (size_t)KP * B);
+        for (int w = tid; w < p.mask_words; w += B) sm[w] = __ldg(p.fmask + w);
+        __syncthreads();
+        fmask = sm;
+    }
+    float* my = slots + tid;
+    const unsigned bstride = (unsigned)B * 4u;                // bytes between a thread's slots
+    const uint32_t mybase = (uint32_t)__cvta_generic_to_shared(my);
+    const uint4* __restrict__ rec = p.frec;
+    const float4* __restrict__ dense4 = reinterpret_cast<const float4*>(p.fdense);
+    const int dld4 = p.dld / 4;
+    const int heavy = p.heavy;
+    const int fld = p.fld;
+
+    // slot[col] += a * v (an explicit fused multiply-add, as in every shape)
+    auto fma_slot = [&](unsigned col, float a, float v) {
+        const uint32_t ad = mybase + col * bstride;
+        float s;
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(s) : "r"(ad));
+        s = __fmaf_rn(a, v, s);
+        asm volatile("st.shared.f32 [%0], %1;" :: "r"(ad), "f"(s) : "memory");
+    };
+    // pairs 3.. of row i (cnt of them in all): 3 to 5 from the record's
+    // second half, the rest from the row-packed pairs; a heavy row from its
+    // dense copy
+    auto pairs_beyond = [&](int i, float a, int cnt) {
+        if (cnt >= heavy) {
+            const float4* d = dense4 + (int64_t)i * dld4;
 #pragma unroll 1
-        for (int q = 0; 4 * q < cw; ++q) {
-            float v0 = my[(4 * q + 0) * B], v1 = my[(4 * q + 1) * B];
-            float v2 = my[(4 * q + 2) * B], v3 = my[(4 * q + 3) * B];
-            for (int off = 1; off < maxg; off <<= 1) {
-                const bool take = lane + off < end;
-                const float t0 = __shfl_down_sync(FULL, v0, off);
-                const float t1 = __shfl_down_sync(FULL, v1, off);
-                const float t2 = __shfl_down_sync(FULL, v2, off);
-                const float t3 = __shfl_down_sync(FULL, v3, off);
-                if (take) {
-                    v0 += t0;
-                    v1 += t1;
-                    v2 += t2;
-                    v3 += t3;
-                }
+            for (int q = 0; 4 * q < KP; ++q) {
+                const float4 v = __ldg(d + q);
+                my[(4 * q + 0) * B] = __fmaf_rn(a, v.x, my[(4 * q + 0) * B]);
+                my[(4 * q + 1) * B] = __fmaf_rn(a, v.y, my[(4 * q + 1) * B]);
+                my[(4 * q + 2) * B] = __fmaf_rn(a, v.z, my[(4 * q + 2) * B]);
+                my[(4 * q + 3) * B] = __fmaf_rn(a, v.w, my[(4 * q + 3) * B]);
             }
-            if (writer) o4[q] = make_float4(v0, v1, v2, v3);
+            return;
         }
+        const uint4 h = __ldg(rec + 2 * i + 1);
+        fma_slot(__byte_perm(h.x, 0u, 0x4440), a, __uint_as_float(h.y));
+        if (cnt > 4) fma_slot(__byte_perm(h.x, 0u, 0x4441), a, __uint_as_float(h.z));
+        if (cnt > 5) fma_slot(__byte_perm(h.x, 0u, 0x4442), a, __uint_as_float(h.w));
+        if (cnt > 6) {
+            const int32_t* cr = p.fcol + (int64_t)i * fld;
+            const float* vr = p.fval + (int64_t)i * fld;
+#pragma unroll 1
+            for (int q = 6; q < cnt; ++q) fma_slot((unsigned)__ldg(cr + q), a, __ldg(vr + q));
+        }
+    };
+    // the first half of row i's record (zero for a padding entry or, with
+    // the bitmask, a zero row)
+    auto load_rec = [&](int i) -> uint4 {
+        bool live = i >= 0;
+        if constexpr (MASK > 0) live = live && ((fmask[i >> 5] >> (i & 31)) & 1u);
+        return live ? __ldg(rec + 2 * i) : make_uint4(0u, 0u, 0u, 0u);
+    };
+    // pair 0 of an entry, then (warp-uniform) its pairs 1 and 2
+    auto light_pairs = [&](const uint4& r, float a, bool more) {
+        const bool lt = record_cnt(r.x) < heavy;
+        fma_slot(__byte_perm(r.x, 0u, 0x4441), a, lt ? __uint_as_float(r.y) : 0.f);
+        if (more) {
+            fma_slot(__byte_perm(r.x, 0u, 0x4442), a, lt ? __uint_as_float(r.z) : 0.f);
+            fma_slot(__byte_perm(r.x, 0u, 0x4443), a, lt ? __uint_as_float(r.w) : 0.f);
+        }
+    };
+
+    const int64_t stride = (int64_t)gridDim.x * (B >> 5);
+    for (int64_t s = (int64_t)blockIdx.x * (B >> 5) + warp; s < p.nslices; s += stride) {
+        const int64_t seg = s * 32 + lane;
+#pragma unroll 4
+        for (int c = 0; c < KP; ++c) my[c * B] = 0.f;
+        const int len = p.slice_len[s];   // a multiple of 4
+        const int nq = len >> 2;
+        const int64_t base = p.slice_ptr[s] + lane * 4;
+        const int4* __restrict__ idx4 = reinterpret_cast<const int4*>(p.idx + base);
+        const float4* __restrict__ val4 = reinterpret_cast<const float4*>(p.val + base);
+        if (lane == 0 && len > 0) {
+            const unsigned bytes = (unsigned)len * 128u;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                         :: "l"(p.idx + p.slice_ptr[s]), "r"(bytes) : "memory");
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                         :: "l"(p.val + p.slice_ptr[s]), "r"(bytes) : "memory");
+        }
+        const int4 none_i = make_int4(-1, -1, -1, -1);
+        const float4 none_a = make_float4(0.f, 0.f, 0.f, 0.f);
+        int4 i0 = nq > 0 ? __ldcs(idx4) : none_i;
+        float4 a0 = nq > 0 ? __ldcs(val4) : none_a;
+        int4 i1 = nq > 1 ? __ldcs(idx4 + 32) : none_i;
+        float4 a1 = nq > 1 ? __ldcs(val4 + 32) : none_a;
+#pragma unroll 1
+        for (int q = 0; q < nq; ++q) {
+            int4 i2 = none_i;
+            float4 a2 = none_a;
+            if (q + 2 < nq) {
+                i2 = __ldcs(idx4 + (int64_t)(q + 2) * 32);
+                a2 = __ldcs(val4 + (int64_t)(q + 2) * 32);
+            }
+            const uint4 r0 = load_rec(i0.x), r1 = load_rec(i0.y);
+            const uint4 r2 = load_rec(i0.z), r3 = load_rec(i0.w);
+            // byte u of `need`: the OR over the warp of entry u's count, so
+            // >= 2 iff some lane's row has two or more nonzeros there and
+            // >= 4 iff some lane's has more than three (heavy rows included:
+            // their pairs 1 and 2 add +0)
+            const unsigned need = __reduce_or_sync(
+                FULL, __byte_perm(__byte_perm(r0.x, r1.x, 0x0040), __byte_perm(r2.x, r3.x, 0x0040), 0x5410));
+            light_pairs(r0, a0.x, (need & 0xffu) >= 2u);
+            light_pairs(r1, a0.y, ((need >> 8) & 0xffu) >= 2u);
+            light_pairs(r2, a0.z, ((need >> 16) & 0xffu) >= 2u);
+            light_pairs(r3, a0.w, (need >> 24) >= 2u);
+            if ((need & 0xfcfcfcfcu) != 0u) {
+                if (record_cnt(r0.x) > 3) pairs_beyond(i0.x, a0.x, record_cnt(r0.x));
+                if (record_cnt(r1.x) > 3) pairs_beyond(i0.y, a0.y, record_cnt(r1.x));
+                if (record_cnt(r2.x) > 3) pairs_beyond(i0.z, a0.z, record_cnt(r2.x));
+                if (record_cnt(r3.x) > 3) pairs_beyond(i0.w, a0.w, record_cnt(r3.x));
+            }
+            i0 = i1;
+            a0 = a1;
+            i1 = i2;
+            a1 = a2;
+        }
+        sell_store_rows<KP>(p, seg, lane, my, B, 0, KP);
     }
 }
 
@@ -553,7 +713,15 @@ __global__ void spmm_combine_kernel(int64_t nsplit, const int32_t* split_row,
     for (int c = lane; c < KP; c += 32) {
         T s0 = T(0);
         const T* pp = partials + (int64_t)first * KP + c;
-        for (int q = 0; q < count; ++q) s0 += pp[(int64_t)q * KP];
+        // eight partials loaded before they are added, in order
+        for (int q0 = 0; q0 < count; q0 += 8) {
+            T b[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) b[u] = q0 + u < count ? pp[(int64_t)(q0 + u) * KP] : T(0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (q0 + u < count) s0 += b[u];
+        }
         Y[(int64_t)row * KP + c] = s0;
     }
 }
@@ -609,7 +777,8 @@ static cudaError_t launch_f32_split(const SpmmParams<float>& p, int64_t nslices,
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    return cudaLaunchKernelEx(&cfg, spmm_sell_f32_kernel<KP, NS, MASK>, p);
+    if constexpr (NS == 1) return cudaLaunchKernelEx(&cfg, spmm_sell1_f32_kernel<KP, MASK>, p);
+    else return cudaLaunchKernelEx(&cfg, spmm_sell_f32_kernel<KP, NS, MASK>, p);
 }
 
 template <int KP, int MASK>
@@ -739,17 +908,23 @@ cudaError_t launch_spmm_h(const SellDev& S, const EllDev& F, float* Y, int sm_co
     }
 }
 
+template <typename K>
+static cudaError_t setup_sell_kernel(K kern, int B, int smem, int& per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, B, (size_t)smem);
+}
+
 template <int KP, int NS, int MASK>
 static cudaError_t setup_sell_one()
 {
-    cudaError_t e = cudaFuncSetAttribute(spmm_sell_f32_kernel<KP, NS, MASK>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
-    if (e != cudaSuccess) return e;
     int B = 0;
     const int smem = sell_block<KP, NS>(B);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, spmm_sell_f32_kernel<KP, NS, MASK>, B, (size_t)smem);
+    cudaError_t e;
+    if constexpr (NS == 1) e = setup_sell_kernel(spmm_sell1_f32_kernel<KP, MASK>, B, smem, per_sm);
+    else e = setup_sell_kernel(spmm_sell_f32_kernel<KP, NS, MASK>, B, smem, per_sm);
     g_sell_per_sm[KP][NS][MASK] = per_sm;
     return e;
 }

@@ -89,6 +89,32 @@ def test_step_parity_planted_scaled(compute):
     assert abs(E.espnmf_residual(ctx) - oracle.residual(U2, Ug)) < 1e-9
 
 
+def test_selector_threshold_hint_miss_falls_back():
+    """The FP32 selector starts each column's search from the threshold that
+    column had in the previous sweep.  Scaling U by 2^10 moves every
+    threshold ten binades away from its hint: the search must fall back to
+    the full radix selection, and the steps (the fallback one, then a warm
+    one) still match the oracle."""
+    A = planted_50k_100k(seed=2, scale=0.05)
+    U0 = uniform_init(A.n, 50, 2)
+    ctx = make_ctx(A, 50, 120, 150, U0, E.TOPT_COLUMN, E.F32)
+    E.espnmf_iterate(ctx, 3)
+    Ucur = E.espnmf_get_factor(ctx, E.U).astype(np.float32) * np.float32(1024.0)
+    E.espnmf_set_factor(ctx, E.U, Ucur)
+    Ucur = Ucur.astype(np.float64)
+    Ao, _ = as_used(A, U0, E.F32)
+    for step in range(2):
+        E.espnmf_als_update_V(ctx)
+        Vg = E.espnmf_get_factor(ctx, E.V)
+        Vo, Vpre = oracle.update_V(Ao, Ucur, 150, oracle.COLUMN, return_pre=True)
+        compare_factor(Vg, Vo, Vpre, 150, E.TOPT_COLUMN, 2e-5, f"hint miss V{step}")
+        E.espnmf_als_update_U(ctx)
+        Ug = E.espnmf_get_factor(ctx, E.U)
+        Uo, Upre = oracle.update_U(Ao, Vg, 120, oracle.COLUMN, return_pre=True)
+        compare_factor(Ug, Uo, Upre, 120, E.TOPT_COLUMN, 2e-5, f"hint miss U{step}")
+        Ucur = Ug
+
+
 @pytest.mark.parametrize("compute", [E.F64, E.F32])
 @pytest.mark.parametrize("k", [1, 3, 33, 64, 72])
 def test_step_parity_factor_widths(compute, k):
@@ -314,14 +340,18 @@ def test_sweep_measures_on_gpu_iterates():
 
 def test_spmm_launch_shapes_give_identical_results():
     """Every FP32 sparse-product shape (1, 2 or 4 warps per slice, any
-    shared-memory carveout, or the tuner's choice) adds the same products in
-    the same order: the sweeps agree bitwise."""
+    shared-memory carveout, any way of skipping zero factor rows, or the
+    tuner's choice) adds the same products in the same order: the sweeps
+    agree bitwise."""
     A = planted_50k_100k(seed=2, scale=0.05)
     U0 = uniform_init(A.n, 50, 2)
     runs = []
     for opts in [{}, {E.OPT_SPMM_SPLIT: 1}, {E.OPT_SPMM_SPLIT: 2}, {E.OPT_SPMM_SPLIT: 4},
                  {E.OPT_SPMM_SPLIT: 2, E.OPT_SPMM_CARVEOUT: 25},
-                 {E.OPT_SPMM_SPLIT: 4, E.OPT_SPMM_CARVEOUT: 100}]:
+                 {E.OPT_SPMM_SPLIT: 4, E.OPT_SPMM_CARVEOUT: 100},
+                 {E.OPT_SPMM_SPLIT: 1, E.OPT_SPMM_MASK: 0},
+                 {E.OPT_SPMM_SPLIT: 1, E.OPT_SPMM_MASK: 2},
+                 {E.OPT_SPMM_SPLIT: 2, E.OPT_SPMM_MASK: 2}]:
         ctx = make_ctx(A, 50, 120, 150, U0, E.TOPT_COLUMN, E.F32)
         for o, v in opts.items():
             E.espnmf_set_option(ctx, o, v)
