@@ -280,9 +280,10 @@ solve_chol_kernel(const float* __restrict__ Y, int64_t ldy, int64_t rows, int k,
     if (bad) atomicOr(status, ST_NONFINITE);
 }
 
-// rows per thread of solve_chol_kernel: two while both rows fit the
-// registers without spilling
-constexpr int solve_rows_per_thread(int KP) { return KP <= 56 ? 1 : 1; }
+// rows per thread of solve_chol_kernel.  Two rows per thread halve the
+// shared-memory reads per FMA but need ~230 registers at k = 50 (8 warps per
+// SM): measured slower on the 50k x 100k workload, so one.
+constexpr int solve_rows_per_thread(int) { return 1; }
 
 template <int KP>
 static cudaError_t launch_solve_chol_kp(const float* Y, int64_t ldy, int64_t rows, int k,

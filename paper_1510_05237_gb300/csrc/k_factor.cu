@@ -597,6 +597,7 @@ emit_s_kernel(EmitSArgs a)
     __shared__ int wcount[kEmitSThreads / 32];
     __shared__ int list[kEmitSThreads];
     __shared__ int ccnt[kEmitSThreads / 32];
+    __shared__ int lcnt[kEmitSThreads];               // this round's row counts
     __shared__ int clist[kEmitSThreads];              // this round's many-survivor rows
     __shared__ uint32_t cbits[kEmitSThreads][WD];     // their survivor bits
     __shared__ DFloat red[kEmitSThreads / 32][4];
@@ -697,6 +698,7 @@ emit_s_kernel(EmitSArgs a)
                 }
             }
             a.cnt[r] = pos;
+            lcnt[tid] = pos;
             if (a.rec) {
                 a.rec[2 * r] = make_uint4(rx | (unsigned)pos, rv0, rv1, rv2);
                 a.rec[2 * r + 1] = make_uint4(rx1, rv3, rv4, rv5);
@@ -810,6 +812,7 @@ emit_s_kernel(EmitSArgs a)
                 for (int c = 32 * WD + lane; c < a.dld; c += 32) dr[c] = 0.f;
             if (lane == 0) {
                 a.cnt[rr] = nb;
+                lcnt[clist[j]] = nb;
                 if (a.rec) {
                     a.rec[2 * rr] = make_uint4(rx, rv[0], rv[1], rv[2]);
                     a.rec[2 * rr + 1] = make_uint4(rx1, rv[3], rv[4], rv[5]);
@@ -839,7 +842,7 @@ emit_s_kernel(EmitSArgs a)
             for (int i = 0; i < tot; ++i) {
                 const int lr = list[i];
                 const int64_t rr = row_of(rnd, lr);
-                const int L = a.cnt[rr];
+                const int L = lcnt[lr];
                 if (L <= kEmitSStage) {
                     const int2* sp = stage + lr * kEmitSStage;
                     for (int ia = 0; ia + 1 < L; ++ia) {

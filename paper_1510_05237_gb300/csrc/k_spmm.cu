@@ -451,8 +451,7 @@ struct FreqParams {
     const int32_t* hwarp;
     int nchunks;
     int* counter;
-    const float* htab;     // [h][KP]
-    const uint8_t* hnz;    // [h]
+    const float* htab;     // [h][KP] (a zero row of the factor is zeros)
     int h;
     float* Y;              // rows x KP: holds the SELL part, receives the sum
     unsigned* status;
@@ -505,17 +504,17 @@ spmm_freq_f32_kernel(FreqParams p)
     using S = FreqShape<KP>;
     constexpr int Q = S::Q, LPG = S::LPG, G = S::G;
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr uint32_t ROW = KP * 4;   // bytes per table row
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ __align__(16) int2 wstage[kHThreads];
-    float* tab = reinterpret_cast<float*>(smem_raw);                       // [h][KP]
-    uint8_t* nz = smem_raw + (size_t)p.h * KP * 4;                          // [h]
+    float* tab = reinterpret_cast<float*>(smem_raw);   // [h + 1][KP], row h zero
     const int tid = threadIdx.x;
     const uint32_t bar = smem_addr(&mbar);
-    const uint32_t bytes = (uint32_t)p.h * KP * 4u;   // a multiple of 16
+    const uint32_t bytes = (uint32_t)p.h * ROW;   // a multiple of 16
 
     // stage the dense table: TMA bulk copies (32 KB each) completing on one
-    // mbarrier; the nonzero flags by plain loads meanwhile
+    // mbarrier; the zero row after it by plain stores meanwhile
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(1u) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -532,7 +531,7 @@ spmm_freq_f32_kernel(FreqParams p)
                    "r"(n), "r"(bar) : "memory");
         }
     }
-    for (int i = tid; i < p.h; i += blockDim.x) nz[i] = p.hnz[i];
+    for (int c = tid; c < KP; c += blockDim.x) tab[(size_t)p.h * KP + c] = 0.f;
     __syncthreads();
     if (!mbar_wait_phase0(bar, p.wait_limit)) {
         // the copy did not land: report, give it one more bounded wait so
@@ -545,11 +544,14 @@ spmm_freq_f32_kernel(FreqParams p)
     const int lane = tid & 31;
     const int grp = lane / LPG, ql = lane % LPG;
     const bool colact = ql < Q;
-    // A chunk of up to 32 of a row's entries is staged per warp as (slot,
-    // value) pairs, slot -1 for a zero table row; group g takes the entry
-    // pairs (2j, 2j + 1) for j = g, g + G, ... (one 128-bit shared load per
-    // pair) and adds them with packed two-lane FMAs (each lane rounds as
-    // fmaf does) into two accumulators.
+    const uint32_t zero_off = (uint32_t)p.h * ROW;
+    const uint32_t lane_base = smem_addr(tab) + 16u * (uint32_t)ql;
+    // A chunk of up to 32 of a row's entries is staged per warp as (byte
+    // offset of the table row, value); the chunk is padded to a multiple of
+    // four with entries on the zero row.  Group g takes the entry pairs
+    // (2j, 2j + 1) for j = g, g + G, ... (one 128-bit shared load per pair)
+    // and adds them with packed two-lane FMAs (each lane rounds as fmaf
+    // does) into two accumulators.  A zero table row adds +0.
     int2* stage = wstage + (tid >> 5) * 32;
     // The warps take chunks of rows in turn (a CTA that starts late, e.g.
     // on an SM shared with another kernel, does not hold the others up);
@@ -587,34 +589,30 @@ spmm_freq_f32_kernel(FreqParams p)
             unsigned long long a0xy = 0ull, a0zw = 0ull, a1xy = 0ull, a1zw = 0ull;
             for (int64_t qb = q0; qb < q1; qb += 32) {
                 const int64_t e = qb + lane;
-                int sl = -1;
+                uint32_t off = zero_off;
                 float a = 0.f;
                 if (e < q1) {
-                    sl = p.hidx[e];
+                    off = (uint32_t)p.hidx[e] * ROW;
                     a = p.hval[e];
-                    if (nz[sl] == 0) sl = -1;
                 }
-                stage[lane] = make_int2(sl, __float_as_int(a));
+                stage[lane] = make_int2((int)off, __float_as_int(a));
                 __syncwarp();
                 const int n = q1 - qb < 32 ? (int)(q1 - qb) : 32;
-                for (int j = 2 * grp; j < n; j += 2 * G) {
+                const int n4 = (n + 3) & ~3;
+                for (int j = 2 * grp; j < n4; j += 2 * G) {
                     const int4 ee = *reinterpret_cast<const int4*>(stage + j);   // entries j, j + 1
-                    const int s1 = j + 1 < n ? ee.z : -1;
                     if (colact) {
-                        if (ee.x >= 0) {
-                            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(
-                                tab + (size_t)ee.x * KP + 4 * ql);
-                            const unsigned long long a2 = pack2(__int_as_float(ee.y));
-                            fma2(a0xy, a2, v.x);
-                            fma2(a0zw, a2, v.y);
-                        }
-                        if (s1 >= 0) {
-                            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(
-                                tab + (size_t)s1 * KP + 4 * ql);
-                            const unsigned long long a2 = pack2(__int_as_float(ee.w));
-                            fma2(a1xy, a2, v.x);
-                            fma2(a1zw, a2, v.y);
-                        }
+                        unsigned long long v0x, v0y, v1x, v1y;
+                        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
+                                     : "=l"(v0x), "=l"(v0y) : "r"(lane_base + (uint32_t)ee.x));
+                        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
+                                     : "=l"(v1x), "=l"(v1y) : "r"(lane_base + (uint32_t)ee.z));
+                        const unsigned long long a0 = pack2(__int_as_float(ee.y));
+                        const unsigned long long a1 = pack2(__int_as_float(ee.w));
+                        fma2(a0xy, a0, v0x);
+                        fma2(a0zw, a0, v0y);
+                        fma2(a1xy, a1, v1x);
+                        fma2(a1zw, a1, v1y);
                     }
                 }
                 __syncwarp();
@@ -870,7 +868,7 @@ cudaError_t launch_spmm_combine(const SellDev& S, int KP, T* Y, int64_t ldy,
 template <int KP>
 static cudaError_t launch_freq(const FreqParams& p, int grid, cudaStream_t st)
 {
-    const size_t smem = (size_t)p.h * KP * 4 + (size_t)p.h;
+    const size_t smem = (size_t)(p.h + 1) * KP * 4;   // the table and a zero row
     spmm_freq_f32_kernel<KP><<<grid, kHThreads, smem, st>>>(p);
     return cudaGetLastError();
 }
@@ -879,7 +877,7 @@ cudaError_t launch_spmm_h(const SellDev& S, const EllDev& F, float* Y, int sm_co
                           unsigned* status, long long wait_limit, cudaStream_t st)
 {
     if (S.h <= 0 || S.hnnz == 0) return cudaSuccess;
-    if (F.htab == nullptr || F.hnz == nullptr || F.h != S.h) return cudaErrorInvalidValue;
+    if (F.htab == nullptr || F.h != S.h) return cudaErrorInvalidValue;
     FreqParams p;
     p.hptr = S.hptr;
     p.hidx = S.hidx;
@@ -888,7 +886,6 @@ cudaError_t launch_spmm_h(const SellDev& S, const EllDev& F, float* Y, int sm_co
     p.nchunks = S.hwarps;
     p.counter = S.hcounter;
     p.htab = static_cast<const float*>(F.htab);
-    p.hnz = F.hnz;
     p.h = S.h;
     p.Y = Y;
     p.status = status;
