@@ -290,6 +290,17 @@ espnmf_status espnmf_set_option(espnmf_ctx *ctx, espnmf_option opt,
 espnmf_status espnmf_spmm_config(espnmf_ctx *ctx, int32_t product, int32_t *split,
                                  int32_t *carveout, int32_t *mask);
 
+/* espnmf_select_stats -- how the column selections of this context's
+ * enforcement steps (FP32 form, column mode) found their thresholds since
+ * espnmf_init: warm = columns whose search started from the previous
+ * threshold of that column and found the new one in the three histogram
+ * bins around it (one pass over the column); full = columns searched from
+ * scratch (first sweeps, a threshold that moved by more than about an
+ * eighth of a binade, or a crowded window).  Both 0 for FP64 contexts.
+ * Synchronises the context's stream.  The paper has no counterpart: this
+ * reports on how the rule after Alg. 2 is evaluated, not on what it keeps. */
+espnmf_status espnmf_select_stats(espnmf_ctx *ctx, int64_t *warm, int64_t *full);
+
 /* espnmf_spmm_frequent -- the frequent part of a sparse product (product 0:
  * A V, 1: A^T U; FP32 contexts only): h = number of gathered factor rows
  * staged densely in shared memory (0: the product has no frequent part)

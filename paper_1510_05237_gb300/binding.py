@@ -95,6 +95,7 @@ def load():
             "espnmf_batch_iterate": [P, i32, P, P, P],
             "espnmf_spmm_config": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
             "espnmf_spmm_frequent": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)],
+            "espnmf_select_stats": [P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -120,7 +121,7 @@ def exported_symbols():
              "espnmf_enforce_topt_buffer_noalloc", "espnmf_loss", "espnmf_grad",
              "espnmf_pg_step", "espnmf_batch_init", "espnmf_batch_destroy",
              "espnmf_batch_ctx", "espnmf_batch_set_option", "espnmf_batch_iterate",
-             "espnmf_spmm_config", "espnmf_spmm_frequent"]
+             "espnmf_spmm_config", "espnmf_spmm_frequent", "espnmf_select_stats"]
     return {n: hasattr(lib, n) for n in names}
 
 
@@ -325,6 +326,14 @@ def espnmf_spmm_config(ctx: Context, product: int):
     _check(load().espnmf_spmm_config(ctx.handle, int(product), ctypes.byref(g), ctypes.byref(c),
                                      ctypes.byref(m)), ctx.handle)
     return g.value, c.value, m.value
+
+
+def espnmf_select_stats(ctx: Context):
+    """(warm, full): column selections that started from the previous
+    threshold and found the new one near it, and those searched from scratch."""
+    w, f = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().espnmf_select_stats(ctx.handle, ctypes.byref(w), ctypes.byref(f)), ctx.handle)
+    return w.value, f.value
 
 
 def espnmf_spmm_frequent(ctx: Context, product: int):

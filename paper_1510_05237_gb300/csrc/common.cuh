@@ -245,12 +245,14 @@ cudaError_t launch_solve(const T* Y, int64_t ldy, int64_t rows, int k,
 // diag_part[c * select_cluster(...) + r], r < select_cluster(...).  With a
 // hint (marking only: k keys, 0 = none), each column starts its search from
 // the hint's threshold and stores its new threshold there; the result does
-// not depend on the hint.
+// not depend on the hint.  With counts, each column adds 1 to counts[0]
+// when the hint's window held its threshold, else to counts[1].
 template <typename T>
 cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
                           int64_t t, int mode, void* tau, uint32_t* cut,
                           cudaStream_t st, int sm_count, uint32_t* rowbits,
-                          double* diag_part, void* hint = nullptr);
+                          double* diag_part, void* hint = nullptr,
+                          unsigned long long* counts = nullptr);
 int select_cluster(int64_t rows, int k, int mode, int sm_count);
 
 // Projects and enforces a caller's dense rows x k buffer in place.

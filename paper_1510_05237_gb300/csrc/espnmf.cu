@@ -118,6 +118,7 @@ struct espnmf_ctx {
     // ceil(k/32) words per row of the larger factor, kept zero between
     // updates) and writes the Gram diagonal (diag_part, k x cluster size)
     uint32_t* rowbits = nullptr;
+    unsigned long long* sel_counts = nullptr;   // FP32: column selections [warm, full search]
     double* diag_part = nullptr;
 
     bool have_R = false;
@@ -688,7 +689,8 @@ espnmf_status do_select(espnmf_ctx* ctx, int64_t rows, int64_t t, bool mark, voi
                                                   t, ctx->mode, ctx->tau, ctx->cut, ctx->st,
                                                   ctx->sm_count, mark ? ctx->rowbits : nullptr,
                                                   mark ? ctx->diag_part : nullptr,
-                                                  mark ? hint : nullptr);
+                                                  mark ? hint : nullptr,
+                                                  mark ? ctx->sel_counts : nullptr);
     });
 }
 
@@ -1193,6 +1195,8 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             const size_t words = (size_t)rmax * ((k + 31) / 32);
             TRY(dmalloc(ctx, &ctx->rowbits, 4 * words));
             CU(cudaMemsetAsync(ctx->rowbits, 0, 4 * words, ctx->st));
+            TRY(dmalloc(ctx, &ctx->sel_counts, 2 * sizeof(unsigned long long)));
+            CU(cudaMemsetAsync(ctx->sel_counts, 0, 2 * sizeof(unsigned long long), ctx->st));
             TRY(dmalloc(ctx, &ctx->diag_part, sizeof(double) * k * 8));
         }
         TRY(dmalloc(ctx, &ctx->scal_part, sizeof(double) * ctx->fin_blocks * 4));
@@ -1666,6 +1670,21 @@ espnmf_status espnmf_spmm_frequent(espnmf_ctx* ctx, int32_t product, int32_t* h,
     const SellDev& S = product == 0 ? ctx->sA : ctx->sAt;
     *h = S.h;
     *hnnz = S.hnnz;
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_select_stats(espnmf_ctx* ctx, int64_t* warm, int64_t* full)
+{
+    TRY(enter(ctx));
+    if (!warm || !full) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "outputs must be non-NULL");
+    *warm = 0;
+    *full = 0;
+    if (!ctx->sel_counts) return ESPNMF_OK;
+    unsigned long long h[2] = {0, 0};
+    CU(cudaMemcpyAsync(h, ctx->sel_counts, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    *warm = (int64_t)h[0];
+    *full = (int64_t)h[1];
     return ESPNMF_OK;
 }
 

@@ -164,6 +164,7 @@ struct SelMark {
     int words = 0;
     double* diag_part = nullptr;
     void* hint = nullptr;   // [k] keys: the last threshold of each column (0: none)
+    unsigned long long* counts = nullptr;   // [2]: warm starts that held, full searches
 };
 
 template <typename T>
@@ -439,6 +440,8 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
         }
     }
 
+    if (hint != nullptr && mark.counts != nullptr && tid == 0 && crank == 0)
+        atomicAdd(mark.counts + (warm ? 0 : 1), 1ull);
     if (!warm) {
         // ---- pass 1: histogram of the top 11 bits of the positive entries
         for (int b = tid; b < kHist; b += blockDim.x) hist[b] = 0;
@@ -618,7 +621,7 @@ template <typename T>
 cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
                           int64_t t, int mode, void* tau, uint32_t* cut,
                           cudaStream_t st, int sm_count, uint32_t* rowbits,
-                          double* diag_part, void* hint)
+                          double* diag_part, void* hint, unsigned long long* counts)
 {
     if (rows == 0) return cudaSuccess;
     const int nseg = mode == TOPT_MATRIX ? 1 : k;
@@ -644,6 +647,7 @@ cudaError_t launch_select(const T* Xt, int64_t ldx, int64_t rows, int k,
         mark.words = (k + 31) / 32;
         mark.diag_part = diag_part;
         mark.hint = hint;
+        mark.counts = counts;
     }
     return cudaLaunchKernelEx(&cfg, select_kernel<T>, Xt, ldx, rows, k, t, mode,
                               static_cast<K*>(tau), cut, mark);
@@ -704,8 +708,8 @@ cudaError_t setup_select()
                                 (int)kSelSmemMax);
 }
 
-template cudaError_t launch_select<float>(const float*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int, uint32_t*, double*, void*);
-template cudaError_t launch_select<double>(const double*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int, uint32_t*, double*, void*);
+template cudaError_t launch_select<float>(const float*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int, uint32_t*, double*, void*, unsigned long long*);
+template cudaError_t launch_select<double>(const double*, int64_t, int64_t, int, int64_t, int, void*, uint32_t*, cudaStream_t, int, uint32_t*, double*, void*, unsigned long long*);
 template cudaError_t launch_apply_thresholds<float>(float*, int64_t, int, int64_t, int, const void*, const uint32_t*, unsigned*, cudaStream_t);
 template cudaError_t launch_apply_thresholds<double>(double*, int64_t, int, int64_t, int, const void*, const uint32_t*, unsigned*, cudaStream_t);
 

@@ -99,12 +99,17 @@ def test_selector_threshold_hint_miss_falls_back():
     U0 = uniform_init(A.n, 50, 2)
     ctx = make_ctx(A, 50, 120, 150, U0, E.TOPT_COLUMN, E.F32)
     E.espnmf_iterate(ctx, 3)
+    w0, f0 = E.espnmf_select_stats(ctx)
+    assert w0 + f0 >= 3 * 2 * 50 and f0 >= 2 * 50   # the first sweep has no hints
     Ucur = E.espnmf_get_factor(ctx, E.U).astype(np.float32) * np.float32(1024.0)
     E.espnmf_set_factor(ctx, E.U, Ucur)
     Ucur = Ucur.astype(np.float64)
     Ao, _ = as_used(A, U0, E.F32)
     for step in range(2):
         E.espnmf_als_update_V(ctx)
+        if step == 0:
+            w1, f1 = E.espnmf_select_stats(ctx)
+            assert (w1, f1) == (w0, f0 + 50)   # every V column missed its hint
         Vg = E.espnmf_get_factor(ctx, E.V)
         Vo, Vpre = oracle.update_V(Ao, Ucur, 150, oracle.COLUMN, return_pre=True)
         compare_factor(Vg, Vo, Vpre, 150, E.TOPT_COLUMN, 2e-5, f"hint miss V{step}")
@@ -113,6 +118,8 @@ def test_selector_threshold_hint_miss_falls_back():
         Uo, Upre = oracle.update_U(Ao, Vg, 120, oracle.COLUMN, return_pre=True)
         compare_factor(Ug, Uo, Upre, 120, E.TOPT_COLUMN, 2e-5, f"hint miss U{step}")
         Ucur = Ug
+    w2, f2 = E.espnmf_select_stats(ctx)
+    assert w2 + f2 == w0 + f0 + 2 * 2 * 50
 
 
 @pytest.mark.parametrize("compute", [E.F64, E.F32])
