@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-matrix", action="store_true",
                    help="skip the whole-matrix enforcement comparison")
+    p.add_argument("--no-accuracy", action="store_true",
+                   help="skip the clustering-accuracy comparison")
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--spmm-shape", default=None,
                    help="SPLIT,CARVEOUT,MASK: fix the sparse products' launch shape "
@@ -390,6 +392,32 @@ def main():
         except Exception as exc:   # reported, not fatal: the headline is the column mode
             modes["matrix"] = {"error": str(exc)}
 
+    # ---------------- clustering accuracy: enforcing during vs after ALS -------
+    # Sec. 3.2: mean accuracy (Eq. 3-4) of the document topics (the columns of
+    # V) against the corpus's planted topics, after JOB_ITERS sweeps of Alg. 2
+    # (t per column enforced in every half-step) and after JOB_ITERS sweeps
+    # of Alg. 1 (no enforcement) with the same top-t applied once at the end.
+    accuracy = None
+    if not args.no_accuracy and A.labels is not None:
+        try:
+            from paper_1510_05237_gb300 import metrics
+            n_cls = int(A.labels.max()) + 1
+            runs = {}
+            for name, mode in (("during", E.TOPT_COLUMN), ("after", E.TOPT_NONE)):
+                c = E.espnmf_init(rp, ci, va, A.n, A.m, K_TOPICS, T_KEEP, T_KEEP, mode, E.F32,
+                                  u0, stream=stream)
+                E.espnmf_iterate(c, JOB_ITERS, want_measures=False)
+                if mode == E.TOPT_NONE:
+                    E.espnmf_enforce_topt(c, E.V, T_KEEP)
+                Vd = E.espnmf_get_factor(c, E.V)
+                E.espnmf_destroy(c)
+                runs[name] = float(metrics.topic_accuracy(Vd, A.labels, n_cls).mean())
+            accuracy = {"enforced_during_als": runs["during"], "enforced_after_als": runs["after"],
+                        "classes": n_cls, "t_v": T_KEEP, "sweeps": JOB_ITERS,
+                        "measure": "mean over the k document topics of Eq. 3-4"}
+        except Exception as exc:   # reported, not fatal
+            accuracy = {"error": str(exc)}
+
     # ---------------- end to end from host buffers ----------------------------
     # A whole job as a user runs it: init from pinned host CSR + U0 (H2D and
     # the context's layout build), JOB_ITERS sweeps with R/E read back, and
@@ -440,7 +468,8 @@ def main():
                              "note": "column selections over the whole run that found the "
                                      "threshold near the previous sweep's (one pass)"},
                 "clocks": clk.summary(), "roofline": roofline, "kernels": kstats,
-                "fp64_form": fp64, "enforcement_modes": modes, "e2e": e2e,
+                "fp64_form": fp64, "enforcement_modes": modes,
+                "clustering_accuracy": accuracy, "e2e": e2e,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -78,6 +78,7 @@ def _load():
             "or_grad_V": (None, csr + [P, P, P]),
             "or_lambda_max": (d, [i32, P]),
             "or_pg_step": (ctypes.c_int, csr + [P, P, ctypes.c_int]),
+            "or_topic_accuracy": (ctypes.c_int, [i64, i32, P, P, i32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -264,3 +265,15 @@ def pg_step(A, U, V, which: int):
     _check(_load().or_pg_step(*_CSR(A).args(U.shape[1]), _ptr(U), _ptr(V),
                               int(which)), "pg_step")
     return U, V
+
+
+def topic_accuracy(V: np.ndarray, labels: np.ndarray, n_J: int) -> np.ndarray:
+    """Sec. 3.2, Eq. 3-4: clustering accuracy of each column of V (documents
+    belong to a topic where V is nonzero), same-label pairs counted one by
+    one.  Returns acc[k]."""
+    V = _f64(V)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    acc = np.zeros(V.shape[1])
+    _check(_load().or_topic_accuracy(V.shape[0], V.shape[1], _ptr(V), _ptr(lab), int(n_J),
+                                     _ptr(acc)), "topic_accuracy")
+    return acc

@@ -18,6 +18,7 @@
  *   - Sec. 3.1: R = ||U_i - U_{i-1}|| / ||U_i||, E = ||A - U V^T|| / ||A||.
  *   - Sec. 4, Eq. 6 (the squared objective) gives the loss used by the
  *     gradient helpers.
+ *   - Sec. 3.2, Eq. 3-4: the document-clustering accuracy of each topic.
  *
  * Readings where the paper is silent (all norms Frobenius; exactly
  * min(t, #positive) entries kept, ties to the lower index; zero Gram
@@ -493,5 +494,53 @@ int or_pg_step(int64_t n, int64_t m, const int64_t *rowptr,
     }
     free(g);
     free(G);
+    return OR_OK;
+}
+
+/*
+ * Sec. 3.2, Eq. 3 and Eq. 4: the document-clustering accuracy of each topic
+ * (column c of V, rows = documents).  A document belongs to topic c when
+ * V[i][c] != 0; n_D is the number of such documents and n_J the number of
+ * classes (journals in the paper; planted topics here), with labels[i] in
+ * [0, n_J).  Acc = (P - alpha) / (beta - alpha), P = the number of pairs
+ * i < k of the topic's documents with the same label (counted pair by
+ * pair), alpha = q (n_J (q - 1) / 2 + r) with q = floor(n_D / n_J),
+ * r = n_D mod n_J (the pairs of an even spread), beta = n_D (n_D - 1) / 2.
+ * Acc = 1 when n_D <= 1 (as the paper sets it) and, a reading, when
+ * beta == alpha (then every spread is as good as any: n_J == 1).  Writes
+ * acc[c] for the k topics; returns OR_ERR_INVALID_ARG on a label outside
+ * [0, n_J) of a member document.
+ */
+int or_topic_accuracy(int64_t m, int32_t k, const double *V, const int32_t *labels,
+                      int32_t n_J, double *acc)
+{
+    if (n_J < 1) return OR_ERR_INVALID_ARG;
+    int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    if (!members) return OR_ERR_OOM;
+    for (int32_t c = 0; c < k; ++c) {
+        int64_t nD = 0;
+        for (int64_t i = 0; i < m; ++i) {
+            if (V[i * k + c] != 0.0) {
+                if (labels[i] < 0 || labels[i] >= n_J) {
+                    free(members);
+                    return OR_ERR_INVALID_ARG;
+                }
+                members[nD++] = i;
+            }
+        }
+        if (nD <= 1) {
+            acc[c] = 1.0;
+            continue;
+        }
+        double same = 0.0;
+        for (int64_t a = 0; a + 1 < nD; ++a)
+            for (int64_t b = a + 1; b < nD; ++b)
+                if (labels[members[a]] == labels[members[b]]) same += 1.0;
+        const double q = (double)(nD / n_J), r = (double)(nD % n_J);
+        const double alpha = q * ((double)n_J * (q - 1.0) / 2.0 + r);
+        const double beta = (double)nD * (double)(nD - 1) / 2.0;
+        acc[c] = beta == alpha ? 1.0 : (same - alpha) / (beta - alpha);
+    }
+    free(members);
     return OR_OK;
 }
