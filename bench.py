@@ -51,6 +51,9 @@ def parse():
                    help="skip the whole-matrix enforcement comparison")
     p.add_argument("--no-accuracy", action="store_true",
                    help="skip the clustering-accuracy comparison")
+    p.add_argument("--footprint", action="store_true",
+                   help="instead of the benchmark: the largest nnz(U) + nnz(V) held over "
+                        "20 sweeps for dense and sparse initial guesses and several t")
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--spmm-shape", default=None,
                    help="SPLIT,CARVEOUT,MASK: fix the sparse products' launch shape "
@@ -187,6 +190,46 @@ def reference_sample(A, U0, frac):
     return time.perf_counter() - t0, m2 / A.m, As.nnz
 
 
+def run_footprint(args):
+    """Memory footprint of enforced sparsity (Sec. 3.2, the maximum-nnz
+    figure): the largest number of factor nonzeros held at any point of a run
+    (after every half-step; U0 counts, as it is stored unenforced) for a
+    dense and two sparse initial guesses and t = 100, 1000, 10000 per column.
+    Prints one JSON line."""
+    import torch
+    import paper_1510_05237_gb300 as E
+    from gen import sparse_init
+    torch.cuda.set_device(0)
+    A, U0 = make_inputs(args.seed)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, ci, va = dev(A.rowptr), dev(A.colidx), dev(A.val.astype(np.float32))
+    stream = torch.cuda.Stream()
+    inits = [("dense U0", U0),
+             ("U0 with 2000 nonzeros per column", sparse_init(A.n, K_TOPICS, 2000, args.seed)),
+             ("U0 with 200 nonzeros per column", sparse_init(A.n, K_TOPICS, 200, args.seed))]
+    rows = []
+    for name, U0x in inits:
+        for t in (100, 1000, 10000):
+            ctx = E.espnmf_init(rp, ci, va, A.n, A.m, K_TOPICS, t, t, E.TOPT_COLUMN, E.F32,
+                                dev(U0x), stream=stream)
+            nnz = lambda: E.espnmf_factor_nnz(ctx, E.U) + E.espnmf_factor_nnz(ctx, E.V)
+            start = nnz()
+            peak = start
+            for _ in range(20):
+                E.espnmf_als_update_V(ctx)
+                peak = max(peak, nnz())
+                E.espnmf_als_update_U(ctx)
+                peak = max(peak, nnz())
+            rows.append({"U0": name, "nnz_U0": int(np.count_nonzero(U0x)), "t": t,
+                         "max_nnz_UV": peak, "final_nnz_UV": nnz(),
+                         "final_E": float(E.espnmf_error(ctx))})
+            E.espnmf_destroy(ctx)
+    print(json.dumps({"experiment": "footprint", "workload": WORKLOAD, "n": A.n, "m": A.m,
+                      "nnz": A.nnz, "k": K_TOPICS, "sweeps": 20, "dense_UV": (A.n + A.m) * K_TOPICS,
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def run_reference(args):
     """The FP64 CPU oracle, as it stands, on the host cores (rank 0 only).
 
@@ -247,6 +290,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.footprint:
+        return run_footprint(args)
     import torch
     import paper_1510_05237_gb300 as E
     ws, rank, local = dist_env()
@@ -407,10 +452,15 @@ def main():
                 c = E.espnmf_init(rp, ci, va, A.n, A.m, K_TOPICS, T_KEEP, T_KEEP, mode, E.F32,
                                   u0, stream=stream)
                 E.espnmf_iterate(c, JOB_ITERS, want_measures=False)
-                if mode == E.TOPT_NONE:
-                    E.espnmf_enforce_topt(c, E.V, T_KEEP)
-                Vd = E.espnmf_get_factor(c, E.V)
+                Vd = E.espnmf_get_factor(c, E.V, dtype=np.float32)
                 E.espnmf_destroy(c)
+                if mode == E.TOPT_NONE:
+                    # the rule once, column by column, by the library's selector
+                    Vt = torch.from_numpy(np.ascontiguousarray(Vd)).cuda()
+                    torch.cuda.synchronize()
+                    E.espnmf_enforce_topt_buffer(Vt, T_KEEP, E.TOPT_COLUMN, stream=stream)
+                    stream.synchronize()
+                    Vd = Vt.cpu().numpy()
                 runs[name] = float(metrics.topic_accuracy(Vd, A.labels, n_cls).mean())
             accuracy = {"enforced_during_als": runs["during"], "enforced_after_als": runs["after"],
                         "classes": n_cls, "t_v": T_KEEP, "sweeps": JOB_ITERS,
