@@ -9,9 +9,10 @@
 // transaction.  A row is cut into 1..32 segments of at most 64 entries held
 // by adjacent lanes; each lane sums its segment and the lanes of a row are
 // combined by a fixed shuffle tree.  The factor row an entry gathers is read
-// sparsely: a bitmask (L1-resident) skips rows that are zero; otherwise one
-// 16-byte record holds the row's count and its first three (column, value)
-// pairs, longer rows continue in the row-packed pairs, and the rare dense
+// sparsely: a bitmask (L1-resident or in shared memory) skips rows that are
+// zero; otherwise the row's 32-byte record (one L2 sector) holds its count
+// and first six (column, value) pairs -- the first 16-byte half the first
+// three -- longer rows continue in the row-packed pairs, and the rare dense
 // row is read from its dense copy.  Every product is added into per-thread
 // accumulators in shared memory, slot c of thread tid at acc[c * B + tid]
 // (a warp's lanes always touch 32 distinct banks, whatever columns they
