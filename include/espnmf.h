@@ -290,6 +290,25 @@ espnmf_status espnmf_set_option(espnmf_ctx *ctx, espnmf_option opt,
 espnmf_status espnmf_spmm_config(espnmf_ctx *ctx, int32_t product, int32_t *split,
                                  int32_t *carveout, int32_t *mask);
 
+/* espnmf_sequential -- Alg. 3 (sequential ALS, Sec. 4) with rank-1 new
+ * topics (k2 = 1, the case the paper times): the k topics are found one
+ * after another.  For topic j, with the converged topics U1 = U[:, :j] and
+ * V1 = V[:, :j], the new column u starts from u0 (the same initial guess for
+ * every topic) and `iters` times
+ *   v = (A^T u - V1 (U1^T u)) / (u^T u)     (Eq. 7), projected, top-t_v,
+ *   u = (A v - U1 (V1^T v)) / (v^T v)       (Eq. 8), projected, top-t_u;
+ * then U[:, j] = u, V[:, j] = v.  The sparse products, the division, the
+ * projection and the top-t rule are those of Alg. 2 with k = 1 (a k = 1
+ * context built from A); the deflation term runs in FP64 sums.  A: as for
+ * espnmf_init (copied).  u0: n values (dtype u0_dtype, host or device).
+ * U_out (n x k) and V_out (m x k): row-major DEVICE buffers of the compute
+ * dtype, written when the call returns ESPNMF_OK (it synchronises).
+ * Errors: espnmf_last_error(NULL).  Requires 1 <= k <= min(n, m), iters >= 1. */
+espnmf_status espnmf_sequential(const espnmf_csr *A, int32_t k, int64_t t_u, int64_t t_v,
+                                int32_t iters, espnmf_dtype compute, const void *u0,
+                                espnmf_dtype u0_dtype, int32_t u0_on_device, void *U_out,
+                                void *V_out, void *stream);
+
 /* espnmf_select_stats -- how the column selections of this context's
  * enforcement steps (FP32 form, column mode) found their thresholds since
  * espnmf_init: warm = columns whose search started from the previous

@@ -79,6 +79,7 @@ def _load():
             "or_lambda_max": (d, [i32, P]),
             "or_pg_step": (ctypes.c_int, csr + [P, P, ctypes.c_int]),
             "or_topic_accuracy": (ctypes.c_int, [i64, i32, P, P, i32, P]),
+            "or_sequential": (ctypes.c_int, csr[:5] + [i32, P, i64, i64, i32, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -277,3 +278,21 @@ def topic_accuracy(V: np.ndarray, labels: np.ndarray, n_J: int) -> np.ndarray:
     _check(_load().or_topic_accuracy(V.shape[0], V.shape[1], _ptr(V), _ptr(lab), int(n_J),
                                      _ptr(acc)), "topic_accuracy")
     return acc
+
+
+def sequential(A, u0: np.ndarray, k: int, t_u: int, t_v: int, iters: int,
+               return_pre: bool = False):
+    """Sec. 4, Alg. 3 with rank-1 topics: k topics found one after another,
+    each from the same initial guess u0 (n-vector), ``iters`` sweeps each.
+    Returns (U, V), and with ``return_pre`` also the last topic's last v and
+    u before the projection."""
+    u0 = _f64(np.asarray(u0).reshape(-1))
+    U = np.zeros((A.n, k))
+    V = np.zeros((A.m, k))
+    vpre = np.zeros(A.m)
+    upre = np.zeros(A.n)
+    c = _CSR(A)
+    _check(_load().or_sequential(*c.args(1)[:5], int(k), _ptr(u0), int(t_u), int(t_v),
+                                 int(iters), _ptr(U), _ptr(V), _ptr(vpre), _ptr(upre)),
+           "sequential")
+    return (U, V, vpre, upre) if return_pre else (U, V)

@@ -544,3 +544,80 @@ int or_topic_accuracy(int64_t m, int32_t k, const double *V, const int32_t *labe
     free(members);
     return OR_OK;
 }
+
+/*
+ * Sec. 4, Alg. 3 (sequential ALS) with rank-1 new topics (k2 = 1, the case
+ * the paper times): the k topics are found one after another.  For topic j,
+ * with the converged topics U1 = U[:, :j] and V1 = V[:, :j] (Eq. 5 splits
+ * U V^T = U1 V1^T + U2 V2^T):
+ *   START  u = u0 (the same initial guess for every topic, a reading)
+ *   repeat iters times:
+ *     v = (A^T u - V1 (U1^T u)) / (u^T u)   (Eq. 7), project, keep t_v largest
+ *     u = (A v - U1 (V1^T v)) / (v^T v)     (Eq. 8), project, keep t_u largest
+ *   U[:, j] = u, V[:, j] = v
+ * A zero divisor (u or v all zero) gives a zero update (the reading for a
+ * zero Gram column).  If vpre/upre are non-NULL they receive the last
+ * topic's last v and u before the projection.  U (n x k), V (m x k)
+ * row-major outputs.
+ */
+int or_sequential(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *colidx,
+                  const double *val, int32_t k, const double *u0, int64_t t_u, int64_t t_v,
+                  int32_t iters, double *U, double *V, double *vpre, double *upre)
+{
+    if (k < 1 || iters < 1 || t_u < 0 || t_v < 0) return OR_ERR_INVALID_ARG;
+    double *u = (double *)malloc(sizeof(double) * (size_t)n);
+    double *v = (double *)malloc(sizeof(double) * (size_t)m);
+    double *g = (double *)malloc(sizeof(double) * (size_t)k);
+    if (!u || !v || !g) { free(u); free(v); free(g); return OR_ERR_OOM; }
+    memset(U, 0, sizeof(double) * (size_t)n * (size_t)k);
+    memset(V, 0, sizeof(double) * (size_t)m * (size_t)k);
+    int st = OR_OK;
+    for (int32_t j = 0; j < k && st == OR_OK; ++j) {
+        memcpy(u, u0, sizeof(double) * (size_t)n);
+        for (int32_t it = 0; it < iters && st == OR_OK; ++it) {
+            /* Eq. 7 */
+            or_spmm_At(n, m, rowptr, colidx, val, 1, u, v);
+            for (int32_t c = 0; c < j; ++c) {
+                double s = 0.0;
+                for (int64_t i = 0; i < n; ++i) s += U[i * k + c] * u[i];
+                g[c] = s;
+            }
+            for (int64_t i = 0; i < m; ++i) {
+                double d = 0.0;
+                for (int32_t c = 0; c < j; ++c) d += V[i * k + c] * g[c];
+                v[i] -= d;
+            }
+            double uu = 0.0;
+            for (int64_t i = 0; i < n; ++i) uu += u[i] * u[i];
+            for (int64_t i = 0; i < m; ++i) v[i] = uu != 0.0 ? v[i] / uu : 0.0;
+            if (vpre && j == k - 1 && it == iters - 1) memcpy(vpre, v, sizeof(double) * (size_t)m);
+            st = or_project(v, m);
+            if (st == OR_OK) st = or_topt(v, m, 1, t_v, OR_TOPT_COLUMN);
+            if (st != OR_OK) break;
+            /* Eq. 8 */
+            or_spmm_A(n, m, rowptr, colidx, val, 1, v, u);
+            for (int32_t c = 0; c < j; ++c) {
+                double s = 0.0;
+                for (int64_t i = 0; i < m; ++i) s += V[i * k + c] * v[i];
+                g[c] = s;
+            }
+            for (int64_t i = 0; i < n; ++i) {
+                double d = 0.0;
+                for (int32_t c = 0; c < j; ++c) d += U[i * k + c] * g[c];
+                u[i] -= d;
+            }
+            double vv = 0.0;
+            for (int64_t i = 0; i < m; ++i) vv += v[i] * v[i];
+            for (int64_t i = 0; i < n; ++i) u[i] = vv != 0.0 ? u[i] / vv : 0.0;
+            if (upre && j == k - 1 && it == iters - 1) memcpy(upre, u, sizeof(double) * (size_t)n);
+            st = or_project(u, n);
+            if (st == OR_OK) st = or_topt(u, n, 1, t_u, OR_TOPT_COLUMN);
+        }
+        for (int64_t i = 0; i < n; ++i) U[i * k + j] = u[i];
+        for (int64_t i = 0; i < m; ++i) V[i * k + j] = v[i];
+    }
+    free(u);
+    free(v);
+    free(g);
+    return st;
+}

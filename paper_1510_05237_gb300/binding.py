@@ -96,6 +96,7 @@ def load():
             "espnmf_spmm_config": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
             "espnmf_spmm_frequent": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)],
             "espnmf_select_stats": [P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+            "espnmf_sequential": [ctypes.POINTER(_CSR), i32, i64, i64, i32, st, P, st, i32, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -121,7 +122,8 @@ def exported_symbols():
              "espnmf_enforce_topt_buffer_noalloc", "espnmf_loss", "espnmf_grad",
              "espnmf_pg_step", "espnmf_batch_init", "espnmf_batch_destroy",
              "espnmf_batch_ctx", "espnmf_batch_set_option", "espnmf_batch_iterate",
-             "espnmf_spmm_config", "espnmf_spmm_frequent", "espnmf_select_stats"]
+             "espnmf_spmm_config", "espnmf_spmm_frequent", "espnmf_select_stats",
+             "espnmf_sequential"]
     return {n: hasattr(lib, n) for n in names}
 
 
@@ -200,6 +202,30 @@ def espnmf_init(rowptr, colidx, values, n: int, m: int, k: int, t_u: int, t_v: i
                          _stream_handle(stream))
     _check(st, None)
     return Context(h, int(n), int(m), int(k), int(compute))
+
+
+def espnmf_sequential(rowptr, colidx, values, n: int, m: int, k: int, t_u: int, t_v: int,
+                      iters: int, u0, compute: int = F32, stream=None):
+    """Alg. 3 (sequential ALS) with rank-1 topics; returns (U, V) as CUDA
+    tensors of the compute dtype (n x k, m x k)."""
+    import torch
+    lib = load()
+    rp, d1, k1 = _ptr(rowptr)
+    ci, d2, k2 = _ptr(colidx)
+    va, d3, k3 = _ptr(values)
+    if not (d1 == d2 == d3):
+        raise ValueError("rowptr, colidx and values must all be host or all device arrays")
+    csr = _CSR(int(n), int(m), int(len(colidx)), rp, ci, va, _dtype_code(values), d1)
+    up, ud, uk = _ptr(u0)
+    tdt = torch.float64 if compute == F64 else torch.float32
+    # written in full by the library, on its stream, before it returns
+    U = torch.empty((int(n), int(k)), dtype=tdt, device="cuda")
+    V = torch.empty((int(m), int(k)), dtype=tdt, device="cuda")
+    _check(lib.espnmf_sequential(ctypes.byref(csr), int(k), int(t_u), int(t_v), int(iters),
+                                 int(compute), up, _dtype_code(u0), ud,
+                                 ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                                 _stream_handle(stream)))
+    return U, V
 
 
 def espnmf_destroy(ctx: Context):
