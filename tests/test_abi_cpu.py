@@ -83,3 +83,33 @@ def test_no_cpu_fallback(lib):
 def test_library_is_built_for_sm103a():
     from paper_1510_05237_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_sequential_validates_and_needs_a_gpu(lib):
+    """espnmf_sequential rejects bad arguments before any device work and,
+    without a CUDA device, fails instead of running on the host."""
+    import ctypes
+    import numpy as np
+    import paper_1510_05237_gb300 as E
+    from paper_1510_05237_gb300 import binding as B
+    from gen import small_zipf, uniform_init
+    A = small_zipf(1)
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
+    va = np.ascontiguousarray(A.val, dtype=np.float64)
+    csr = B._CSR(A.n, A.m, len(ci), rp.ctypes.data, ci.ctypes.data, va.ctypes.data, E.F64, 0)
+    u0 = np.ascontiguousarray(uniform_init(A.n, 1, 1)[:, 0])
+    out_u = np.zeros(A.n * 4)
+    out_v = np.zeros(A.m * 4)
+
+    def call(k, iters):
+        return lib.espnmf_sequential(ctypes.byref(csr), k, 10, 10, iters, E.F64,
+                                     ctypes.c_void_p(u0.ctypes.data), E.F64, 0,
+                                     ctypes.c_void_p(out_u.ctypes.data),
+                                     ctypes.c_void_p(out_v.ctypes.data), None)
+    assert call(0, 1) == E.ERR_INVALID_ARG
+    assert call(2, 0) == E.ERR_INVALID_ARG
+    assert call(A.m + 1, 1) == E.ERR_INVALID_ARG
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        assert call(2, 1) == E.ERR_CUDA
