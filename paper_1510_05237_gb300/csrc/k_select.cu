@@ -14,16 +14,19 @@
 //           copied to a candidate list in shared memory,
 //   then    the remaining bits are resolved by radix rounds over the
 //           candidates only, and ties by a radix select over their indices.
-// One thread-block cluster (up to 8 CTAs) owns a column (or the whole
-// matrix); each CTA reads its slice of the column straight from global
+// When it marks survivors (FP32 form, column mode) one CTA of 1024 threads
+// owns a column and starts from a hint, the column's threshold of the
+// previous selection: one pass counts and marks the entries above the three
+// bins around the hint and lists the entries in them; when the t-th largest
+// is among those, passes 1 and 2 are skipped (rounds over the list only),
+// otherwise the marks are taken back and the search runs as above.
+// Otherwise a thread-block cluster of up to two CTAs owns a column (or the
+// whole matrix); the CTAs add their histograms through distributed shared
+// memory.  Every CTA reads its slice of the column straight from global
 // memory (the candidate was just written, so it is in the L2) with 16-byte
-// loads, and the CTAs add their histograms through distributed shared
-// memory.  Shared memory holds only the histogram and the candidate list, so
-// several clusters share an SM.  Histogram updates are aggregated per warp
-// (lanes with the same bucket add once), which matters because the positive
-// entries of a column crowd into a few buckets.  If any CTA's candidates
-// overflow its list, the cluster resolves the bucket with passes over the
-// data instead (same result, slower).
+// loads; shared memory holds only the histogram and the candidate list.  If
+// a CTA's candidates overflow its list, the bucket is resolved with passes
+// over the data instead (same result, slower).
 //
 // Output per segment s (column, or 0 in matrix mode): tau[s] (bit pattern)
 // and cut[s]: an entry survives iff it is positive and its bits are > tau,
