@@ -358,6 +358,8 @@ espnmf_status espnmf_sync(espnmf_ctx *ctx);
  *   t, mode  as for the context (t >= 0).
  * Every entry that is not > 0 becomes +0; of the positive entries only
  * min(t, #positive) per column (COLUMN) or in total (MATRIX) survive.
+ * If X holds a NaN or an infinity the call returns ESPNMF_ERR_NONFINITE and
+ * leaves X unchanged.
  * Scratch memory is allocated from the stream-ordered allocator and freed
  * before the call returns.  Enqueued on `stream` (NULL: legacy default
  * stream); synchronises that stream to report errors. */
@@ -384,9 +386,12 @@ espnmf_status espnmf_enforce_topt_buffer(void *X, int64_t rows, int32_t k,
  * that loads the library until the process exits).
  *   - X larger than ESPNMF_NOALLOC_MAX_ELEMS (rows * ld(k) or rows) is
  *     rejected with ESPNMF_ERR_INVALID_ARG; nothing is modified.
- *   - The first call on a device (with that device current) looks up the
- *     array's device address once; make that first call before any stream
- *     capture.
+ *   - X holding a NaN or an infinity gives ESPNMF_ERR_NONFINITE and X is
+ *     left unchanged.
+ *   - Every call looks up the array's device address on the current device
+ *     (no cached address survives a device reset); the first call on a
+ *     device may load the library's device code there, so make it before
+ *     any stream capture.
  *   - All calls share the array: calls whose work overlaps on the GPU
  *     (other streams, other host threads on the same device) race on it and
  *     must be serialised by the caller.

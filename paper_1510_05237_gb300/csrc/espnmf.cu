@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1786,10 +1787,16 @@ espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuerr(e, "device");
-    static bool setup_done[64] = {};
-    if (dev < 64 && !setup_done[dev]) {
-        if ((e = setup_select()) != cudaSuccess) return cuerr(e, "setup");
-        setup_done[dev] = true;
+    {
+        // per-device kernel attribute set-up, once, under a lock (callers
+        // may come from several host threads)
+        static std::mutex setup_mu;
+        static bool setup_done[64] = {};
+        std::lock_guard<std::mutex> lock(setup_mu);
+        if (dev >= 64 || !setup_done[dev]) {
+            if ((e = setup_select()) != cudaSuccess) return cuerr(e, "setup");
+            if (dev < 64) setup_done[dev] = true;
+        }
     }
     const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
     const int64_t ldx = (rows + 31) / 32 * 32;

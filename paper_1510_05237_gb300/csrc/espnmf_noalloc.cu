@@ -11,12 +11,15 @@
 //
 // Every GPU that loads the library holds the array until the process exits.
 // Host code cannot use the array's name as a device address (on the host it
-// is only a stand-in), so the first call on each device, with that device
-// current, asks the runtime for the array's device address once
-// (cudaGetSymbolAddress) and keeps it.  All calls share the array and it
-// keeps the previous call's contents: the parts that must start at zero are
-// cleared on every call, and calls that overlap on the GPU (different
-// streams, or different host threads on one device) race on it.
+// is only a stand-in), so every call, with the call's device current, asks
+// the runtime for the array's device address (cudaGetSymbolAddress, which
+// allocates nothing) rather than keeping an address that a device reset
+// would make stale.  The first call on a device may load the library's
+// device code there, so it should come before any stream capture.  All
+// calls share the array and it keeps the previous call's contents: the
+// parts that must start at zero are cleared on every call, and calls that
+// overlap on the GPU (different streams, or different host threads on one
+// device) race on it.
 #include <mutex>
 
 #include "../../include/espnmf.h"
@@ -41,8 +44,6 @@ constexpr size_t kNoallocBytes = kXtBytes + kTauBytes + kCutBytes + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 std::mutex g_setup_mu;
-constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
 
 // Failures are described through espnmf_last_error(NULL), like the other
 // context-free calls.
@@ -58,19 +59,17 @@ espnmf_status fail(espnmf_status s, const char* msg, cudaError_t e = cudaSuccess
     return s;
 }
 
-// Device address of the scratch array on the current device (set up once).
-espnmf_status scratch_for(int dev, unsigned char** out)
+// Device address of the scratch array on the current device, looked up on
+// every call, and the selector's kernel attributes set for that device.
+espnmf_status scratch_for(unsigned char** out)
 {
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "cudaGetSymbolAddress", e);
-        e = setup_select();
-        if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "selector set-up", e);
-        g_scratch_addr[dev] = static_cast<unsigned char*>(ptr);
-    }
-    *out = g_scratch_addr[dev];
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "cudaGetSymbolAddress", e);
+    e = setup_select();
+    if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "selector set-up", e);
+    *out = static_cast<unsigned char*>(ptr);
     return ESPNMF_OK;
 }
 
@@ -98,9 +97,8 @@ espnmf_status espnmf_enforce_topt_buffer_noalloc(void* X, int64_t rows, int32_t 
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "device", e);
-    if (dev >= kMaxDevices) return fail(ESPNMF_ERR_UNSUPPORTED, "device index too large");
     unsigned char* ws = nullptr;
-    espnmf_status st0 = scratch_for(dev, &ws);
+    espnmf_status st0 = scratch_for(&ws);
     if (st0 != ESPNMF_OK) return st0;
 
     cudaStream_t st = (cudaStream_t)stream;
@@ -130,7 +128,7 @@ espnmf_status espnmf_enforce_topt_buffer_noalloc(void* X, int64_t rows, int32_t 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(ESPNMF_ERR_CUDA, "enforce_topt_buffer_noalloc", e);
-    if (hstat & ST_NONFINITE) return fail(ESPNMF_ERR_NONFINITE, "non-finite value in X");
+    if (hstat & ST_NONFINITE) return fail(ESPNMF_ERR_NONFINITE, "non-finite value in X (X unchanged)");
     return ESPNMF_OK;
 }
 

@@ -32,9 +32,11 @@ constexpr int kCholThreads = 256;
 // 1 / sqrt(d) for d > 0: an FP32 seed refined by two FP64 Newton steps
 // x <- x (3 - d x^2) / 2 (each step doubles the correct bits: 23 -> 46 ->
 // full precision); a short dependent chain on this GPU's slow FP64 pipe.
+// The seed needs d and 1/sqrt(d) inside the normal FP32 range, so pivots
+// outside [1e-30, 1e30] take the IEEE FP64 square root and division.
 __device__ __forceinline__ double rsqrt_fp64(double d)
 {
-    if (!(d > 1e-300 && d < 1e300)) return 1.0 / sqrt(d);
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
     double x = (double)rsqrtf((float)d);
     double t = d * x;
     x = x * fma(-0.5 * t, x, 1.5);

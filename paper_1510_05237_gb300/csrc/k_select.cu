@@ -670,6 +670,9 @@ __global__ void apply_thresholds_kernel(T* X, int64_t rows, int k, int64_t ld, i
                                         const typename KeyBits<T>::K* __restrict__ tau,
                                         const uint32_t* __restrict__ cut, unsigned* status)
 {
+    // a non-finite entry was already seen (by the column-major copy that
+    // feeds the selector): X is left as the caller gave it
+    if (*reinterpret_cast<volatile unsigned*>(status) & ST_NONFINITE) return;
     bool bad = false;
     const int64_t total = rows * k;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;

@@ -423,3 +423,31 @@ def test_benchmark_corpus_uses_the_frequent_part():
     assert h_av == 0 and e_av == 0
     ctx64 = make_ctx(A, 50, 120, 150, uniform_init(A.n, 50, 2), E.TOPT_COLUMN, E.F64)
     assert E.espnmf_spmm_frequent(ctx64, 1) == (0, 0)
+
+
+@pytest.mark.parametrize("scale", [1e20, 1e-20])
+def test_step_parity_with_factor_scaled_far_from_one(scale):
+    """A factor scaled by 1e20 (or 1e-20) puts the Gram pivots near 1e40
+    (1e-40), outside the FP32 range that seeds the Cholesky pivot's inverse
+    square root; the FP32 form must still solve the system (the result
+    scales by 1/scale) and match the oracle."""
+    A = small_zipf(6)
+    U0 = uniform_init(A.n, 8, 6) * scale
+    step_parity(A, 8, 90, 70, U0, E.TOPT_COLUMN, E.F32, f"scale={scale:g}")
+
+
+@pytest.mark.parametrize("compute", [E.F64, E.F32])
+def test_enforce_topt_buffer_leaves_nonfinite_input_unchanged(compute):
+    import torch
+    rng = np.random.default_rng(10)
+    X = (rng.integers(-3, 6, (500, 7)) * 0.25).astype(np.float64)
+    X[17, 3] = np.nan
+    X[40, 0] = np.inf
+    dt = torch.float64 if compute == E.F64 else torch.float32
+    Xd = torch.tensor(X, dtype=dt, device="cuda")
+    before = Xd.clone()
+    with pytest.raises(E.EspnmfError) as ei:
+        E.espnmf_enforce_topt_buffer(Xd, 10, E.TOPT_COLUMN)
+    assert ei.value.status == E.ERR_NONFINITE
+    assert torch.equal(torch.isnan(Xd), torch.isnan(before))
+    assert torch.equal(torch.nan_to_num(Xd), torch.nan_to_num(before))

@@ -322,3 +322,29 @@ def test_lambda_max_and_pg_step_descends():
     U2, V2 = oracle.pg_step(A, U1, V1, 1)
     assert oracle.loss(A, U2, V2) <= f1 * (1 + 1e-14)
     assert np.all(U2 >= 0) and np.all(V2 >= 0)
+
+
+def test_pg_step_size_is_pinned_by_the_rank_one_minimiser():
+    """With k = 1 the objective is a 1-D quadratic in each entry of u:
+    f(u) = ||A - u v^T||^2 has gradient 2 (u v^T v - A v) and curvature
+    2 v^T v, so a step of length 1 / (2 v^T v) from any u lands exactly on
+    the unconstrained minimiser A v / v^T v; the projection then clamps it
+    at 0 and keeps u's support.  The expected value below is that closed
+    form, written out independently of the oracle: a step of twice the
+    length (1 / v^T v) would land on 2 A v / v^T v - u instead."""
+    rng = np.random.default_rng(37)
+    D = rand_sparse(rng, 11, 8, 0.6)
+    A = corpus_from_dense(D)
+    u = rng.random((11, 1)) + 0.1
+    u[[2, 7]] = 0.0                     # outside the support: stays 0
+    v = rng.random((8, 1)) + 0.1
+    U1, V1 = oracle.pg_step(A, u, v, 0)
+    ls = (D @ v[:, 0]) / float(v[:, 0] @ v[:, 0])
+    expect = np.where(u[:, 0] > 0, np.maximum(ls, 0.0), 0.0)
+    assert np.allclose(U1[:, 0], expect, rtol=1e-12, atol=1e-14)
+    assert np.array_equal(V1, v)
+    # and the V step from the same closed form with the roles swapped
+    U2, V2 = oracle.pg_step(A, u, v, 1)
+    ls_v = (D.T @ u[:, 0]) / float(u[:, 0] @ u[:, 0])
+    expect_v = np.where(v[:, 0] > 0, np.maximum(ls_v, 0.0), 0.0)
+    assert np.allclose(V2[:, 0], expect_v, rtol=1e-12, atol=1e-14)

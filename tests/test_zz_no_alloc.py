@@ -53,3 +53,25 @@ def test_noalloc_selector_rejects_inputs_beyond_its_array():
     Y = torch.ones(E.NOALLOC_MAX_ELEMS // 4, 4, device="cuda")
     E.espnmf_enforce_topt_buffer_noalloc(Y, 3)
     assert int((Y != 0).sum()) == 12
+
+
+def test_noalloc_selector_leaves_nonfinite_input_unchanged():
+    import torch
+    rng = np.random.default_rng(11)
+    X = make_x(rng, 300, 9)
+    X[5, 4] = np.nan
+    for dtype in (torch.float32, torch.float64):
+        Xd = torch.tensor(X, dtype=dtype, device="cuda")
+        before = Xd.clone()
+        for call in range(2):
+            with pytest.raises(E.EspnmfError) as ei:
+                E.espnmf_enforce_topt_buffer_noalloc(Xd, 4)
+            assert ei.value.status == E.ERR_NONFINITE
+            assert torch.equal(torch.nan_to_num(Xd), torch.nan_to_num(before))
+        # the array is usable again after the rejected calls
+        Y = torch.tensor(np.maximum(X, 0), dtype=dtype, device="cuda")
+        Y[5, 4] = 0.0
+        Z = Y.clone()
+        E.espnmf_enforce_topt_buffer(Y, 4)
+        E.espnmf_enforce_topt_buffer_noalloc(Z, 4)
+        assert torch.equal(Y, Z)
