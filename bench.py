@@ -108,6 +108,18 @@ class Clocks:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def snapshot(self):
+        """One read-only reading, taken right before and right after the
+        timed region, so that a short region still has a record."""
+        try:
+            out = subprocess.run(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits"],
+                capture_output=True, text=True, timeout=10).stdout
+            self.lines.extend(ln.strip() for ln in out.splitlines() if ln.strip())
+        except Exception:
+            pass
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -162,16 +174,50 @@ def make_inputs(seed):
     return A, U0
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline(A, U0, sweeps=1):
+    """The FP64 C oracle on the host: one thread (the reported value), and
+    the same source built with OpenMP on every host core beside it."""
     import oracle
     A32 = A.astype(np.float32)
     oracle.build()
     t0 = time.perf_counter()
     oracle.iterate(A32, U0, T_KEEP, T_KEEP, oracle.COLUMN, sweeps)
     dt = time.perf_counter() - t0
+    ncores = os.cpu_count() or 1
+    all_cores = None
+    try:
+        oracle.build(threads=True)
+        t0 = time.perf_counter()
+        oracle.iterate(A32, U0, T_KEEP, T_KEEP, oracle.COLUMN, sweeps, threads=ncores)
+        dt_all = time.perf_counter() - t0
+        all_cores = {"value": sweeps / dt_all, "unit": UNIT, "cores": ncores,
+                     "build": "same oracle source with OpenMP (bitwise equal results)"}
+    except Exception as exc:   # reported, not fatal
+        all_cores = {"error": str(exc)}
     return {"value": sweeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": ncores,
             "sample": f"{sweeps} sweep(s) of the full {WORKLOAD} workload "
-                      f"(n={A.n}, m={A.m}, nnz={A.nnz}) from U0, FP64 C oracle, 1 thread"}
+                      f"(n={A.n}, m={A.m}, nnz={A.nnz}) from U0, FP64 C oracle, 1 thread",
+            "all_cores": all_cores}
 
 
 REF_BUDGET_S = 150.0   # target wall time of the whole reference arm
@@ -319,6 +365,7 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "n": A.n, "m": A.m, "nnz": A.nnz,
                        "k": K_TOPICS, "t": T_KEEP, "mode": "column"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -369,10 +416,12 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     barrier()
     with Clocks(local) as clk:
+        clk.snapshot()
         ev0.record(stream)
         E.espnmf_iterate(ctx, args.steps, want_measures=False)
         ev1.record(stream)
         ev1.synchronize()
+        clk.snapshot()
     barrier()
     ms = ev0.elapsed_time(ev1)
     if dist is not None:

@@ -22,8 +22,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "espnmf_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle.so")
+_LIB_OMP = os.path.join(_OUT_DIR, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 OK, INVALID_ARG, BAD_MATRIX, SINGULAR, NONFINITE, OOM = 0, 1, 2, 3, 4, 5
 COLUMN, MATRIX, NONE = 0, 1, 2
@@ -35,25 +36,29 @@ class OracleError(RuntimeError):
         self.status = status
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liboracle.so``."""
+def build(force: bool = False, threads: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so``, or with
+    ``threads`` the same source with OpenMP into ``liboracle_omp.so`` (used
+    only for the benchmark's all-cores CPU baseline; its results are
+    bitwise those of the single-threaded build)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
+    lib = _LIB_OMP if threads else _LIB
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= os.path.getmtime(_SRC)):
+        return lib
+    tmp = lib + f".{os.getpid()}.tmp"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+                           "-ffp-contract=off", *(["-fopenmp"] if threads else []),
+                           _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, lib)
+    return lib
 
 
-def _load():
-    global _lib
+def _load(threads: bool = False):
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
+        if threads in _libs:
+            return _libs[threads]
+        lib = ctypes.CDLL(build(threads=threads))
         i64, i32, d = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         P = ctypes.c_void_p
         csr = [i64, i64, P, P, P, i32]
@@ -80,12 +85,13 @@ def _load():
             "or_pg_step": (ctypes.c_int, csr + [P, P, ctypes.c_int]),
             "or_topic_accuracy": (ctypes.c_int, [i64, i32, P, P, i32, P]),
             "or_sequential": (ctypes.c_int, csr[:5] + [i32, P, i64, i64, i32, P, P, P, P]),
+            "or_set_threads": (None, [i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
             f.restype = res
             f.argtypes = args
-        _lib = lib
+        _libs[threads] = lib
         return lib
 
 
@@ -227,15 +233,19 @@ def error_direct(A, U, V) -> float:
 
 
 def iterate(A, U0: np.ndarray, t_u: int, t_v: int, mode: int = COLUMN,
-            iters: int = 1):
-    """Alg. 2 for ``iters`` sweeps.  Returns (U, V, R[iters], E[iters])."""
+            iters: int = 1, threads: int | None = None):
+    """Alg. 2 for ``iters`` sweeps.  Returns (U, V, R[iters], E[iters]).
+    With ``threads``, the OpenMP build on that many threads (same results)."""
+    lib = _load(True) if threads else _load()
+    if threads:
+        lib.or_set_threads(int(threads))
     U0 = _f64(U0)
     k = U0.shape[1]
     U = np.zeros((A.n, k))
     V = np.zeros((A.m, k))
     R = np.zeros(max(iters, 1))
     E = np.zeros(max(iters, 1))
-    _check(_load().or_iterate(*_CSR(A).args(k), _ptr(U0), int(t_u), int(t_v),
+    _check(lib.or_iterate(*_CSR(A).args(k), _ptr(U0), int(t_u), int(t_v),
                               int(mode), int(iters), _ptr(R), _ptr(E), _ptr(U),
                               _ptr(V)), "iterate")
     return U, V, R[:iters], E[:iters]

@@ -348,3 +348,16 @@ def test_pg_step_size_is_pinned_by_the_rank_one_minimiser():
     ls_v = (D.T @ u[:, 0]) / float(u[:, 0] @ u[:, 0])
     expect_v = np.where(v[:, 0] > 0, np.maximum(ls_v, 0.0), 0.0)
     assert np.allclose(V2[:, 0], expect_v, rtol=1e-12, atol=1e-14)
+
+
+def test_openmp_build_gives_bitwise_the_same_sweeps():
+    """The all-cores CPU baseline runs the oracle's OpenMP build; its loops
+    split work between threads without reordering any sum, so its sweeps
+    equal the single-threaded build's bit for bit."""
+    A = small_zipf(3)
+    U0 = uniform_init(A.n, 7, 3)
+    for mode, t in ((oracle.COLUMN, 40), (oracle.MATRIX, 300), (oracle.NONE, 0)):
+        a = oracle.iterate(A, U0, t, t, mode, 3)
+        b = oracle.iterate(A, U0, t, t, mode, 3, threads=4)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
