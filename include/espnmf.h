@@ -181,6 +181,31 @@ espnmf_status espnmf_set_factor(espnmf_ctx *ctx, espnmf_which which,
                                 int32_t on_device);
 
 /* ------------------------------------------------------------------------ */
+/* Checkpoints (the paper has no counterpart: this is run management)       */
+
+/* espnmf_save -- writes the context's state to the file `path` (replaced
+ * atomically through `path`.tmp): format version, n, m, k, t_u, t_v, mode,
+ * arithmetic, the number of completed sweeps, the caller's 64-bit `tag`
+ * (e.g. the seed of the initial guess), U and V dense row-major in the
+ * context's arithmetic, the FP64 Gram matrices U^T U and V^T V, and a
+ * checksum.  A is not saved.  Synchronises. */
+espnmf_status espnmf_save(espnmf_ctx *ctx, const char *path, uint64_t tag);
+
+/* espnmf_load -- restores a state written by espnmf_save into a context
+ * made by espnmf_init from the same A with the same k, t_u, t_v, mode and
+ * arithmetic (any U0 of the right shape): U, V, their Gram matrices and the
+ * sweep count.  The sweeps that follow repeat, bit for bit, those of the
+ * context that saved the state.  tag and sweeps (may be NULL) receive the
+ * saved tag and sweep count.  A file of another shape, mode, t or
+ * arithmetic, a truncated file or a checksum mismatch gives
+ * ESPNMF_ERR_INVALID_ARG and leaves the context unchanged.  Synchronises. */
+espnmf_status espnmf_load(espnmf_ctx *ctx, const char *path, uint64_t *tag, int64_t *sweeps);
+
+/* espnmf_sweeps_done -- completed sweeps (U updates) since espnmf_init, or
+ * since the state restored by espnmf_load counting its saved sweeps. */
+espnmf_status espnmf_sweeps_done(espnmf_ctx *ctx, int64_t *sweeps);
+
+/* ------------------------------------------------------------------------ */
 /* Measures (Sec. 3.1)                                                      */
 
 /* espnmf_residual -- R = ||U_i - U_{i-1}||_F / ||U_i||_F of the last

@@ -95,6 +95,9 @@ def load():
             "espnmf_batch_iterate": [P, i32, P, P, P],
             "espnmf_spmm_config": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
             "espnmf_spmm_frequent": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)],
+            "espnmf_save": [P, ctypes.c_char_p, ctypes.c_uint64],
+            "espnmf_load": [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i64)],
+            "espnmf_sweeps_done": [P, ctypes.POINTER(i64)],
             "espnmf_select_stats": [P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
             "espnmf_sequential": [ctypes.POINTER(_CSR), i32, i64, i64, i32, st, P, st, i32, P, P, P],
         }
@@ -123,7 +126,7 @@ def exported_symbols():
              "espnmf_pg_step", "espnmf_batch_init", "espnmf_batch_destroy",
              "espnmf_batch_ctx", "espnmf_batch_set_option", "espnmf_batch_iterate",
              "espnmf_spmm_config", "espnmf_spmm_frequent", "espnmf_select_stats",
-             "espnmf_sequential"]
+             "espnmf_sequential", "espnmf_save", "espnmf_load", "espnmf_sweeps_done"]
     return {n: hasattr(lib, n) for n in names}
 
 
@@ -352,6 +355,26 @@ def espnmf_spmm_config(ctx: Context, product: int):
     _check(load().espnmf_spmm_config(ctx.handle, int(product), ctypes.byref(g), ctypes.byref(c),
                                      ctypes.byref(m)), ctx.handle)
     return g.value, c.value, m.value
+
+
+def espnmf_save(ctx: Context, path: str, tag: int = 0):
+    """Writes the context's state (U, V, their Grams, the sweep count and
+    ``tag``) to ``path``."""
+    _check(load().espnmf_save(ctx.handle, os.fsencode(path), int(tag)), ctx.handle)
+
+
+def espnmf_load(ctx: Context, path: str):
+    """Restores a saved state into ``ctx``; returns (tag, sweeps)."""
+    tag, sw = ctypes.c_uint64(), ctypes.c_int64()
+    _check(load().espnmf_load(ctx.handle, os.fsencode(path), ctypes.byref(tag), ctypes.byref(sw)),
+           ctx.handle)
+    return tag.value, sw.value
+
+
+def espnmf_sweeps_done(ctx: Context) -> int:
+    sw = ctypes.c_int64()
+    _check(load().espnmf_sweeps_done(ctx.handle, ctypes.byref(sw)), ctx.handle)
+    return sw.value
 
 
 def espnmf_select_stats(ctx: Context):

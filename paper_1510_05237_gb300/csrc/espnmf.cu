@@ -136,6 +136,7 @@ struct espnmf_ctx {
     bool have_R = false;
     bool Y_is_AV = false;
     bool met_valid = false;
+    int64_t sweeps = 0;   // completed U updates (Alg. 2 sweeps) since init or load
 
     bool use_graph = true;
     // FP32 sparse-product launch shapes, [0] A V (rows of A), [1] A^T U
@@ -814,6 +815,7 @@ espnmf_status half_update(espnmf_ctx* ctx, bool updV)
         ctx->Y_is_AV = true;
         ctx->met_valid = true;
         ctx->have_R = true;
+        ++ctx->sweeps;
     }
     return ESPNMF_OK;
 }
@@ -828,12 +830,13 @@ espnmf_status enqueue_sweep(espnmf_ctx* ctx)
 struct HostState {
     int ucur, vcur;
     bool upend, vpend, uvalid, vvalid, have_R, Y_is_AV, met_valid;
+    int64_t sweeps;
 };
 
 HostState save_state(const espnmf_ctx* c)
 {
     return {c->U.cur, c->V.cur, c->U.chol_pending, c->V.chol_pending, c->U.valid, c->V.valid,
-            c->have_R, c->Y_is_AV, c->met_valid};
+            c->have_R, c->Y_is_AV, c->met_valid, c->sweeps};
 }
 
 void restore_state(espnmf_ctx* c, const HostState& s)
@@ -847,6 +850,7 @@ void restore_state(espnmf_ctx* c, const HostState& s)
     c->have_R = s.have_R;
     c->Y_is_AV = s.Y_is_AV;
     c->met_valid = s.met_valid;
+    c->sweeps = s.sweeps;
 }
 
 void drop_graphs(espnmf_ctx* ctx)
@@ -887,6 +891,7 @@ void after_sweep_state(espnmf_ctx* c)
     c->V.chol_pending = true;
     c->U.valid = c->V.valid = true;
     c->have_R = c->Y_is_AV = c->met_valid = true;
+    ++c->sweeps;
 }
 
 espnmf_status ensure_hist(espnmf_ctx* ctx, int need)
@@ -997,6 +1002,57 @@ espnmf_status ensure_product_for(espnmf_ctx* ctx, espnmf_which which)
         TRY(do_spmm(ctx, true, ctx->U.buf[ctx->U.cur]));
         ctx->Y_is_AV = false;
     }
+    return ESPNMF_OK;
+}
+
+// --- checkpoints -------------------------------------------------------------------
+
+// File layout (little-endian): the 8-byte magic, then the header fields in
+// the order of CkptHeader, the factors U (n x k) and V (m x k) dense
+// row-major in the context's arithmetic, the FP64 Gram matrices U^T U and
+// V^T V (k x k each), and an FNV-1a 64-bit checksum of everything before it.
+constexpr char kCkptMagic[8] = {'E', 'S', 'P', 'N', 'M', 'F', 'C', 'K'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+    uint32_t version;
+    uint32_t dtype;     // ESPNMF_F64 or ESPNMF_F32
+    int64_t n, m;
+    int32_t k, mode;
+    int64_t t_u, t_v;
+    int64_t sweeps;
+    uint64_t tag;
+    uint32_t v_valid;   // V holds a value (at least one V update ran)
+    uint32_t reserved;
+};
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t bytes)
+{
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < bytes; ++i) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+// Factor F as dense row-major bytes in the context's arithmetic (values as
+// stored, zeros included).
+espnmf_status factor_dense_host(espnmf_ctx* ctx, const Factor& F, std::vector<unsigned char>& out)
+{
+    const EllDev& E = F.buf[F.cur];
+    const int64_t rows = F.rows;
+    const int k = ctx->k, ld = E.ld;
+    const size_t es = ctx->esz;
+    std::vector<int32_t> cnt(rows), col((size_t)rows * ld);
+    std::vector<unsigned char> v((size_t)rows * ld * es);
+    CU(cudaMemcpy(cnt.data(), E.cnt, 4 * rows, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(col.data(), E.col, 4 * (size_t)rows * ld, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(v.data(), E.val, es * (size_t)rows * ld, cudaMemcpyDeviceToHost));
+    out.assign((size_t)rows * k * es, 0);
+    for (int64_t r = 0; r < rows; ++r)
+        for (int q = 0; q < cnt[r]; ++q)
+            memcpy(&out[((size_t)r * k + col[(size_t)r * ld + q]) * es], &v[((size_t)r * ld + q) * es], es);
     return ESPNMF_OK;
 }
 
@@ -1425,6 +1481,117 @@ espnmf_status espnmf_set_factor(espnmf_ctx* ctx, espnmf_which which, const void*
     if (which == ESPNMF_V) ctx->Y_is_AV = false;
     else ctx->have_R = false;
     return check_status(ctx);
+}
+
+espnmf_status espnmf_save(espnmf_ctx* ctx, const char* path, uint64_t tag)
+{
+    TRY(enter(ctx));
+    if (!path) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "path is NULL");
+    if (!ctx->U.valid) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "U has no value");
+    TRY(check_status(ctx));
+    CkptHeader h = {};
+    h.version = kCkptVersion;
+    h.dtype = (uint32_t)ctx->dt;
+    h.n = ctx->n;
+    h.m = ctx->m;
+    h.k = ctx->k;
+    h.mode = ctx->mode;
+    h.t_u = ctx->t_u;
+    h.t_v = ctx->t_v;
+    h.sweeps = ctx->sweeps;
+    h.tag = tag;
+    h.v_valid = ctx->V.valid ? 1u : 0u;
+    std::vector<unsigned char> Ub, Vb;
+    TRY(factor_dense_host(ctx, ctx->U, Ub));
+    if (ctx->V.valid) TRY(factor_dense_host(ctx, ctx->V, Vb));
+    else Vb.assign((size_t)ctx->m * ctx->k * ctx->esz, 0);
+    const size_t kk = (size_t)ctx->k * ctx->k;
+    std::vector<double> GU(kk), GV(kk, 0.0);
+    CU(cudaMemcpy(GU.data(), ctx->U.G, 8 * kk, cudaMemcpyDeviceToHost));
+    if (ctx->V.valid) CU(cudaMemcpy(GV.data(), ctx->V.G, 8 * kk, cudaMemcpyDeviceToHost));
+    uint64_t sum = 0xcbf29ce484222325ull;
+    sum = fnv1a(sum, kCkptMagic, sizeof kCkptMagic);
+    sum = fnv1a(sum, &h, sizeof h);
+    sum = fnv1a(sum, Ub.data(), Ub.size());
+    sum = fnv1a(sum, Vb.data(), Vb.size());
+    sum = fnv1a(sum, GU.data(), 8 * kk);
+    sum = fnv1a(sum, GV.data(), 8 * kk);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "cannot open %s for writing", tmp.c_str());
+    bool ok = fwrite(kCkptMagic, sizeof kCkptMagic, 1, f) == 1 && fwrite(&h, sizeof h, 1, f) == 1 &&
+              fwrite(Ub.data(), 1, Ub.size(), f) == Ub.size() &&
+              fwrite(Vb.data(), 1, Vb.size(), f) == Vb.size() &&
+              fwrite(GU.data(), 8, kk, f) == kk && fwrite(GV.data(), 8, kk, f) == kk &&
+              fwrite(&sum, sizeof sum, 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "writing %s failed", path);
+    }
+    return ESPNMF_OK;
+}
+
+espnmf_status espnmf_load(espnmf_ctx* ctx, const char* path, uint64_t* tag, int64_t* sweeps)
+{
+    TRY(enter(ctx));
+    if (!path) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "path is NULL");
+    FILE* f = fopen(path, "rb");
+    if (!f) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "cannot open %s", path);
+    char magic[8] = {};
+    CkptHeader h = {};
+    const bool head_ok = fread(magic, sizeof magic, 1, f) == 1 && fread(&h, sizeof h, 1, f) == 1 &&
+                         memcmp(magic, kCkptMagic, sizeof magic) == 0;
+    auto bad = [&](const char* why) {
+        fclose(f);
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "%s: %s", path, why);
+    };
+    if (!head_ok) return bad("not a checkpoint of this library");
+    if (h.version != kCkptVersion) return bad("unsupported checkpoint version");
+    if (h.dtype != (uint32_t)ctx->dt || h.n != ctx->n || h.m != ctx->m || h.k != ctx->k ||
+        h.mode != ctx->mode || h.t_u != ctx->t_u || h.t_v != ctx->t_v)
+        return bad("saved by a context of another shape, mode, t or arithmetic");
+    const size_t es = ctx->esz, kk = (size_t)ctx->k * ctx->k;
+    std::vector<unsigned char> Ub((size_t)h.n * h.k * es), Vb((size_t)h.m * h.k * es);
+    std::vector<double> GU(kk), GV(kk);
+    uint64_t stored = 0;
+    const bool body_ok = fread(Ub.data(), 1, Ub.size(), f) == Ub.size() &&
+                         fread(Vb.data(), 1, Vb.size(), f) == Vb.size() &&
+                         fread(GU.data(), 8, kk, f) == kk && fread(GV.data(), 8, kk, f) == kk &&
+                         fread(&stored, sizeof stored, 1, f) == 1;
+    if (!body_ok) return bad("truncated");
+    fclose(f);
+    uint64_t sum = 0xcbf29ce484222325ull;
+    sum = fnv1a(sum, kCkptMagic, sizeof kCkptMagic);
+    sum = fnv1a(sum, &h, sizeof h);
+    sum = fnv1a(sum, Ub.data(), Ub.size());
+    sum = fnv1a(sum, Vb.data(), Vb.size());
+    sum = fnv1a(sum, GU.data(), 8 * kk);
+    sum = fnv1a(sum, GV.data(), 8 * kk);
+    if (sum != stored) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "%s: checksum mismatch", path);
+    // the factors as stored (their Grams are then replaced by the saved
+    // ones, so that the next sweep repeats the uninterrupted run exactly)
+    drop_graphs(ctx);
+    TRY(set_factor_impl(ctx, ctx->U, Ub.data(), ctx->dt, 0));
+    if (h.v_valid) TRY(set_factor_impl(ctx, ctx->V, Vb.data(), ctx->dt, 0));
+    CU(cudaMemcpyAsync(ctx->U.G, GU.data(), 8 * kk, cudaMemcpyHostToDevice, ctx->st));
+    if (h.v_valid) CU(cudaMemcpyAsync(ctx->V.G, GV.data(), 8 * kk, cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    ctx->V.valid = h.v_valid != 0;
+    ctx->met_valid = false;
+    ctx->Y_is_AV = false;
+    ctx->have_R = false;
+    ctx->sweeps = h.sweeps;
+    if (tag) *tag = h.tag;
+    if (sweeps) *sweeps = h.sweeps;
+    return check_status(ctx);
+}
+
+espnmf_status espnmf_sweeps_done(espnmf_ctx* ctx, int64_t* sweeps)
+{
+    TRY(enter(ctx));
+    if (sweeps) *sweeps = ctx->sweeps;
+    return ESPNMF_OK;
 }
 
 espnmf_status espnmf_residual(espnmf_ctx* ctx, double* R)

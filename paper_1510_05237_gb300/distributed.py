@@ -11,24 +11,27 @@ other factor, and three exchanges:
   * its Gram matrix: a sum of the slabs' Grams (all-reduce, FP64);
   * the enforcement: the global top-t of a column lies inside the union of
     the ranks' local top-t, so each rank selects its local top-t, the
-    candidates are all-gathered in global row order, the same selection is
-    run again on the union (identical on every rank), and each rank keeps
-    those of its candidates that survive.  Ties go to the lower global row,
-    as in the single-GPU selector, because the union is laid out in global
-    row order.
+    candidates (global row index and row values, gathered separately) are
+    all-gathered in global row order, the same selection is run again on the
+    union (identical on every rank), and each rank keeps those of its
+    candidates that survive.  Ties go to the lower global row, as in the
+    single-GPU selector, because the union is laid out in global row order.
 
-The residual and the error need only sums of per-slab scalars (all-reduce).
+The residual and the error need only sums of per-slab scalars (all-reduce)
+and are finished with tensor operations on the same device.
 
-The local steps (sparse product, solve and projection, selection) are passed
-in as functions: on GPU ranks they are the library's kernels (the selection
-defaults to ``espnmf_enforce_topt_buffer``); the collectives come from
-``torch.distributed`` (NCCL on GPUs, gloo on CPUs).
+Every function takes and returns torch tensors and keeps them on their
+device: CUDA tensors with the NCCL backend on GPU ranks (no host round
+trip), CPU tensors with gloo.  The local steps (sparse product, solve and
+projection, selection) are passed in as functions: on GPU ranks they are the
+library's kernels (the selection defaults to ``espnmf_enforce_topt_buffer``
+on the device tensor); the collectives come from ``torch.distributed``.
 """
 from __future__ import annotations
 
 from typing import Callable, Sequence
 
-import numpy as np
+import torch
 
 
 def slab(total: int, world: int, rank: int) -> tuple[int, int]:
@@ -43,64 +46,59 @@ def _dist():
     return dist
 
 
-def allreduce_sum(x: np.ndarray) -> np.ndarray:
-    """Sum over ranks (FP64 arrays stay FP64)."""
-    import torch
-    t = torch.from_numpy(np.ascontiguousarray(x)).clone()
+def allreduce_sum(x: torch.Tensor) -> torch.Tensor:
+    """Sum over ranks, on x's device and in x's dtype (a new tensor)."""
+    t = x.contiguous().clone()
     _dist().all_reduce(t)
-    return t.numpy()
+    return t
 
 
-def allgather_rows(local: np.ndarray, world: int) -> np.ndarray:
-    """Concatenation of every rank's rows, in rank order."""
-    import torch
+def allgather_rows(local: torch.Tensor, world: int) -> torch.Tensor:
+    """Concatenation of every rank's rows, in rank order, on local's device."""
     dist = _dist()
-    t = torch.from_numpy(np.ascontiguousarray(local))
-    sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
-    dist.all_gather(sizes, torch.tensor([t.shape[0]], dtype=torch.int64))
-    cap = int(max(int(s) for s in sizes))
-    pad = torch.zeros((cap,) + tuple(t.shape[1:]), dtype=t.dtype)
+    t = local.contiguous()
+    dev = t.device
+    sizes = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
+    dist.all_gather(sizes, torch.tensor([t.shape[0]], dtype=torch.int64, device=dev))
+    counts = [int(s) for s in torch.cat(sizes).cpu()]   # world integers: the slab sizes
+    cap = max(counts)
+    pad = torch.zeros((cap,) + tuple(t.shape[1:]), dtype=t.dtype, device=dev)
     pad[: t.shape[0]] = t
     parts = [torch.zeros_like(pad) for _ in range(world)]
     dist.all_gather(parts, pad)
-    return np.concatenate([p[: int(s)].numpy() for p, s in zip(parts, sizes)], axis=0)
+    return torch.cat([p[:c] for p, c in zip(parts, counts)], dim=0)
 
 
-def default_select(X: np.ndarray, t: int) -> np.ndarray:
-    """Per-column top-t of a projected candidate with the library's selector
-    (lower row index wins ties); X is rows x k, returned enforced."""
-    import torch
+def default_select(X: torch.Tensor, t: int) -> torch.Tensor:
+    """Per-column top-t of a projected candidate (rows x k CUDA tensor) with
+    the library's selector, in place on the device (lower row wins ties)."""
     from . import binding as B
-    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
-    B.espnmf_enforce_topt_buffer(Xd, t, B.TOPT_COLUMN)
-    torch.cuda.synchronize()
-    return Xd.cpu().numpy()
+    B.espnmf_enforce_topt_buffer(X, t, B.TOPT_COLUMN)
+    return X
 
 
-def global_topt(X_local: np.ndarray, row0: int, t: int, world: int,
-                select: Callable[[np.ndarray, int], np.ndarray] = default_select) -> np.ndarray:
+def global_topt(X_local: torch.Tensor, row0: int, t: int, world: int,
+                select: Callable[[torch.Tensor, int], torch.Tensor] = default_select) -> torch.Tensor:
     """Exact per-column top-t of the row-sharded projected candidate whose
     rows [row0, row0 + len) this rank holds; returns this rank's enforced
     rows."""
-    k = X_local.shape[1]
-    mine = select(X_local.copy(), t)                     # local top-t (superset of the final)
-    rows = np.flatnonzero((mine != 0).any(axis=1))
-    cand = np.concatenate([(rows + row0)[:, None].astype(np.float64), mine[rows]], axis=1)
-    union = allgather_rows(cand, world)                  # global row order (slabs ascend)
-    kept = select(union[:, 1:].copy(), t)                # the same on every rank
-    out = np.zeros_like(X_local)
-    grows = union[:, 0].astype(np.int64)
-    here = (grows >= row0) & (grows < row0 + X_local.shape[0])
-    out[grows[here] - row0] = kept[here]
-    assert out.shape[1] == k
+    mine = select(X_local.clone(), t)                    # local top-t (superset of the final)
+    rows = torch.nonzero((mine != 0).any(dim=1)).flatten()
+    grow = allgather_rows(rows + row0, world)            # global row order (slabs ascend)
+    union = allgather_rows(mine[rows], world)
+    kept = select(union.clone(), t)                      # the same on every rank
+    out = torch.zeros_like(X_local)
+    here = (grow >= row0) & (grow < row0 + X_local.shape[0])
+    out[grow[here] - row0] = kept[here]
     return out
 
 
-def sharded_half_update(product_rows: Callable[[np.ndarray], np.ndarray],
-                        gram: Callable[[np.ndarray], np.ndarray],
-                        solve_project: Callable[[np.ndarray, np.ndarray], np.ndarray],
-                        other_local: np.ndarray, row0: int, t: int, world: int,
-                        select: Callable[[np.ndarray, int], np.ndarray] = default_select) -> np.ndarray:
+def sharded_half_update(product_rows: Callable[[torch.Tensor], torch.Tensor],
+                        gram: Callable[[torch.Tensor], torch.Tensor],
+                        solve_project: Callable[[torch.Tensor, torch.Tensor], torch.Tensor],
+                        other_local: torch.Tensor, row0: int, t: int, world: int,
+                        select: Callable[[torch.Tensor, int], torch.Tensor] = default_select
+                        ) -> torch.Tensor:
     """One half-step of Alg. 2 on this rank's slab.
 
     product_rows(O): this slab's rows of A^T O (or A O) from the full other
@@ -113,16 +111,21 @@ def sharded_half_update(product_rows: Callable[[np.ndarray], np.ndarray],
     return global_topt(X, row0, t, world, select)
 
 
-def sharded_measures(d2_local: float, u2_local: float, cross_local: float,
-                     a2_local: float, G_U: np.ndarray, G_V: np.ndarray) -> tuple[float, float]:
-    """R and E (Sec. 3.1) from per-slab sums: d2 = ||U_new - U_old||^2,
-    u2 = ||U_new||^2, cross = <U, A V>, a2 = ||A||^2 over the slab's rows;
-    E^2 ||A||^2 = ||A||^2 - 2 <U, A V> + <U^T U, V^T V>."""
-    s = allreduce_sum(np.array([d2_local, u2_local, cross_local, a2_local], dtype=np.float64))
-    d2, u2, cross, a2 = (float(v) for v in s)
-    R = 0.0 if u2 == 0.0 and d2 == 0.0 else (float("inf") if u2 == 0.0 else float(np.sqrt(d2 / u2)))
-    f = a2 - 2.0 * cross + float(np.sum(G_U * G_V))
-    E = 0.0 if a2 == 0.0 else float(np.sqrt(max(f, 0.0)) / np.sqrt(a2))
+def sharded_measures(sums_local: torch.Tensor, G_U: torch.Tensor,
+                     G_V: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+    """R and E (Sec. 3.1) from per-slab FP64 sums [d2, u2, cross, a2]:
+    d2 = ||U_new - U_old||^2, u2 = ||U_new||^2, cross = <U, A V>, a2 = ||A||^2
+    over the slab's rows; E^2 ||A||^2 = ||A||^2 - 2 <U, A V> + <U^T U, V^T V>.
+    Returns two 0-d tensors on the sums' device."""
+    s = allreduce_sum(sums_local.to(torch.float64))
+    d2, u2, cross, a2 = s[0], s[1], s[2], s[3]
+    zero = torch.zeros((), dtype=torch.float64, device=s.device)
+    inf = torch.full((), float("inf"), dtype=torch.float64, device=s.device)
+    R = torch.where(u2 == 0, torch.where(d2 == 0, zero, inf),
+                    torch.sqrt(d2 / torch.where(u2 == 0, torch.ones_like(u2), u2)))
+    f = a2 - 2.0 * cross + torch.sum(G_U.to(torch.float64) * G_V.to(torch.float64))
+    E = torch.where(a2 == 0, zero,
+                    torch.sqrt(torch.clamp(f, min=0.0)) / torch.sqrt(torch.where(a2 == 0, torch.ones_like(a2), a2)))
     return R, E
 
 

@@ -24,6 +24,11 @@ def _free_port() -> int:
         return s.getsockname()[1]
 
 
+def _np(fn):
+    """An oracle step (numpy in, numpy out) as a step on CPU tensors."""
+    return lambda *ts: torch.from_numpy(np.ascontiguousarray(fn(*(t.numpy() for t in ts))))
+
+
 def _sweep_rank(rank, world, port, A, U0, t_u, t_v, out_dir):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -31,30 +36,32 @@ def _sweep_rank(rank, world, port, A, U0, t_u, t_v, out_dir):
     try:
         r0, r1 = D.slab(A.n, world, rank)      # my terms: rows of U
         d0, d1 = D.slab(A.m, world, rank)      # my documents: rows of V
-        k = U0.shape[1]
-        solve_project = lambda Y, G: oracle.project(oracle.ls_solve(Y, G))  # noqa: E731
+        T = lambda a: torch.from_numpy(np.ascontiguousarray(a))  # noqa: E731
+        solve_project = _np(lambda Y, G: oracle.project(oracle.ls_solve(Y, G)))
+        gram, topt = _np(oracle.gram), lambda X, t: _np(lambda x: oracle.topt(x, t))(X)
         # V half: my rows of A^T U from the gathered U
-        V_loc = D.sharded_half_update(lambda U: oracle.spmm_At(A, U)[d0:d1], oracle.gram,
-                                      solve_project, U0[r0:r1], d0, t_v, world, oracle.topt)
+        V_loc = D.sharded_half_update(_np(lambda U: oracle.spmm_At(A, U)[d0:d1]), gram,
+                                      solve_project, T(U0[r0:r1]), d0, t_v, world, topt)
         # U half: my rows of A V
         AV = {}
 
         def prod_U(V):
-            AV["Y"] = oracle.spmm_A(A, V)[r0:r1]
-            AV["V"] = V
-            return AV["Y"]
+            AV["Y"] = oracle.spmm_A(A, V.numpy())[r0:r1]
+            return T(AV["Y"])
 
-        U_loc = D.sharded_half_update(prod_U, oracle.gram, solve_project, V_loc, r0, t_u,
-                                      world, oracle.topt)
-        G_U = D.allreduce_sum(oracle.gram(U_loc))
-        G_V = D.allreduce_sum(oracle.gram(V_loc))
+        U_loc = D.sharded_half_update(prod_U, gram, solve_project, V_loc, r0, t_u,
+                                      world, topt)
+        G_U = D.allreduce_sum(gram(U_loc))
+        G_V = D.allreduce_sum(gram(V_loc))
         rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
         a2 = float(np.sum(A.val[(rows >= r0) & (rows < r1)] ** 2))
-        R, E = D.sharded_measures(float(np.sum((U_loc - U0[r0:r1]) ** 2)),
-                                  float(np.sum(U_loc ** 2)), float(np.sum(U_loc * AV["Y"])),
-                                  a2, G_U, G_V)
-        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), U=U_loc, V=V_loc, R=R, E=E,
-                 r=np.array([r0, r1, d0, d1]))
+        Un = U_loc.numpy()
+        sums = T(np.array([np.sum((Un - U0[r0:r1]) ** 2), np.sum(Un ** 2),
+                           np.sum(Un * AV["Y"]), a2], dtype=np.float64))
+        R, E = D.sharded_measures(sums, G_U, G_V)
+        assert R.dim() == 0 and E.dim() == 0 and R.dtype == torch.float64
+        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), U=Un, V=V_loc.numpy(), R=float(R),
+                 E=float(E), r=np.array([r0, r1, d0, d1]))
     finally:
         dist.destroy_process_group()
 
