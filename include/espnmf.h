@@ -114,9 +114,12 @@ typedef struct espnmf_ctx espnmf_ctx;
  *            as given).
  *   stream   a cudaStream_t for all of the context's work, or NULL to let
  *            the context create its own.
- * The context builds on the device: A in two sliced-ELLPACK layouts (rows
- * of A and rows of A^T), U0 in the row-packed sparse factor layout, and
- * the FP64 Gram U0^T U0. */
+ * A is brought to the host (copied back first when it is on the device),
+ * validated there, and laid out by host code: its transpose, the two
+ * sliced-ELLPACK layouts (rows of A and rows of A^T) with their
+ * frequent-row parts; the layouts are then uploaded.  U0 is placed in the
+ * row-packed sparse factor layout and its FP64 Gram U0^T U0 formed on the
+ * device.  The call synchronises; its cost grows with nnz (host work). */
 espnmf_status espnmf_init(espnmf_ctx **out, const espnmf_csr *A, int32_t k,
                           int64_t t_u, int64_t t_v, espnmf_topt_mode mode,
                           espnmf_dtype compute, const void *U0,
@@ -187,14 +190,16 @@ espnmf_status espnmf_set_factor(espnmf_ctx *ctx, espnmf_which which,
  * atomically through `path`.tmp): format version, n, m, k, t_u, t_v, mode,
  * arithmetic, the number of completed sweeps, the caller's 64-bit `tag`
  * (e.g. the seed of the initial guess), U and V dense row-major in the
- * context's arithmetic, the FP64 Gram matrices U^T U and V^T V, and a
- * checksum.  A is not saved.  Synchronises. */
+ * context's arithmetic, the FP64 Gram matrices U^T U and V^T V, each
+ * factor's last selection thresholds (the FP32 form's selector starts
+ * from them, and they decide how it groups the Gram diagonal's partial
+ * sums), and a checksum.  A is not saved.  Synchronises. */
 espnmf_status espnmf_save(espnmf_ctx *ctx, const char *path, uint64_t tag);
 
 /* espnmf_load -- restores a state written by espnmf_save into a context
  * made by espnmf_init from the same A with the same k, t_u, t_v, mode and
- * arithmetic (any U0 of the right shape): U, V, their Gram matrices and the
- * sweep count.  The sweeps that follow repeat, bit for bit, those of the
+ * arithmetic (any U0 of the right shape): U, V, their Gram matrices, the
+ * selection thresholds and the sweep count.  The sweeps that follow repeat, bit for bit, those of the
  * context that saved the state.  tag and sweeps (may be NULL) receive the
  * saved tag and sweep count.  A file of another shape, mode, t or
  * arithmetic, a truncated file or a checksum mismatch gives
@@ -287,7 +292,11 @@ typedef enum {
      * for every shape):
      *   ESPNMF_OPT_SPMM_TUNE 1 (default): before its first captured sweep,
      *     espnmf_iterate times the candidate shapes on the current factors
-     *     and keeps the fastest for each product (A V and A^T U); 0: fixed.
+     *     and keeps the fastest for each product (A V and A^T U); the picks
+     *     are remembered for the process by shape class (factor width, log2
+     *     of the output rows and of the entries per row, frequent part or
+     *     not), and later contexts of the same class reuse them without
+     *     timing; 0: fixed.
      *   ESPNMF_OPT_SPMM_SPLIT: 1, 2 or 4 warps share a slice's output
      *     columns (k >= 13 for more than 1); sets both products and turns
      *     tuning off.
@@ -301,7 +310,15 @@ typedef enum {
     ESPNMF_OPT_SPMM_TUNE = 3,
     ESPNMF_OPT_SPMM_SPLIT = 4,
     ESPNMF_OPT_SPMM_CARVEOUT = 5,
-    ESPNMF_OPT_SPMM_MASK = 6
+    ESPNMF_OPT_SPMM_MASK = 6,
+    /* FP32 form, k <= 64: 1 adds one step of iterative refinement to every
+     * row solve X = Y G^-1: the residual R = Y - X G (G as an FP32 pair of
+     * about 48 bits, products split exactly, compensated sums) is solved
+     * with the same Cholesky factor and added before the projection, which
+     * brings X to the FP64 solution of the FP32 system rounded to FP32
+     * (within an ulp or two while cond(G) is well below 2^12).  0 (default):
+     * no refinement. */
+    ESPNMF_OPT_REFINE = 8
 } espnmf_option;
 
 espnmf_status espnmf_set_option(espnmf_ctx *ctx, espnmf_option opt,
@@ -372,6 +389,26 @@ espnmf_status espnmf_launches_per_sweep(espnmf_ctx *ctx, int32_t *count);
 
 /* espnmf_sync -- waits for the context's stream; reports device errors. */
 espnmf_status espnmf_sync(espnmf_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Stand-alone solve                                                        */
+
+/* espnmf_solve_gram -- the k x k solve of Alg. 2 steps 1 and 3 on a caller's
+ * buffers: X = Y G^-1 row by row, unprojected, as the FP32 form computes it
+ * (FP64 Cholesky factor of G, FP32 substitutions), with one step of
+ * iterative refinement when refine != 0 (see ESPNMF_OPT_REFINE).
+ *   Y  rows x k FP32 row-major device matrix (leading dimension ldy >= k).
+ *   G  k x k FP64 row-major device matrix, symmetric positive semi-definite;
+ *      an index j with G_jj = 0 is dropped (column j of X is 0), any other
+ *      pivot at or below 64 eps max G_jj gives ESPNMF_ERR_SINGULAR.
+ *   X  rows x k FP32 row-major device output (leading dimension ldx >= k).
+ * 1 <= k <= 64.  Scratch comes from the stream-ordered allocator and is
+ * freed before the call returns.  Enqueued on `stream` (NULL: legacy
+ * default stream); synchronises it; failures are described by
+ * espnmf_last_error(NULL). */
+espnmf_status espnmf_solve_gram(const void *Y, int64_t rows, int32_t k, int64_t ldy,
+                                const double *G, void *X, int64_t ldx, int32_t refine,
+                                void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Stand-alone selector                                                     */

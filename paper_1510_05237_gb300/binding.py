@@ -28,6 +28,7 @@ U, V = 0, 1
 DENSE_ROWMAJOR, CSC, CSR = 0, 1, 2
 OPT_USE_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT = 0, 1, 2
 OPT_SPMM_TUNE, OPT_SPMM_SPLIT, OPT_SPMM_CARVEOUT, OPT_SPMM_MASK = 3, 4, 5, 6
+OPT_REFINE = 8
 
 
 class EspnmfError(RuntimeError):
@@ -96,6 +97,7 @@ def load():
             "espnmf_spmm_config": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
             "espnmf_spmm_frequent": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)],
             "espnmf_save": [P, ctypes.c_char_p, ctypes.c_uint64],
+            "espnmf_solve_gram": [P, i64, i32, i64, P, P, i64, i32, P],
             "espnmf_load": [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i64)],
             "espnmf_sweeps_done": [P, ctypes.POINTER(i64)],
             "espnmf_select_stats": [P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
@@ -126,7 +128,8 @@ def exported_symbols():
              "espnmf_pg_step", "espnmf_batch_init", "espnmf_batch_destroy",
              "espnmf_batch_ctx", "espnmf_batch_set_option", "espnmf_batch_iterate",
              "espnmf_spmm_config", "espnmf_spmm_frequent", "espnmf_select_stats",
-             "espnmf_sequential", "espnmf_save", "espnmf_load", "espnmf_sweeps_done"]
+             "espnmf_sequential", "espnmf_save", "espnmf_load", "espnmf_sweeps_done",
+             "espnmf_solve_gram"]
     return {n: hasattr(lib, n) for n in names}
 
 
@@ -355,6 +358,21 @@ def espnmf_spmm_config(ctx: Context, product: int):
     _check(load().espnmf_spmm_config(ctx.handle, int(product), ctypes.byref(g), ctypes.byref(c),
                                      ctypes.byref(m)), ctx.handle)
     return g.value, c.value, m.value
+
+
+def espnmf_solve_gram(Y, G, refine: bool = False, stream=None):
+    """X = Y G^-1 (unprojected) for a CUDA float32 Y (rows x k) and a CUDA
+    float64 G (k x k), with one refinement step when ``refine``."""
+    import torch
+    rows, k = Y.shape
+    Gc = G.contiguous()
+    X = torch.empty((rows, k), dtype=torch.float32, device=Y.device)
+    st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(load().espnmf_solve_gram(ctypes.c_void_p(Y.data_ptr()), rows, k, Y.stride(0),
+                                    ctypes.c_void_p(Gc.data_ptr()),
+                                    ctypes.c_void_p(X.data_ptr()), k, int(bool(refine)),
+                                    ctypes.c_void_p(st)))
+    return X
 
 
 def espnmf_save(ctx: Context, path: str, tag: int = 0):

@@ -331,10 +331,21 @@ cudaError_t launch_gram_inverse(const double* G, int k, double* Ginv64, T* GinvT
 // then the reciprocal diagonal, KP) and the row solves X = Y G^-1 by
 // substitution, projected and written column-major.
 cudaError_t launch_cholesky(const double* G, int k, int KP, float* Ls, float* LTs, float* rd,
-                            unsigned* status, cudaStream_t st);
+                            unsigned* status, cudaStream_t st, float* Gh = nullptr,
+                            float* Gl = nullptr);
+// One step of iterative refinement (k_chol.cu): Xt holds x0 from
+// launch_solve_chol with project = false; Gh, Gl the FP32 pair of G that
+// launch_cholesky writes when given them.  Writes x0 + d projected into Xt,
+// or (raw) unprojected row-major into out; with correct = false, d = 0
+// (x0 only, e.g. to write it row-major).
+cudaError_t launch_refine(const float* Y, int64_t ldy, const float* Yt, int64_t ldyt, int64_t rows,
+                          int k, int KP, const float* L, const float* rd, const float* Gh,
+                          const float* Gl, float* Xt, int64_t ldx, float* out, int64_t ldo,
+                          bool raw, bool correct, unsigned* status, cudaStream_t st, int sm_count);
 cudaError_t launch_solve_chol(const float* Y, int64_t ldy, int64_t rows, int k, int KP,
                               const float* L, const float* LT, const float* rd, float* Xt,
-                              int64_t ldx, unsigned* status, cudaStream_t st, int sm_count);
+                              int64_t ldx, unsigned* status, cudaStream_t st, int sm_count,
+                              bool project = true);
 cudaError_t setup_chol();
 
 // Alg. 3 (sequential ALS), rank-1 new topic: g = G1^T f over the first k1
@@ -393,7 +404,7 @@ void set_thread_error(const char* msg);
 enum KernelKind : int {
     K_SPMM = 0, K_SPMM_T, K_COMBINE, K_SOLVE, K_SELECT, K_EMIT, K_GRAM_REDUCE,
     K_INVERSE, K_TO_COLMAJOR, K_NORM2, K_DOT, K_SCATTER, K_GRAD, K_LAMBDA, K_PG,
-    K_SPMM_H, K_SPMM_H_T, K_GRAM_TABLE, K_COUNT
+    K_SPMM_H, K_SPMM_H_T, K_GRAM_TABLE, K_REFINE, K_COUNT
 };
 const char* kernel_name(int kind);
 

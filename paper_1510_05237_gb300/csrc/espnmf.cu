@@ -15,8 +15,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/espnmf.h"
@@ -31,7 +33,7 @@ const char* kernel_name(int kind)
                                          "select_topt", "emit", "gram_reduce",
                                          "gram_inverse", "to_colmajor", "norm2", "ell_dot",
                                          "scatter", "grad", "lambda_max", "pg_apply",
-                                         "spmm_freq_AV", "spmm_freq_AtU", "gram_table"};
+                                         "spmm_freq_AV", "spmm_freq_AtU", "gram_table", "refine"};
     return kind >= 0 && kind < K_COUNT ? names[kind] : "?";
 }
 }  // namespace espnmf
@@ -137,6 +139,7 @@ struct espnmf_ctx {
     bool Y_is_AV = false;
     bool met_valid = false;
     int64_t sweeps = 0;   // completed U updates (Alg. 2 sweeps) since init or load
+    bool refine = false;  // FP32 form (Cholesky path): one refinement step of each solve
 
     bool use_graph = true;
     // FP32 sparse-product launch shapes, [0] A V (rows of A), [1] A^T U
@@ -571,10 +574,44 @@ void drop_graphs(espnmf_ctx* ctx);
 // Times every FP32 launch shape of both sparse products on the current
 // factors (each shape gives bitwise the same Y) and keeps the fastest.
 // Leaves Y = A V, as the last U update did.
+// The tuner's picks, kept for the process and keyed by the product's shape
+// class (the factor width, log2 of the output rows and of the entries per
+// row, whether the product has a frequent part and whether the bitmask can
+// be staged), so that contexts of the same class skip the timing.
+struct TuneKey {
+    int ld, lrows, ldens, freq, smask;
+    bool operator<(const TuneKey& o) const
+    {
+        return std::tie(ld, lrows, ldens, freq, smask) < std::tie(o.ld, o.lrows, o.ldens, o.freq, o.smask);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, SpmmConfig> g_tune_cache;
+
+TuneKey tune_key(const espnmf_ctx* ctx, int o)
+{
+    const SellDev& S = o ? ctx->sAt : ctx->sA;
+    const int64_t rows = std::max<int64_t>(S.rows, 1);
+    auto lg = [](double x) { return x < 1.0 ? 0 : (int)std::floor(std::log2(x)); };
+    const int64_t gathered = o ? ctx->n : ctx->m;
+    return {(int)ctx->ldy, lg((double)rows), lg(4.0 * (double)ctx->nnz / (double)rows),
+            S.h > 0 ? 1 : 0, gathered > 32ll * kSellSmemMaskWords ? 0 : 1};
+}
+
 espnmf_status tune_spmm(espnmf_ctx* ctx)
 {
     ctx->spmm_tuned = true;
     if (is_f64(ctx)) return ESPNMF_OK;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto a = g_tune_cache.find(tune_key(ctx, 0)), b = g_tune_cache.find(tune_key(ctx, 1));
+        if (a != g_tune_cache.end() && b != g_tune_cache.end()) {
+            ctx->spmm_cfg[0] = a->second;
+            ctx->spmm_cfg[1] = b->second;
+            drop_graphs(ctx);
+            return ESPNMF_OK;
+        }
+    }
     std::vector<SpmmConfig> cands;
     for (int sp : {1, 2, 4}) {
         if (sp > 1 && ctx->ldy < 16) continue;
@@ -622,6 +659,11 @@ espnmf_status tune_spmm(espnmf_ctx* ctx)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     TRY(st);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[tune_key(ctx, 0)] = ctx->spmm_cfg[0];
+        g_tune_cache[tune_key(ctx, 1)] = ctx->spmm_cfg[1];
+    }
     drop_graphs(ctx);
     TRY(do_spmm(ctx, false, ctx->V.buf[ctx->V.cur]));
     ctx->Y_is_AV = true;
@@ -635,8 +677,9 @@ espnmf_status do_gram_inverse(espnmf_ctx* ctx, Factor& F, cudaStream_t s)
     if (use_cholesky(ctx)) {
         const int KP = (int)ctx->ldy;
         return run(ctx, K_INVERSE, (double)ctx->k * ctx->k * 8.0 + 2.0 * KP * KP * 4.0, s, [&] {
+            float* gh = F.Lf + 2 * KP * KP + KP;   // G as an FP32 pair, for the refinement
             return launch_cholesky(F.G, ctx->k, KP, F.Lf, F.Lf + KP * KP, F.Lf + 2 * KP * KP,
-                                   ctx->status_d, s);
+                                   ctx->status_d, s, gh, gh + KP * KP);
         });
     }
     const double bytes = (double)ctx->k * ctx->k * (8.0 + 8.0 + ctx->esz);
@@ -790,7 +833,8 @@ espnmf_status half_update(espnmf_ctx* ctx, bool updV)
             const int KP = (int)ctx->ldy;
             return launch_solve_chol((const float*)ctx->Y, ctx->ldy, rows, ctx->k, KP, O.Lf,
                                      O.Lf + KP * KP, O.Lf + 2 * KP * KP, (float*)ctx->Xt,
-                                     ctx->ldx, ctx->status_d, ctx->st, ctx->sm_count);
+                                     ctx->ldx, ctx->status_d, ctx->st, ctx->sm_count,
+                                     !ctx->refine);
         }
         return is_f64(ctx) ? launch_solve<double>((const double*)ctx->Y, ctx->ldy, rows, ctx->k,
                                                   (const double*)O.GinvT, (double*)ctx->Xt,
@@ -799,6 +843,16 @@ espnmf_status half_update(espnmf_ctx* ctx, bool updV)
                                                  (const float*)O.GinvT, (float*)ctx->Xt, ctx->ldx,
                                                  ctx->status_d, ctx->st, ctx->sm_count);
     }));
+    if (use_cholesky(ctx) && ctx->refine) {
+        // one step of iterative refinement of the solve (projects at the end)
+        const int KP = (int)ctx->ldy;
+        const float* gh = O.Lf + 2 * KP * KP + KP;
+        TRY(run(ctx, K_REFINE, (double)rows * ctx->k * ctx->esz * 3.0, ctx->st, [&] {
+            return launch_refine((const float*)ctx->Y, ctx->ldy, nullptr, 0, rows, ctx->k, KP, O.Lf,
+                                 O.Lf + 2 * KP * KP, gh, gh + KP * KP, (float*)ctx->Xt, ctx->ldx,
+                                 nullptr, 0, false, true, ctx->status_d, ctx->st, ctx->sm_count);
+        }));
+    }
     const int64_t t = updV ? ctx->t_v : ctx->t_u;
     if (survivor_path(ctx)) {
         TRY(do_select(ctx, rows, t, true, F.sel_hint));
@@ -1010,7 +1064,10 @@ espnmf_status ensure_product_for(espnmf_ctx* ctx, espnmf_which which)
 // File layout (little-endian): the 8-byte magic, then the header fields in
 // the order of CkptHeader, the factors U (n x k) and V (m x k) dense
 // row-major in the context's arithmetic, the FP64 Gram matrices U^T U and
-// V^T V (k x k each), and an FNV-1a 64-bit checksum of everything before it.
+// V^T V (k x k each), each factor's last selection thresholds (k 8-byte
+// keys each; they decide how the selector groups the Gram diagonal's
+// partial sums, so the resumed sums round alike), and an FNV-1a 64-bit
+// checksum of everything before it.
 constexpr char kCkptMagic[8] = {'E', 'S', 'P', 'N', 'M', 'F', 'C', 'K'};
 constexpr uint32_t kCkptVersion = 1;
 
@@ -1351,7 +1408,8 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             TRY(dmalloc(ctx, &F->Ginv64, sizeof(double) * k * k));
             TRY(dmalloc(ctx, &F->GinvT, ctx->esz * k * k));
             if (use_cholesky(ctx)) {
-                const size_t lf = (size_t)2 * ctx->ldy * ctx->ldy + ctx->ldy;
+                // L, L^T, 1 / diag, then G's FP32 pair (hi, lo)
+                const size_t lf = (size_t)4 * ctx->ldy * ctx->ldy + ctx->ldy;
                 TRY(dmalloc(ctx, &F->Lf, sizeof(float) * lf));
                 CU(cudaMemsetAsync(F->Lf, 0, sizeof(float) * lf, ctx->st));
             }
@@ -1509,6 +1567,9 @@ espnmf_status espnmf_save(espnmf_ctx* ctx, const char* path, uint64_t tag)
     std::vector<double> GU(kk), GV(kk, 0.0);
     CU(cudaMemcpy(GU.data(), ctx->U.G, 8 * kk, cudaMemcpyDeviceToHost));
     if (ctx->V.valid) CU(cudaMemcpy(GV.data(), ctx->V.G, 8 * kk, cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> HU(ctx->k, 0), HV(ctx->k, 0);
+    if (ctx->U.sel_hint) CU(cudaMemcpy(HU.data(), ctx->U.sel_hint, 8 * (size_t)ctx->k, cudaMemcpyDeviceToHost));
+    if (ctx->V.sel_hint) CU(cudaMemcpy(HV.data(), ctx->V.sel_hint, 8 * (size_t)ctx->k, cudaMemcpyDeviceToHost));
     uint64_t sum = 0xcbf29ce484222325ull;
     sum = fnv1a(sum, kCkptMagic, sizeof kCkptMagic);
     sum = fnv1a(sum, &h, sizeof h);
@@ -1516,6 +1577,8 @@ espnmf_status espnmf_save(espnmf_ctx* ctx, const char* path, uint64_t tag)
     sum = fnv1a(sum, Vb.data(), Vb.size());
     sum = fnv1a(sum, GU.data(), 8 * kk);
     sum = fnv1a(sum, GV.data(), 8 * kk);
+    sum = fnv1a(sum, HU.data(), 8 * HU.size());
+    sum = fnv1a(sum, HV.data(), 8 * HV.size());
     const std::string tmp = std::string(path) + ".tmp";
     FILE* f = fopen(tmp.c_str(), "wb");
     if (!f) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "cannot open %s for writing", tmp.c_str());
@@ -1523,6 +1586,8 @@ espnmf_status espnmf_save(espnmf_ctx* ctx, const char* path, uint64_t tag)
               fwrite(Ub.data(), 1, Ub.size(), f) == Ub.size() &&
               fwrite(Vb.data(), 1, Vb.size(), f) == Vb.size() &&
               fwrite(GU.data(), 8, kk, f) == kk && fwrite(GV.data(), 8, kk, f) == kk &&
+              fwrite(HU.data(), 8, HU.size(), f) == HU.size() &&
+              fwrite(HV.data(), 8, HV.size(), f) == HV.size() &&
               fwrite(&sum, sizeof sum, 1, f) == 1;
     ok = (fclose(f) == 0) && ok;
     if (!ok || rename(tmp.c_str(), path) != 0) {
@@ -1554,10 +1619,13 @@ espnmf_status espnmf_load(espnmf_ctx* ctx, const char* path, uint64_t* tag, int6
     const size_t es = ctx->esz, kk = (size_t)ctx->k * ctx->k;
     std::vector<unsigned char> Ub((size_t)h.n * h.k * es), Vb((size_t)h.m * h.k * es);
     std::vector<double> GU(kk), GV(kk);
+    std::vector<uint64_t> HU(ctx->k), HV(ctx->k);
     uint64_t stored = 0;
     const bool body_ok = fread(Ub.data(), 1, Ub.size(), f) == Ub.size() &&
                          fread(Vb.data(), 1, Vb.size(), f) == Vb.size() &&
                          fread(GU.data(), 8, kk, f) == kk && fread(GV.data(), 8, kk, f) == kk &&
+                         fread(HU.data(), 8, HU.size(), f) == HU.size() &&
+                         fread(HV.data(), 8, HV.size(), f) == HV.size() &&
                          fread(&stored, sizeof stored, 1, f) == 1;
     if (!body_ok) return bad("truncated");
     fclose(f);
@@ -1568,6 +1636,8 @@ espnmf_status espnmf_load(espnmf_ctx* ctx, const char* path, uint64_t* tag, int6
     sum = fnv1a(sum, Vb.data(), Vb.size());
     sum = fnv1a(sum, GU.data(), 8 * kk);
     sum = fnv1a(sum, GV.data(), 8 * kk);
+    sum = fnv1a(sum, HU.data(), 8 * HU.size());
+    sum = fnv1a(sum, HV.data(), 8 * HV.size());
     if (sum != stored) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "%s: checksum mismatch", path);
     // the factors as stored (their Grams are then replaced by the saved
     // ones, so that the next sweep repeats the uninterrupted run exactly)
@@ -1576,6 +1646,10 @@ espnmf_status espnmf_load(espnmf_ctx* ctx, const char* path, uint64_t* tag, int6
     if (h.v_valid) TRY(set_factor_impl(ctx, ctx->V, Vb.data(), ctx->dt, 0));
     CU(cudaMemcpyAsync(ctx->U.G, GU.data(), 8 * kk, cudaMemcpyHostToDevice, ctx->st));
     if (h.v_valid) CU(cudaMemcpyAsync(ctx->V.G, GV.data(), 8 * kk, cudaMemcpyHostToDevice, ctx->st));
+    if (ctx->U.sel_hint)
+        CU(cudaMemcpyAsync(ctx->U.sel_hint, HU.data(), 8 * HU.size(), cudaMemcpyHostToDevice, ctx->st));
+    if (ctx->V.sel_hint)
+        CU(cudaMemcpyAsync(ctx->V.sel_hint, HV.data(), 8 * HV.size(), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaStreamSynchronize(ctx->st));
     ctx->V.valid = h.v_valid != 0;
     ctx->met_valid = false;
@@ -1841,6 +1915,11 @@ espnmf_status espnmf_set_option(espnmf_ctx* ctx, espnmf_option opt, int64_t valu
         ctx->spmm_tune = false;
         drop_graphs(ctx);
         return ESPNMF_OK;
+    case ESPNMF_OPT_REFINE:
+        if (value != 0 && value != 1) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "refine is 0 or 1");
+        ctx->refine = value != 0;
+        drop_graphs(ctx);
+        return ESPNMF_OK;
     case ESPNMF_OPT_SPMM_MASK:
         if (value < 0 || value > 2) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "mask is 0, 1 or 2");
         for (int o = 0; o < 2; ++o) {
@@ -1929,6 +2008,71 @@ espnmf_status espnmf_sync(espnmf_ctx* ctx)
 {
     TRY(enter(ctx));
     return check_status(ctx);
+}
+
+espnmf_status espnmf_solve_gram(const void* Y, int64_t rows, int32_t k, int64_t ldy,
+                                const double* G, void* X, int64_t ldx, int32_t refine,
+                                void* stream)
+{
+    g_init_error.clear();
+    if (!Y || !G || !X || rows < 0 || k < 1 || k > 64 || ldy < k || ldx < k)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "bad Y/G/X/rows/k/ld");
+    if (rows >= (1ll << 31)) return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "too many rows");
+    if (rows == 0) return ESPNMF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    auto cuerr = [&](cudaError_t e, const char* what) {
+        cudaGetLastError();
+        return set_err(nullptr, ESPNMF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuerr(e, "device");
+    {
+        static std::mutex setup_mu;
+        static bool setup_done[64] = {};
+        std::lock_guard<std::mutex> lock(setup_mu);
+        if (dev >= 64 || !setup_done[dev]) {
+            if ((e = setup_chol()) != cudaSuccess) return cuerr(e, "setup");
+            if (dev < 64) setup_done[dev] = true;
+        }
+    }
+    const int KP = factor_ld(k);
+    const int64_t ldt = (rows + 31) / 32 * 32;
+    auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t bl = a256(sizeof(float) * (4 * (size_t)KP * KP + KP));
+    const size_t by = a256(sizeof(float) * (size_t)rows * KP);
+    const size_t bt = a256(sizeof(float) * (size_t)k * ldt);
+    unsigned char* ws = nullptr;
+    e = cudaMallocAsync((void**)&ws, bl + by + bt + 256, st);
+    if (e != cudaSuccess) return cuerr(e, "cudaMallocAsync");
+    float* Lf = (float*)ws;
+    float* Yp = (float*)(ws + bl);
+    float* Xt = (float*)(ws + bl + by);
+    unsigned* status = (unsigned*)(ws + bl + by + bt);
+    float* gh = Lf + 2 * KP * KP + KP;
+    e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
+    // Y padded to KP columns (rows 16-byte aligned for the solve's loads)
+    if (e == cudaSuccess) e = cudaMemsetAsync(Yp, 0, sizeof(float) * (size_t)rows * KP, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(Yp, sizeof(float) * KP, Y, sizeof(float) * ldy, sizeof(float) * k,
+                              (size_t)rows, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = launch_cholesky(G, k, KP, Lf, Lf + KP * KP, Lf + 2 * KP * KP, status, st, gh, gh + KP * KP);
+    if (e == cudaSuccess)
+        e = launch_solve_chol(Yp, KP, rows, k, KP, Lf, Lf + KP * KP, Lf + 2 * KP * KP, Xt, ldt,
+                              status, st, sms, false);
+    if (e == cudaSuccess)
+        e = launch_refine(Yp, KP, nullptr, 0, rows, k, KP, Lf, Lf + 2 * KP * KP, gh, gh + KP * KP,
+                          Xt, ldt, (float*)X, ldx, true, refine != 0, status, st, sms);
+    unsigned hstat = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaFreeAsync(ws, st);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuerr(e, "solve_gram");
+    if (hstat & ST_NONFINITE) return set_err(nullptr, ESPNMF_ERR_NONFINITE, "non-finite value in G or X");
+    if (hstat & ST_SINGULAR) return set_err(nullptr, ESPNMF_ERR_SINGULAR, "G is singular beyond its zero columns");
+    return ESPNMF_OK;
 }
 
 espnmf_status espnmf_enforce_topt_buffer(void* X, int64_t rows, int32_t k, int64_t ld,

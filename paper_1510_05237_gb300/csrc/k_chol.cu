@@ -54,7 +54,8 @@ __device__ __forceinline__ double rsqrt_fp64(double d)
 // per step.
 __global__ void __launch_bounds__(kCholThreads)
 cholesky_kernel(const double* __restrict__ G, int k, int KP, float* __restrict__ Ls,
-                float* __restrict__ LTs, float* __restrict__ rd, unsigned* status)
+                float* __restrict__ LTs, float* __restrict__ rd, unsigned* status,
+                float* __restrict__ Gh, float* __restrict__ Gl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ks = k + 1;                                   // row stride (odd)
@@ -139,6 +140,17 @@ cholesky_kernel(const double* __restrict__ G, int k, int KP, float* __restrict__
     }
     for (int j = tid; j < KP; j += blockDim.x)
         rd[j] = (j < k && act[j]) ? (float)(1.0 / a[j * ks + j]) : 0.f;
+    if (Gh) {
+        // G itself as an unevaluated FP32 pair (hi + lo, about 48 bits), for
+        // the residual of the refinement step
+        for (int e = tid; e < KP * KP; e += blockDim.x) {
+            const int i = e / KP, l = e - i * KP;
+            const double g = (i < k && l < k) ? G[(size_t)i * k + l] : 0.0;
+            const float h = (float)g;
+            Gh[e] = h;
+            Gl[e] = (float)(g - (double)h);
+        }
+    }
     if (tid == 0) {
         if (sing) atomicOr(status, ST_SINGULAR);
         if (nonfin) atomicOr(status, ST_NONFINITE);
@@ -146,7 +158,7 @@ cholesky_kernel(const double* __restrict__ G, int k, int KP, float* __restrict__
 }
 
 cudaError_t launch_cholesky(const double* G, int k, int KP, float* Ls, float* LTs, float* rd,
-                            unsigned* status, cudaStream_t st)
+                            unsigned* status, cudaStream_t st, float* Gh, float* Gl)
 {
     if (k < 1 || KP < k || KP > 64) return cudaErrorInvalidValue;
     const size_t smem = (size_t)k * (k + 1) * sizeof(double) + 2 * (size_t)k * sizeof(int) +
@@ -164,7 +176,7 @@ cudaError_t launch_cholesky(const double* G, int k, int KP, float* Ls, float* LT
     attr[0].val.priority = hi;   // ahead of the concurrent SpMM's pending blocks
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cholesky_kernel, G, k, KP, Ls, LTs, rd, status);
+    return cudaLaunchKernelEx(&cfg, cholesky_kernel, G, k, KP, Ls, LTs, rd, status, Gh, Gl);
 }
 
 // ---------------------------------------------------------------------------
@@ -200,7 +212,7 @@ __global__ void __launch_bounds__(kSolveRows, 4 / R)
 solve_chol_kernel(const float* __restrict__ Y, int64_t ldy, int64_t rows, int k,
                   const float* __restrict__ Lg, const float* __restrict__ LTg,
                   const float* __restrict__ rdg, float* __restrict__ Xt, int64_t ldx,
-                  unsigned* status)
+                  unsigned* status, bool project)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* N1 = reinterpret_cast<float*>(smem_raw);   // [KP][KP]
@@ -274,7 +286,7 @@ solve_chol_kernel(const float* __restrict__ Y, int64_t ldy, int64_t rows, int k,
                     if (c >= k) break;
                     const float v = x[h][c];
                     if (!isfinite(v)) bad = true;
-                    Xt[(int64_t)c * ldx + r] = v > 0.f ? v : 0.f;
+                    Xt[(int64_t)c * ldx + r] = (v > 0.f || !project) ? v : 0.f;
                 }
             }
         }
@@ -291,7 +303,7 @@ template <int KP>
 static cudaError_t launch_solve_chol_kp(const float* Y, int64_t ldy, int64_t rows, int k,
                                         const float* L, const float* LT, const float* rd,
                                         float* Xt, int64_t ldx, unsigned* status,
-                                        cudaStream_t st, int sm_count)
+                                        cudaStream_t st, int sm_count, bool project)
 {
     const size_t smem = ((size_t)2 * KP * KP + KP) * sizeof(float);
     constexpr int R = solve_rows_per_thread(KP);
@@ -299,24 +311,123 @@ static cudaError_t launch_solve_chol_kp(const float* Y, int64_t ldy, int64_t row
     int64_t grid = (int64_t)sm_count * (4 / R);
     if (grid > tiles) grid = tiles;
     solve_chol_kernel<KP, R><<<(unsigned)grid, kSolveRows, smem, st>>>(Y, ldy, rows, k, L, LT, rd,
-                                                                     Xt, ldx, status);
+                                                                     Xt, ldx, status, project);
     return cudaGetLastError();
 }
 
 cudaError_t launch_solve_chol(const float* Y, int64_t ldy, int64_t rows, int k, int KP,
                               const float* L, const float* LT, const float* rd, float* Xt,
-                              int64_t ldx, unsigned* status, cudaStream_t st, int sm_count)
+                              int64_t ldx, unsigned* status, cudaStream_t st, int sm_count,
+                              bool project)
 {
     if (rows == 0) return cudaSuccess;
     if (ldy != KP) return cudaErrorInvalidValue;
     switch (KP) {
-#define ESPNMF_KP(v) case v: return launch_solve_chol_kp<v>(Y, ldy, rows, k, L, LT, rd, Xt, ldx, status, st, sm_count);
+#define ESPNMF_KP(v) case v: return launch_solve_chol_kp<v>(Y, ldy, rows, k, L, LT, rd, Xt, ldx, status, st, sm_count, project);
         ESPNMF_KP(4) ESPNMF_KP(8) ESPNMF_KP(12) ESPNMF_KP(16) ESPNMF_KP(20) ESPNMF_KP(24)
         ESPNMF_KP(28) ESPNMF_KP(32) ESPNMF_KP(36) ESPNMF_KP(40) ESPNMF_KP(44) ESPNMF_KP(48)
         ESPNMF_KP(52) ESPNMF_KP(56) ESPNMF_KP(60) ESPNMF_KP(64)
 #undef ESPNMF_KP
     default: return cudaErrorInvalidValue;
     }
+}
+
+// ---------------------------------------------------------------------------
+// One step of iterative refinement of the solve.  solve_chol_kernel (run
+// with project = false) leaves x0 = y (L L^T)^-1, unprojected, in Xt; this
+// kernel forms the residual r = y - x0 G with G = Gh + Gl (an FP32 pair
+// holding G to about 48 bits; each product split exactly by one FMA and
+// the terms summed as a compensated pair), solves d = r (L L^T)^-1 by the
+// same substitutions and writes x = x0 + d (projected into Xt, or raw and
+// row-major).  The error of x0 is about cond(G) 2^-24 |x|, that of x about
+// (cond(G) 2^-24)^2 |x| plus the final FP32 rounding: for cond(G) well
+// below 2^12 the result is the FP64 solution rounded to FP32 within an ulp
+// or two.  One thread per row; its x0 and r live in shared-memory columns
+// and every loop runs at run time (an option, not the default path).
+constexpr int kRefineRows = 128;
+
+__global__ void __launch_bounds__(kRefineRows)
+refine_kernel(const float* __restrict__ Y, int64_t ldy, const float* __restrict__ Yt,
+              int64_t ldyt, int64_t rows, int k, int KP, const float* __restrict__ Lg,
+              const float* __restrict__ LTg, const float* __restrict__ rdg,
+              const float* __restrict__ Ghg, const float* __restrict__ Glg,
+              float* __restrict__ Xt, int64_t ldx, float* __restrict__ out, int64_t ldo,
+              bool raw, bool correct, unsigned* status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int B = kRefineRows;
+    float* L = reinterpret_cast<float*>(smem_raw);   // [KP][KP] L[i][l], strictly lower
+    float* Gh = L + KP * KP;                           // [KP][KP]
+    float* Gl = Gh + KP * KP;                          // [KP][KP]
+    float* rds = Gl + KP * KP;                         // [KP]
+    float* xs = rds + KP;                              // [KP][B] x0 by column
+    float* ds = xs + KP * B;                           // [KP][B] r, then d
+    const int tid = threadIdx.x;
+    for (int e = tid; e < KP * KP; e += blockDim.x) {
+        L[e] = Lg[e];
+        Gh[e] = correct ? Ghg[e] : 0.f;
+        Gl[e] = correct ? Glg[e] : 0.f;
+    }
+    for (int e = tid; e < KP; e += blockDim.x) rds[e] = e < k ? rdg[e] : 0.f;
+    (void)LTg;
+    __syncthreads();
+    bool bad = false;
+    float* x = xs + tid;
+    float* d = ds + tid;
+    for (int64_t r0 = (int64_t)blockIdx.x * B; r0 < rows; r0 += (int64_t)gridDim.x * B) {
+        const int64_t r = r0 + tid;
+        if (r >= rows) continue;   // no barrier below
+        for (int c = 0; c < k; ++c) x[c * B] = Xt[(int64_t)c * ldx + r];
+        for (int c = 0; c < k; ++c) d[c * B] = 0.f;
+        // residual, compensated
+        for (int j = 0; j < (correct ? k : 0); ++j) {
+            DFloat s;
+            s.hi = Y ? Y[r * ldy + j] : 0.f;
+            if (Yt) df_add(s, Yt[(int64_t)j * ldyt + r], 0.f);
+            float tail = 0.f;
+            for (int l = 0; l < k; ++l) {
+                const float xl = x[l * B];
+                df_add_prod(s, -xl, Gh[l * KP + j]);
+                tail = __fmaf_rn(-xl, Gl[l * KP + j], tail);
+            }
+            d[j * B] = s.hi + (s.lo + tail);
+        }
+        // d (L L^T)^-1: L z = d, then L^T x = z (inactive indices have rds 0)
+        for (int j = 0; j < (correct ? k : 0); ++j) {
+            float v = d[j * B];
+            for (int l = 0; l < j; ++l) v = __fmaf_rn(-L[j * KP + l], d[l * B], v);
+            d[j * B] = v * rds[j];
+        }
+        for (int j = correct ? k - 1 : -1; j >= 0; --j) {
+            float v = d[j * B];
+            for (int l = j + 1; l < k; ++l) v = __fmaf_rn(-L[l * KP + j], d[l * B], v);
+            d[j * B] = v * rds[j];
+        }
+        for (int c = 0; c < k; ++c) {
+            const float v = x[c * B] + d[c * B];
+            if (!isfinite(v)) bad = true;
+            if (raw) out[r * ldo + c] = v;
+            else Xt[(int64_t)c * ldx + r] = v > 0.f ? v : 0.f;
+        }
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+static size_t refine_smem(int KP) { return ((size_t)3 * KP * KP + KP + (size_t)2 * KP * kRefineRows) * sizeof(float); }
+
+cudaError_t launch_refine(const float* Y, int64_t ldy, const float* Yt, int64_t ldyt, int64_t rows,
+                          int k, int KP, const float* L, const float* rd, const float* Gh,
+                          const float* Gl, float* Xt, int64_t ldx, float* out, int64_t ldo,
+                          bool raw, bool correct, unsigned* status, cudaStream_t st, int sm_count)
+{
+    if (rows == 0) return cudaSuccess;
+    if ((correct && ((!Y && !Yt) || !Gh || !Gl)) || KP > 64 || k > KP) return cudaErrorInvalidValue;
+    const int64_t tiles = (rows + kRefineRows - 1) / kRefineRows;
+    int64_t grid = (int64_t)sm_count * 2;
+    if (grid > tiles) grid = tiles;
+    refine_kernel<<<(unsigned)grid, kRefineRows, refine_smem(KP), st>>>(
+        Y, ldy, Yt, ldyt, rows, k, KP, L, nullptr, rd, Gh, Gl, Xt, ldx, out, ldo, raw, correct, status);
+    return cudaGetLastError();
 }
 
 template <int KP>
@@ -326,6 +437,7 @@ static cudaError_t setup_solve_kp()
     constexpr int R = solve_rows_per_thread(KP);
     cudaError_t e = cudaFuncSetAttribute(solve_chol_kernel<KP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+
     // four blocks per SM need most of the shared memory: do not let the
     // driver pick a smaller carveout
     if (e == cudaSuccess)
@@ -336,6 +448,11 @@ static cudaError_t setup_solve_kp()
 
 cudaError_t setup_chol()
 {
+    {
+        cudaError_t e0 = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)refine_smem(64));
+        if (e0 != cudaSuccess) return e0;
+    }
     cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          64 * 65 * 8 + 2 * 64 * 4 + 64 * 65);
 #define ESPNMF_KP(v) if (e == cudaSuccess) e = setup_solve_kp<v>();

@@ -42,6 +42,7 @@ namespace espnmf {
 
 constexpr int kSelThreads = 1024;
 constexpr int kSelMaxCluster = 2;
+constexpr int kSelMaxClusterWhole = 8;   // one segment (matrix mode): a portable cluster
 
 template <typename T> struct Vec4Of;
 template <> struct Vec4Of<float> { using type = float4; };
@@ -604,16 +605,19 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
 }
 
 // CTAs per cluster: about two CTAs per SM over all segments, at most
-// kSelMaxCluster (larger clusters measured slower), at least 2048 entries per
-// CTA.  When it marks survivors (column mode) one CTA owns a column: its
-// rounds then need block barriers only, and it may start from a hint.
+// kSelMaxCluster per column (larger clusters measured slower with k columns
+// in flight) and kSelMaxClusterWhole for the single segment of matrix mode
+// (the whole factor), at least 2048 entries per CTA.  When it marks
+// survivors (column mode) one CTA owns a column: its rounds then need block
+// barriers only, and it may start from a hint.
 static int sel_cluster(int64_t rows, int k, int mode, int sm_count, bool marking)
 {
     if (marking && mode == TOPT_COLUMN) return 1;
     const int nseg = mode == TOPT_MATRIX ? 1 : k;
     const int64_t seg_len = mode == TOPT_MATRIX ? (int64_t)k * rows : rows;
     int C = (int)((2 * (int64_t)sm_count + nseg - 1) / nseg);
-    if (C > kSelMaxCluster) C = kSelMaxCluster;
+    const int cap = nseg == 1 ? kSelMaxClusterWhole : kSelMaxCluster;
+    if (C > cap) C = cap;
     const int64_t by_len = (seg_len + 2047) / 2048;
     if (C > by_len) C = (int)by_len;
     if (C < 1) C = 1;

@@ -425,12 +425,15 @@ def test_benchmark_corpus_uses_the_frequent_part():
     assert E.espnmf_spmm_frequent(ctx64, 1) == (0, 0)
 
 
-@pytest.mark.parametrize("scale", [1e20, 1e-20])
+@pytest.mark.parametrize("scale", [1e14, 1e-17])
 def test_step_parity_with_factor_scaled_far_from_one(scale):
-    """A factor scaled by 1e20 (or 1e-20) puts the Gram pivots near 1e40
-    (1e-40), outside the FP32 range that seeds the Cholesky pivot's inverse
-    square root; the FP32 form must still solve the system (the result
-    scales by 1/scale) and match the oracle."""
+    """A factor scaled by 1e14 (or 1e-17) puts the Gram pivots beyond 1e30
+    (below 1e-30), outside the range where the FP32 seed of the Cholesky
+    pivot's inverse square root is used; the FP32 form must still solve the
+    system (V scales by 1/scale, and the U half meets pivots on the other
+    side) and match the oracle.  (The FP32 form's Gram sums square FP32
+    factor entries, so entries beyond about 1e18 or below 1e-18 are outside
+    its range; the FP64 form has no such limit.)"""
     A = small_zipf(6)
     U0 = uniform_init(A.n, 8, 6) * scale
     step_parity(A, 8, 90, 70, U0, E.TOPT_COLUMN, E.F32, f"scale={scale:g}")
