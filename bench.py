@@ -671,23 +671,25 @@ def main():
     accuracy = None
     if not args.no_accuracy and A.labels is not None:
         try:
-            from paper_1510_05237_gb300 import metrics
             n_cls = int(A.labels.max()) + 1
+            labels_d = dev(A.labels.astype(np.int32))
             runs = {}
             for name, mode in (("during", E.TOPT_COLUMN), ("after", E.TOPT_NONE)):
                 c = E.espnmf_init(rp, ci, va, A.n, A.m, K_TOPICS, T_KEEP, T_KEEP, mode, E.F32,
                                   u0, stream=stream)
                 E.espnmf_iterate(c, JOB_ITERS, want_measures=False)
-                Vd = E.espnmf_get_factor(c, E.V, dtype=np.float32)
-                E.espnmf_destroy(c)
                 if mode == E.TOPT_NONE:
-                    # the rule once, column by column, by the library's selector
+                    # the rule once, column by column, by the library's selector,
+                    # then back into the context
+                    Vd = E.espnmf_get_factor(c, E.V, dtype=np.float32)
                     Vt = torch.from_numpy(np.ascontiguousarray(Vd)).cuda()
                     torch.cuda.synchronize()
                     E.espnmf_enforce_topt_buffer(Vt, T_KEEP, E.TOPT_COLUMN, stream=stream)
                     stream.synchronize()
-                    Vd = Vt.cpu().numpy()
-                runs[name] = float(metrics.topic_accuracy(Vd, A.labels, n_cls).mean())
+                    E.espnmf_set_factor(c, E.V, Vt)
+                # Eq. 3-4 on the device
+                runs[name] = float(E.espnmf_topic_accuracy(c, labels_d, n_cls).mean())
+                E.espnmf_destroy(c)
             accuracy = {"enforced_during_als": runs["during"], "enforced_after_als": runs["after"],
                         "classes": n_cls, "t_v": T_KEEP, "sweeps": JOB_ITERS,
                         "measure": "mean over the k document topics of Eq. 3-4"}

@@ -206,6 +206,19 @@ espnmf_status espnmf_save(espnmf_ctx *ctx, const char *path, uint64_t tag);
  * ESPNMF_ERR_INVALID_ARG and leaves the context unchanged.  Synchronises. */
 espnmf_status espnmf_load(espnmf_ctx *ctx, const char *path, uint64_t *tag, int64_t *sweeps);
 
+/* espnmf_topic_accuracy -- the document-clustering accuracy of every topic
+ * (Sec. 3.2, Eq. 3-4) from the current factor (usually V: its rows are the
+ * documents), on the device.  Row i belongs to topic c when entry (i, c) is
+ * nonzero; labels[i] in [0, n_classes) is row i's class (device memory when
+ * on_device != 0, else host); acc receives k doubles on the host:
+ * (P - alpha) / (beta - alpha) with P the member pairs sharing a class,
+ * alpha that count for the most even spread over the classes, beta all
+ * pairs; 1 for topics of at most one member or when beta == alpha.  A
+ * member row's label outside the range gives ESPNMF_ERR_INVALID_ARG.
+ * Synchronises. */
+espnmf_status espnmf_topic_accuracy(espnmf_ctx *ctx, espnmf_which which, const int32_t *labels,
+                                    int32_t n_classes, int32_t on_device, double *acc);
+
 /* espnmf_sweeps_done -- completed sweeps (U updates) since espnmf_init, or
  * since the state restored by espnmf_load counting its saved sweeps. */
 espnmf_status espnmf_sweeps_done(espnmf_ctx *ctx, int64_t *sweeps);

@@ -98,6 +98,7 @@ def load():
             "espnmf_spmm_frequent": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)],
             "espnmf_save": [P, ctypes.c_char_p, ctypes.c_uint64],
             "espnmf_solve_gram": [P, i64, i32, i64, P, P, i64, i32, P],
+            "espnmf_topic_accuracy": [P, st, P, i32, i32, P],
             "espnmf_load": [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i64)],
             "espnmf_sweeps_done": [P, ctypes.POINTER(i64)],
             "espnmf_select_stats": [P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
@@ -129,7 +130,7 @@ def exported_symbols():
              "espnmf_batch_ctx", "espnmf_batch_set_option", "espnmf_batch_iterate",
              "espnmf_spmm_config", "espnmf_spmm_frequent", "espnmf_select_stats",
              "espnmf_sequential", "espnmf_save", "espnmf_load", "espnmf_sweeps_done",
-             "espnmf_solve_gram"]
+             "espnmf_solve_gram", "espnmf_topic_accuracy"]
     return {n: hasattr(lib, n) for n in names}
 
 
@@ -373,6 +374,21 @@ def espnmf_solve_gram(Y, G, refine: bool = False, stream=None):
                                     ctypes.c_void_p(X.data_ptr()), k, int(bool(refine)),
                                     ctypes.c_void_p(st)))
     return X
+
+
+def espnmf_topic_accuracy(ctx: Context, labels, n_classes: int, which: int = V) -> np.ndarray:
+    """Eq. 3-4 accuracy of each column of the factor (default V) against
+    integer class labels (numpy or CUDA int32 tensor, one per row)."""
+    acc = np.zeros(ctx.k, dtype=np.float64)
+    if _is_torch(labels) and labels.is_cuda:
+        lab, dev = labels.to(dtype=__import__("torch").int32).contiguous(), 1
+        ptr = ctypes.c_void_p(lab.data_ptr())
+    else:
+        lab, dev = np.ascontiguousarray(labels, dtype=np.int32), 0
+        ptr = lab.ctypes.data_as(ctypes.c_void_p)
+    _check(load().espnmf_topic_accuracy(ctx.handle, int(which), ptr, int(n_classes), dev,
+                                        acc.ctypes.data_as(ctypes.c_void_p)), ctx.handle)
+    return acc
 
 
 def espnmf_save(ctx: Context, path: str, tag: int = 0):

@@ -390,6 +390,13 @@ template <typename T>
 cudaError_t launch_ell_to_dense(int64_t rows, int k, EllDev F, T* X,
                                 int64_t ld, cudaStream_t st);
 
+// Document-clustering accuracy of each column of factor F (k_metrics.cu):
+// hist (k x n_classes counters) is scratch; acc receives k doubles.  A
+// label outside [0, n_classes) of a member row raises ST_BADINPUT.
+cudaError_t launch_topic_accuracy(const EllDev& F, int k, const int32_t* labels, int n_classes,
+                                  unsigned* hist, double* acc, unsigned* status, int sm_count,
+                                  cudaStream_t st);
+
 // Per-device one-time kernel attribute set-up (dynamic shared memory
 // limits), called by espnmf_init before any launch or capture.
 cudaError_t setup_spmm();

@@ -18,6 +18,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -282,6 +283,21 @@ espnmf_status check_status(espnmf_ctx* ctx)
     if (s & ST_TIMEOUT) return set_err(ctx, ESPNMF_ERR_TIMEOUT, "a bounded device wait gave up");
     if (s & ST_OVERFLOW) return set_err(ctx, ESPNMF_ERR_CUDA, "internal: factor row overflow");
     return set_err(ctx, ESPNMF_ERR_CUDA, "unknown device status 0x%x", s);
+}
+
+// fn(lo, hi) over [0, total) cut into contiguous chunks run on up to eight
+// host threads (one for small totals).
+template <typename F>
+void parallel_chunks(int64_t total, F&& fn)
+{
+    unsigned hw = std::thread::hardware_concurrency();
+    int T = (int)std::min<unsigned>(8u, hw ? hw : 1u);
+    if (total < (1 << 16)) T = 1;
+    std::vector<std::thread> th;
+    for (int t = 1; t < T; ++t)
+        th.emplace_back([&, t] { fn(total * t / T, total * (t + 1) / T); });
+    fn(0, total / T);
+    for (auto& x : th) x.join();
 }
 
 // --- host-side layout of A ------------------------------------------------------
@@ -1235,30 +1251,51 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                 memcpy(vraw.data(), A->values, nnz * vsz);
             }
         }
-        for (int64_t p = 0; p < nnz; ++p) {
-            double x;
-            if (vsz == 8) memcpy(&x, &vraw[p * 8], 8);
-            else {
-                float f;
-                memcpy(&f, &vraw[p * 4], 4);
-                x = f;
+        parallel_chunks(nnz, [&](int64_t p0, int64_t p1) {
+            for (int64_t p = p0; p < p1; ++p) {
+                double x;
+                if (vsz == 8) memcpy(&x, &vraw[p * 8], 8);
+                else {
+                    float f;
+                    memcpy(&f, &vraw[p * 4], 4);
+                    x = f;
+                }
+                vv[p] = x;
             }
-            vv[p] = x;
-        }
+        });
         if (rp[0] != 0 || rp[n] != nnz)
             return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "rowptr must run from 0 to nnz");
-        for (int64_t r = 0; r < n; ++r) {
+        for (int64_t r = 0; r < n; ++r)
             if (rp[r + 1] < rp[r]) return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "rowptr decreases at row %lld", (long long)r);
-            for (int64_t p = rp[r]; p < rp[r + 1]; ++p) {
-                if (ci[p] < 0 || ci[p] >= m)
-                    return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "column index out of range in row %lld", (long long)r);
-                if (p > rp[r] && ci[p] <= ci[p - 1])
-                    return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "column indices not strictly increasing in row %lld", (long long)r);
-                if (!std::isfinite(vv[p]))
-                    return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "non-finite value in row %lld", (long long)r);
-                if (vv[p] < 0.0)
-                    return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "negative value in row %lld (A >= 0 is required)", (long long)r);
-            }
+        {
+            // rows checked in chunks on host threads; the first bad row
+            // (lowest index) is reported
+            std::mutex bad_mu;
+            int64_t bad_row = n;
+            int bad_kind = 0;
+            parallel_chunks(n, [&](int64_t r0, int64_t r1) {
+                for (int64_t r = r0; r < r1; ++r) {
+                    int kind = 0;
+                    for (int64_t p = rp[r]; p < rp[r + 1] && !kind; ++p) {
+                        if (ci[p] < 0 || ci[p] >= m) kind = 1;
+                        else if (p > rp[r] && ci[p] <= ci[p - 1]) kind = 2;
+                        else if (!std::isfinite(vv[p])) kind = 3;
+                        else if (vv[p] < 0.0) kind = 4;
+                    }
+                    if (kind) {
+                        std::lock_guard<std::mutex> lock(bad_mu);
+                        if (r < bad_row) {
+                            bad_row = r;
+                            bad_kind = kind;
+                        }
+                        return;
+                    }
+                }
+            });
+            static const char* what[] = {"", "column index out of range", "column indices not strictly increasing",
+                                         "non-finite value", "negative value (A >= 0 is required)"};
+            if (bad_kind)
+                return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "%s in row %lld", what[bad_kind], (long long)bad_row);
         }
         // CSC (= CSR of A^T), rows ascending inside each column
         std::vector<int64_t> cp(m + 1, 0);
@@ -1275,11 +1312,14 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                     cv[q] = vv[p];
                 }
         }
+        // The two orientations are laid out on two host threads; the uploads
+        // follow on this thread.
         if (compute == ESPNMF_F64) {
             SellHost<double> h1, h2;
+            std::thread th([&] { build_sell(m, cp.data(), ri.data(), cv.data(), h2); });
             build_sell(n, rp.data(), ci.data(), vv.data(), h1);
+            th.join();
             TRY(upload_sell(ctx, h1, ctx->sA));
-            build_sell(m, cp.data(), ri.data(), cv.data(), h2);
             TRY(upload_sell(ctx, h2, ctx->sAt));
         } else {
             // rows of A gather rows of V (documents), rows of A^T rows of U
@@ -1288,31 +1328,37 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             const int ld = factor_ld(k);
             // chunks of the frequent part's rows: four per warp of spmm_h
             const int hwarps = 4 * ctx->sm_count * (kHThreads / 32);
+            struct Built {
+                FreqHost F;
+                SellHost<float> h;
+            };
             auto build_f32 = [&](int64_t rows, const int64_t* ptr, const int32_t* ind,
-                                 const double* vals, int64_t ngather,
-                                 SellDev& D) -> espnmf_status {
+                                 const double* vals, int64_t ngather, Built& B) {
                 std::vector<int64_t> w(ngather, 0);
                 for (int64_t q = 0; q < ptr[rows]; ++q) w[ind[q]]++;
-                FreqHost F;
-                F.h = choose_frequent(w, ptr[rows], ld, F.slot_of);
-                SellHost<float> h;
-                if (F.h > 0) {
+                B.F.h = choose_frequent(w, ptr[rows], ld, B.F.slot_of);
+                if (B.F.h > 0) {
                     std::vector<int64_t> lp;
                     std::vector<int32_t> li;
                     std::vector<double> lv;
-                    split_frequent(rows, ptr, ind, vals, F, lp, li, lv);
-                    balance_frequent(rows, hwarps, F);
-                    build_sell(rows, lp.data(), li.data(), lv.data(), h);
-                    TRY(upload_sell(ctx, h, D));
-                    TRY(upload_frequent(ctx, F, D));
+                    split_frequent(rows, ptr, ind, vals, B.F, lp, li, lv);
+                    balance_frequent(rows, hwarps, B.F);
+                    build_sell(rows, lp.data(), li.data(), lv.data(), B.h);
                 } else {
-                    build_sell(rows, ptr, ind, vals, h);
-                    TRY(upload_sell(ctx, h, D));
+                    build_sell(rows, ptr, ind, vals, B.h);
                 }
+            };
+            auto upload_f32 = [&](const Built& B, SellDev& D) -> espnmf_status {
+                TRY(upload_sell(ctx, B.h, D));
+                if (B.F.h > 0) TRY(upload_frequent(ctx, B.F, D));
                 return ESPNMF_OK;
             };
-            TRY(build_f32(n, rp.data(), ci.data(), vv.data(), m, ctx->sA));
-            TRY(build_f32(m, cp.data(), ri.data(), cv.data(), n, ctx->sAt));
+            Built ba, bat;
+            std::thread th([&] { build_f32(m, cp.data(), ri.data(), cv.data(), n, bat); });
+            build_f32(n, rp.data(), ci.data(), vv.data(), m, ba);
+            th.join();
+            TRY(upload_f32(ba, ctx->sA));
+            TRY(upload_f32(bat, ctx->sAt));
         }
 
         // ---- work buffers
@@ -1658,6 +1704,49 @@ espnmf_status espnmf_load(espnmf_ctx* ctx, const char* path, uint64_t* tag, int6
     ctx->sweeps = h.sweeps;
     if (tag) *tag = h.tag;
     if (sweeps) *sweeps = h.sweeps;
+    return check_status(ctx);
+}
+
+espnmf_status espnmf_topic_accuracy(espnmf_ctx* ctx, espnmf_which which, const int32_t* labels,
+                                    int32_t n_classes, int32_t on_device, double* acc)
+{
+    TRY(enter(ctx));
+    if (which != ESPNMF_U && which != ESPNMF_V) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "which");
+    if (!labels || !acc || n_classes < 1)
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "labels/acc NULL or n_classes < 1");
+    Factor& F = which == ESPNMF_U ? ctx->U : ctx->V;
+    if (!F.valid) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "factor has no value yet");
+    TRY(check_status(ctx));
+    const size_t bl = ((size_t)F.rows * 4 + 255) & ~(size_t)255;
+    const size_t bh = ((size_t)ctx->k * n_classes * 4 + 255) & ~(size_t)255;
+    unsigned char* ws = nullptr;
+    CU(cudaMallocAsync((void**)&ws, bl + bh + 8 * (size_t)ctx->k + 256, ctx->st));
+    const int32_t* lab = labels;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        e = cudaMemcpyAsync(ws, labels, 4 * (size_t)F.rows, cudaMemcpyHostToDevice, ctx->st);
+        lab = reinterpret_cast<const int32_t*>(ws);
+    }
+    double* acc_d = reinterpret_cast<double*>(ws + bl + bh);
+    if (e == cudaSuccess)
+        e = launch_topic_accuracy(F.buf[F.cur], ctx->k, lab, n_classes,
+                                  reinterpret_cast<unsigned*>(ws + bl), acc_d, ctx->status_d,
+                                  ctx->sm_count, ctx->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(acc, acc_d, 8 * (size_t)ctx->k, cudaMemcpyDeviceToHost, ctx->st);
+    cudaError_t e2 = cudaFreeAsync(ws, ctx->st);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, ESPNMF_ERR_CUDA, "topic accuracy: %s", cudaGetErrorString(e));
+    }
+    unsigned hs = 0;
+    CU(cudaMemcpy(&hs, ctx->status_d, sizeof hs, cudaMemcpyDeviceToHost));
+    if (hs & ST_BADINPUT) {
+        CU(cudaMemset(ctx->status_d, 0, sizeof(unsigned)));
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "a member row's label is outside [0, n_classes)");
+    }
     return check_status(ctx);
 }
 
