@@ -2159,8 +2159,9 @@ espnmf_status espnmf_solve_gram(const void* Y, int64_t rows, int32_t k, int64_t 
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuerr(e, "solve_gram");
-    if (hstat & ST_NONFINITE) return set_err(nullptr, ESPNMF_ERR_NONFINITE, "non-finite value in G or X");
+    // a singular G is the cause of the non-finite X it leads to: report it first
     if (hstat & ST_SINGULAR) return set_err(nullptr, ESPNMF_ERR_SINGULAR, "G is singular beyond its zero columns");
+    if (hstat & ST_NONFINITE) return set_err(nullptr, ESPNMF_ERR_NONFINITE, "non-finite value in G or X");
     return ESPNMF_OK;
 }
 
