@@ -61,6 +61,9 @@ def parse():
                    help="instead of the benchmark: 512 uneven independent problems, 30 sweeps, "
                         "the batched graph against a loop of single-problem contexts")
     p.add_argument("--batch-problems", type=int, default=512)
+    p.add_argument("--bf16-effect", action="store_true",
+                   help="instead of the benchmark: final E after 50 sweeps with A's values and "
+                        "U0 rounded to BF16 (FP32 arithmetic) against the FP64 form")
     p.add_argument("--sweep-t", action="store_true",
                    help="instead of the benchmark: R and E after 75 iterations against t for "
                         "sparse U, sparse V and both (the shape of Sec. 3.1's figure)")
@@ -392,6 +395,41 @@ def run_sweep_t(args):
     return 0
 
 
+def to_bf16(x: np.ndarray) -> np.ndarray:
+    """FP32 values rounded to the nearest BF16 (ties to even), as FP32."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def run_bf16_effect(args):
+    """What BF16 inputs would cost in accuracy on the benchmark: the FP32
+    form run on A's values and U0 rounded to BF16 (8 significant bits),
+    against the FP64 form on the original A.  Prints one JSON line."""
+    import torch
+    import paper_1510_05237_gb300 as E
+    torch.cuda.set_device(0)
+    A, U0 = make_inputs(args.seed)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, ci = dev(A.rowptr), dev(A.colidx)
+    stream = torch.cuda.Stream()
+    out = {"experiment": "bf16_effect", "workload": WORKLOAD, "sweeps": JOB_ITERS}
+    runs = {"fp64": (dev(A.val), dev(U0), E.F64),
+            "fp32": (dev(A.val.astype(np.float32)), dev(U0.astype(np.float32)), E.F32),
+            "bf16_inputs": (dev(to_bf16(A.val.astype(np.float32))),
+                            dev(to_bf16(U0.astype(np.float32))), E.F32)}
+    for name, (va, u0, comp) in runs.items():
+        c = E.espnmf_init(rp, ci, va, A.n, A.m, K_TOPICS, T_KEEP, T_KEEP, E.TOPT_COLUMN, comp,
+                          u0, stream=stream)
+        R, Es = E.espnmf_iterate(c, JOB_ITERS)
+        out[name] = {"final_E": float(Es[-1]), "final_R": float(R[-1])}
+        E.espnmf_destroy(c)
+    for name in ("fp32", "bf16_inputs"):
+        out[name]["abs_dE_vs_fp64"] = abs(out[name]["final_E"] - out["fp64"]["final_E"])
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_footprint(args):
     """Memory footprint of enforced sparsity (Sec. 3.2, the maximum-nnz
     figure): the largest number of factor nonzeros held at any point of a run
@@ -501,6 +539,8 @@ def main():
         return run_batch(args)
     if args.sweep_t:
         return run_sweep_t(args)
+    if args.bf16_effect:
+        return run_bf16_effect(args)
     import torch
     import paper_1510_05237_gb300 as E
     ws, rank, local = dist_env()
