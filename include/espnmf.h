@@ -345,22 +345,28 @@ espnmf_status espnmf_set_option(espnmf_ctx *ctx, espnmf_option opt,
 espnmf_status espnmf_spmm_config(espnmf_ctx *ctx, int32_t product, int32_t *split,
                                  int32_t *carveout, int32_t *mask);
 
-/* espnmf_sequential -- Alg. 3 (sequential ALS, Sec. 4) with rank-1 new
- * topics (k2 = 1, the case the paper times): the k topics are found one
- * after another.  For topic j, with the converged topics U1 = U[:, :j] and
- * V1 = V[:, :j], the new column u starts from u0 (the same initial guess for
- * every topic) and `iters` times
- *   v = (A^T u - V1 (U1^T u)) / (u^T u)     (Eq. 7), projected, top-t_v,
- *   u = (A v - U1 (V1^T v)) / (v^T v)       (Eq. 8), projected, top-t_u;
- * then U[:, j] = u, V[:, j] = v.  The sparse products, the division, the
- * projection and the top-t rule are those of Alg. 2 with k = 1 (a k = 1
- * context built from A); the deflation term runs in FP64 sums.  A: as for
- * espnmf_init (copied).  u0: n values (dtype u0_dtype, host or device).
- * U_out (n x k) and V_out (m x k): row-major DEVICE buffers of the compute
- * dtype, written when the call returns ESPNMF_OK (it synchronises).
- * Errors: espnmf_last_error(NULL).  Requires 1 <= k <= min(n, m), iters >= 1. */
-espnmf_status espnmf_sequential(const espnmf_csr *A, int32_t k, int64_t t_u, int64_t t_v,
-                                int32_t iters, espnmf_dtype compute, const void *u0,
+/* espnmf_sequential -- Alg. 3 (sequential ALS, Sec. 4): k = eta * k2
+ * topics found k2 at a time.  Block b (columns b*k2 .. b*k2 + k2 - 1) starts
+ * from U2 = U0 (the same n x k2 initial guess for every block) and, with the
+ * converged topics U1 = U[:, :b*k2], V1 = V[:, :b*k2], runs `iters` times
+ *   V2 = (A^T U2 - V1 (U1^T U2)) (U2^T U2)^-1   (Eq. 7), projected, top-t_v
+ *                                                per column,
+ *   U2 = (A V2 - U1 (V1^T V2)) (V2^T V2)^-1     (Eq. 8), projected, top-t_u
+ *                                                per column;
+ * then U[:, block] = U2, V[:, block] = V2.  The first block (no converged
+ * topics) is Alg. 2 with k2 topics from U0, the START of Alg. 3.  k2 = 1
+ * gives rank-1 topics, the case the paper times, where the k2 x k2 solve is
+ * a division.  The sparse products, the solve, the projection and the top-t
+ * rule are those of Alg. 2 with k = k2 (a k = k2 context built from A, FP32
+ * or FP64 form); the deflation term runs in FP64 sums.  A: as for
+ * espnmf_init (copied).  U0: n x k2 row-major (dtype u0_dtype, host or
+ * device).  U_out (n x k) and V_out (m x k): row-major DEVICE buffers of the
+ * compute dtype, written when the call returns ESPNMF_OK (it synchronises).
+ * Errors: espnmf_last_error(NULL).  Requires 1 <= k2, k a multiple of k2,
+ * k <= min(n, m), iters >= 1; a singular k2 x k2 Gram (other than zero
+ * columns, which give zero output columns) returns ESPNMF_ERR_SINGULAR. */
+espnmf_status espnmf_sequential(const espnmf_csr *A, int32_t k, int32_t k2, int64_t t_u,
+                                int64_t t_v, int32_t iters, espnmf_dtype compute, const void *U0,
                                 espnmf_dtype u0_dtype, int32_t u0_on_device, void *U_out,
                                 void *V_out, void *stream);
 

@@ -84,7 +84,7 @@ def _load(threads: bool = False):
             "or_lambda_max": (d, [i32, P]),
             "or_pg_step": (ctypes.c_int, csr + [P, P, ctypes.c_int]),
             "or_topic_accuracy": (ctypes.c_int, [i64, i32, P, P, i32, P]),
-            "or_sequential": (ctypes.c_int, csr[:5] + [i32, P, i64, i64, i32, P, P, P, P]),
+            "or_sequential": (ctypes.c_int, csr[:5] + [i32, i32, P, i64, i64, i32, P, P, P, P]),
             "or_set_threads": (None, [i32]),
         }
         for name, (res, args) in sig.items():
@@ -290,19 +290,22 @@ def topic_accuracy(V: np.ndarray, labels: np.ndarray, n_J: int) -> np.ndarray:
     return acc
 
 
-def sequential(A, u0: np.ndarray, k: int, t_u: int, t_v: int, iters: int,
-               return_pre: bool = False):
-    """Sec. 4, Alg. 3 with rank-1 topics: k topics found one after another,
-    each from the same initial guess u0 (n-vector), ``iters`` sweeps each.
-    Returns (U, V), and with ``return_pre`` also the last topic's last v and
-    u before the projection."""
-    u0 = _f64(np.asarray(u0).reshape(-1))
+def sequential(A, U0: np.ndarray, k: int, t_u: int, t_v: int, iters: int,
+               return_pre: bool = False, k2: int = 1):
+    """Sec. 4, Alg. 3: k topics found k2 at a time (k a multiple of k2), each
+    block from the same initial guess U0 (n x k2; an n-vector when k2 = 1),
+    ``iters`` sweeps per block; the first block is Alg. 2.  Returns (U, V),
+    and with ``return_pre`` also the last block's last V2 and U2 before the
+    projection (m x k2, n x k2; vectors when k2 = 1)."""
+    U0 = _f64(np.asarray(U0).reshape(A.n, k2))
     U = np.zeros((A.n, k))
     V = np.zeros((A.m, k))
-    vpre = np.zeros(A.m)
-    upre = np.zeros(A.n)
+    vpre = np.zeros((A.m, k2))
+    upre = np.zeros((A.n, k2))
     c = _CSR(A)
-    _check(_load().or_sequential(*c.args(1)[:5], int(k), _ptr(u0), int(t_u), int(t_v),
+    _check(_load().or_sequential(*c.args(1)[:5], int(k), int(k2), _ptr(U0), int(t_u), int(t_v),
                                  int(iters), _ptr(U), _ptr(V), _ptr(vpre), _ptr(upre)),
            "sequential")
+    if k2 == 1:
+        vpre, upre = vpre[:, 0], upre[:, 0]
     return (U, V, vpre, upre) if return_pre else (U, V)

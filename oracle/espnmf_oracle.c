@@ -577,79 +577,105 @@ int or_topic_accuracy(int64_t m, int32_t k, const double *V, const int32_t *labe
 }
 
 /*
- * Sec. 4, Alg. 3 (sequential ALS) with rank-1 new topics (k2 = 1, the case
- * the paper times): the k topics are found one after another.  For topic j,
- * with the converged topics U1 = U[:, :j] and V1 = V[:, :j] (Eq. 5 splits
- * U V^T = U1 V1^T + U2 V2^T):
- *   START  u = u0 (the same initial guess for every topic, a reading)
- *   repeat iters times:
- *     v = (A^T u - V1 (U1^T u)) / (u^T u)   (Eq. 7), project, keep t_v largest
- *     u = (A v - U1 (V1^T v)) / (v^T v)     (Eq. 8), project, keep t_u largest
- *   U[:, j] = u, V[:, j] = v
- * A zero divisor (u or v all zero) gives a zero update (the reading for a
- * zero Gram column).  If vpre/upre are non-NULL they receive the last
- * topic's last v and u before the projection.  U (n x k), V (m x k)
- * row-major outputs.
+ * Sec. 4, Alg. 3 (sequential ALS): the k = eta * k2 topics are found k2 at a
+ * time.  Eq. 5 splits U V^T = U1 V1^T + U2 V2^T, with U1, V1 the topics
+ * converged so far (the first k1 = b * k2 columns of U, V when block b is
+ * found) and U2 (n x k2), V2 (m x k2) the new block.
+ *   START (b = 0): U2, V2 from Alg. 2 with k2 topics and U0 as the initial
+ *          guess (or_update_V / or_update_U, iters sweeps).
+ *   NEXT  (b = 1 .. eta - 1): U2 = U0 (the same initial guess for every
+ *          block, a reading), then iters times
+ *            V2 = (A^T U2 - V1 (U1^T U2)) (U2^T U2)^-1   (Eq. 7),
+ *                 projected, t_v largest kept per column;
+ *            U2 = (A V2 - U1 (V1^T V2)) (V2^T V2)^-1     (Eq. 8),
+ *                 projected, t_u largest kept per column.
+ *   Append: U[:, k1 : k1 + k2] = U2, V[:, k1 : k1 + k2] = V2.
+ * The k2 x k2 solves are those of Alg. 2 (or_ls_solve: a zero Gram column
+ * gives a zero output column).  For k2 = 1 the solve is the division by
+ * u^T u (v^T v) the paper mentions.  U0: n x k2 row-major.  If vpre/upre
+ * are non-NULL they receive the last block's last V2 (m x k2) and U2
+ * (n x k2) before the projection.  U (n x k), V (m x k) row-major outputs.
  */
 int or_sequential(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *colidx,
-                  const double *val, int32_t k, const double *u0, int64_t t_u, int64_t t_v,
-                  int32_t iters, double *U, double *V, double *vpre, double *upre)
+                  const double *val, int32_t k, int32_t k2, const double *U0, int64_t t_u,
+                  int64_t t_v, int32_t iters, double *U, double *V, double *vpre, double *upre)
 {
-    if (k < 1 || iters < 1 || t_u < 0 || t_v < 0) return OR_ERR_INVALID_ARG;
-    double *u = (double *)malloc(sizeof(double) * (size_t)n);
-    double *v = (double *)malloc(sizeof(double) * (size_t)m);
-    double *g = (double *)malloc(sizeof(double) * (size_t)k);
-    if (!u || !v || !g) { free(u); free(v); free(g); return OR_ERR_OOM; }
+    if (k < 1 || k2 < 1 || k % k2 != 0 || iters < 1 || t_u < 0 || t_v < 0)
+        return OR_ERR_INVALID_ARG;
+    const int32_t eta = k / k2;
+    const size_t nk2 = (size_t)n * (size_t)k2, mk2 = (size_t)m * (size_t)k2;
+    double *U2 = (double *)malloc(sizeof(double) * nk2 + 8);
+    double *V2 = (double *)malloc(sizeof(double) * mk2 + 8);
+    double *Y = (double *)malloc(sizeof(double) * (nk2 > mk2 ? nk2 : mk2) + 8);
+    double *G = (double *)malloc(sizeof(double) * (size_t)k2 * (size_t)k2 + 8);
+    double *g = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k2 + 8);
+    if (!U2 || !V2 || !Y || !G || !g) {
+        free(U2); free(V2); free(Y); free(G); free(g);
+        return OR_ERR_OOM;
+    }
     memset(U, 0, sizeof(double) * (size_t)n * (size_t)k);
     memset(V, 0, sizeof(double) * (size_t)m * (size_t)k);
     int st = OR_OK;
-    for (int32_t j = 0; j < k && st == OR_OK; ++j) {
-        memcpy(u, u0, sizeof(double) * (size_t)n);
+    for (int32_t b = 0; b < eta && st == OR_OK; ++b) {
+        const int32_t k1 = b * k2;
+        const int last = b == eta - 1;
+        memcpy(U2, U0, sizeof(double) * nk2);
         for (int32_t it = 0; it < iters && st == OR_OK; ++it) {
-            /* Eq. 7 */
-            or_spmm_At(n, m, rowptr, colidx, val, 1, u, v);
-            for (int32_t c = 0; c < j; ++c) {
-                double s = 0.0;
-                for (int64_t i = 0; i < n; ++i) s += U[i * k + c] * u[i];
-                g[c] = s;
+            double *vp = last && it == iters - 1 ? vpre : NULL;
+            double *up = last && it == iters - 1 ? upre : NULL;
+            if (b == 0) {
+                /* START: Alg. 2 steps 1-4 with k2 topics */
+                st = or_update_V(n, m, rowptr, colidx, val, k2, U2, t_v, OR_TOPT_COLUMN, V2, vp);
+                if (st == OR_OK)
+                    st = or_update_U(n, m, rowptr, colidx, val, k2, V2, t_u, OR_TOPT_COLUMN, U2, up);
+                continue;
             }
-            for (int64_t i = 0; i < m; ++i) {
-                double d = 0.0;
-                for (int32_t c = 0; c < j; ++c) d += V[i * k + c] * g[c];
-                v[i] -= d;
-            }
-            double uu = 0.0;
-            for (int64_t i = 0; i < n; ++i) uu += u[i] * u[i];
-            for (int64_t i = 0; i < m; ++i) v[i] = uu != 0.0 ? v[i] / uu : 0.0;
-            if (vpre && j == k - 1 && it == iters - 1) memcpy(vpre, v, sizeof(double) * (size_t)m);
-            st = or_project(v, m);
-            if (st == OR_OK) st = or_topt(v, m, 1, t_v, OR_TOPT_COLUMN);
+            /* Eq. 7: Y = A^T U2 - V1 (U1^T U2), then V2 = Y (U2^T U2)^-1 */
+            or_spmm_At(n, m, rowptr, colidx, val, k2, U2, Y);
+            for (int32_t c = 0; c < k1; ++c)
+                for (int32_t j = 0; j < k2; ++j) {
+                    double s = 0.0;
+                    for (int64_t i = 0; i < n; ++i) s += U[i * k + c] * U2[i * k2 + j];
+                    g[c * k2 + j] = s;
+                }
+            for (int64_t i = 0; i < m; ++i)
+                for (int32_t j = 0; j < k2; ++j) {
+                    double d = 0.0;
+                    for (int32_t c = 0; c < k1; ++c) d += V[i * k + c] * g[c * k2 + j];
+                    Y[i * k2 + j] -= d;
+                }
+            or_gram(n, k2, U2, G);
+            st = or_ls_solve(m, k2, Y, G, V2);
+            if (st == OR_OK && vp) memcpy(vp, V2, sizeof(double) * mk2);
+            if (st == OR_OK) st = or_project(V2, (int64_t)mk2);
+            if (st == OR_OK) st = or_topt(V2, m, k2, t_v, OR_TOPT_COLUMN);
             if (st != OR_OK) break;
-            /* Eq. 8 */
-            or_spmm_A(n, m, rowptr, colidx, val, 1, v, u);
-            for (int32_t c = 0; c < j; ++c) {
-                double s = 0.0;
-                for (int64_t i = 0; i < m; ++i) s += V[i * k + c] * v[i];
-                g[c] = s;
-            }
-            for (int64_t i = 0; i < n; ++i) {
-                double d = 0.0;
-                for (int32_t c = 0; c < j; ++c) d += U[i * k + c] * g[c];
-                u[i] -= d;
-            }
-            double vv = 0.0;
-            for (int64_t i = 0; i < m; ++i) vv += v[i] * v[i];
-            for (int64_t i = 0; i < n; ++i) u[i] = vv != 0.0 ? u[i] / vv : 0.0;
-            if (upre && j == k - 1 && it == iters - 1) memcpy(upre, u, sizeof(double) * (size_t)n);
-            st = or_project(u, n);
-            if (st == OR_OK) st = or_topt(u, n, 1, t_u, OR_TOPT_COLUMN);
+            /* Eq. 8: Y = A V2 - U1 (V1^T V2), then U2 = Y (V2^T V2)^-1 */
+            or_spmm_A(n, m, rowptr, colidx, val, k2, V2, Y);
+            for (int32_t c = 0; c < k1; ++c)
+                for (int32_t j = 0; j < k2; ++j) {
+                    double s = 0.0;
+                    for (int64_t i = 0; i < m; ++i) s += V[i * k + c] * V2[i * k2 + j];
+                    g[c * k2 + j] = s;
+                }
+            for (int64_t i = 0; i < n; ++i)
+                for (int32_t j = 0; j < k2; ++j) {
+                    double d = 0.0;
+                    for (int32_t c = 0; c < k1; ++c) d += U[i * k + c] * g[c * k2 + j];
+                    Y[i * k2 + j] -= d;
+                }
+            or_gram(m, k2, V2, G);
+            st = or_ls_solve(n, k2, Y, G, U2);
+            if (st == OR_OK && up) memcpy(up, U2, sizeof(double) * nk2);
+            if (st == OR_OK) st = or_project(U2, (int64_t)nk2);
+            if (st == OR_OK) st = or_topt(U2, n, k2, t_u, OR_TOPT_COLUMN);
         }
-        for (int64_t i = 0; i < n; ++i) U[i * k + j] = u[i];
-        for (int64_t i = 0; i < m; ++i) V[i * k + j] = v[i];
+        for (int64_t i = 0; i < n; ++i)
+            for (int32_t j = 0; j < k2; ++j) U[i * k + k1 + j] = U2[i * k2 + j];
+        for (int64_t i = 0; i < m; ++i)
+            for (int32_t j = 0; j < k2; ++j) V[i * k + k1 + j] = V2[i * k2 + j];
     }
-    free(u);
-    free(v);
-    free(g);
+    free(U2); free(V2); free(Y); free(G); free(g);
     return st;
 }
 

@@ -102,7 +102,8 @@ def load():
             "espnmf_load": [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i64)],
             "espnmf_sweeps_done": [P, ctypes.POINTER(i64)],
             "espnmf_select_stats": [P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
-            "espnmf_sequential": [ctypes.POINTER(_CSR), i32, i64, i64, i32, st, P, st, i32, P, P, P],
+            "espnmf_sequential": [ctypes.POINTER(_CSR), i32, i32, i64, i64, i32, st, P, st, i32, P, P,
+                                  P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -212,24 +213,27 @@ def espnmf_init(rowptr, colidx, values, n: int, m: int, k: int, t_u: int, t_v: i
 
 
 def espnmf_sequential(rowptr, colidx, values, n: int, m: int, k: int, t_u: int, t_v: int,
-                      iters: int, u0, compute: int = F32, stream=None):
-    """Alg. 3 (sequential ALS) with rank-1 topics; returns (U, V) as CUDA
+                      iters: int, U0, compute: int = F32, stream=None, k2: int = 1):
+    """Alg. 3 (sequential ALS): k topics found k2 at a time from the initial
+    guess U0 (n x k2, or an n-vector for k2 = 1); returns (U, V) as CUDA
     tensors of the compute dtype (n x k, m x k)."""
     import torch
     lib = load()
-    rp, d1, k1 = _ptr(rowptr)
-    ci, d2, k2 = _ptr(colidx)
-    va, d3, k3 = _ptr(values)
+    rp, d1, _ = _ptr(rowptr)
+    ci, d2, _ = _ptr(colidx)
+    va, d3, _ = _ptr(values)
     if not (d1 == d2 == d3):
         raise ValueError("rowptr, colidx and values must all be host or all device arrays")
+    if tuple(U0.shape) not in ((int(n), int(k2)),) + (((int(n),),) if k2 == 1 else ()):
+        raise ValueError(f"U0 must be n x k2 = {n} x {k2}, got {tuple(U0.shape)}")
     csr = _CSR(int(n), int(m), int(len(colidx)), rp, ci, va, _dtype_code(values), d1)
-    up, ud, uk = _ptr(u0)
+    up, ud, _ = _ptr(U0)
     tdt = torch.float64 if compute == F64 else torch.float32
     # written in full by the library, on its stream, before it returns
     U = torch.empty((int(n), int(k)), dtype=tdt, device="cuda")
     V = torch.empty((int(m), int(k)), dtype=tdt, device="cuda")
-    _check(lib.espnmf_sequential(ctypes.byref(csr), int(k), int(t_u), int(t_v), int(iters),
-                                 int(compute), up, _dtype_code(u0), ud,
+    _check(lib.espnmf_sequential(ctypes.byref(csr), int(k), int(k2), int(t_u), int(t_v),
+                                 int(iters), int(compute), up, _dtype_code(U0), ud,
                                  ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(V.data_ptr()),
                                  _stream_handle(stream)))
     return U, V

@@ -348,19 +348,20 @@ cudaError_t launch_solve_chol(const float* Y, int64_t ldy, int64_t rows, int k, 
                               bool project = true);
 cudaError_t setup_chol();
 
-// Alg. 3 (sequential ALS), rank-1 new topic: g = G1^T f over the first k1
-// columns of G1 (rows_f x ld1, the fixed factor's converged topics) and the
-// rank-1 factor f (row-packed: cnt, val with row stride ld), then
-// Y[i * ldy] -= (H1 g)_i for the rows_h rows of H1 (the updated factor's
-// converged topics).  g holds k1 doubles of scratch.
+// Alg. 3 (sequential ALS), a new block of k2 topics: g = G1^T F (k1 x k2)
+// over the first k1 columns of G1 (rows_f x ld1, the fixed factor's
+// converged topics) and the block factor F (row-packed: cnt, col, val with
+// row stride ld), then Y[i][j] -= (H1 g)_ij for the rows_h rows of H1 (the
+// updated factor's converged topics), j < k2.  g holds k1 * k2 doubles of
+// scratch.
 template <typename T>
 cudaError_t launch_seq_deflate(int64_t rows_f, const T* G1, int64_t rows_h, const T* H1, int ld1,
-                               int k1, const int32_t* cnt, const T* val, int ld, double* g, T* Y,
-                               int64_t ldy, cudaStream_t st);
-// H[i * ld1 + j] = the rank-1 factor's value in row i.
+                               int k1, int k2, const int32_t* cnt, const int32_t* col, const T* val,
+                               int ld, double* g, T* Y, int64_t ldy, cudaStream_t st);
+// H[i * ld1 + j0 + j] = the block factor's value in row i, column j < k2.
 template <typename T>
-cudaError_t launch_seq_append(int64_t rows, const int32_t* cnt, const T* val, int ld, T* H, int ld1,
-                              int j, cudaStream_t st);
+cudaError_t launch_seq_append(int64_t rows, const int32_t* cnt, const int32_t* col, const T* val,
+                              int ld, int k2, T* H, int ld1, int j0, cudaStream_t st);
 
 // out = sum of squares of val[0, count) and val2[0, count2) (val2 may be
 // NULL), in a fixed order.

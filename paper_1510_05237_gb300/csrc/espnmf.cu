@@ -77,7 +77,7 @@ struct Stat {
 }  // namespace
 
 // Alg. 3 (sequential ALS): the converged topics held densely (rows x ld1,
-// first k1 columns valid) while a k = 1 context finds the next one.
+// first k1 columns valid) while a k = k2 context finds the next block.
 struct Deflation {
     void* U1 = nullptr;
     void* V1 = nullptr;
@@ -833,11 +833,11 @@ espnmf_status half_update(espnmf_ctx* ctx, bool updV)
         const void* G1 = updV ? ctx->defl.U1 : ctx->defl.V1;
         void* H1 = updV ? ctx->defl.V1 : ctx->defl.U1;
         CU(is_f64(ctx) ? launch_seq_deflate<double>(O.rows, (const double*)G1, rows, (const double*)H1,
-                                                    ctx->defl.ld1, ctx->defl.k1, f.cnt,
+                                                    ctx->defl.ld1, ctx->defl.k1, ctx->k, f.cnt, f.col,
                                                     (const double*)f.val, f.ld, ctx->defl.g,
                                                     (double*)ctx->Y, ctx->ldy, ctx->st)
                        : launch_seq_deflate<float>(O.rows, (const float*)G1, rows, (const float*)H1,
-                                                   ctx->defl.ld1, ctx->defl.k1, f.cnt,
+                                                   ctx->defl.ld1, ctx->defl.k1, ctx->k, f.cnt, f.col,
                                                    (const float*)f.val, f.ld, ctx->defl.g,
                                                    (float*)ctx->Y, ctx->ldy, ctx->st));
     }
@@ -2453,25 +2453,27 @@ espnmf_status espnmf_batch_iterate(espnmf_batch* b, int32_t iters, espnmf_status
     return worst;
 }
 
-// Alg. 3 (sequential ALS, Sec. 4) with rank-1 new topics, on one k = 1
-// context: for each topic, the context's U is reset to u0, `iters` sweeps of
-// half-updates run with the converged topics subtracted after each sparse
-// product (the deflation hook of half_update), and the topic is appended to
-// the dense U1, V1.
-espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int64_t t_u, int64_t t_v,
-                                int32_t iters, espnmf_dtype compute, const void* u0,
+// Alg. 3 (sequential ALS, Sec. 4) on one k = k2 context: for each block of
+// k2 topics the context's U is reset to U0, `iters` sweeps of half-updates
+// run with the converged topics subtracted after each sparse product (the
+// deflation hook of half_update; none for the first block, which is Alg. 2
+// itself), and the block is appended to the dense U1, V1.
+espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int32_t k2, int64_t t_u,
+                                int64_t t_v, int32_t iters, espnmf_dtype compute, const void* U0,
                                 espnmf_dtype u0_dtype, int32_t u0_on_device, void* U_out,
                                 void* V_out, void* stream)
 {
     espnmf::set_thread_error("");
-    if (!A || !u0 || !U_out || !V_out)
-        return batch_fail(ESPNMF_ERR_INVALID_ARG, "A, u0, U_out and V_out must be non-NULL");
-    if (k < 1 || iters < 1)
-        return batch_fail(ESPNMF_ERR_INVALID_ARG, "need k >= 1 and iters >= 1");
+    if (!A || !U0 || !U_out || !V_out)
+        return batch_fail(ESPNMF_ERR_INVALID_ARG, "A, U0, U_out and V_out must be non-NULL");
+    if (k < 1 || k2 < 1 || iters < 1)
+        return batch_fail(ESPNMF_ERR_INVALID_ARG, "need k >= 1, k2 >= 1 and iters >= 1");
+    if (k % k2 != 0)
+        return batch_fail(ESPNMF_ERR_INVALID_ARG, "k must be a multiple of k2");
     if (k > A->n || k > A->m)
         return batch_fail(ESPNMF_ERR_INVALID_ARG, "k must be <= min(n, m)");
     espnmf_ctx* c = nullptr;
-    espnmf_status st = espnmf_init(&c, A, 1, t_u, t_v, ESPNMF_TOPT_COLUMN, compute, u0, u0_dtype,
+    espnmf_status st = espnmf_init(&c, A, k2, t_u, t_v, ESPNMF_TOPT_COLUMN, compute, U0, u0_dtype,
                                    u0_on_device, stream);
     if (st != ESPNMF_OK) return st;
     auto fail = [&](espnmf_status s) {
@@ -2485,16 +2487,16 @@ espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int64_t t_u, int
     Deflation& d = c->defl;
     if ((st = dmalloc(c, &d.U1, es * (size_t)n * k)) != ESPNMF_OK) return fail(st);
     if ((st = dmalloc(c, &d.V1, es * (size_t)m * k)) != ESPNMF_OK) return fail(st);
-    if ((st = dmalloc(c, &d.g, sizeof(double) * (size_t)k)) != ESPNMF_OK) return fail(st);
+    if ((st = dmalloc(c, &d.g, sizeof(double) * (size_t)k * k2)) != ESPNMF_OK) return fail(st);
     if (cudaMemsetAsync(d.U1, 0, es * (size_t)n * k, c->st) != cudaSuccess ||
         cudaMemsetAsync(d.V1, 0, es * (size_t)m * k, c->st) != cudaSuccess)
         return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: memset"));
     d.ld1 = k;
-    for (int32_t j = 0; j < k; ++j) {
+    for (int32_t j0 = 0; j0 < k; j0 += k2) {
         d.k1 = 0;
-        if (j > 0 && (st = espnmf_set_factor(c, ESPNMF_U, u0, u0_dtype, u0_on_device)) != ESPNMF_OK)
+        if (j0 > 0 && (st = espnmf_set_factor(c, ESPNMF_U, U0, u0_dtype, u0_on_device)) != ESPNMF_OK)
             return fail(st);
-        d.k1 = j;
+        d.k1 = j0;
         for (int32_t it = 0; it < iters; ++it) {
             if ((st = espnmf_als_update_V(c)) != ESPNMF_OK) return fail(st);
             if ((st = espnmf_als_update_U(c)) != ESPNMF_OK) return fail(st);
@@ -2502,15 +2504,15 @@ espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int64_t t_u, int
         d.k1 = 0;
         const EllDev& fu = c->U.buf[c->U.cur];
         const EllDev& fv = c->V.buf[c->V.cur];
-        cudaError_t e = f64 ? launch_seq_append<double>(n, fu.cnt, (const double*)fu.val, fu.ld,
-                                                        (double*)d.U1, k, j, c->st)
-                            : launch_seq_append<float>(n, fu.cnt, (const float*)fu.val, fu.ld,
-                                                       (float*)d.U1, k, j, c->st);
+        cudaError_t e = f64 ? launch_seq_append<double>(n, fu.cnt, fu.col, (const double*)fu.val,
+                                                        fu.ld, k2, (double*)d.U1, k, j0, c->st)
+                            : launch_seq_append<float>(n, fu.cnt, fu.col, (const float*)fu.val,
+                                                       fu.ld, k2, (float*)d.U1, k, j0, c->st);
         if (e == cudaSuccess)
-            e = f64 ? launch_seq_append<double>(m, fv.cnt, (const double*)fv.val, fv.ld,
-                                                (double*)d.V1, k, j, c->st)
-                    : launch_seq_append<float>(m, fv.cnt, (const float*)fv.val, fv.ld,
-                                               (float*)d.V1, k, j, c->st);
+            e = f64 ? launch_seq_append<double>(m, fv.cnt, fv.col, (const double*)fv.val, fv.ld, k2,
+                                                (double*)d.V1, k, j0, c->st)
+                    : launch_seq_append<float>(m, fv.cnt, fv.col, (const float*)fv.val, fv.ld, k2,
+                                               (float*)d.V1, k, j0, c->st);
         if (e != cudaSuccess)
             return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: %s", cudaGetErrorString(e)));
     }

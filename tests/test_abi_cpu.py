@@ -102,14 +102,16 @@ def test_sequential_validates_and_needs_a_gpu(lib):
     out_u = np.zeros(A.n * 4)
     out_v = np.zeros(A.m * 4)
 
-    def call(k, iters):
-        return lib.espnmf_sequential(ctypes.byref(csr), k, 10, 10, iters, E.F64,
+    def call(k, iters, k2=1):
+        return lib.espnmf_sequential(ctypes.byref(csr), k, k2, 10, 10, iters, E.F64,
                                      ctypes.c_void_p(u0.ctypes.data), E.F64, 0,
                                      ctypes.c_void_p(out_u.ctypes.data),
                                      ctypes.c_void_p(out_v.ctypes.data), None)
     assert call(0, 1) == E.ERR_INVALID_ARG
     assert call(2, 0) == E.ERR_INVALID_ARG
     assert call(A.m + 1, 1) == E.ERR_INVALID_ARG
+    assert call(3, 1, k2=2) == E.ERR_INVALID_ARG      # k not a multiple of k2
+    assert call(2, 1, k2=0) == E.ERR_INVALID_ARG
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         assert call(2, 1) == E.ERR_CUDA
