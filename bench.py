@@ -67,6 +67,11 @@ def parse():
     p.add_argument("--sweep-t", action="store_true",
                    help="instead of the benchmark: R and E after 75 iterations against t for "
                         "sparse U, sparse V and both (the shape of Sec. 3.1's figure)")
+    p.add_argument("--large", action="store_true",
+                   help="instead of the benchmark: the 1M x 2M Zipf(1.05) corpus (~400M nnz), "
+                        "k = 100, t = 5000 per column, 10 timed sweeps, FP32 and FP64 forms")
+    p.add_argument("--large-scale", type=float, default=1.0,
+                   help="with --large: shrink the corpus (n, m by this factor)")
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--spmm-shape", default=None,
                    help="SPLIT,CARVEOUT,MASK: fix the sparse products' launch shape "
@@ -446,6 +451,114 @@ def run_bf16_effect(args):
     return 0
 
 
+def mem_available_gb() -> float:
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 2**20
+    except OSError:
+        pass
+    return 0.0
+
+
+def peak_rss_gb() -> float:
+    try:
+        for line in open("/proc/self/status"):
+            if line.startswith("VmHWM:"):
+                return int(line.split()[1]) / 2**20
+    except OSError:
+        pass
+    return 0.0
+
+
+def run_large(args):
+    """The large corpus: 1M terms x 2M docs, Zipf(1.05) term ids, lognormal
+    lengths with mean 200 (~400M nnz), k = 100, t = 5000 per column, 10
+    sweeps.  The corpus is generated on the device (gen.device_corpus); the
+    FP32 form is timed with CUDA events over 10 graph-replayed sweeps after
+    3 warm-up sweeps (A, 3.2 GB per orientation, is far larger than L2), the
+    sparse product's roofline comes from the per-kernel event profile, and
+    the FP64 form runs the same 13 sweeps for the final-error comparison.
+    espnmf_init builds A's layouts on the host (~25 GB at this size), so the
+    run is skipped with an "unavailable" line when the host has less than
+    64 GB available.  Prints one JSON line."""
+    import torch
+    import paper_1510_05237_gb300 as E
+    from gen.device_corpus import uniform_init_device, zipf_1m_2m_device
+    torch.cuda.set_device(0)
+    k, t, sweeps, warm = 100, max(1, int(round(5000 * args.large_scale))), 10, 3
+    need = 64.0 * min(1.0, args.large_scale * 4)
+    avail = mem_available_gb()
+    free_dev = torch.cuda.mem_get_info()[0] / 2**30
+    if avail < need or free_dev < 80.0 * min(1.0, args.large_scale * 4):
+        print(json.dumps({"experiment": "large", "unavailable":
+                          f"host MemAvailable {avail:.0f} GB (need {need:.0f}) or device free "
+                          f"{free_dev:.0f} GB too small"}), flush=True)
+        return 0
+    t0 = time.perf_counter()
+    A = zipf_1m_2m_device(seed=args.seed + 1, scale=args.large_scale)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    U0 = uniform_init_device(A.n, k, args.seed + 1)
+    stream = torch.cuda.Stream()
+    out = {"experiment": "large", "workload": A.name, "n": A.n, "m": A.m, "nnz": A.nnz, "k": k,
+           "t": t, "sweeps_timed": sweeps, "warmup": warm, "generation_seconds": t_gen,
+           "host_mem_available_gb": avail, "data": "synthetic, generated on the device"}
+    Efinal = {}
+    for comp, name in ((E.F32, "fp32"), (E.F64, "fp64")):
+        vals = A.val if comp == E.F32 else A.val.double()
+        u0 = U0 if comp == E.F32 else U0.double()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = E.espnmf_init(A.rowptr, A.colidx, vals, A.n, A.m, k, t, t, E.TOPT_COLUMN, comp, u0,
+                            stream=stream)
+        E.espnmf_sync(ctx)
+        t_init = time.perf_counter() - t0
+        E.espnmf_iterate(ctx, warm, want_measures=False)
+        E.espnmf_sync(ctx)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        E.espnmf_iterate(ctx, sweeps, want_measures=False)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / sweeps
+        Efinal[name] = float(E.espnmf_error(ctx))
+        res = {"init_seconds": t_init, "ms_per_sweep": ms, "value": 1000.0 / ms, "unit": UNIT,
+               "final_E": Efinal[name], "sweeps_before_E": warm + sweeps,
+               "host_peak_rss_gb": peak_rss_gb()}
+        if comp == E.F32:
+            E.espnmf_set_option(ctx, E.OPT_PROFILE, 1)
+            E.espnmf_kernel_stats_reset(ctx)
+            E.espnmf_iterate(ctx, 3, want_measures=False)
+            stats = E.espnmf_kernel_stats(ctx)
+            E.espnmf_set_option(ctx, E.OPT_PROFILE, 0)
+            get = lambda nm: stats.get(nm, (0, 0.0, 0.0))
+            t_prod = sum(get(nm)[1] for nm in ("spmm_AV", "spmm_AtU", "spmm_freq_AV",
+                                               "spmm_freq_AtU", "spmm_combine")) / 3 / 2
+            bpp = (2 * A.nnz * 8 + (A.n + 1 + A.m + 1) * 8 + (A.n + A.m) * k * 4) / 2.0
+            hbm, src = peaks()
+            ach = bpp / (t_prod / 1000.0) / 1e9
+            res["roofline_spmm"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                    "frac": ach / hbm, "peak_source": src,
+                                    "bytes_per_launch": bpp, "ms_per_launch": t_prod,
+                                    "per_launch": "one sparse product (mean of A V and A^T U)"}
+            tot = sum(v[1] for v in stats.values())
+            res["kernels"] = {nm: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1),
+                                   "share": v[1] / max(tot, 1e-12)}
+                              for nm, v in stats.items() if v[0] > 0}
+            res["spmm_frequent"] = {nm: E.espnmf_spmm_frequent(ctx, p)
+                                    for nm, p in (("AV", 0), ("AtU", 1))}
+        E.espnmf_destroy(ctx)
+        del vals, u0
+        torch.cuda.empty_cache()
+        out[name] = res
+    out["abs_dE_fp32_vs_fp64"] = abs(Efinal["fp32"] - Efinal["fp64"])
+    out["speedup_fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_footprint(args):
     """Memory footprint of enforced sparsity (Sec. 3.2, the maximum-nnz
     figure): the largest number of factor nonzeros held at any point of a run
@@ -557,6 +670,8 @@ def main():
         return run_sweep_t(args)
     if args.bf16_effect:
         return run_bf16_effect(args)
+    if args.large:
+        return run_large(args)
     import torch
     import paper_1510_05237_gb300 as E
     ws, rank, local = dist_env()
