@@ -362,13 +362,16 @@ espnmf_status espnmf_spmm_config(espnmf_ctx *ctx, int32_t product, int32_t *spli
  * espnmf_init (copied).  U0: n x k2 row-major (dtype u0_dtype, host or
  * device).  U_out (n x k) and V_out (m x k): row-major DEVICE buffers of the
  * compute dtype, written when the call returns ESPNMF_OK (it synchronises).
+ * seconds_out (may be NULL): the stream time from the end of the context's
+ * set-up to the last block's append (CUDA events on the call's stream): the
+ * ALS iterations of all blocks, without building A's layouts.
  * Errors: espnmf_last_error(NULL).  Requires 1 <= k2, k a multiple of k2,
  * k <= min(n, m), iters >= 1; a singular k2 x k2 Gram (other than zero
  * columns, which give zero output columns) returns ESPNMF_ERR_SINGULAR. */
 espnmf_status espnmf_sequential(const espnmf_csr *A, int32_t k, int32_t k2, int64_t t_u,
                                 int64_t t_v, int32_t iters, espnmf_dtype compute, const void *U0,
                                 espnmf_dtype u0_dtype, int32_t u0_on_device, void *U_out,
-                                void *V_out, void *stream);
+                                void *V_out, double *seconds_out, void *stream);
 
 /* espnmf_select_stats -- how the column selections of this context's
  * enforcement steps (FP32 form, column mode) found their thresholds since

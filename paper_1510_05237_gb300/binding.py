@@ -103,7 +103,7 @@ def load():
             "espnmf_sweeps_done": [P, ctypes.POINTER(i64)],
             "espnmf_select_stats": [P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
             "espnmf_sequential": [ctypes.POINTER(_CSR), i32, i32, i64, i64, i32, st, P, st, i32, P, P,
-                                  P],
+                                  P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -213,10 +213,12 @@ def espnmf_init(rowptr, colidx, values, n: int, m: int, k: int, t_u: int, t_v: i
 
 
 def espnmf_sequential(rowptr, colidx, values, n: int, m: int, k: int, t_u: int, t_v: int,
-                      iters: int, U0, compute: int = F32, stream=None, k2: int = 1):
+                      iters: int, U0, compute: int = F32, stream=None, k2: int = 1,
+                      return_seconds: bool = False):
     """Alg. 3 (sequential ALS): k topics found k2 at a time from the initial
     guess U0 (n x k2, or an n-vector for k2 = 1); returns (U, V) as CUDA
-    tensors of the compute dtype (n x k, m x k)."""
+    tensors of the compute dtype (n x k, m x k), and with ``return_seconds``
+    also the stream time of the iterations (set-up excluded)."""
     import torch
     lib = load()
     rp, d1, _ = _ptr(rowptr)
@@ -232,11 +234,12 @@ def espnmf_sequential(rowptr, colidx, values, n: int, m: int, k: int, t_u: int, 
     # written in full by the library, on its stream, before it returns
     U = torch.empty((int(n), int(k)), dtype=tdt, device="cuda")
     V = torch.empty((int(m), int(k)), dtype=tdt, device="cuda")
+    secs = ctypes.c_double()
     _check(lib.espnmf_sequential(ctypes.byref(csr), int(k), int(k2), int(t_u), int(t_v),
                                  int(iters), int(compute), up, _dtype_code(U0), ud,
                                  ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(V.data_ptr()),
-                                 _stream_handle(stream)))
-    return U, V
+                                 ctypes.byref(secs), _stream_handle(stream)))
+    return (U, V, secs.value) if return_seconds else (U, V)
 
 
 def espnmf_destroy(ctx: Context):

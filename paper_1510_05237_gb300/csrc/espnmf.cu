@@ -2461,7 +2461,7 @@ espnmf_status espnmf_batch_iterate(espnmf_batch* b, int32_t iters, espnmf_status
 espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int32_t k2, int64_t t_u,
                                 int64_t t_v, int32_t iters, espnmf_dtype compute, const void* U0,
                                 espnmf_dtype u0_dtype, int32_t u0_on_device, void* U_out,
-                                void* V_out, void* stream)
+                                void* V_out, double* seconds_out, void* stream)
 {
     espnmf::set_thread_error("");
     if (!A || !U0 || !U_out || !V_out)
@@ -2476,11 +2476,17 @@ espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int32_t k2, int6
     espnmf_status st = espnmf_init(&c, A, k2, t_u, t_v, ESPNMF_TOPT_COLUMN, compute, U0, u0_dtype,
                                    u0_on_device, stream);
     if (st != ESPNMF_OK) return st;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     auto fail = [&](espnmf_status s) {
         const std::string msg = c->err;
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
         espnmf_destroy(c);
         return batch_fail(s, msg.empty() ? "sequential ALS failed" : msg);
     };
+    if (seconds_out &&
+        (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess))
+        return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: event"));
     const bool f64 = is_f64(c);
     const size_t es = c->esz;
     const int64_t n = c->n, m = c->m;
@@ -2492,6 +2498,8 @@ espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int32_t k2, int6
         cudaMemsetAsync(d.V1, 0, es * (size_t)m * k, c->st) != cudaSuccess)
         return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: memset"));
     d.ld1 = k;
+    if (ev[0] && cudaEventRecord(ev[0], c->st) != cudaSuccess)
+        return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: event"));
     for (int32_t j0 = 0; j0 < k; j0 += k2) {
         d.k1 = 0;
         if (j0 > 0 && (st = espnmf_set_factor(c, ESPNMF_U, U0, u0_dtype, u0_on_device)) != ESPNMF_OK)
@@ -2516,12 +2524,22 @@ espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int32_t k2, int6
         if (e != cudaSuccess)
             return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: %s", cudaGetErrorString(e)));
     }
+    if (ev[1] && cudaEventRecord(ev[1], c->st) != cudaSuccess)
+        return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: event"));
     if (cudaMemcpyAsync(U_out, d.U1, es * (size_t)n * k, cudaMemcpyDeviceToDevice, c->st) != cudaSuccess ||
         cudaMemcpyAsync(V_out, d.V1, es * (size_t)m * k, cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
         return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: copy-out"));
     if ((st = check_status(c)) != ESPNMF_OK) return fail(st);
     if (cudaStreamSynchronize(c->st) != cudaSuccess)
         return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: synchronize"));
+    if (seconds_out) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess)
+            return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: event time"));
+        *seconds_out = ms / 1000.0;
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
     espnmf_destroy(c);
     return ESPNMF_OK;
 }

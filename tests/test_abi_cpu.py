@@ -106,7 +106,7 @@ def test_sequential_validates_and_needs_a_gpu(lib):
         return lib.espnmf_sequential(ctypes.byref(csr), k, k2, 10, 10, iters, E.F64,
                                      ctypes.c_void_p(u0.ctypes.data), E.F64, 0,
                                      ctypes.c_void_p(out_u.ctypes.data),
-                                     ctypes.c_void_p(out_v.ctypes.data), None)
+                                     ctypes.c_void_p(out_v.ctypes.data), None, None)
     assert call(0, 1) == E.ERR_INVALID_ARG
     assert call(2, 0) == E.ERR_INVALID_ARG
     assert call(A.m + 1, 1) == E.ERR_INVALID_ARG
