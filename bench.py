@@ -548,6 +548,26 @@ def run_large(args):
                               for nm, v in stats.items() if v[0] > 0}
             res["spmm_frequent"] = {nm: E.espnmf_spmm_frequent(ctx, p)
                                     for nm, p in (("AV", 0), ("AtU", 1))}
+            # multiply-adds of A^T U at this iterate: entry (doc, term) adds
+            # the term's U row, nnz_U(term) pairs; the frequent table holds
+            # the h terms of highest document frequency
+            Ud = torch.from_numpy(E.espnmf_get_factor(ctx, E.U)).to("cuda")
+            row_nnz = (Ud != 0).sum(dim=1).double()
+            del Ud
+            df = torch.diff(A.rowptr).double()
+            h = res["spmm_frequent"]["AtU"][0]
+            in_tab = torch.zeros_like(df, dtype=torch.bool)
+            if h > 0:
+                in_tab[torch.topk(df, h).indices] = True
+            fma = df * row_nnz
+            res["atu_work"] = {
+                "fma_total": float(fma.sum()), "fma_table": float(fma[in_tab].sum()),
+                "fma_sell": float(fma[~in_tab].sum()),
+                "entries_sell": float(df[~in_tab].sum()),
+                "pairs_per_sell_entry": float(fma[~in_tab].sum() / max(float(df[~in_tab].sum()), 1.0)),
+                "u_rows_nonzero": int((row_nnz > 0).sum()),
+                "u_rows_over_16": int((row_nnz > 16).sum()),
+                "u_nnz": int(row_nnz.sum())}
         E.espnmf_destroy(ctx)
         del vals, u0
         torch.cuda.empty_cache()
