@@ -300,15 +300,123 @@ void parallel_chunks(int64_t total, F&& fn)
     for (auto& x : th) x.join();
 }
 
+// fn(lo, hi) over [0, total) cut into contiguous chunks of about equal
+// weight, where prefix[i] is the weight of items [0, i) (row pointers, slice
+// pointers), on up to eight host threads.
+template <typename F>
+void parallel_weighted(int64_t total, const int64_t* prefix, F&& fn)
+{
+    unsigned hw = std::thread::hardware_concurrency();
+    int T = (int)std::min<unsigned>(8u, hw ? hw : 1u);
+    const int64_t W = prefix[total] - prefix[0];
+    if (W < (1 << 16) || total < 2) T = 1;
+    std::vector<int64_t> cut(T + 1, total);
+    cut[0] = 0;
+    for (int t = 1; t < T; ++t)
+        cut[t] = std::lower_bound(prefix, prefix + total + 1, prefix[0] + W * t / T) - prefix;
+    std::vector<std::thread> th;
+    for (int t = 1; t < T; ++t)
+        if (cut[t] < cut[t + 1]) th.emplace_back([&, t] { fn(cut[t], cut[t + 1]); });
+    if (cut[0] < cut[1]) fn(cut[0], cut[1]);
+    for (auto& x : th) x.join();
+}
+
+// Host vectors whose resize leaves the new elements uninitialised (every
+// element is written by the parallel passes that follow), so that building
+// a layout does not pay a serial zero-fill of each buffer first.
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+    template <typename U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <typename U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <typename U>
+    void construct(U* p) noexcept
+    {
+        ::new (static_cast<void*>(p)) U;
+    }
+    template <typename U, typename... Args>
+    void construct(U* p, Args&&... args)
+    {
+        ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+    }
+};
+template <typename T>
+using hvec = std::vector<T, NoInitAlloc<T>>;
+
+// CSC of an n x m CSR matrix (= CSR of its transpose), rows ascending inside
+// each column: a counting sort by column over row ranges of about equal nnz,
+// one per host thread.  Thread t's entries of column j are placed after
+// those of threads < t, so every column lists its rows in ascending order,
+// exactly as one serial pass would.
+void transpose_csr(int64_t n, int64_t m, const int64_t* rp, const int32_t* ci, const double* vv,
+                   std::vector<int64_t>& cp, hvec<int32_t>& ri, hvec<double>& cv)
+{
+    const int64_t nnz = rp[n];
+    unsigned hw = std::thread::hardware_concurrency();
+    int T = (int)std::min<unsigned>(8u, hw ? hw : 1u);
+    if (nnz < (1 << 18)) T = 1;
+    std::vector<int64_t> r0(T + 1, n);
+    r0[0] = 0;
+    for (int t = 1; t < T; ++t)
+        r0[t] = std::lower_bound(rp, rp + n + 1, nnz * t / T) - rp;
+    std::vector<std::vector<int64_t>> off(T);
+    auto on_threads = [&](auto&& fn) {
+        std::vector<std::thread> th;
+        for (int t = 1; t < T; ++t) th.emplace_back([&, t] { fn(t); });
+        fn(0);
+        for (auto& x : th) x.join();
+    };
+    on_threads([&](int t) {
+        off[t].assign(m, 0);
+        int64_t* c = off[t].data();
+        for (int64_t p = rp[r0[t]]; p < rp[r0[t + 1]]; ++p) c[ci[p]]++;
+    });
+    cp.assign(m + 1, 0);
+    parallel_chunks(m, [&](int64_t j0, int64_t j1) {
+        for (int64_t j = j0; j < j1; ++j) {
+            int64_t s = 0;
+            for (int t = 0; t < T; ++t) s += off[t][j];
+            cp[j + 1] = s;
+        }
+    });
+    for (int64_t j = 0; j < m; ++j) cp[j + 1] += cp[j];
+    parallel_chunks(m, [&](int64_t j0, int64_t j1) {
+        for (int64_t j = j0; j < j1; ++j) {
+            int64_t base = cp[j];
+            for (int t = 0; t < T; ++t) {
+                const int64_t c = off[t][j];
+                off[t][j] = base;
+                base += c;
+            }
+        }
+    });
+    ri.resize(nnz);
+    cv.resize(nnz);
+    on_threads([&](int t) {
+        int64_t* o = off[t].data();
+        for (int64_t r = r0[t]; r < r0[t + 1]; ++r)
+            for (int64_t p = rp[r]; p < rp[r + 1]; ++p) {
+                const int64_t q = o[ci[p]]++;
+                ri[q] = (int32_t)r;
+                cv[q] = vv[p];
+            }
+    });
+}
+
 // --- host-side layout of A ------------------------------------------------------
 
 template <typename T>
 struct SellHost {
     int64_t rows = 0, nseg = 0, nslices = 0, total = 0, nnz = 0, npart = 0;
     std::vector<int64_t> slice_ptr;
-    std::vector<int32_t> slice_len, idx, seg_row, seg_part, seg_grp, split_row, split_first,
+    std::vector<int32_t> slice_len, seg_row, seg_part, seg_grp, split_row, split_first,
         split_count;
-    std::vector<T> val;
+    hvec<int32_t> idx;
+    hvec<T> val;
 };
 
 // Lays out the rows of a CSR matrix for spmm_sell.  Every row becomes a
@@ -400,23 +508,31 @@ void build_sell(int64_t rows, const int64_t* ptr, const int32_t* ind, const doub
         S.slice_ptr[s + 1] = S.slice_ptr[s] + (int64_t)mx * 32;
     }
     S.total = S.slice_ptr[S.nslices];
-    S.idx.assign(S.total, -1);
-    S.val.assign(S.total, T(0));
+    S.idx.resize(S.total);
+    S.val.resize(S.total);
     S.seg_row.resize(S.nseg);
     S.seg_part.resize(S.nseg);
     S.seg_grp.resize(S.nseg);
-    for (int64_t g = 0; g < S.nseg; ++g) {
-        const Lane& ln = lanes[g];
-        S.seg_row[g] = ln.row;
-        S.seg_part[g] = ln.part;
-        S.seg_grp[g] = ln.grp;
-        const int64_t o = S.slice_ptr[g / 32] + (g % 32) * 4;
-        for (int p = 0; p < ln.len; ++p) {
-            const int64_t at = o + (int64_t)(p / 4) * 128 + p % 4;
-            S.idx[at] = ind[ln.start + p];
-            S.val[at] = (T)vals[ln.start + p];
+    // slices in parallel (chunks of about equal storage): padding first,
+    // then each lane's entries
+    parallel_weighted(S.nslices, S.slice_ptr.data(), [&](int64_t s0, int64_t s1) {
+        for (int64_t s = s0; s < s1; ++s) {
+            std::fill(S.idx.begin() + S.slice_ptr[s], S.idx.begin() + S.slice_ptr[s + 1], -1);
+            std::fill(S.val.begin() + S.slice_ptr[s], S.val.begin() + S.slice_ptr[s + 1], T(0));
+            for (int64_t g = s * 32; g < s * 32 + 32; ++g) {
+                const Lane& ln = lanes[g];
+                S.seg_row[g] = ln.row;
+                S.seg_part[g] = ln.part;
+                S.seg_grp[g] = ln.grp;
+                const int64_t o = S.slice_ptr[s] + (g % 32) * 4;
+                for (int p = 0; p < ln.len; ++p) {
+                    const int64_t at = o + (int64_t)(p / 4) * 128 + p % 4;
+                    S.idx[at] = ind[ln.start + p];
+                    S.val[at] = (T)vals[ln.start + p];
+                }
+            }
         }
-    }
+    });
 }
 
 // The frequent part of an FP32 product.  The gathered rows that the most
@@ -453,40 +569,48 @@ struct FreqHost {
     int h = 0;
     std::vector<int32_t> slot_of;
     std::vector<int64_t> hptr;
-    std::vector<uint16_t> hidx;
-    std::vector<float> hval;
+    hvec<uint16_t> hidx;
+    hvec<float> hval;
     std::vector<int32_t> hwarp;
 };
 
 void split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
-                    FreqHost& F, std::vector<int64_t>& lptr, std::vector<int32_t>& lind,
-                    std::vector<double>& lval)
+                    FreqHost& F, std::vector<int64_t>& lptr, hvec<int32_t>& lind,
+                    hvec<double>& lval)
 {
     F.hptr.assign(rows + 1, 0);
     lptr.assign(rows + 1, 0);
+    parallel_weighted(rows, ptr, [&](int64_t r0, int64_t r1) {
+        for (int64_t r = r0; r < r1; ++r) {
+            int64_t nh = 0;
+            for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) nh += F.slot_of[ind[q]] >= 0;
+            F.hptr[r + 1] = nh;
+            lptr[r + 1] = ptr[r + 1] - ptr[r] - nh;
+        }
+    });
     for (int64_t r = 0; r < rows; ++r) {
-        int64_t nh = 0;
-        for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) nh += F.slot_of[ind[q]] >= 0;
-        F.hptr[r + 1] = F.hptr[r] + nh;
-        lptr[r + 1] = lptr[r] + (ptr[r + 1] - ptr[r] - nh);
+        F.hptr[r + 1] += F.hptr[r];
+        lptr[r + 1] += lptr[r];
     }
     F.hidx.resize(F.hptr[rows]);
     F.hval.resize(F.hptr[rows]);
     lind.resize(lptr[rows]);
     lval.resize(lptr[rows]);
-    for (int64_t r = 0; r < rows; ++r) {
-        int64_t a = F.hptr[r], b = lptr[r];
-        for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) {
-            const int32_t sl = F.slot_of[ind[q]];
-            if (sl >= 0) {
-                F.hidx[a] = (uint16_t)sl;
-                F.hval[a++] = (float)vals[q];
-            } else {
-                lind[b] = ind[q];
-                lval[b++] = vals[q];
+    parallel_weighted(rows, ptr, [&](int64_t r0, int64_t r1) {
+        for (int64_t r = r0; r < r1; ++r) {
+            int64_t a = F.hptr[r], b = lptr[r];
+            for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) {
+                const int32_t sl = F.slot_of[ind[q]];
+                if (sl >= 0) {
+                    F.hidx[a] = (uint16_t)sl;
+                    F.hval[a++] = (float)vals[q];
+                } else {
+                    lind[b] = ind[q];
+                    lval[b++] = vals[q];
+                }
             }
         }
-    }
+    });
 }
 
 // Chunks of output rows for the warps of spmm_freq: contiguous ranges of
@@ -1230,34 +1354,42 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         CU(setup_factor());
         CU(setup_chol());
 
-        // ---- A: bring to the host, validate, build both layouts
+        // ---- A: validate and build both layouts on host threads.  A on the
+        // device is first copied to the host; host arrays are read in place.
         const int64_t n = A->n, m = A->m, nnz = A->nnz;
-        std::vector<int64_t> rp(n + 1);
-        std::vector<int32_t> ci(nnz);
-        std::vector<double> vv(nnz);
         const size_t vsz = A->vdtype == ESPNMF_F64 ? 8 : 4;
-        std::vector<unsigned char> vraw(nnz * vsz);
+        std::vector<int64_t> rp_h;
+        hvec<int32_t> ci_h;
+        hvec<unsigned char> vraw_h;
+        const int64_t* rp = nullptr;
+        const int32_t* ci = nullptr;
+        const unsigned char* vraw = nullptr;
         if (A->on_device) {
-            CU(cudaMemcpy(rp.data(), A->rowptr, (n + 1) * 8, cudaMemcpyDeviceToHost));
+            rp_h.resize(n + 1);
+            ci_h.resize(nnz);
+            vraw_h.resize(nnz * vsz);
+            CU(cudaMemcpy(rp_h.data(), A->rowptr, (n + 1) * 8, cudaMemcpyDeviceToHost));
             if (nnz) {
-                CU(cudaMemcpy(ci.data(), A->colidx, nnz * 4, cudaMemcpyDeviceToHost));
-                CU(cudaMemcpy(vraw.data(), A->values, nnz * vsz, cudaMemcpyDeviceToHost));
+                CU(cudaMemcpy(ci_h.data(), A->colidx, nnz * 4, cudaMemcpyDeviceToHost));
+                CU(cudaMemcpy(vraw_h.data(), A->values, nnz * vsz, cudaMemcpyDeviceToHost));
             }
+            rp = rp_h.data();
+            ci = ci_h.data();
+            vraw = vraw_h.data();
         } else {
             if (!A->rowptr) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "rowptr is NULL");
-            memcpy(rp.data(), A->rowptr, (n + 1) * 8);
-            if (nnz) {
-                memcpy(ci.data(), A->colidx, nnz * 4);
-                memcpy(vraw.data(), A->values, nnz * vsz);
-            }
+            rp = A->rowptr;
+            ci = A->colidx;
+            vraw = static_cast<const unsigned char*>(A->values);
         }
+        hvec<double> vv(nnz);
         parallel_chunks(nnz, [&](int64_t p0, int64_t p1) {
             for (int64_t p = p0; p < p1; ++p) {
                 double x;
-                if (vsz == 8) memcpy(&x, &vraw[p * 8], 8);
+                if (vsz == 8) memcpy(&x, vraw + p * 8, 8);
                 else {
                     float f;
-                    memcpy(&f, &vraw[p * 4], 4);
+                    memcpy(&f, vraw + p * 4, 4);
                     x = f;
                 }
                 vv[p] = x;
@@ -1273,7 +1405,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             std::mutex bad_mu;
             int64_t bad_row = n;
             int bad_kind = 0;
-            parallel_chunks(n, [&](int64_t r0, int64_t r1) {
+            parallel_weighted(n, rp, [&](int64_t r0, int64_t r1) {
                 for (int64_t r = r0; r < r1; ++r) {
                     int kind = 0;
                     for (int64_t p = rp[r]; p < rp[r + 1] && !kind; ++p) {
@@ -1298,26 +1430,16 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                 return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "%s in row %lld", what[bad_kind], (long long)bad_row);
         }
         // CSC (= CSR of A^T), rows ascending inside each column
-        std::vector<int64_t> cp(m + 1, 0);
-        for (int64_t p = 0; p < nnz; ++p) cp[ci[p] + 1]++;
-        for (int64_t j = 0; j < m; ++j) cp[j + 1] += cp[j];
-        std::vector<int32_t> ri(nnz);
-        std::vector<double> cv(nnz);
-        {
-            std::vector<int64_t> nx(cp.begin(), cp.end() - 1);
-            for (int64_t r = 0; r < n; ++r)
-                for (int64_t p = rp[r]; p < rp[r + 1]; ++p) {
-                    const int64_t q = nx[ci[p]]++;
-                    ri[q] = (int32_t)r;
-                    cv[q] = vv[p];
-                }
-        }
+        std::vector<int64_t> cp;
+        hvec<int32_t> ri;
+        hvec<double> cv;
+        transpose_csr(n, m, rp, ci, vv.data(), cp, ri, cv);
         // The two orientations are laid out on two host threads; the uploads
         // follow on this thread.
         if (compute == ESPNMF_F64) {
             SellHost<double> h1, h2;
             std::thread th([&] { build_sell(m, cp.data(), ri.data(), cv.data(), h2); });
-            build_sell(n, rp.data(), ci.data(), vv.data(), h1);
+            build_sell(n, rp, ci, vv.data(), h1);
             th.join();
             TRY(upload_sell(ctx, h1, ctx->sA));
             TRY(upload_sell(ctx, h2, ctx->sAt));
@@ -1332,15 +1454,18 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                 FreqHost F;
                 SellHost<float> h;
             };
+            // optr: the other orientation's row pointers, whose row lengths
+            // are the entries that reference each gathered row
             auto build_f32 = [&](int64_t rows, const int64_t* ptr, const int32_t* ind,
-                                 const double* vals, int64_t ngather, Built& B) {
-                std::vector<int64_t> w(ngather, 0);
-                for (int64_t q = 0; q < ptr[rows]; ++q) w[ind[q]]++;
+                                 const double* vals, int64_t ngather, const int64_t* optr,
+                                 Built& B) {
+                std::vector<int64_t> w(ngather);
+                for (int64_t g = 0; g < ngather; ++g) w[g] = optr[g + 1] - optr[g];
                 B.F.h = choose_frequent(w, ptr[rows], ld, B.F.slot_of);
                 if (B.F.h > 0) {
                     std::vector<int64_t> lp;
-                    std::vector<int32_t> li;
-                    std::vector<double> lv;
+                    hvec<int32_t> li;
+                    hvec<double> lv;
                     split_frequent(rows, ptr, ind, vals, B.F, lp, li, lv);
                     balance_frequent(rows, hwarps, B.F);
                     build_sell(rows, lp.data(), li.data(), lv.data(), B.h);
@@ -1354,8 +1479,8 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                 return ESPNMF_OK;
             };
             Built ba, bat;
-            std::thread th([&] { build_f32(m, cp.data(), ri.data(), cv.data(), n, bat); });
-            build_f32(n, rp.data(), ci.data(), vv.data(), m, ba);
+            std::thread th([&] { build_f32(m, cp.data(), ri.data(), cv.data(), n, rp, bat); });
+            build_f32(n, rp, ci, vv.data(), m, cp.data(), ba);
             th.join();
             TRY(upload_f32(ba, ctx->sA));
             TRY(upload_f32(bat, ctx->sAt));
