@@ -527,11 +527,57 @@ def run_large(args):
                "final_E": Efinal[name], "sweeps_before_E": warm + sweeps,
                "host_peak_rss_gb": peak_rss_gb()}
         if comp == E.F32:
+            res["spmm_frequent"] = {nm: E.espnmf_spmm_frequent(ctx, p)
+                                    for nm, p in (("AV", 0), ("AtU", 1))}
+            res["spmm_shapes"] = {nm: dict(zip(("split", "carveout", "mask"),
+                                               E.espnmf_spmm_config(ctx, p)))
+                                  for nm, p in (("AV", 0), ("AtU", 1))}
+            # multiply-adds of A^T U at this iterate: entry (doc, term) adds
+            # the term's U row, nnz_U(term) pairs; the frequent table holds
+            # the h terms of highest document frequency
+            Ud = torch.from_numpy(E.espnmf_get_factor(ctx, E.U)).to("cuda")
+            row_nnz = (Ud != 0).sum(dim=1).double()
+            del Ud
+            df = torch.diff(A.rowptr).double()
+            h = res["spmm_frequent"]["AtU"][0]
+            in_tab = torch.zeros_like(df, dtype=torch.bool)
+            if h > 0:
+                in_tab[torch.topk(df, h).indices] = True
+            heavy = row_nnz >= 28          # the dense-copy threshold at k = 100
+            fma = df * row_nnz
+            res["atu_work"] = {
+                "fma_total": float(fma.sum()), "fma_table": float(fma[in_tab].sum()),
+                "fma_sell": float(fma[~in_tab].sum()),
+                "entries_sell": float(df[~in_tab].sum()),
+                "entries_sell_heavy_rows": float(df[~in_tab & heavy].sum()),
+                "pairs_per_sell_entry": float(fma[~in_tab].sum() / max(float(df[~in_tab].sum()), 1.0)),
+                "u_rows_nonzero": int((row_nnz > 0).sum()),
+                "u_rows_heavy": int(heavy.sum()),
+                "u_nnz": int(row_nnz.sum())}
+            def gram_cond():
+                out = {}
+                for nm, which in (("U", E.U), ("V", E.V)):
+                    F = torch.from_numpy(E.espnmf_get_factor(ctx, which)).to("cuda")
+                    G = F.T @ F
+                    keep = torch.diagonal(G) > 0
+                    ev = torch.linalg.eigvalsh(G[keep][:, keep])
+                    out[nm] = {"zero_columns": int((~keep).sum()),
+                               "cond": float(ev[-1] / ev[0]) if ev[0] > 0 else float("inf")}
+                    del F, G
+                return out
+            res["gram_condition_after_timed_sweeps"] = gram_cond()
+            # per-kernel event times over 3 more (eager) sweeps
             E.espnmf_set_option(ctx, E.OPT_PROFILE, 1)
             E.espnmf_kernel_stats_reset(ctx)
             E.espnmf_iterate(ctx, 3, want_measures=False)
             stats = E.espnmf_kernel_stats(ctx)
             E.espnmf_set_option(ctx, E.OPT_PROFILE, 0)
+            try:
+                E.espnmf_sync(ctx)
+                res["status_after_profiled_sweeps"] = "ok"
+            except E.EspnmfError as err:
+                res["status_after_profiled_sweeps"] = str(err)
+            res["gram_condition_after_profiled_sweeps"] = gram_cond()
             get = lambda nm: stats.get(nm, (0, 0.0, 0.0))
             t_prod = sum(get(nm)[1] for nm in ("spmm_AV", "spmm_AtU", "spmm_freq_AV",
                                                "spmm_freq_AtU", "spmm_combine")) / 3 / 2
@@ -546,28 +592,6 @@ def run_large(args):
             res["kernels"] = {nm: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1),
                                    "share": v[1] / max(tot, 1e-12)}
                               for nm, v in stats.items() if v[0] > 0}
-            res["spmm_frequent"] = {nm: E.espnmf_spmm_frequent(ctx, p)
-                                    for nm, p in (("AV", 0), ("AtU", 1))}
-            # multiply-adds of A^T U at this iterate: entry (doc, term) adds
-            # the term's U row, nnz_U(term) pairs; the frequent table holds
-            # the h terms of highest document frequency
-            Ud = torch.from_numpy(E.espnmf_get_factor(ctx, E.U)).to("cuda")
-            row_nnz = (Ud != 0).sum(dim=1).double()
-            del Ud
-            df = torch.diff(A.rowptr).double()
-            h = res["spmm_frequent"]["AtU"][0]
-            in_tab = torch.zeros_like(df, dtype=torch.bool)
-            if h > 0:
-                in_tab[torch.topk(df, h).indices] = True
-            fma = df * row_nnz
-            res["atu_work"] = {
-                "fma_total": float(fma.sum()), "fma_table": float(fma[in_tab].sum()),
-                "fma_sell": float(fma[~in_tab].sum()),
-                "entries_sell": float(df[~in_tab].sum()),
-                "pairs_per_sell_entry": float(fma[~in_tab].sum() / max(float(df[~in_tab].sum()), 1.0)),
-                "u_rows_nonzero": int((row_nnz > 0).sum()),
-                "u_rows_over_16": int((row_nnz > 16).sum()),
-                "u_nnz": int(row_nnz.sum())}
         E.espnmf_destroy(ctx)
         del vals, u0
         torch.cuda.empty_cache()
