@@ -13,13 +13,11 @@
 // zero; otherwise the row's 32-byte record (one L2 sector) holds its count
 // and first six (column, value) pairs -- the first 16-byte half the first
 // three -- longer rows continue in the row-packed pairs, and the rare dense
-// row is read from its dense copy, by the whole warp (each lane taking every
-// 32nd column) for the lanes whose entries reference one, in lane order.
-// Every product is added into per-thread accumulators in shared memory, slot
-// c of thread tid at acc[c * (B + 1) + tid] (a warp's lanes always touch 32
-// distinct banks, whatever columns they update, and so do the 32 columns of
-// one thread's slots), so a thread needs few registers and many warps stay
-// resident to hide the latency of the gathers.
+// row is read from its dense copy.  Every product is added into per-thread
+// accumulators in shared memory, slot c of thread tid at acc[c * B + tid]
+// (a warp's lanes always touch 32 distinct banks, whatever columns they
+// update), so a thread needs few registers and many warps stay resident to
+// hide the latency of the gathers.
 //
 // Frequent part (spmm_freq_f32, FP32 form): on text corpora the factor rows
 // of the most frequent terms end up in nearly every column's top t, so the
@@ -71,7 +69,7 @@ struct SpmmParams {
 // columns [c0, c0 + cw) of the row of Y, or of its partial row.
 template <int KP>
 __device__ __forceinline__ void sell_store_rows(const SpmmParams<float>& p, int64_t seg, int lane,
-                                                const float* my, int SB, int c0, int cw)
+                                                const float* my, int B, int c0, int cw)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const int grp = p.seg_grp[seg];
@@ -85,8 +83,8 @@ __device__ __forceinline__ void sell_store_rows(const SpmmParams<float>& p, int6
     const bool writer = row >= 0 && lane == head;
 #pragma unroll 1
     for (int q = 0; 4 * q < cw; ++q) {
-        float v0 = my[(4 * q + 0) * SB], v1 = my[(4 * q + 1) * SB];
-        float v2 = my[(4 * q + 2) * SB], v3 = my[(4 * q + 3) * SB];
+        float v0 = my[(4 * q + 0) * B], v1 = my[(4 * q + 1) * B];
+        float v2 = my[(4 * q + 2) * B], v3 = my[(4 * q + 3) * B];
         for (int off = 1; off < maxg; off <<= 1) {
             const bool take = lane + off < end;
             const float t0 = __shfl_down_sync(FULL, v0, off);
@@ -127,17 +125,16 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int B = blockDim.x;
-    const int SB = B + 1;                     // slot stride (see heavy_rows)
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const int h = warp % NS;                  // column block of this warp
     const int c0 = h * CW;
     const int cw = KP - c0 < CW ? KP - c0 : CW;   // columns owned (> 0, multiple of 4)
-    float* slots = reinterpret_cast<float*>(smem_raw);                   // CW x (B + 1)
+    float* slots = reinterpret_cast<float*>(smem_raw);                   // CW x B
     const uint32_t* __restrict__ fmask = p.fmask;
     if constexpr (MASK == 2) {
-        uint32_t* sm = reinterpret_cast<uint32_t*>(slots + (size_t)CW * SB);
+        uint32_t* sm = reinterpret_cast<uint32_t*>(slots + (size_t)CW * B);
         for (int w = tid; w < p.mask_words; w += B) sm[w] = __ldg(p.fmask + w);
         __syncthreads();
         fmask = sm;
@@ -145,6 +142,8 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
     if (cw <= 0) return;
     float* my = slots + tid;
     const uint4* __restrict__ rec = p.frec;
+    const float4* __restrict__ dense4 = reinterpret_cast<const float4*>(p.fdense) + c0 / 4;
+    const int dld4 = p.dld / 4;
     const int heavy = p.heavy;
     const int fld = p.fld;
     const unsigned ucw = (unsigned)cw;
@@ -154,30 +153,22 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
     // launch shapes (different instantiations) round the same way.
     auto add = [&](unsigned c, float a, float v) {
         const unsigned r = c - (unsigned)c0;
-        if (r < ucw) my[r * SB] = __fmaf_rn(a, v, my[r * SB]);
+        if (r < ucw) my[r * B] = __fmaf_rn(a, v, my[r * B]);
     };
-    // The heavy rows among one entry position of the warp's lanes (bit L of
-    // hv: lane L's row is heavy), in lane order: the whole warp adds row i's
-    // dense copy times a into lane L's slots, each lane taking the columns
-    // c0 + lane, c0 + lane + 32, ... (coalesced loads; with the slot stride
-    // B + 1 the 32 slots of one owner fall in 32 different banks).  Every
-    // slot receives the same products in the same order as when each lane
-    // added its own heavy row.
-    auto heavy_rows = [&](unsigned hv, int i, float a) {
-        while (hv) {
-            const int L = __ffs(hv) - 1;
-            hv &= hv - 1;
-            const int iL = __shfl_sync(FULL, i, L);
-            const float aL = __shfl_sync(FULL, a, L);
-            const float* d = p.fdense + (int64_t)iL * p.dld + c0;
-            float* ow = slots + (tid - lane + L);
-#pragma unroll 1
-            for (int r = lane; r < cw; r += 32) ow[r * SB] = __fmaf_rn(aL, __ldg(d + r), ow[r * SB]);
-        }
-    };
-    // the pairs of row i beyond the record's three (a row below the heavy
-    // threshold)
+    // the pairs of row i beyond the record's three, or the whole dense copy
+    // of a heavy row
     auto gather_long = [&](int i, float a, int cnt) {
+        if (cnt >= heavy) {
+            const float4* d = dense4 + (int64_t)i * dld4;
+            for (int q = 0; 4 * q < cw; ++q) {
+                const float4 v = __ldg(d + q);
+                my[(4 * q + 0) * B] = __fmaf_rn(a, v.x, my[(4 * q + 0) * B]);
+                my[(4 * q + 1) * B] = __fmaf_rn(a, v.y, my[(4 * q + 1) * B]);
+                my[(4 * q + 2) * B] = __fmaf_rn(a, v.z, my[(4 * q + 2) * B]);
+                my[(4 * q + 3) * B] = __fmaf_rn(a, v.w, my[(4 * q + 3) * B]);
+            }
+            return;
+        }
         const int32_t* cr = p.fcol + (int64_t)i * fld;
         const float* vr = p.fval + (int64_t)i * fld;
         add((unsigned)__ldg(cr + 3), a, __ldg(vr + 3));
@@ -196,7 +187,7 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
     for (int64_t s = (int64_t)blockIdx.x * (B >> 5) / NS + warp / NS; s < p.nslices; s += stride) {
         const int64_t seg = s * 32 + lane;
 #pragma unroll 4
-        for (int c = 0; c < CW; ++c) my[c * SB] = 0.f;
+        for (int c = 0; c < CW; ++c) my[c * B] = 0.f;
         const int len = p.slice_len[s];   // a multiple of 4
         const int nq = len >> 2;
         const int64_t base = p.slice_ptr[s] + lane * 4;
@@ -277,13 +268,8 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
             }
             if (need >> 12) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int cu = record_cnt(rc[u].x);
-                    const bool lng = (mine >> (12 + u)) & 1u;
-                    const unsigned hv = __ballot_sync(FULL, lng && cu >= heavy);
-                    if (lng && cu < heavy) gather_long(ii[u], aa[u], cu);
-                    if (hv) heavy_rows(hv, ii[u], aa[u]);
-                }
+                for (int u = 0; u < 4; ++u)
+                    if (mine & (1u << (12 + u))) gather_long(ii[u], aa[u], record_cnt(rc[u].x));
             }
             i0 = i1;
             a0 = a1;
@@ -291,7 +277,7 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
             a1 = a2;
         }
 
-        sell_store_rows<KP>(p, seg, lane, my, SB, c0, cw);
+        sell_store_rows<KP>(p, seg, lane, my, B, c0, cw);
     }
 }
 
@@ -316,22 +302,23 @@ spmm_sell1_f32_kernel(SpmmParams<float> p)
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int B = blockDim.x;
-    const int SB = B + 1;                     // slot stride (see heavy_rows)
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    float* slots = reinterpret_cast<float*>(smem_raw);                   // KP x (B + 1)
+    float* slots = reinterpret_cast<float*>(smem_raw);                   // KP x B
     const uint32_t* __restrict__ fmask = p.fmask;
     if constexpr (MASK == 2) {
-        uint32_t* sm = reinterpret_cast<uint32_t*>(slots + (size_t)KP * SB);
+        uint32_t* sm = reinterpret_cast<uint32_t*>(slots + (size_t)KP * B);
         for (int w = tid; w < p.mask_words; w += B) sm[w] = __ldg(p.fmask + w);
         __syncthreads();
         fmask = sm;
     }
     float* my = slots + tid;
-    const unsigned bstride = (unsigned)SB * 4u;               // bytes between a thread's slots
+    const unsigned bstride = (unsigned)B * 4u;                // bytes between a thread's slots
     const uint32_t mybase = (uint32_t)__cvta_generic_to_shared(my);
     const uint4* __restrict__ rec = p.frec;
+    const float4* __restrict__ dense4 = reinterpret_cast<const float4*>(p.fdense);
+    const int dld4 = p.dld / 4;
     const int heavy = p.heavy;
     const int fld = p.fld;
 
@@ -343,28 +330,22 @@ spmm_sell1_f32_kernel(SpmmParams<float> p)
         s = __fmaf_rn(a, v, s);
         asm volatile("st.shared.f32 [%0], %1;" :: "r"(ad), "f"(s) : "memory");
     };
-    // The heavy rows among one entry position of the warp's lanes (bit L of
-    // hv: lane L's row is heavy), in lane order: the whole warp adds row i's
-    // dense copy times a into lane L's slots, each lane taking the columns
-    // lane, lane + 32, ... (coalesced loads; with the slot stride B + 1 the
-    // 32 slots of one owner fall in 32 different banks).  Every slot
-    // receives the same products in the same order as when each lane added
-    // its own heavy row.
-    auto heavy_rows = [&](unsigned hv, int i, float a) {
-        while (hv) {
-            const int L = __ffs(hv) - 1;
-            hv &= hv - 1;
-            const int iL = __shfl_sync(FULL, i, L);
-            const float aL = __shfl_sync(FULL, a, L);
-            const float* d = p.fdense + (int64_t)iL * p.dld;
-            float* ow = slots + (tid - lane + L);
-#pragma unroll 1
-            for (int c = lane; c < KP; c += 32) ow[c * SB] = __fmaf_rn(aL, __ldg(d + c), ow[c * SB]);
-        }
-    };
-    // pairs 3.. of row i (cnt of them in all, below the heavy threshold): 3
-    // to 5 from the record's second half, the rest from the row-packed pairs
+    // pairs 3.. of row i (cnt of them in all): 3 to 5 from the record's
+    // second half, the rest from the row-packed pairs; a heavy row from its
+    // dense copy
     auto pairs_beyond = [&](int i, float a, int cnt) {
+        if (cnt >= heavy) {
+            const float4* d = dense4 + (int64_t)i * dld4;
+#pragma unroll 1
+            for (int q = 0; 4 * q < KP; ++q) {
+                const float4 v = __ldg(d + q);
+                my[(4 * q + 0) * B] = __fmaf_rn(a, v.x, my[(4 * q + 0) * B]);
+                my[(4 * q + 1) * B] = __fmaf_rn(a, v.y, my[(4 * q + 1) * B]);
+                my[(4 * q + 2) * B] = __fmaf_rn(a, v.z, my[(4 * q + 2) * B]);
+                my[(4 * q + 3) * B] = __fmaf_rn(a, v.w, my[(4 * q + 3) * B]);
+            }
+            return;
+        }
         const uint4 h = __ldg(rec + 2 * i + 1);
         fma_slot(__byte_perm(h.x, 0u, 0x4440), a, __uint_as_float(h.y));
         if (cnt > 4) fma_slot(__byte_perm(h.x, 0u, 0x4441), a, __uint_as_float(h.z));
@@ -397,7 +378,7 @@ spmm_sell1_f32_kernel(SpmmParams<float> p)
     for (int64_t s = (int64_t)blockIdx.x * (B >> 5) + warp; s < p.nslices; s += stride) {
         const int64_t seg = s * 32 + lane;
 #pragma unroll 4
-        for (int c = 0; c < KP; ++c) my[c * SB] = 0.f;
+        for (int c = 0; c < KP; ++c) my[c * B] = 0.f;
         const int len = p.slice_len[s];   // a multiple of 4
         const int nq = len >> 2;
         const int64_t base = p.slice_ptr[s] + lane * 4;
@@ -437,26 +418,17 @@ spmm_sell1_f32_kernel(SpmmParams<float> p)
             light_pairs(r2, a0.z, ((need >> 16) & 0xffu) >= 2u);
             light_pairs(r3, a0.w, (need >> 24) >= 2u);
             if ((need & 0xfcfcfcfcu) != 0u) {
-                // entry by entry: the lanes' rows of four or more nonzeros
-                // below the heavy threshold each on their own lane, then the
-                // heavy rows by the whole warp
-                auto beyond = [&](const uint4& r, int i, float a) {
-                    const int c = record_cnt(r.x);
-                    const unsigned hv = __ballot_sync(FULL, c >= heavy);
-                    if (c > 3 && c < heavy) pairs_beyond(i, a, c);
-                    if (hv) heavy_rows(hv, i, a);
-                };
-                beyond(r0, i0.x, a0.x);
-                beyond(r1, i0.y, a0.y);
-                beyond(r2, i0.z, a0.z);
-                beyond(r3, i0.w, a0.w);
+                if (record_cnt(r0.x) > 3) pairs_beyond(i0.x, a0.x, record_cnt(r0.x));
+                if (record_cnt(r1.x) > 3) pairs_beyond(i0.y, a0.y, record_cnt(r1.x));
+                if (record_cnt(r2.x) > 3) pairs_beyond(i0.z, a0.z, record_cnt(r2.x));
+                if (record_cnt(r3.x) > 3) pairs_beyond(i0.w, a0.w, record_cnt(r3.x));
             }
             i0 = i1;
             a0 = a1;
             i1 = i2;
             a1 = a2;
         }
-        sell_store_rows<KP>(p, seg, lane, my, SB, 0, KP);
+        sell_store_rows<KP>(p, seg, lane, my, B, 0, KP);
     }
 }
 
@@ -776,7 +748,7 @@ static int sell_block(int& B)
     B = spmm_block(CW, 4, 56 * 1024);
     B = B / (32 * NS) * (32 * NS);
     if (B < 32 * NS) B = 32 * NS;
-    return CW * (B + 1) * 4;
+    return CW * B * 4;
 }
 
 template <int KP, int NS, int MASK>
