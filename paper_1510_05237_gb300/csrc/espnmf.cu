@@ -9,6 +9,8 @@
 // The inverse of a factor's Gram only feeds the *next* half-step's solve,
 // so it is deferred to the start of that half and runs beside its SpMM.
 #include <cuda_runtime.h>
+#include <chrono>
+#include <cstdlib>
 
 #include <algorithm>
 #include <cmath>
@@ -1334,6 +1336,17 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             return fail_init(ctx, ESPNMF_ERR_CUDA);
         }
     }
+    // ESPNMF_TRACE_INIT set: the host time of each phase of the set-up on
+    // stderr (the device work of a phase is not waited for)
+    const bool trace = std::getenv("ESPNMF_TRACE_INIT") != nullptr;
+    auto t_last = std::chrono::steady_clock::now();
+    auto phase = [&](const char* what) {
+        if (!trace) return;
+        const auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "espnmf_init: %-28s %8.2f ms\n", what,
+                     std::chrono::duration<double, std::milli>(now - t_last).count());
+        t_last = now;
+    };
     espnmf_status s = [&]() -> espnmf_status {
         if (stream) {
             ctx->st = (cudaStream_t)stream;
@@ -1354,6 +1367,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         CU(setup_factor());
         CU(setup_chol());
 
+        phase("streams, kernel attributes");
         // ---- A: validate and build both layouts on host threads.  A on the
         // device is first copied to the host; host arrays are read in place.
         const int64_t n = A->n, m = A->m, nnz = A->nnz;
@@ -1429,11 +1443,13 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             if (bad_kind)
                 return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "%s in row %lld", what[bad_kind], (long long)bad_row);
         }
+        phase("copy, convert, validate A");
         // CSC (= CSR of A^T), rows ascending inside each column
         std::vector<int64_t> cp;
         hvec<int32_t> ri;
         hvec<double> cv;
         transpose_csr(n, m, rp, ci, vv.data(), cp, ri, cv);
+        phase("transpose");
         // The two orientations are laid out on two host threads; the uploads
         // follow on this thread.
         if (compute == ESPNMF_F64) {
@@ -1482,10 +1498,12 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             std::thread th([&] { build_f32(m, cp.data(), ri.data(), cv.data(), n, rp, bat); });
             build_f32(n, rp, ci, vv.data(), m, cp.data(), ba);
             th.join();
+            phase("layouts built");
             TRY(upload_f32(ba, ctx->sA));
             TRY(upload_f32(bat, ctx->sAt));
         }
 
+        phase("layouts uploaded");
         // ---- work buffers
         const int64_t rmax = std::max(n, m);
         ctx->ldy = factor_ld(k);
@@ -1528,6 +1546,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         CU(cudaMemsetAsync(ctx->status_d, 0, sizeof(unsigned), ctx->st));
         CU(cudaMallocHost(&ctx->status_h, sizeof(unsigned)));
 
+        phase("work buffers");
         for (Factor* F : {&ctx->U, &ctx->V}) {
             F->rows = F == &ctx->U ? n : m;
             const int ld = factor_ld(k);
@@ -1586,6 +1605,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             }
         }
 
+        phase("factor buffers");
         // ---- ||A||^2 from the values the kernels use
         if (is_f64(ctx))
             TRY(run(ctx, K_NORM2, (double)ctx->sA.total * 8, ctx->st, [&] {
@@ -1602,6 +1622,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         // ---- U = U0 (Alg. 2 START; not enforced)
         TRY(set_factor_impl(ctx, ctx->U, U0, U0_dtype, U0_on_device));
         TRY(check_status(ctx));
+        phase("norm, U0, synchronise");
         return ESPNMF_OK;
     }();
     if (s != ESPNMF_OK) return fail_init(ctx, s);
