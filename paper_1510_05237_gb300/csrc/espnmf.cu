@@ -9,13 +9,13 @@
 // The inverse of a factor's Gram only feeds the *next* half-step's solve,
 // so it is deferred to the start of that half and runs beside its SpMM.
 #include <cuda_runtime.h>
-#include <chrono>
-#include <cstdlib>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
