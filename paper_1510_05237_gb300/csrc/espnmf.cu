@@ -287,13 +287,22 @@ espnmf_status check_status(espnmf_ctx* ctx)
     return set_err(ctx, ESPNMF_ERR_CUDA, "unknown device status 0x%x", s);
 }
 
-// fn(lo, hi) over [0, total) cut into contiguous chunks run on up to eight
-// host threads (one for small totals).
+// Host threads for one parallel pass: all hardware threads (at most 32),
+// or half of them inside one of the two layout builds that run at once.
+thread_local int t_share = 1;
+int host_threads()
+{
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int all = (int)std::min<unsigned>(32u, hw ? hw : 1u);
+    return std::max(1, all / t_share);
+}
+
+// fn(lo, hi) over [0, total) cut into contiguous chunks run on the host
+// threads (one for small totals).
 template <typename F>
 void parallel_chunks(int64_t total, F&& fn)
 {
-    unsigned hw = std::thread::hardware_concurrency();
-    int T = (int)std::min<unsigned>(8u, hw ? hw : 1u);
+    int T = host_threads();
     if (total < (1 << 16)) T = 1;
     std::vector<std::thread> th;
     for (int t = 1; t < T; ++t)
@@ -308,8 +317,7 @@ void parallel_chunks(int64_t total, F&& fn)
 template <typename F>
 void parallel_weighted(int64_t total, const int64_t* prefix, F&& fn)
 {
-    unsigned hw = std::thread::hardware_concurrency();
-    int T = (int)std::min<unsigned>(8u, hw ? hw : 1u);
+    int T = host_threads();
     const int64_t W = prefix[total] - prefix[0];
     if (W < (1 << 16) || total < 2) T = 1;
     std::vector<int64_t> cut(T + 1, total);
@@ -358,8 +366,7 @@ void transpose_csr(int64_t n, int64_t m, const int64_t* rp, const int32_t* ci, c
                    std::vector<int64_t>& cp, hvec<int32_t>& ri, hvec<double>& cv)
 {
     const int64_t nnz = rp[n];
-    unsigned hw = std::thread::hardware_concurrency();
-    int T = (int)std::min<unsigned>(8u, hw ? hw : 1u);
+    int T = host_threads();
     if (nnz < (1 << 18)) T = 1;
     std::vector<int64_t> r0(T + 1, n);
     r0[0] = 0;
@@ -1454,8 +1461,13 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         // follow on this thread.
         if (compute == ESPNMF_F64) {
             SellHost<double> h1, h2;
-            std::thread th([&] { build_sell(m, cp.data(), ri.data(), cv.data(), h2); });
+            std::thread th([&] {
+                t_share = 2;
+                build_sell(m, cp.data(), ri.data(), cv.data(), h2);
+            });
+            t_share = 2;
             build_sell(n, rp, ci, vv.data(), h1);
+            t_share = 1;
             th.join();
             TRY(upload_sell(ctx, h1, ctx->sA));
             TRY(upload_sell(ctx, h2, ctx->sAt));
@@ -1495,8 +1507,13 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                 return ESPNMF_OK;
             };
             Built ba, bat;
-            std::thread th([&] { build_f32(m, cp.data(), ri.data(), cv.data(), n, rp, bat); });
+            std::thread th([&] {
+                t_share = 2;
+                build_f32(m, cp.data(), ri.data(), cv.data(), n, rp, bat);
+            });
+            t_share = 2;
             build_f32(n, rp, ci, vv.data(), m, cp.data(), ba);
+            t_share = 1;
             th.join();
             phase("layouts built");
             TRY(upload_f32(ba, ctx->sA));
