@@ -333,13 +333,14 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
     int base_bucket = 0;   // lowest first-histogram bin among the candidates
     bool warm = false;
 
-    // ---- warm start (column mode, one CTA per column): the threshold of
-    // the previous selection of this column names a first-histogram bin; one
-    // pass counts the entries above that bin's neighbours and lists the
-    // entries of the three bins.  If the t-th largest lies among them, the
-    // first histogram and its pass are not needed; otherwise the marks
-    // set above the window are taken back and the full search follows.
-    if (hint != nullptr && C == 1 && !matrix) {
+    // ---- warm start (column mode): the threshold of the previous selection
+    // of this column names a first-histogram bin; one pass counts the
+    // entries above that bin's neighbours and lists the entries of the
+    // three bins (each CTA of the column's cluster over its own part, the
+    // counts then summed over the cluster).  If the t-th largest lies among
+    // them, the first histogram and its pass are not needed; otherwise the
+    // marks set above the window are taken back and the full search follows.
+    if (hint != nullptr && !matrix) {
         const K h = hint[seg];
         if (h != (K)0 && h != ~(K)0) {
             const int hb = bucket_of(h);
@@ -424,9 +425,30 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
             above = __reduce_add_sync(0xffffffffu, above);
             if (lane == 0 && above) atomicAdd(&s_above, (unsigned long long)above);
             __syncthreads();
-            const unsigned long long ab = s_above, nca = *ccount;
+            const unsigned long long nca = *ccount;
+            unsigned long long ab = s_above, nca_all = nca;
+            bool overflow = nca > (unsigned long long)kCandCap;
             __syncthreads();
-            if (nca <= (unsigned long long)kCandCap && ab < need && ab + nca >= need) {
+            if (C > 1) {
+                // the cluster's totals: each CTA publishes its two counts
+                // (below 2^32: a CTA holds fewer entries) in its histogram
+                if (tid == 0) {
+                    hist[0] = (unsigned)ab;
+                    hist[1] = (unsigned)nca;
+                }
+                cluster.sync();
+                ab = 0;
+                nca_all = 0;
+                overflow = false;
+                for (int r = 0; r < C; ++r) {
+                    const unsigned* hr = cluster.map_shared_rank(hist, r);
+                    ab += hr[0];
+                    nca_all += hr[1];
+                    overflow = overflow || hr[1] > (unsigned)kCandCap;
+                }
+                cluster.sync();   // remote reads done: the histograms may be reused
+            }
+            if (!overflow && ab < need && ab + nca_all >= need) {
                 warm = true;
                 need -= ab;
                 prefix = 0;
@@ -608,11 +630,14 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
 // kSelMaxCluster per column (larger clusters measured slower with k columns
 // in flight) and kSelMaxClusterWhole for the single segment of matrix mode
 // (the whole factor), at least 2048 entries per CTA.  When it marks
-// survivors (column mode) one CTA owns a column: its rounds then need block
-// barriers only, and it may start from a hint.
+// survivors (column mode) the cluster size is a fixed function of the
+// column length (it decides how the Gram diagonal's partial sums are
+// grouped, so it must not depend on timing): two CTAs for columns of at
+// least kSelMarkSplitRows entries, else one.
+constexpr int64_t kSelMarkSplitRows = 32768;
 static int sel_cluster(int64_t rows, int k, int mode, int sm_count, bool marking)
 {
-    if (marking && mode == TOPT_COLUMN) return 1;
+    if (marking && mode == TOPT_COLUMN) return rows >= kSelMarkSplitRows ? 2 : 1;
     const int nseg = mode == TOPT_MATRIX ? 1 : k;
     const int64_t seg_len = mode == TOPT_MATRIX ? (int64_t)k * rows : rows;
     int C = (int)((2 * (int64_t)sm_count + nseg - 1) / nseg);
