@@ -409,6 +409,19 @@ espnmf_status espnmf_kernel_stats_reset(espnmf_ctx *ctx);
 /* Number of kernel launches one sweep (update_V + update_U) enqueues. */
 espnmf_status espnmf_launches_per_sweep(espnmf_ctx *ctx, int32_t *count);
 
+/* espnmf_checked_flags -- in a library compiled with -DESPNMF_CHECKED (the
+ * checked build: build(checked=True), loaded by the binding when the
+ * environment sets ESPNMF_CHECKED=1), the union of the bounds checks that
+ * failed in any kernel since the last call, then cleared: bit 0 a gathered
+ * factor row beyond the factor, bit 1 a pair's column beyond the row width,
+ * bit 2 a row's pair count beyond its capacity, bit 3 a frequent-table slot
+ * beyond the table, bit 4 an output or partial row out of range, bit 5 a
+ * candidate or survivor row beyond the column.  A failed check skips its
+ * access.  0: every checked access was in range.  Any other build: *flags
+ * = 0 and ESPNMF_ERR_UNSUPPORTED.  Reads device memory (synchronises with
+ * the device). */
+espnmf_status espnmf_checked_flags(uint32_t *flags);
+
 /* espnmf_sync -- waits for the context's stream; reports device errors. */
 espnmf_status espnmf_sync(espnmf_ctx *ctx);
 

@@ -49,7 +49,9 @@ _lock = threading.Lock()
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the checked build when the
+    environment sets ESPNMF_CHECKED=1, else the regular one."""
+    return _build.LIB_CHECKED if os.environ.get("ESPNMF_CHECKED") == "1" else _build.LIB
 
 
 def load():
@@ -58,10 +60,11 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"CUDA library not built: {_build.LIB} is missing "
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
                                "(run __graft_entry__.build())")
-        lib = ctypes.CDLL(_build.LIB)
+        lib = ctypes.CDLL(path)
         P, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         st = ctypes.c_int
         sig = {
@@ -84,6 +87,7 @@ def load():
             "espnmf_kernel_stats_reset": [P],
             "espnmf_launches_per_sweep": [P, ctypes.POINTER(i32)],
             "espnmf_sync": [P],
+            "espnmf_checked_flags": [P],
             "espnmf_enforce_topt_buffer": [P, i64, i32, i64, st, i64, st, P],
             "espnmf_enforce_topt_buffer_noalloc": [P, i64, i32, i64, st, i64, st, P],
             "espnmf_loss": [P, ctypes.POINTER(d)],
@@ -125,7 +129,8 @@ def exported_symbols():
              "espnmf_enforce_topt", "espnmf_set_factor", "espnmf_residual", "espnmf_error",
              "espnmf_factor_nnz", "espnmf_get_factor", "espnmf_set_option",
              "espnmf_kernel_stat_count", "espnmf_kernel_stat", "espnmf_kernel_stats_reset",
-             "espnmf_launches_per_sweep", "espnmf_sync", "espnmf_enforce_topt_buffer",
+             "espnmf_launches_per_sweep", "espnmf_sync", "espnmf_checked_flags",
+             "espnmf_enforce_topt_buffer",
              "espnmf_enforce_topt_buffer_noalloc", "espnmf_loss", "espnmf_grad",
              "espnmf_pg_step", "espnmf_batch_init", "espnmf_batch_destroy",
              "espnmf_batch_ctx", "espnmf_batch_set_option", "espnmf_batch_iterate",
@@ -467,6 +472,14 @@ def espnmf_launches_per_sweep(ctx: Context) -> int:
 
 def espnmf_sync(ctx: Context):
     _check(load().espnmf_sync(ctx.handle), ctx.handle)
+
+
+def espnmf_checked_flags() -> int:
+    """The bounds checks that failed since the last call (checked build;
+    raises EspnmfError(UNSUPPORTED) in the regular build)."""
+    f = ctypes.c_uint32()
+    _check(load().espnmf_checked_flags(ctypes.byref(f)))
+    return f.value
 
 
 def espnmf_enforce_topt_buffer(X, t: int, mode: int = TOPT_COLUMN, stream=None):

@@ -3,7 +3,10 @@
 Each ``csrc/*.cu`` is compiled by its own nvcc process (in parallel), then
 the objects are linked into one shared library with the C ABI of
 ``include/espnmf.h``.  A rebuild happens only when a source or header is
-newer than the library.
+newer than the library.  ``build(checked=True)`` makes the checked build
+``_lib/libespnmf_checked.so`` (``-DESPNMF_CHECKED``: device-side bounds
+checks of the data-dependent accesses, reported by espnmf_checked_flags),
+which the binding loads when the environment sets ESPNMF_CHECKED=1.
 """
 from __future__ import annotations
 
@@ -21,6 +24,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIB_DIR, "libespnmf.so")
+LIB_CHECKED = os.path.join(LIB_DIR, "libespnmf_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -44,26 +48,32 @@ def _deps():
             glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    obj_dir = OBJ_DIR + ("_checked" if checked else "")
+    if not force and up_to_date(checked):
+        return lib
     nvcc = nvcc_path()
-    os.makedirs(OBJ_DIR, exist_ok=True)
+    os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
     flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
              "--expt-relaxed-constexpr", "-I", INCLUDE]
+    if checked:
+        flags += ["-DESPNMF_CHECKED"]
     if ptxas_info:
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -75,15 +85,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     srcs = _sources()
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                ptxas_info="--ptxas" in sys.argv))
+                ptxas_info="--ptxas" in sys.argv, checked="--checked" in sys.argv))

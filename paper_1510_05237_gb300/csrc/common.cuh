@@ -22,6 +22,51 @@ enum : unsigned {
 
 enum TopMode : int { TOPT_COLUMN = 0, TOPT_MATRIX = 1, TOPT_NONE = 2 };
 
+// Checked build (compiled with -DESPNMF_CHECKED): bounds checks of the
+// indexed accesses whose index comes from data -- a factor row gathered by
+// the sparse product, a pair's column and a row's pair count, a frequent
+// table slot, an output or partial row, a candidate or survivor row.  A
+// failed check sets its bit in this translation unit's flag word and the
+// access is skipped; espnmf_checked_flags() reports (and clears) the union
+// over all kernels.  Without the flag ESPNMF_CHECK is the constant true and
+// the checks compile to nothing.
+enum : unsigned {
+    CHK_FACTOR_ROW = 1u,   // gathered factor row >= the factor's rows
+    CHK_COLUMN = 2u,       // a pair's column >= the row width
+    CHK_COUNT = 4u,        // a row's pair count > its capacity
+    CHK_SLOT = 8u,         // a frequent-table slot >= the table's rows
+    CHK_OUT_ROW = 16u,     // an output or partial row out of range
+    CHK_CAND_ROW = 32u,    // a candidate or survivor row >= the column length
+};
+#ifdef ESPNMF_CHECKED
+static __device__ unsigned g_check_flags;
+__device__ __forceinline__ bool espnmf_check(bool ok, unsigned bit)
+{
+    if (!ok) atomicOr(&g_check_flags, bit);
+    return ok;
+}
+#define ESPNMF_CHECK(cond, bit) ::espnmf::espnmf_check((cond), (bit))
+// Defines `unsigned name()` reading and clearing this unit's flag word.
+#define ESPNMF_CHECK_READER(name)                                          \
+    unsigned name()                                                        \
+    {                                                                      \
+        unsigned v = 0, z = 0;                                             \
+        if (cudaMemcpyFromSymbol(&v, g_check_flags, sizeof v) != cudaSuccess) \
+            return 0xffffffffu;                                            \
+        cudaMemcpyToSymbol(g_check_flags, &z, sizeof z);                   \
+        return v;                                                          \
+    }
+#else
+#define ESPNMF_CHECK(cond, bit) true
+#define ESPNMF_CHECK_READER(name) \
+    unsigned name() { return 0; }
+#endif
+// per translation unit: the flags its kernels raised (checked build)
+unsigned check_flags_spmm();
+unsigned check_flags_select();
+unsigned check_flags_factor();
+unsigned check_flags_seq();
+
 // For non-negative IEEE numbers the bit pattern read as an unsigned integer
 // orders exactly like the value; the selector works on these keys.
 template <typename T> struct KeyBits;

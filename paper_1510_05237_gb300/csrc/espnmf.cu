@@ -2707,4 +2707,24 @@ espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int32_t k2, int6
     return ESPNMF_OK;
 }
 
+espnmf_status espnmf_checked_flags(uint32_t* flags)
+{
+    if (!flags) return batch_fail(ESPNMF_ERR_INVALID_ARG, "flags is NULL");
+#ifdef ESPNMF_CHECKED
+    const unsigned part[4] = {check_flags_spmm(), check_flags_select(), check_flags_factor(),
+                              check_flags_seq()};
+    *flags = 0;
+    for (unsigned v : part) {
+        if (v == 0xffffffffu)
+            return batch_fail(ESPNMF_ERR_CUDA, "could not read the check flags (no usable CUDA device)");
+        *flags |= v;
+    }
+    espnmf::set_thread_error("");
+    return ESPNMF_OK;
+#else
+    *flags = 0;
+    return batch_fail(ESPNMF_ERR_UNSUPPORTED, "not a checked build (compile with -DESPNMF_CHECKED)");
+#endif
+}
+
 }  // extern "C"

@@ -646,7 +646,8 @@ emit_s_kernel(EmitSArgs a)
             }
         }
         if (valid && !coop) {
-            const int Lo = (a.residual || a.zero_old) ? a.cnt_old[r] : 0;
+            int Lo = (a.residual || a.zero_old) ? a.cnt_old[r] : 0;
+            if (!ESPNMF_CHECK(Lo <= ld, CHK_COUNT)) Lo = ld;
             const int32_t* co = a.col_old + r * ld;
             const float* vo = a.val_old + r * ld;
             int32_t* wc = a.col + r * ld;
@@ -660,6 +661,7 @@ emit_s_kernel(EmitSArgs a)
                 while (mb) {
                     const int c = 32 * w + __ffs(mb) - 1;
                     mb &= mb - 1u;
+                    if (!ESPNMF_CHECK(c < a.k, CHK_COLUMN)) continue;
                     const float x = a.Xt[(int64_t)c * a.ldx + r];
                     wc[pos] = c;
                     wv[pos] = x;
@@ -778,7 +780,8 @@ emit_s_kernel(EmitSArgs a)
 #pragma unroll
             for (int w = 0; w < WD; ++w) {
                 const int c = 32 * w + lane;
-                const bool sv = (bw[w] >> lane) & 1u;
+                const bool bit = (bw[w] >> lane) & 1u;
+                const bool sv = bit && ESPNMF_CHECK(c < a.k, CHK_COLUMN);
                 const int pos = before + __popc(bw[w] & ((1u << lane) - 1u));
                 float x = 0.f;
                 if (sv) {
@@ -999,6 +1002,8 @@ gram_table_kernel(const float* __restrict__ htab, const uint8_t* __restrict__ hn
         if (e < ntri) gp[(size_t)e * P + pcol0 + blockIdx.x] = make_float2(acc[s].hi, acc[s].lo);
     }
 }
+
+ESPNMF_CHECK_READER(check_flags_factor)
 
 cudaError_t launch_gram_table(const EllDev& F, int k, double* gram_part, int P, int pcol0,
                               int nblocks, cudaStream_t st)

@@ -277,6 +277,7 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
     DFloat msq;   // compensated FP32 (only FP32 contexts mark)
     const uint32_t mbit = 1u << (seg & 31);
     auto mark_one = [&](K key, uint32_t row) {
+        if (!ESPNMF_CHECK((int64_t)row < rows, CHK_CAND_ROW)) return;
         atomicOr(mark.rowbits + (seg >> 5) + (size_t)row * mark.words, mbit);
         const float x = (float)KeyBits<T>::value(key);
         df_add_prod(msq, x, x);
@@ -591,7 +592,8 @@ select_kernel(const T* __restrict__ Xt, int64_t ldx, int64_t rows, int k,
             const int s0 = exponent_of((uint32_t)((K)base_bucket << TS));
             unsigned long long isq0 = 0, isq1 = 0;
             for (int q = tid; q < nc; q += blockDim.x) {
-                if (keep_entry<T>(KeyBits<T>::value(ckey[q]), tau, cut, cidx[q])) {
+                if (keep_entry<T>(KeyBits<T>::value(ckey[q]), tau, cut, cidx[q]) &&
+                    ESPNMF_CHECK((int64_t)cidx[q] < rows, CHK_CAND_ROW)) {
                     atomicOr(mark.rowbits + (seg >> 5) + (size_t)cidx[q] * mark.words, mbit);
                     const unsigned long long m = mantissa24((uint32_t)ckey[q]);
                     if (exponent_of((uint32_t)ckey[q]) == s0) isq0 += m * m;
@@ -691,6 +693,8 @@ int select_cluster(int64_t rows, int k, int mode, int sm_count)
 {
     return sel_cluster(rows, k, mode, sm_count, true);
 }
+
+ESPNMF_CHECK_READER(check_flags_select)
 
 // In-place projection + enforcement of a caller's dense rows x k buffer
 // (leading dimension ld) with thresholds from select_kernel.

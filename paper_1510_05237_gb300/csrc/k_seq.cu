@@ -78,8 +78,13 @@ seq_append_kernel(int64_t rows, const int32_t* __restrict__ cnt, const int32_t* 
     T* h = H + i * ld1 + j0;
     for (int j = 0; j < k2; ++j) h[j] = T(0);
     const int nc = cnt[i];
-    for (int q = 0; q < nc; ++q) h[col[i * ld + q]] = val[i * ld + q];
+    for (int q = 0; q < nc; ++q) {
+        const int c = col[i * ld + q];
+        if (ESPNMF_CHECK((unsigned)c < (unsigned)k2, CHK_COLUMN)) h[c] = val[i * ld + q];
+    }
 }
+
+ESPNMF_CHECK_READER(check_flags_seq)
 
 static unsigned seq_grid(int64_t rows) { return (unsigned)((rows + kSeqThreads - 1) / kSeqThreads); }
 

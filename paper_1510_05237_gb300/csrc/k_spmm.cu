@@ -58,6 +58,9 @@ struct SpmmParams {
     int mask_words;   // words of fmask (staged in shared memory when MASK == 2)
     int dld;
     int fld;
+    int64_t frows;   // rows of the gathered factor
+    int64_t yrows;   // output rows
+    int64_t npart;   // partial rows
     int heavy;
     int k;
     T* Y;        // rows x KP (ldy == KP)
@@ -77,10 +80,11 @@ __device__ __forceinline__ void sell_store_rows(const SpmmParams<float>& p, int6
     const int maxg = __reduce_max_sync(FULL, (unsigned)(end - head));
     const int row = p.seg_row[seg];
     const int part = p.seg_part[seg];
-    float* out = (part < 0 ? p.Y + (int64_t)(row < 0 ? 0 : row) * KP
-                           : p.partials + (int64_t)part * KP) + c0;
+    const bool in_range = row < 0 || ESPNMF_CHECK(part < 0 ? row < p.yrows : part < p.npart, CHK_OUT_ROW);
+    float* out = (part < 0 ? p.Y + (int64_t)(row < 0 || !in_range ? 0 : row) * KP
+                           : p.partials + (int64_t)(in_range ? part : 0) * KP) + c0;
     float4* o4 = reinterpret_cast<float4*>(out);
-    const bool writer = row >= 0 && lane == head;
+    const bool writer = row >= 0 && in_range && lane == head;
 #pragma unroll 1
     for (int q = 0; 4 * q < cw; ++q) {
         float v0 = my[(4 * q + 0) * B], v1 = my[(4 * q + 1) * B];
@@ -153,11 +157,12 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
     // launch shapes (different instantiations) round the same way.
     auto add = [&](unsigned c, float a, float v) {
         const unsigned r = c - (unsigned)c0;
-        if (r < ucw) my[r * B] = __fmaf_rn(a, v, my[r * B]);
+        if (r < ucw && ESPNMF_CHECK(c < (unsigned)KP, CHK_COLUMN)) my[r * B] = __fmaf_rn(a, v, my[r * B]);
     };
     // the pairs of row i beyond the record's three, or the whole dense copy
     // of a heavy row
     auto gather_long = [&](int i, float a, int cnt) {
+        if (!ESPNMF_CHECK(cnt <= fld, CHK_COUNT)) return;
         if (cnt >= heavy) {
             const float4* d = dense4 + (int64_t)i * dld4;
             for (int q = 0; 4 * q < cw; ++q) {
@@ -226,18 +231,24 @@ spmm_sell_f32_kernel(SpmmParams<float> p)
                 i2 = __ldcs(idx4 + (int64_t)(q + 2) * 32);
                 a2 = __ldcs(val4 + (int64_t)(q + 2) * 32);
             }
-            const int ii[4] = {i0.x, i0.y, i0.z, i0.w};
+            int ii[4] = {i0.x, i0.y, i0.z, i0.w};
             const float aa[4] = {a0.x, a0.y, a0.z, a0.w};
             uint4 rc[4];
             if constexpr (MASK > 0) {
                 // skip the records of zero rows (one more dependent load)
                 uint32_t mw[4];
 #pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (ii[u] >= 0 && !ESPNMF_CHECK(ii[u] < p.frows, CHK_FACTOR_ROW)) ii[u] = -1;
+#pragma unroll
                 for (int u = 0; u < 4; ++u) mw[u] = ii[u] >= 0 ? fmask[ii[u] >> 5] : 0u;
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     rc[u] = (ii[u] >= 0 && ((mw[u] >> (ii[u] & 31)) & 1u)) ? __ldg(rec + 2 * ii[u]) : zero4;
             } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (ii[u] >= 0 && !ESPNMF_CHECK(ii[u] < p.frows, CHK_FACTOR_ROW)) ii[u] = -1;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) rc[u] = ii[u] >= 0 ? __ldg(rec + 2 * ii[u]) : zero4;
             }
@@ -324,6 +335,7 @@ spmm_sell1_f32_kernel(SpmmParams<float> p)
 
     // slot[col] += a * v (an explicit fused multiply-add, as in every shape)
     auto fma_slot = [&](unsigned col, float a, float v) {
+        if (!ESPNMF_CHECK(col < (unsigned)KP, CHK_COLUMN)) return;
         const uint32_t ad = mybase + col * bstride;
         float s;
         asm volatile("ld.shared.f32 %0, [%1];" : "=f"(s) : "r"(ad));
@@ -334,6 +346,7 @@ spmm_sell1_f32_kernel(SpmmParams<float> p)
     // second half, the rest from the row-packed pairs; a heavy row from its
     // dense copy
     auto pairs_beyond = [&](int i, float a, int cnt) {
+        if (!ESPNMF_CHECK(cnt <= fld, CHK_COUNT)) return;
         if (cnt >= heavy) {
             const float4* d = dense4 + (int64_t)i * dld4;
 #pragma unroll 1
@@ -360,7 +373,7 @@ spmm_sell1_f32_kernel(SpmmParams<float> p)
     // the first half of row i's record (zero for a padding entry or, with
     // the bitmask, a zero row)
     auto load_rec = [&](int i) -> uint4 {
-        bool live = i >= 0;
+        bool live = i >= 0 && ESPNMF_CHECK(i < p.frows, CHK_FACTOR_ROW);
         if constexpr (MASK > 0) live = live && ((fmask[i >> 5] >> (i & 31)) & 1u);
         return live ? __ldg(rec + 2 * i) : make_uint4(0u, 0u, 0u, 0u);
     };
@@ -593,8 +606,11 @@ spmm_freq_f32_kernel(FreqParams p)
                 uint32_t off = zero_off;
                 float a = 0.f;
                 if (e < q1) {
-                    off = (uint32_t)p.hidx[e] * ROW;
-                    a = p.hval[e];
+                    const unsigned sl = p.hidx[e];
+                    if (ESPNMF_CHECK(sl < (unsigned)p.h, CHK_SLOT)) {
+                        off = sl * ROW;
+                        a = p.hval[e];
+                    }
                 }
                 stage[lane] = make_int2((int)off, __float_as_int(a));
                 __syncwarp();
@@ -654,9 +670,11 @@ spmm_sell_f64_kernel(SpmmParams<double> p, int KP)
     const int heavy = p.heavy;
     for (int p0 = 0; p0 < len; ++p0) {
         const int64_t at = base + (int64_t)(p0 >> 2) * 128 + (p0 & 3);
-        const int i = __ldcs(p.idx + at);
+        int i = __ldcs(p.idx + at);
         const double a = __ldcs(p.val + at);
-        const int cnt = i >= 0 ? __ldg(p.fcnt + i) : 0;
+        if (i >= 0 && !ESPNMF_CHECK(i < p.frows, CHK_FACTOR_ROW)) i = -1;
+        int cnt = i >= 0 ? __ldg(p.fcnt + i) : 0;
+        if (!ESPNMF_CHECK(cnt <= KP, CHK_COUNT)) cnt = 0;
         if (cnt >= heavy) {
             const double2* r = reinterpret_cast<const double2*>(p.fdense + (int64_t)i * p.dld);
             for (int q = 0; q < (p.k + 1) / 2; ++q) {
@@ -671,6 +689,12 @@ spmm_sell_f64_kernel(SpmmParams<double> p, int KP)
                 const int4 cc = __ldg(cr + (q >> 2));
                 const double2 v01 = __ldg(vr + (q >> 1));
                 const double2 v23 = __ldg(vr + (q >> 1) + 1);
+                const bool ok = ESPNMF_CHECK((unsigned)cc.x < (unsigned)KP &&
+                                                 (q + 1 >= cnt || (unsigned)cc.y < (unsigned)KP) &&
+                                                 (q + 2 >= cnt || (unsigned)cc.z < (unsigned)KP) &&
+                                                 (q + 3 >= cnt || (unsigned)cc.w < (unsigned)KP),
+                                             CHK_COLUMN);
+                if (!ok) continue;
                 my[cc.x * B] = fma(a, v01.x, my[cc.x * B]);
                 if (q + 1 < cnt) my[cc.y * B] = fma(a, v01.y, my[cc.y * B]);
                 if (q + 2 < cnt) my[cc.z * B] = fma(a, v23.x, my[cc.z * B]);
@@ -683,7 +707,8 @@ spmm_sell_f64_kernel(SpmmParams<double> p, int KP)
     const int maxg = __reduce_max_sync(0xffffffffu, (unsigned)(end - head));
     const int row = p.seg_row[seg];
     const int part = p.seg_part[seg];
-    double* out = (row >= 0 && lane == head)
+    const bool in_range = row < 0 || ESPNMF_CHECK(part < 0 ? row < p.yrows : part < p.npart, CHK_OUT_ROW);
+    double* out = (row >= 0 && in_range && lane == head)
                       ? (part < 0 ? p.Y + (int64_t)row * KP : p.partials + (int64_t)part * KP)
                       : nullptr;
     for (int c = 0; c < KP; ++c) {
@@ -831,6 +856,9 @@ cudaError_t launch_spmm(const SellDev& S, const EllDev& F, int k, T* Y,
     p.k = k;
     p.Y = Y;
     p.partials = static_cast<T*>(S.partials);
+    p.frows = F.rows;
+    p.yrows = S.rows;
+    p.npart = S.npart;
     const int KP = F.ld;
     if constexpr (sizeof(T) == 4) {
         switch (KP) {
@@ -963,6 +991,8 @@ cudaError_t setup_spmm()
 #undef ESPNMF_SETUP
     return e;
 }
+
+ESPNMF_CHECK_READER(check_flags_spmm)
 
 template cudaError_t launch_spmm<float>(const SellDev&, const EllDev&, int, float*, int64_t, SpmmConfig, cudaStream_t, int);
 template cudaError_t launch_spmm<double>(const SellDev&, const EllDev&, int, double*, int64_t, SpmmConfig, cudaStream_t, int);

@@ -115,3 +115,31 @@ def test_sequential_validates_and_needs_a_gpu(lib):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         assert call(2, 1) == E.ERR_CUDA
+
+
+def test_checked_flags_entry_point(lib):
+    """espnmf_checked_flags: in the regular build it reports UNSUPPORTED and
+    clears the output; in the checked build without a GPU it fails with
+    ERR_CUDA instead of returning made-up flags."""
+    import ctypes
+    import os
+    import subprocess
+    import sys
+    import paper_1510_05237_gb300 as E
+    f = ctypes.c_uint32(7)
+    assert lib.espnmf_checked_flags(ctypes.byref(f)) == E.ERR_UNSUPPORTED and f.value == 0
+    assert lib.espnmf_checked_flags(None) == E.ERR_INVALID_ARG
+    from paper_1510_05237_gb300 import build as B
+    if not os.path.exists(B.LIB_CHECKED):
+        pytest.skip("checked build not present")
+    code = ("import ctypes, paper_1510_05237_gb300 as E\n"
+            "from paper_1510_05237_gb300 import binding as b\n"
+            "assert b.library_path().endswith('libespnmf_checked.so')\n"
+            "f = ctypes.c_uint32(7)\n"
+            "print(E.load().espnmf_checked_flags(ctypes.byref(f)))\n")
+    env = dict(os.environ, ESPNMF_CHECKED="1", CUDA_VISIBLE_DEVICES="")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert int(r.stdout.strip().splitlines()[-1]) == E.ERR_CUDA
