@@ -316,8 +316,8 @@ def run_sequential(args):
                    "k = 50 context); seconds: set-up excluded (Alg. 3: stream time of its "
                    "iterations from CUDA events inside espnmf_sequential; Alg. 2: stream time of "
                    "espnmf_iterate(100) from CUDA events, graph capture and launch-shape tuning "
-                   "included); Alg. 3's "
-                   "half-steps run eagerly (not graph-replayed)")
+                   "included); both replay their sweeps from captured graphs after the "
+                   "first sweep (Alg. 3: of each block)")
     print(json.dumps(out), flush=True)
     return 0
 

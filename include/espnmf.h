@@ -358,7 +358,9 @@ espnmf_status espnmf_spmm_config(espnmf_ctx *ctx, int32_t product, int32_t *spli
  * gives rank-1 topics, the case the paper times, where the k2 x k2 solve is
  * a division.  The sparse products, the solve, the projection and the top-t
  * rule are those of Alg. 2 with k = k2 (a k = k2 context built from A, FP32
- * or FP64 form); the deflation term runs in FP64 sums.  A: as for
+ * or FP64 form); the deflation term runs in FP64 sums.  Each block's sweeps
+ * after its first are replayed from captured CUDA graphs, as
+ * espnmf_iterate runs them.  A: as for
  * espnmf_init (copied).  U0: n x k2 row-major (dtype u0_dtype, host or
  * device).  U_out (n x k) and V_out (m x k): row-major DEVICE buffers of the
  * compute dtype, written when the call returns ESPNMF_OK (it synchronises).

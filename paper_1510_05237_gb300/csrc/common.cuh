@@ -397,12 +397,14 @@ cudaError_t setup_chol();
 // over the first k1 columns of G1 (rows_f x ld1, the fixed factor's
 // converged topics) and the block factor F (row-packed: cnt, col, val with
 // row stride ld), then Y[i][j] -= (H1 g)_ij for the rows_h rows of H1 (the
-// updated factor's converged topics), j < k2.  g holds k1 * k2 doubles of
-// scratch.
+// updated factor's converged topics), j < k2.  k1 is read from device
+// memory (*k1, at most k1_max), so a captured sweep serves every block; with
+// k1 = 0 Y is left unchanged.  g holds k1_max * k2 doubles of scratch.
 template <typename T>
 cudaError_t launch_seq_deflate(int64_t rows_f, const T* G1, int64_t rows_h, const T* H1, int ld1,
-                               int k1, int k2, const int32_t* cnt, const int32_t* col, const T* val,
-                               int ld, double* g, T* Y, int64_t ldy, cudaStream_t st);
+                               int k1_max, const int* k1, int k2, const int32_t* cnt,
+                               const int32_t* col, const T* val, int ld, double* g, T* Y,
+                               int64_t ldy, cudaStream_t st);
 // H[i * ld1 + j0 + j] = the block factor's value in row i, column j < k2.
 template <typename T>
 cudaError_t launch_seq_append(int64_t rows, const int32_t* cnt, const int32_t* col, const T* val,

@@ -81,10 +81,12 @@ struct Stat {
 // Alg. 3 (sequential ALS): the converged topics held densely (rows x ld1,
 // first k1 columns valid) while a k = k2 context finds the next block.
 struct Deflation {
+    bool active = false;   // espnmf_sequential's context: the hook runs in every half-step
     void* U1 = nullptr;
     void* V1 = nullptr;
     int ld1 = 0;
-    int k1 = 0;
+    int k1_max = 0;        // the most converged topics a block has (k - k2)
+    int* k1 = nullptr;     // device: the converged topics of the current block
     double* g = nullptr;
 };
 
@@ -960,18 +962,20 @@ espnmf_status half_update(espnmf_ctx* ctx, bool updV)
     O.chol_pending = false;
 
     TRY(do_spmm(ctx, updV, O.buf[O.cur]));
-    if (ctx->defl.k1 > 0) {
-        // Alg. 3: subtract the converged topics' part (Eq. 7 / Eq. 8)
+    if (ctx->defl.active) {
+        // Alg. 3: subtract the converged topics' part (Eq. 7 / Eq. 8); the
+        // number of converged topics is read on the device
+        const Deflation& d = ctx->defl;
         const EllDev& f = O.buf[O.cur];
-        const void* G1 = updV ? ctx->defl.U1 : ctx->defl.V1;
-        void* H1 = updV ? ctx->defl.V1 : ctx->defl.U1;
+        const void* G1 = updV ? d.U1 : d.V1;
+        void* H1 = updV ? d.V1 : d.U1;
         CU(is_f64(ctx) ? launch_seq_deflate<double>(O.rows, (const double*)G1, rows, (const double*)H1,
-                                                    ctx->defl.ld1, ctx->defl.k1, ctx->k, f.cnt, f.col,
-                                                    (const double*)f.val, f.ld, ctx->defl.g,
+                                                    d.ld1, d.k1_max, d.k1, ctx->k, f.cnt, f.col,
+                                                    (const double*)f.val, f.ld, d.g,
                                                     (double*)ctx->Y, ctx->ldy, ctx->st)
                        : launch_seq_deflate<float>(O.rows, (const float*)G1, rows, (const float*)H1,
-                                                   ctx->defl.ld1, ctx->defl.k1, ctx->k, f.cnt, f.col,
-                                                   (const float*)f.val, f.ld, ctx->defl.g,
+                                                   d.ld1, d.k1_max, d.k1, ctx->k, f.cnt, f.col,
+                                                   (const float*)f.val, f.ld, d.g,
                                                    (float*)ctx->Y, ctx->ldy, ctx->st));
     }
     CU(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
@@ -2617,10 +2621,12 @@ espnmf_status espnmf_batch_iterate(espnmf_batch* b, int32_t iters, espnmf_status
 }
 
 // Alg. 3 (sequential ALS, Sec. 4) on one k = k2 context: for each block of
-// k2 topics the context's U is reset to U0, `iters` sweeps of half-updates
-// run with the converged topics subtracted after each sparse product (the
-// deflation hook of half_update; none for the first block, which is Alg. 2
-// itself), and the block is appended to the dense U1, V1.
+// k2 topics the context's U is reset to U0, `iters` sweeps run (graph
+// replays after the first, as espnmf_iterate runs them) with the converged
+// topics subtracted after each sparse product (the deflation hook of
+// half_update, which reads the number of converged topics on the device;
+// none for the first block, which is Alg. 2 itself), and the block is
+// appended to the dense U1, V1.
 espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int32_t k2, int64_t t_u,
                                 int64_t t_v, int32_t iters, espnmf_dtype compute, const void* U0,
                                 espnmf_dtype u0_dtype, int32_t u0_on_device, void* U_out,
@@ -2661,18 +2667,30 @@ espnmf_status espnmf_sequential(const espnmf_csr* A, int32_t k, int32_t k2, int6
         cudaMemsetAsync(d.V1, 0, es * (size_t)m * k, c->st) != cudaSuccess)
         return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: memset"));
     d.ld1 = k;
+    // the converged topics of block b, b * k2, copied on the stream into the
+    // device word the deflation reads before the block's sweeps
+    const int nblocks = k / k2;
+    int* kvals = nullptr;
+    {
+        std::vector<int> kv(nblocks);
+        for (int b = 0; b < nblocks; ++b) kv[b] = b * k2;
+        if ((st = dupload(c, &kvals, kv.data(), sizeof(int) * (size_t)nblocks)) != ESPNMF_OK)
+            return fail(st);
+    }
+    if ((st = dmalloc(c, &d.k1, sizeof(int))) != ESPNMF_OK) return fail(st);
+    d.k1_max = k - k2;
+    d.active = true;
     if (ev[0] && cudaEventRecord(ev[0], c->st) != cudaSuccess)
         return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: event"));
-    for (int32_t j0 = 0; j0 < k; j0 += k2) {
-        d.k1 = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        const int j0 = b * k2;
         if (j0 > 0 && (st = espnmf_set_factor(c, ESPNMF_U, U0, u0_dtype, u0_on_device)) != ESPNMF_OK)
             return fail(st);
-        d.k1 = j0;
-        for (int32_t it = 0; it < iters; ++it) {
-            if ((st = espnmf_als_update_V(c)) != ESPNMF_OK) return fail(st);
-            if ((st = espnmf_als_update_U(c)) != ESPNMF_OK) return fail(st);
-        }
-        d.k1 = 0;
+        if (cudaMemcpyAsync(d.k1, kvals + b, sizeof(int), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+            return fail(set_err(c, ESPNMF_ERR_CUDA, "sequential: block start"));
+        // the block's sweeps: the first eagerly (the first block's V does not
+        // exist yet), the rest replayed from the context's captured sweeps
+        if ((st = espnmf_iterate(c, iters, nullptr, nullptr)) != ESPNMF_OK) return fail(st);
         const EllDev& fu = c->U.buf[c->U.cur];
         const EllDev& fv = c->V.buf[c->V.cur];
         cudaError_t e = f64 ? launch_seq_append<double>(n, fu.cnt, fu.col, (const double*)fu.val,

@@ -16,17 +16,19 @@ namespace espnmf {
 constexpr int kSeqThreads = 256;
 
 // g[c * k2 + j] = sum_i G1[i][c] F[i][j] for c < k1, j < k2 (one block per
-// (c, j)), over the rows where F -- row-packed: cnt[i] pairs (column,
-// value) at [i * ld, i * ld + cnt[i]) -- has column j.  Per-thread sums in
-// row order, then a fixed tree.
+// (c, j); the grid covers the largest k1, *k1 is read on the device so that
+// one captured sweep serves every block of topics), over the rows where F --
+// row-packed: cnt[i] pairs (column, value) at [i * ld, i * ld + cnt[i]) --
+// has column j.  Per-thread sums in row order, then a fixed tree.
 template <typename T>
 __global__ void __launch_bounds__(kSeqThreads)
 seq_dot_kernel(int64_t rows, const T* __restrict__ G1, int ld1, const int32_t* __restrict__ cnt,
                const int32_t* __restrict__ col, const T* __restrict__ val, int ld, int k2,
-               double* __restrict__ g)
+               const int* __restrict__ k1p, double* __restrict__ g)
 {
     __shared__ double red[kSeqThreads];
     const int c = blockIdx.x, j = blockIdx.y;
+    if (c >= *k1p) return;
     double s = 0.0;
     for (int64_t i = threadIdx.x; i < rows; i += kSeqThreads) {
         const int nc = cnt[i];
@@ -50,11 +52,12 @@ seq_dot_kernel(int64_t rows, const T* __restrict__ G1, int ld1, const int32_t* _
 // nothing and are skipped) and the difference rounded once.
 template <typename T>
 __global__ void __launch_bounds__(kSeqThreads)
-seq_deflate_kernel(int64_t rows, int k1, int k2, const T* __restrict__ H1, int ld1,
-                   const double* __restrict__ g, T* __restrict__ Y, int64_t ldy)
+seq_deflate_kernel(int64_t rows, const int* __restrict__ k1p, int k2, const T* __restrict__ H1,
+                   int ld1, const double* __restrict__ g, T* __restrict__ Y, int64_t ldy)
 {
     const int64_t i = (int64_t)blockIdx.x * kSeqThreads + threadIdx.x;
-    if (i >= rows) return;
+    const int k1 = *k1p;
+    if (i >= rows || k1 <= 0) return;
     const T* h = H1 + i * ld1;
     for (int j = 0; j < k2; ++j) {
         double s = 0.0;
@@ -90,12 +93,13 @@ static unsigned seq_grid(int64_t rows) { return (unsigned)((rows + kSeqThreads -
 
 template <typename T>
 cudaError_t launch_seq_deflate(int64_t rows_f, const T* G1, int64_t rows_h, const T* H1, int ld1,
-                               int k1, int k2, const int32_t* cnt, const int32_t* col, const T* val,
-                               int ld, double* g, T* Y, int64_t ldy, cudaStream_t st)
+                               int k1_max, const int* k1, int k2, const int32_t* cnt,
+                               const int32_t* col, const T* val, int ld, double* g, T* Y,
+                               int64_t ldy, cudaStream_t st)
 {
-    if (k1 <= 0) return cudaSuccess;
-    seq_dot_kernel<T><<<dim3((unsigned)k1, (unsigned)k2), kSeqThreads, 0, st>>>(
-        rows_f, G1, ld1, cnt, col, val, ld, k2, g);
+    if (k1_max <= 0) return cudaSuccess;
+    seq_dot_kernel<T><<<dim3((unsigned)k1_max, (unsigned)k2), kSeqThreads, 0, st>>>(
+        rows_f, G1, ld1, cnt, col, val, ld, k2, k1, g);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || rows_h == 0) return e;
     seq_deflate_kernel<T><<<seq_grid(rows_h), kSeqThreads, 0, st>>>(rows_h, k1, k2, H1, ld1, g, Y, ldy);
@@ -112,10 +116,11 @@ cudaError_t launch_seq_append(int64_t rows, const int32_t* cnt, const int32_t* c
 }
 
 template cudaError_t launch_seq_deflate<float>(int64_t, const float*, int64_t, const float*, int, int,
-                                               int, const int32_t*, const int32_t*, const float*, int,
-                                               double*, float*, int64_t, cudaStream_t);
+                                               const int*, int, const int32_t*, const int32_t*,
+                                               const float*, int, double*, float*, int64_t,
+                                               cudaStream_t);
 template cudaError_t launch_seq_deflate<double>(int64_t, const double*, int64_t, const double*, int,
-                                                int, int, const int32_t*, const int32_t*,
+                                                int, const int*, int, const int32_t*, const int32_t*,
                                                 const double*, int, double*, double*, int64_t,
                                                 cudaStream_t);
 template cudaError_t launch_seq_append<float>(int64_t, const int32_t*, const int32_t*, const float*,
