@@ -211,12 +211,8 @@ __device__ __forceinline__ void fma2f(float& s0, float& s1, float a0, float a1, 
 // N1[j][i] = -L[i][j] (i > j) and N2[j][i] = -L[j][i] (i < j), zero
 // elsewhere, so a step reads its coefficients as aligned 16-byte rows; a
 // zero coefficient leaves the unknown it meets unchanged.
-// resident blocks asked of the compiler: four of one row per thread (at most
-// 128 registers), three of two rows per thread (at most 170)
-constexpr int solve_min_blocks(int R) { return R == 1 ? 4 : 3; }
-
 template <int KP, int R>
-__global__ void __launch_bounds__(kSolveRows, solve_min_blocks(R))
+__global__ void __launch_bounds__(kSolveRows, 4 / R)
 solve_chol_kernel(const float* __restrict__ Y, int64_t ldy, int64_t rows, int k,
                   const float* __restrict__ Lg, const float* __restrict__ LTg,
                   const float* __restrict__ rdg, float* __restrict__ Xt, int64_t ldx,
@@ -302,12 +298,10 @@ solve_chol_kernel(const float* __restrict__ Y, int64_t ldy, int64_t rows, int k,
     if (bad) atomicOr(status, ST_NONFINITE);
 }
 
-// rows per thread of solve_chol_kernel.  The kernel is bound by the
-// delivery of the factor's coefficients from shared memory to registers
-// (every row reads all k^2 of them); two rows per thread halve that per row.
-// Up to a row width of 56 they fit in 170 registers (three blocks, 12 warps
-// per SM, a few spilled words); wider rows keep one row per thread.
-constexpr int solve_rows_per_thread(int KP) { return KP <= 56 ? 2 : 1; }
+// rows per thread of solve_chol_kernel.  Two rows per thread halve the
+// shared-memory reads per FMA but need ~230 registers at k = 50 (8 warps per
+// SM): measured slower on the 50k x 100k workload, so one.
+constexpr int solve_rows_per_thread(int) { return 1; }
 
 template <int KP>
 static cudaError_t launch_solve_chol_kp(const float* Y, int64_t ldy, int64_t rows, int k,
@@ -318,7 +312,7 @@ static cudaError_t launch_solve_chol_kp(const float* Y, int64_t ldy, int64_t row
     const size_t smem = ((size_t)2 * KP * KP + KP) * sizeof(float);
     constexpr int R = solve_rows_per_thread(KP);
     const int64_t tiles = (rows + kSolveRows * R - 1) / (kSolveRows * R);
-    int64_t grid = (int64_t)sm_count * solve_min_blocks(R);
+    int64_t grid = (int64_t)sm_count * (4 / R);
     if (grid > tiles) grid = tiles;
     solve_chol_kernel<KP, R><<<(unsigned)grid, kSolveRows, smem, st>>>(Y, ldy, rows, k, L, LT, rd,
                                                                      Xt, ldx, status, project);
