@@ -415,17 +415,11 @@ def run_sweep_t(args):
     return 0
 
 
-def to_bf16(x: np.ndarray) -> np.ndarray:
-    """FP32 values rounded to the nearest BF16 (ties to even), as FP32."""
-    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
-    return u.astype(np.uint32).view(np.float32)
-
-
 def run_bf16_effect(args):
-    """What BF16 inputs would cost in accuracy on the benchmark: the FP32
-    form run on A's values and U0 rounded to BF16 (8 significant bits),
-    against the FP64 form on the original A.  Prints one JSON line."""
+    """What BF16 inputs cost in accuracy on the benchmark: the FP32 form run
+    on A's values and U0 given to the library as BF16 tensors (8
+    significant bits; widened exactly at set-up), against the FP64 form on
+    the original A.  Prints one JSON line."""
     import torch
     import paper_1510_05237_gb300 as E
     torch.cuda.set_device(0)
@@ -436,8 +430,8 @@ def run_bf16_effect(args):
     out = {"experiment": "bf16_effect", "workload": WORKLOAD, "sweeps": JOB_ITERS}
     runs = {"fp64": (dev(A.val), dev(U0), E.F64),
             "fp32": (dev(A.val.astype(np.float32)), dev(U0.astype(np.float32)), E.F32),
-            "bf16_inputs": (dev(to_bf16(A.val.astype(np.float32))),
-                            dev(to_bf16(U0.astype(np.float32))), E.F32)}
+            "bf16_inputs": (dev(A.val.astype(np.float32)).to(torch.bfloat16),
+                            dev(U0.astype(np.float32)).to(torch.bfloat16), E.F32)}
     for name, (va, u0, comp) in runs.items():
         c = E.espnmf_init(rp, ci, va, A.n, A.m, K_TOPICS, T_KEEP, T_KEEP, E.TOPT_COLUMN, comp,
                           u0, stream=stream)

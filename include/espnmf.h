@@ -108,7 +108,10 @@ typedef struct espnmf_ctx espnmf_ctx;
  *            Must be >= 0.
  *   mode     enforcement mode (see espnmf_topt_mode).
  *   compute  ESPNMF_F64 or ESPNMF_F32 (ESPNMF_BF16 returns UNSUPPORTED).
- *   U0       initial guess, n x k row-major of type U0_dtype (F64 or F32),
+ *            A's values (A->vdtype) and U0 may be F64, F32 or BF16; BF16
+ *            inputs are widened exactly (the BF16 bits are the high half of
+ *            an FP32 word) and computed on in the compute type.
+ *   U0       initial guess, n x k row-major of type U0_dtype (F64, F32 or BF16),
  *            host (U0_on_device = 0) or device memory; entries must be
  *            finite and >= 0.  U0 is not enforced (Alg. 2 starts from it
  *            as given).
@@ -176,7 +179,7 @@ espnmf_status espnmf_enforce_topt(espnmf_ctx *ctx, espnmf_which which,
                                   int64_t t);
 
 /* espnmf_set_factor -- replaces U or V with a dense rows x k row-major
- * matrix (F64 or F32, host or device), finite and >= 0, without
+ * matrix (F64, F32 or BF16, host or device), finite and >= 0, without
  * enforcement; refreshes its Gram matrix.  Used to start a step from a
  * chosen iterate. */
 espnmf_status espnmf_set_factor(espnmf_ctx *ctx, espnmf_which which,

@@ -164,6 +164,8 @@ def _ptr(x):
 
 def _dtype_code(x) -> int:
     name = str(x.dtype)
+    if "bfloat16" in name:
+        return BF16
     if "float64" in name:
         return F64
     if "float32" in name:

@@ -61,6 +61,9 @@ __device__ __forceinline__ bool espnmf_check(bool ok, unsigned bit)
 #define ESPNMF_CHECK_READER(name) \
     unsigned name() { return 0; }
 #endif
+// y[0, count) = the FP32 values of the BF16 words x[0, count) (exact).
+cudaError_t launch_bf16_to_f32(const uint16_t* x, int64_t count, float* y, cudaStream_t st);
+
 // per translation unit: the flags its kernels raised (checked build)
 unsigned check_flags_spmm();
 unsigned check_flags_select();

@@ -1128,16 +1128,26 @@ espnmf_status set_factor_impl(espnmf_ctx* ctx, Factor& F, const void* src, espnm
                               int on_device)
 {
     if (!src) return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "factor pointer is NULL");
-    if (dtype != ESPNMF_F64 && dtype != ESPNMF_F32)
-        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "factor dtype must be F64 or F32");
-    const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
+    if (dtype != ESPNMF_F64 && dtype != ESPNMF_F32 && dtype != ESPNMF_BF16)
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "factor dtype must be F64, F32 or BF16");
+    const size_t es = dtype == ESPNMF_F64 ? 8 : dtype == ESPNMF_F32 ? 4 : 2;
     const size_t bytes = (size_t)F.rows * ctx->k * es;
     const void* dptr = src;
     void* tmp = nullptr;
+    void* tmp32 = nullptr;
     if (!on_device) {
         CU(cudaMallocAsync(&tmp, bytes ? bytes : 16, ctx->st));
         CU(cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, ctx->st));
         dptr = tmp;
+    }
+    if (dtype == ESPNMF_BF16) {
+        // widened to FP32 (exact), then handled as an FP32 factor
+        const int64_t count = F.rows * (int64_t)ctx->k;
+        CU(cudaMallocAsync(&tmp32, count ? (size_t)count * 4 : 16, ctx->st));
+        CU(launch_bf16_to_f32(static_cast<const uint16_t*>(dptr), count, static_cast<float*>(tmp32),
+                              ctx->st));
+        dptr = tmp32;
+        dtype = ESPNMF_F32;
     }
     const double cb = (double)F.rows * ctx->k * (es + ctx->esz);
     espnmf_status s = run(ctx, K_TO_COLMAJOR, cb, ctx->st, [&] {
@@ -1156,6 +1166,7 @@ espnmf_status set_factor_impl(espnmf_ctx* ctx, Factor& F, const void* src, espnm
                                  ctx->ldx, ctx->status_d, true, ctx->st);
     });
     if (tmp) CU(cudaFreeAsync(tmp, ctx->st));
+    if (tmp32) CU(cudaFreeAsync(tmp32, ctx->st));
     TRY(s);
     TRY(check_status(ctx));
     // thresholds that keep every positive entry (U0 is not enforced)
@@ -1319,10 +1330,10 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
     if (mode == ESPNMF_TOPT_MATRIX &&
         ((int64_t)k * A->n >= (1ll << 31) || (int64_t)k * A->m >= (1ll << 31)))
         return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "matrix mode needs rows*k < 2^31");
-    if (A->vdtype != ESPNMF_F64 && A->vdtype != ESPNMF_F32)
-        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "A values must be F64 or F32");
-    if (U0_dtype != ESPNMF_F64 && U0_dtype != ESPNMF_F32)
-        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "U0 dtype must be F64 or F32");
+    if (A->vdtype != ESPNMF_F64 && A->vdtype != ESPNMF_F32 && A->vdtype != ESPNMF_BF16)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "A values must be F64, F32 or BF16");
+    if (U0_dtype != ESPNMF_F64 && U0_dtype != ESPNMF_F32 && U0_dtype != ESPNMF_BF16)
+        return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "U0 dtype must be F64, F32 or BF16");
     if (A->nnz > 0 && (!A->rowptr || !A->colidx || !A->values))
         return set_err(nullptr, ESPNMF_ERR_INVALID_ARG, "A arrays are NULL");
 
@@ -1382,7 +1393,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         // ---- A: validate and build both layouts on host threads.  A on the
         // device is first copied to the host; host arrays are read in place.
         const int64_t n = A->n, m = A->m, nnz = A->nnz;
-        const size_t vsz = A->vdtype == ESPNMF_F64 ? 8 : 4;
+        const size_t vsz = A->vdtype == ESPNMF_F64 ? 8 : A->vdtype == ESPNMF_F32 ? 4 : 2;
         std::vector<int64_t> rp_h;
         hvec<int32_t> ci_h;
         hvec<unsigned char> vraw_h;
@@ -1411,10 +1422,19 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         parallel_chunks(nnz, [&](int64_t p0, int64_t p1) {
             for (int64_t p = p0; p < p1; ++p) {
                 double x;
-                if (vsz == 8) memcpy(&x, vraw + p * 8, 8);
-                else {
+                if (vsz == 8) {
+                    memcpy(&x, vraw + p * 8, 8);
+                } else if (vsz == 4) {
                     float f;
                     memcpy(&f, vraw + p * 4, 4);
+                    x = f;
+                } else {
+                    // BF16: the high half of the FP32 word (exact)
+                    uint16_t b;
+                    memcpy(&b, vraw + p * 2, 2);
+                    const uint32_t w = (uint32_t)b << 16;
+                    float f;
+                    memcpy(&f, &w, 4);
                     x = f;
                 }
                 vv[p] = x;

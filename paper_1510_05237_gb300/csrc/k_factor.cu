@@ -1445,6 +1445,24 @@ cudaError_t launch_dense_to_colmajor(const Tin* X, int64_t rows, int k,
     return cudaGetLastError();
 }
 
+// A caller's BF16 factor as FP32: the BF16 bits are the high half of the
+// FP32 word, so the conversion is exact.
+__global__ void bf16_to_f32_kernel(const uint16_t* __restrict__ x, int64_t count,
+                                   float* __restrict__ y)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = __uint_as_float((uint32_t)x[e] << 16);
+}
+
+cudaError_t launch_bf16_to_f32(const uint16_t* x, int64_t count, float* y, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    const int64_t grid = std::min<int64_t>((count + 255) / 256, 4096);
+    bf16_to_f32_kernel<<<(unsigned)grid, 256, 0, st>>>(x, count, y);
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void ell_to_dense_kernel(int64_t rows, int k, int eld,
                                     const int32_t* cnt, const int32_t* col,
