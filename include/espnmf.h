@@ -45,7 +45,7 @@ typedef enum {
     ESPNMF_ERR_OOM = 5,           /* device or host allocation failed */
     ESPNMF_ERR_CUDA = 6,          /* a CUDA call failed (no device, launch error, ...) */
     ESPNMF_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
-    ESPNMF_ERR_UNSUPPORTED = 8    /* a valid request this build does not implement */
+    ESPNMF_ERR_UNSUPPORTED = 8    /* a valid request the library does not implement */
 } espnmf_status;
 
 /* Arithmetic of a context (or the element type of a buffer).

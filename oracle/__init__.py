@@ -183,7 +183,7 @@ def topt(X: np.ndarray, t: int, mode: int = COLUMN) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# Alg. 2 half-steps, measures and the driver
+# Alg. 2 half-steps, measures and the sweep loop
 
 def update_V(A, U: np.ndarray, t_v: int, mode: int = COLUMN,
              return_pre: bool = False):
