@@ -574,7 +574,8 @@ def run_large(args):
             res["gram_condition_after_profiled_sweeps"] = gram_cond()
             get = lambda nm: stats.get(nm, (0, 0.0, 0.0))
             t_prod = sum(get(nm)[1] for nm in ("spmm_AV", "spmm_AtU", "spmm_freq_AV",
-                                               "spmm_freq_AtU", "spmm_combine")) / 3 / 2
+                                               "spmm_freq_AtU", "spmm_freq2_AV",
+                                               "spmm_freq2_AtU", "spmm_combine")) / 3 / 2
             bpp = (2 * A.nnz * 8 + (A.n + 1 + A.m + 1) * 8 + (A.n + A.m) * k * 4) / 2.0
             hbm, src = peaks()
             ach = bpp / (t_prod / 1000.0) / 1e9
@@ -781,7 +782,8 @@ def main():
     # per nonzero, int64 row pointers) and Y (rows x k f32) written once.
     get = lambda name: stats.get(name, (0, 0.0, 0.0))
     t_prod = sum(get(nm)[1] for nm in ("spmm_AV", "spmm_AtU", "spmm_freq_AV",
-                                       "spmm_freq_AtU", "spmm_combine")) / prof_steps
+                                       "spmm_freq_AtU", "spmm_freq2_AV", "spmm_freq2_AtU",
+                                       "spmm_combine")) / prof_steps
     b_av = A.nnz * 8 + (A.n + 1) * 8 + A.n * K_TOPICS * 4
     b_atu = A.nnz * 8 + (A.m + 1) * 8 + A.m * K_TOPICS * 4
     ms_per_product = t_prod / 2.0

@@ -391,12 +391,17 @@ espnmf_status espnmf_select_stats(espnmf_ctx *ctx, int64_t *warm, int64_t *full)
 
 /* espnmf_spmm_frequent -- the frequent part of a sparse product (product 0:
  * A V, 1: A^T U; FP32 contexts only): h = number of gathered factor rows
- * staged densely in shared memory (0: the product has no frequent part)
- * and hnnz = the entries of A routed to them.  The rows are chosen once by
- * espnmf_init: the gathered rows referenced by the most entries of A (the
- * frequent terms, for A^T U), as many as fit a 200 KB table, kept when they
- * carry at least a tenth of the entries.  The paper has no counterpart:
- * this is a layout choice of the sparse product of Alg. 2 steps 1 and 3. */
+ * read densely (0: the product has no frequent part) and hnnz = the
+ * entries of A routed to them.  The rows are chosen once by espnmf_init:
+ * the gathered rows referenced by the most entries of A (the frequent
+ * terms, for A^T U), kept when they carry at least a tenth of the entries.
+ * As many as fit a 200 KB table are staged in shared memory; in column
+ * mode the part takes up to t of them (at most t rows of the gathered
+ * factor can be nonzero in every column), and when that adds at least 256
+ * rows beyond the shared-memory table, the extra rows are read from the
+ * factor's table in global memory (a second launch).  The paper has no
+ * counterpart: this is a layout choice of the sparse product of Alg. 2
+ * steps 1 and 3. */
 espnmf_status espnmf_spmm_frequent(espnmf_ctx *ctx, int32_t product, int32_t *h,
                                    int64_t *hnnz);
 

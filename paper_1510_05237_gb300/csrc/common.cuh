@@ -188,7 +188,8 @@ struct SellDev {
     // dense table, hval = the value.  The output rows are cut into chunks
     // [hwarp[c], hwarp[c+1]) of about equal cost, which the warps of spmm_h
     // take in turn.  slot_of[g] is the slot of gathered row g or -1.
-    int h = 0;
+    int h = 0;                     // table rows in all (slots 0 .. h - 1)
+    int h1 = 0;                    // of them staged in shared memory (slots < h1)
     int64_t hnnz = 0;
     int64_t* hptr = nullptr;       // [rows+1]
     uint16_t* hidx = nullptr;      // [hnnz]
@@ -197,6 +198,16 @@ struct SellDev {
     int hwarps = 0;                // number of chunks
     int* hcounter = nullptr;       // next chunk to take (reset before each launch)
     int32_t* slot_of = nullptr;    // [rows of the gathered factor]
+    // The second tier: the entries whose gathered row has a slot h1 .. h - 1,
+    // read from the factor's table in global memory (it stays in the L2),
+    // stored per output row like the first tier's.
+    int64_t h2nnz = 0;
+    int64_t* h2ptr = nullptr;      // [rows+1]
+    uint16_t* h2idx = nullptr;     // [h2nnz] absolute slots
+    void* h2val = nullptr;         // [h2nnz]
+    int32_t* h2warp = nullptr;     // [h2warps+1]
+    int h2warps = 0;
+    int* h2counter = nullptr;
 };
 
 // A factor (U: n x k, V: m x k) in row-packed sparse form: row i holds
@@ -271,13 +282,17 @@ template <typename T>
 cudaError_t launch_spmm_combine(const SellDev& S, int k, T* Y, int64_t ldy,
                                 cudaStream_t st);
 // Frequent part of an FP32 product (S.h > 0): Y += the products of the
-// entries whose gathered row is one of the h frequent rows, from F.htab
-// staged in shared memory.  Runs after launch_spmm (and the combine), one
-// CTA per SM; `wait_limit` bounds the wait for the staging copy.
+// entries whose gathered row is one of the h frequent rows.  tier 1: the
+// first S.h1 rows of F.htab staged in shared memory (TMA bulk copies;
+// `wait_limit` bounds the wait for them); tier 2: the rows h1 .. h - 1 read
+// from F.htab in global memory (L2).  Runs after launch_spmm (and the
+// combine), tier 1 before tier 2, one CTA per SM.
 constexpr int kHThreads = 1024;
-constexpr size_t kHTableBytes = 200 * 1024;   // largest dense table staged
+constexpr size_t kHTableBytes = 200 * 1024;    // largest dense table staged
+constexpr size_t kH2TableBytes = 16u << 20;    // largest table of both tiers
+constexpr int kMinTier2Rows = 256;             // a smaller second tier is not built
 cudaError_t launch_spmm_h(const SellDev& S, const EllDev& F, float* Y, int sm_count,
-                          unsigned* status, long long wait_limit, cudaStream_t st);
+                          unsigned* status, long long wait_limit, cudaStream_t st, int tier);
 
 template <typename T>
 cudaError_t launch_solve(const T* Y, int64_t ldy, int64_t rows, int k,
@@ -462,7 +477,7 @@ void set_thread_error(const char* msg);
 enum KernelKind : int {
     K_SPMM = 0, K_SPMM_T, K_COMBINE, K_SOLVE, K_SELECT, K_EMIT, K_GRAM_REDUCE,
     K_INVERSE, K_TO_COLMAJOR, K_NORM2, K_DOT, K_SCATTER, K_GRAD, K_LAMBDA, K_PG,
-    K_SPMM_H, K_SPMM_H_T, K_GRAM_TABLE, K_REFINE, K_COUNT
+    K_SPMM_H, K_SPMM_H_T, K_GRAM_TABLE, K_REFINE, K_SPMM_H2, K_SPMM_H2_T, K_COUNT
 };
 const char* kernel_name(int kind);
 

@@ -36,7 +36,8 @@ const char* kernel_name(int kind)
                                          "select_topt", "emit", "gram_reduce",
                                          "gram_inverse", "to_colmajor", "norm2", "ell_dot",
                                          "scatter", "grad", "lambda_max", "pg_apply",
-                                         "spmm_freq_AV", "spmm_freq_AtU", "gram_table", "refine"};
+                                         "spmm_freq_AV", "spmm_freq_AtU", "gram_table", "refine",
+                                         "spmm_freq2_AV", "spmm_freq2_AtU"};
     return kind >= 0 && kind < K_COUNT ? names[kind] : "?";
 }
 }  // namespace espnmf
@@ -549,40 +550,55 @@ void build_sell(int64_t rows, const int64_t* ptr, const int32_t* ind, const doub
 // The frequent part of an FP32 product.  The gathered rows that the most
 // entries reference (weight = entries per gathered row) are candidates when
 // they are referenced at least 4x as often as the average row (and at least
-// 16 times); up to kHTableBytes / (ld * 4) of them (and < 2^16) form the
-// table, in decreasing weight (ties: lower index first).  The part is kept
-// only if its entries are at least a tenth of all.  Returns h (0: none) and
-// fills slot_of.
-int choose_frequent(const std::vector<int64_t>& weight, int64_t nnz, int ld,
-                    std::vector<int32_t>& slot_of)
+// 16 times), in decreasing weight (ties: lower index first).  The first
+// kHTableBytes / (ld * 4) of them form the table staged in shared memory
+// (tier 1).  Column enforcement keeps t rows per factor column, so at most
+// t gathered rows can be nonzero in every column: with t_rows = t (0 in the
+// other modes) the table takes up to t candidates, those beyond tier 1
+// read from global memory (tier 2, kept only if it holds at least
+// kMinTier2Rows rows; at most kH2TableBytes and 2^16 - 1 rows in all).  The
+// part is kept only if its entries are at least a tenth of all.  Returns h
+// (0: none), sets h1 (rows in tier 1) and fills slot_of.
+int choose_frequent(const std::vector<int64_t>& weight, int64_t nnz, int ld, int64_t t_rows,
+                    std::vector<int32_t>& slot_of, int& h1)
 {
     const int64_t ng = (int64_t)weight.size();
     slot_of.assign(ng, -1);
+    h1 = 0;
     if (ng == 0 || nnz == 0) return 0;
-    const int64_t cap = std::min<int64_t>((int64_t)(kHTableBytes / ((size_t)ld * 4)), 65535);
+    const int64_t cap1 = std::min<int64_t>((int64_t)(kHTableBytes / ((size_t)ld * 4)), 65535);
+    const int64_t cap_all = std::min<int64_t>((int64_t)(kH2TableBytes / ((size_t)ld * 4)), 65535);
     const double floor_w = std::max(16.0, 4.0 * (double)nnz / (double)ng);
     std::vector<int32_t> order;
     for (int64_t g = 0; g < ng; ++g)
         if ((double)weight[g] >= floor_w) order.push_back((int32_t)g);
     std::stable_sort(order.begin(), order.end(),
                      [&](int32_t a, int32_t b) { return weight[a] > weight[b]; });
+    int64_t cap = cap1;
+    const int64_t want = std::min<int64_t>({(int64_t)order.size(), t_rows, cap_all});
+    if (want - cap1 >= kMinTier2Rows) cap = want;
     if ((int64_t)order.size() > cap) order.resize(cap);
     int64_t covered = 0;
     for (int32_t g : order) covered += weight[g];
     if (order.empty() || covered * 10 < nnz) return 0;
     for (size_t q = 0; q < order.size(); ++q) slot_of[order[q]] = (int32_t)q;
+    h1 = (int)std::min<int64_t>((int64_t)order.size(), cap1);
     return (int)order.size();
 }
 
 // Splits a CSR matrix into the entries of frequent gathered rows (per
 // output row: slot and value) and the rest (a CSR matrix for build_sell).
 struct FreqHost {
-    int h = 0;
+    int h = 0, h1 = 0;
     std::vector<int32_t> slot_of;
-    std::vector<int64_t> hptr;
+    std::vector<int64_t> hptr;     // tier 1 (slots < h1)
     hvec<uint16_t> hidx;
     hvec<float> hval;
     std::vector<int32_t> hwarp;
+    std::vector<int64_t> h2ptr;    // tier 2 (slots h1 .. h - 1)
+    hvec<uint16_t> h2idx;
+    hvec<float> h2val;
+    std::vector<int32_t> h2warp;
 };
 
 void split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
@@ -590,31 +606,44 @@ void split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const 
                     hvec<double>& lval)
 {
     F.hptr.assign(rows + 1, 0);
+    F.h2ptr.assign(rows + 1, 0);
     lptr.assign(rows + 1, 0);
+    const int h1 = F.h1;
     parallel_weighted(rows, ptr, [&](int64_t r0, int64_t r1) {
         for (int64_t r = r0; r < r1; ++r) {
-            int64_t nh = 0;
-            for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) nh += F.slot_of[ind[q]] >= 0;
-            F.hptr[r + 1] = nh;
-            lptr[r + 1] = ptr[r + 1] - ptr[r] - nh;
+            int64_t n1 = 0, n2 = 0;
+            for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) {
+                const int32_t sl = F.slot_of[ind[q]];
+                n1 += sl >= 0 && sl < h1;
+                n2 += sl >= h1;
+            }
+            F.hptr[r + 1] = n1;
+            F.h2ptr[r + 1] = n2;
+            lptr[r + 1] = ptr[r + 1] - ptr[r] - n1 - n2;
         }
     });
     for (int64_t r = 0; r < rows; ++r) {
         F.hptr[r + 1] += F.hptr[r];
+        F.h2ptr[r + 1] += F.h2ptr[r];
         lptr[r + 1] += lptr[r];
     }
     F.hidx.resize(F.hptr[rows]);
     F.hval.resize(F.hptr[rows]);
+    F.h2idx.resize(F.h2ptr[rows]);
+    F.h2val.resize(F.h2ptr[rows]);
     lind.resize(lptr[rows]);
     lval.resize(lptr[rows]);
     parallel_weighted(rows, ptr, [&](int64_t r0, int64_t r1) {
         for (int64_t r = r0; r < r1; ++r) {
-            int64_t a = F.hptr[r], b = lptr[r];
+            int64_t a = F.hptr[r], a2 = F.h2ptr[r], b = lptr[r];
             for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) {
                 const int32_t sl = F.slot_of[ind[q]];
-                if (sl >= 0) {
+                if (sl >= 0 && sl < h1) {
                     F.hidx[a] = (uint16_t)sl;
                     F.hval[a++] = (float)vals[q];
+                } else if (sl >= h1) {
+                    F.h2idx[a2] = (uint16_t)sl;
+                    F.h2val[a2++] = (float)vals[q];
                 } else {
                     lind[b] = ind[q];
                     lval[b++] = vals[q];
@@ -626,26 +655,34 @@ void split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const 
 
 // Chunks of output rows for the warps of spmm_freq: contiguous ranges of
 // about equal cost (entries, plus a fixed cost per row that has any).
-void balance_frequent(int64_t rows, int nwarps, FreqHost& F)
+void balance_rows(int64_t rows, int nwarps, const std::vector<int64_t>& ptr,
+                  std::vector<int32_t>& chunks)
 {
     std::vector<int64_t> cost(rows + 1, 0);
     for (int64_t r = 0; r < rows; ++r) {
-        const int64_t e = F.hptr[r + 1] - F.hptr[r];
+        const int64_t e = ptr[r + 1] - ptr[r];
         cost[r + 1] = cost[r] + (e > 0 ? e + 8 : 0);
     }
-    F.hwarp.assign(nwarps + 1, 0);
+    chunks.assign(nwarps + 1, 0);
     int64_t r = 0;
     for (int w = 1; w < nwarps; ++w) {
         const double target = (double)cost[rows] * w / nwarps;
         while (r < rows && (double)cost[r] < target) ++r;
-        F.hwarp[w] = (int32_t)r;
+        chunks[w] = (int32_t)r;
     }
-    F.hwarp[nwarps] = (int32_t)rows;
+    chunks[nwarps] = (int32_t)rows;
+}
+
+void balance_frequent(int64_t rows, int nwarps, FreqHost& F)
+{
+    balance_rows(rows, nwarps, F.hptr, F.hwarp);
+    if (F.h > F.h1) balance_rows(rows, nwarps, F.h2ptr, F.h2warp);
 }
 
 espnmf_status upload_frequent(espnmf_ctx* ctx, const FreqHost& H, SellDev& D)
 {
     D.h = H.h;
+    D.h1 = H.h1;
     D.hnnz = (int64_t)H.hidx.size();
     D.hwarps = (int)H.hwarp.size() - 1;
     TRY(dupload(ctx, &D.slot_of, H.slot_of.data(), H.slot_of.size() * 4));
@@ -654,6 +691,15 @@ espnmf_status upload_frequent(espnmf_ctx* ctx, const FreqHost& H, SellDev& D)
     TRY(dupload(ctx, &D.hval, H.hval.data(), H.hval.size() * 4));
     TRY(dupload(ctx, &D.hwarp, H.hwarp.data(), H.hwarp.size() * 4));
     TRY(dmalloc(ctx, &D.hcounter, sizeof(int)));
+    if (H.h > H.h1) {
+        D.h2nnz = (int64_t)H.h2idx.size();
+        D.h2warps = (int)H.h2warp.size() - 1;
+        TRY(dupload(ctx, &D.h2ptr, H.h2ptr.data(), H.h2ptr.size() * 8));
+        TRY(dupload(ctx, &D.h2idx, H.h2idx.data(), H.h2idx.size() * 2));
+        TRY(dupload(ctx, &D.h2val, H.h2val.data(), H.h2val.size() * 4));
+        TRY(dupload(ctx, &D.h2warp, H.h2warp.data(), H.h2warp.size() * 4));
+        TRY(dmalloc(ctx, &D.h2counter, sizeof(int)));
+    }
     CU(cudaStreamSynchronize(ctx->st));
     return ESPNMF_OK;
 }
@@ -708,13 +754,22 @@ espnmf_status do_spmm(espnmf_ctx* ctx, bool transA, const EllDev& F)
                                : launch_spmm_combine<float>(S, (int)ctx->ldy, (float*)ctx->Y, ctx->ldy, ctx->st);
         }));
     }
-    if (S.h > 0 && S.hnnz > 0) {
+    if (S.h1 > 0 && S.hnnz > 0) {
         // entries (slot + value), row pointers, Y read and written back
         const double hb = (double)S.hnnz * 6.0 + (double)(S.rows + 1) * 8.0 +
                           2.0 * (double)S.rows * ctx->ldy * 4.0;
         TRY(run(ctx, transA ? K_SPMM_H_T : K_SPMM_H, hb, ctx->st, [&] {
             return launch_spmm_h(S, F, (float*)ctx->Y, ctx->sm_count, ctx->status_d,
-                                 ctx->wait_limit, ctx->st);
+                                 ctx->wait_limit, ctx->st, 1);
+        }));
+    }
+    if (S.h > S.h1 && S.h2nnz > 0) {
+        // the second tier: its entries, row pointers, Y read and written back
+        const double hb = (double)S.h2nnz * 6.0 + (double)(S.rows + 1) * 8.0 +
+                          2.0 * (double)S.rows * ctx->ldy * 4.0;
+        TRY(run(ctx, transA ? K_SPMM_H2_T : K_SPMM_H2, hb, ctx->st, [&] {
+            return launch_spmm_h(S, F, (float*)ctx->Y, ctx->sm_count, ctx->status_d,
+                                 ctx->wait_limit, ctx->st, 2);
         }));
     }
     return ESPNMF_OK;
@@ -1506,14 +1561,17 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                 FreqHost F;
                 SellHost<float> h;
             };
+            const bool col_mode = mode == ESPNMF_TOPT_COLUMN;
             // optr: the other orientation's row pointers, whose row lengths
             // are the entries that reference each gathered row
+            // t_rows: the gathered factor's t per column (column mode), the
+            // most rows that can be nonzero in all of its columns
             auto build_f32 = [&](int64_t rows, const int64_t* ptr, const int32_t* ind,
                                  const double* vals, int64_t ngather, const int64_t* optr,
-                                 Built& B) {
+                                 int64_t t_rows, Built& B) {
                 std::vector<int64_t> w(ngather);
                 for (int64_t g = 0; g < ngather; ++g) w[g] = optr[g + 1] - optr[g];
-                B.F.h = choose_frequent(w, ptr[rows], ld, B.F.slot_of);
+                B.F.h = choose_frequent(w, ptr[rows], ld, t_rows, B.F.slot_of, B.F.h1);
                 if (B.F.h > 0) {
                     std::vector<int64_t> lp;
                     hvec<int32_t> li;
@@ -1533,10 +1591,10 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             Built ba, bat;
             std::thread th([&] {
                 t_share = 2;
-                build_f32(m, cp.data(), ri.data(), cv.data(), n, rp, bat);
+                build_f32(m, cp.data(), ri.data(), cv.data(), n, rp, col_mode ? t_u : 0, bat);
             });
             t_share = 2;
-            build_f32(n, rp, ci, vv.data(), m, cp.data(), ba);
+            build_f32(n, rp, ci, vv.data(), m, cp.data(), col_mode ? t_v : 0, ba);
             t_share = 1;
             th.join();
             phase("layouts built");
@@ -1611,8 +1669,9 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                 TRY(dmalloc(ctx, &nzmask, 4 * words));
                 CU(cudaMemsetAsync(nzmask, 0, 4 * words, ctx->st));
                 if (Gp.h > 0) {
-                    TRY(dmalloc(ctx, &htab, (size_t)Gp.h * ld * 4));
-                    CU(cudaMemsetAsync(htab, 0, (size_t)Gp.h * ld * 4, ctx->st));
+                    // the h table rows and a zero row (read by the second tier)
+                    TRY(dmalloc(ctx, &htab, ((size_t)Gp.h + 1) * ld * 4));
+                    CU(cudaMemsetAsync(htab, 0, ((size_t)Gp.h + 1) * ld * 4, ctx->st));
                     TRY(dmalloc(ctx, &hnz, (size_t)Gp.h));
                     CU(cudaMemsetAsync(hnz, 0, (size_t)Gp.h, ctx->st));
                 }
@@ -2217,7 +2276,7 @@ espnmf_status espnmf_spmm_frequent(espnmf_ctx* ctx, int32_t product, int32_t* h,
         return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "product must be 0 or 1, outputs non-NULL");
     const SellDev& S = product == 0 ? ctx->sA : ctx->sAt;
     *h = S.h;
-    *hnnz = S.hnnz;
+    *hnnz = S.hnnz + S.h2nnz;
     return ESPNMF_OK;
 }
 
@@ -2272,9 +2331,12 @@ espnmf_status espnmf_launches_per_sweep(espnmf_ctx* ctx, int32_t* count)
     // U update: A V (+ combine, + frequent part), solve, select, emit,
     // (+ U's table Gram), reduce; the V update likewise with A^T U
     const bool sv = survivor_path(ctx);
-    int per_half_A = 5 + (ctx->sA.nsplit > 0 ? 1 : 0) + (ctx->sA.h > 0 && ctx->sA.hnnz > 0 ? 1 : 0) +
+    auto freq_launches = [](const SellDev& S) {
+        return (S.h1 > 0 && S.hnnz > 0 ? 1 : 0) + (S.h > S.h1 && S.h2nnz > 0 ? 1 : 0);
+    };
+    int per_half_A = 5 + (ctx->sA.nsplit > 0 ? 1 : 0) + freq_launches(ctx->sA) +
                      (sv && ctx->sAt.h > 0 ? 1 : 0);
-    int per_half_At = 5 + (ctx->sAt.nsplit > 0 ? 1 : 0) + (ctx->sAt.h > 0 && ctx->sAt.hnnz > 0 ? 1 : 0) +
+    int per_half_At = 5 + (ctx->sAt.nsplit > 0 ? 1 : 0) + freq_launches(ctx->sAt) +
                       (sv && ctx->sA.h > 0 ? 1 : 0);
     *count = per_half_A + per_half_At + 2;   // + the two Gram inverse launches
     return ESPNMF_OK;

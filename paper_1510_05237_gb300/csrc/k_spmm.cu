@@ -511,7 +511,11 @@ __device__ __forceinline__ bool mbar_wait_phase0(uint32_t mbar, long long limit)
     return false;
 }
 
-template <int KP>
+// GLOBAL = false: the first tier, the table staged in shared memory (p.h
+// rows and a zero row after them); GLOBAL = true: the second tier, table
+// rows read from the factor's table in global memory (p.htab, p.h rows and
+// its zero row h), which stays in the L2.
+template <int KP, bool GLOBAL>
 __global__ void __launch_bounds__(kHThreads, 1)
 spmm_freq_f32_kernel(FreqParams p)
 {
@@ -529,6 +533,7 @@ spmm_freq_f32_kernel(FreqParams p)
 
     // stage the dense table: TMA bulk copies (32 KB each) completing on one
     // mbarrier; the zero row after it by plain stores meanwhile
+    if constexpr (!GLOBAL) {
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(1u) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -554,12 +559,14 @@ spmm_freq_f32_kernel(FreqParams p)
         mbar_wait_phase0(bar, p.wait_limit);
         return;
     }
+    }
 
     const int lane = tid & 31;
     const int grp = lane / LPG, ql = lane % LPG;
     const bool colact = ql < Q;
     const uint32_t zero_off = (uint32_t)p.h * ROW;
-    const uint32_t lane_base = smem_addr(tab) + 16u * (uint32_t)ql;
+    const uint32_t lane_base = GLOBAL ? 0u : smem_addr(tab) + 16u * (uint32_t)ql;
+    const unsigned char* gbase = reinterpret_cast<const unsigned char*>(p.htab) + 16u * (uint32_t)ql;
     // A chunk of up to 32 of a row's entries is staged per warp as (byte
     // offset of the table row, value); the chunk is padded to a multiple of
     // four with entries on the zero row.  Group g takes the entry pairs
@@ -620,10 +627,17 @@ spmm_freq_f32_kernel(FreqParams p)
                     const int4 ee = *reinterpret_cast<const int4*>(stage + j);   // entries j, j + 1
                     if (colact) {
                         unsigned long long v0x, v0y, v1x, v1y;
-                        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
-                                     : "=l"(v0x), "=l"(v0y) : "r"(lane_base + (uint32_t)ee.x));
-                        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
-                                     : "=l"(v1x), "=l"(v1y) : "r"(lane_base + (uint32_t)ee.z));
+                        if constexpr (GLOBAL) {
+                            asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2];"
+                                         : "=l"(v0x), "=l"(v0y) : "l"(gbase + (uint32_t)ee.x));
+                            asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2];"
+                                         : "=l"(v1x), "=l"(v1y) : "l"(gbase + (uint32_t)ee.z));
+                        } else {
+                            asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
+                                         : "=l"(v0x), "=l"(v0y) : "r"(lane_base + (uint32_t)ee.x));
+                            asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
+                                         : "=l"(v1x), "=l"(v1y) : "r"(lane_base + (uint32_t)ee.z));
+                        }
                         const unsigned long long a0 = pack2(__int_as_float(ee.y));
                         const unsigned long long a1 = pack2(__int_as_float(ee.w));
                         fma2(a0xy, a0, v0x);
@@ -895,36 +909,41 @@ cudaError_t launch_spmm_combine(const SellDev& S, int KP, T* Y, int64_t ldy,
 }
 
 template <int KP>
-static cudaError_t launch_freq(const FreqParams& p, int grid, cudaStream_t st)
+static cudaError_t launch_freq(const FreqParams& p, int grid, bool global, cudaStream_t st)
 {
-    const size_t smem = (size_t)(p.h + 1) * KP * 4;   // the table and a zero row
-    spmm_freq_f32_kernel<KP><<<grid, kHThreads, smem, st>>>(p);
+    if (global) {
+        spmm_freq_f32_kernel<KP, true><<<grid, kHThreads, 0, st>>>(p);
+    } else {
+        const size_t smem = (size_t)(p.h + 1) * KP * 4;   // the table and a zero row
+        spmm_freq_f32_kernel<KP, false><<<grid, kHThreads, smem, st>>>(p);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_spmm_h(const SellDev& S, const EllDev& F, float* Y, int sm_count,
-                          unsigned* status, long long wait_limit, cudaStream_t st)
+                          unsigned* status, long long wait_limit, cudaStream_t st, int tier)
 {
-    if (S.h <= 0 || S.hnnz == 0) return cudaSuccess;
+    const bool global = tier == 2;
+    if (global ? (S.h <= S.h1 || S.h2nnz == 0) : (S.h1 <= 0 || S.hnnz == 0)) return cudaSuccess;
     if (F.htab == nullptr || F.h != S.h) return cudaErrorInvalidValue;
     FreqParams p;
-    p.hptr = S.hptr;
-    p.hidx = S.hidx;
-    p.hval = static_cast<const float*>(S.hval);
-    p.hwarp = S.hwarp;
-    p.nchunks = S.hwarps;
-    p.counter = S.hcounter;
+    p.hptr = global ? S.h2ptr : S.hptr;
+    p.hidx = global ? S.h2idx : S.hidx;
+    p.hval = static_cast<const float*>(global ? S.h2val : S.hval);
+    p.hwarp = global ? S.h2warp : S.hwarp;
+    p.nchunks = global ? S.h2warps : S.hwarps;
+    p.counter = global ? S.h2counter : S.hcounter;
     p.htab = static_cast<const float*>(F.htab);
-    p.h = S.h;
+    p.h = global ? S.h : S.h1;
     p.Y = Y;
     p.status = status;
     p.wait_limit = wait_limit < (1ll << 20) ? wait_limit : (1ll << 20);
     const int grid = sm_count;
-    if ((size_t)S.h * F.ld * 4 > kHTableBytes) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(S.hcounter, 0, sizeof(int), st);
+    if (!global && (size_t)S.h1 * F.ld * 4 > kHTableBytes) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     switch (F.ld) {
-#define ESPNMF_KP(v) case v: return launch_freq<v>(p, grid, st);
+#define ESPNMF_KP(v) case v: return launch_freq<v>(p, grid, global, st);
         ESPNMF_KP(4) ESPNMF_KP(8) ESPNMF_KP(12) ESPNMF_KP(16) ESPNMF_KP(20) ESPNMF_KP(24)
         ESPNMF_KP(28) ESPNMF_KP(32) ESPNMF_KP(36) ESPNMF_KP(40) ESPNMF_KP(44) ESPNMF_KP(48)
         ESPNMF_KP(52) ESPNMF_KP(56) ESPNMF_KP(60) ESPNMF_KP(64) ESPNMF_KP(80) ESPNMF_KP(96)
@@ -967,7 +986,7 @@ static cudaError_t setup_sell_occupancy()
 template <int KP>
 static cudaError_t setup_f32()
 {
-    cudaError_t e = cudaFuncSetAttribute(spmm_freq_f32_kernel<KP>,
+    cudaError_t e = cudaFuncSetAttribute(spmm_freq_f32_kernel<KP, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kHTableBytes + kHTableBytes / 16));
     if constexpr (KP >= 16) {

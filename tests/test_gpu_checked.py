@@ -22,7 +22,7 @@ SCRIPT = r'''
 import json, sys
 import numpy as np, torch
 import paper_1510_05237_gb300 as E
-from gen import planted_50k_100k, small_zipf, uniform_init
+from gen import planted_50k_100k, small_zipf, uniform_init, zipf_corpus
 checked = E.library_path().endswith("_checked.so")
 dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
 out = {"checked": checked, "runs": {}}
@@ -52,6 +52,9 @@ run("zipf_fp64_column", A2, 10, 100, 100, E.TOPT_COLUMN, E.F64, 3, uniform_init(
 run("zipf_fp32_matrix", A2, 10, 700, 500, E.TOPT_MATRIX, E.F32, 3, uniform_init(A2.n, 10, 4))
 A3 = planted_50k_100k(seed=5, scale=0.05)
 run("planted_fp32_k72", A3, 72, 150, 200, E.TOPT_COLUMN, E.F32, 3, uniform_init(A3.n, 72, 5))
+A4 = zipf_corpus(60000, 40000, 60.0, 1.05, 7, sigma=0.7)
+run("zipf_fp32_k100_two_tier_frequent", A4, 100, 1200, 400, E.TOPT_COLUMN, E.F32, 3,
+    uniform_init(A4.n, 100, 7))
 U, V = E.espnmf_sequential(dev(A2.rowptr), dev(A2.colidx), dev(A2.val.astype(np.float32)),
                            A2.n, A2.m, 4, 100, 80, 2, dev(uniform_init(A2.n, 2, 6).astype(np.float32)),
                            E.F32, k2=2)
