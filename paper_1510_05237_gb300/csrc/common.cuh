@@ -161,6 +161,25 @@ constexpr int kMaxK = 256;
 // entry p is at slice_ptr[s/32] + (p/4)*128 + 4*l + p%4 (slice lengths are
 // multiples of 4), so a lane reads four entries with one 16-byte load and a
 // warp 512 consecutive bytes.  Padding entries have idx = -1.
+// One tier of a product's frequent part.  Each output row with entries in
+// the tier holds them contiguously in ent[], padded with entries on the zero
+// table row (value +0) to a multiple of `pad` (4 or the kernel's step, a
+// divisor of 32); an entry is (byte offset of its table row, FP32 value
+// bits).  rows[j] = (output row, end of its entries in units of four), the
+// rows with entries in ascending order; chunk[c] .. chunk[c + 1] are the rows
+// of work chunk c (about equal cost), which the warps of spmm_freq take in
+// turn through `counter`.
+struct FreqTierDev {
+    int64_t nnz = 0;               // entries of A in the tier
+    int64_t nent = 0;              // entries stored (padding included)
+    uint2* ent = nullptr;          // [nent]
+    int2* rows = nullptr;          // [nrows]
+    int nrows = 0;
+    int32_t* chunk = nullptr;      // [nchunks + 1]
+    int nchunks = 0;
+    int* counter = nullptr;        // next chunk to take (reset before each launch)
+};
+
 struct SellDev {
     int64_t rows = 0;        // output rows
     int64_t nseg = 0;
@@ -181,33 +200,16 @@ struct SellDev {
     int64_t npart = 0;             // partial slots
     void* partials = nullptr;      // [npart * k] of T
     // Frequent part (FP32 form only; h = 0: none).  The h gathered rows that
-    // the most entries reference (the frequent terms of A^T U) are staged
-    // densely in shared memory by spmm_h; their entries are kept out of the
-    // SELL arrays above and stored per output row instead: entries
-    // [hptr[r], hptr[r+1]) of row r, hidx = slot of the gathered row in the
-    // dense table, hval = the value.  The output rows are cut into chunks
-    // [hwarp[c], hwarp[c+1]) of about equal cost, which the warps of spmm_h
-    // take in turn.  slot_of[g] is the slot of gathered row g or -1.
+    // the most entries reference (the frequent terms of A^T U) form a dense
+    // table; their entries are kept out of the SELL arrays above and stored
+    // per output row instead, in two tiers by the gathered row's slot:
+    // tier 0 (slots < h1) is read by spmm_freq from the table staged in
+    // shared memory, tier 1 (slots h1 .. h - 1) from the factor's table in
+    // global memory.  slot_of[g] is the slot of gathered row g or -1.
     int h = 0;                     // table rows in all (slots 0 .. h - 1)
     int h1 = 0;                    // of them staged in shared memory (slots < h1)
-    int64_t hnnz = 0;
-    int64_t* hptr = nullptr;       // [rows+1]
-    uint16_t* hidx = nullptr;      // [hnnz]
-    void* hval = nullptr;          // [hnnz] of T
-    int32_t* hwarp = nullptr;      // [hwarps+1] row ranges (work chunks)
-    int hwarps = 0;                // number of chunks
-    int* hcounter = nullptr;       // next chunk to take (reset before each launch)
     int32_t* slot_of = nullptr;    // [rows of the gathered factor]
-    // The second tier: the entries whose gathered row has a slot h1 .. h - 1,
-    // read from the factor's table in global memory (it stays in the L2),
-    // stored per output row like the first tier's.
-    int64_t h2nnz = 0;
-    int64_t* h2ptr = nullptr;      // [rows+1]
-    uint16_t* h2idx = nullptr;     // [h2nnz] absolute slots
-    void* h2val = nullptr;         // [h2nnz]
-    int32_t* h2warp = nullptr;     // [h2warps+1]
-    int h2warps = 0;
-    int* h2counter = nullptr;
+    FreqTierDev ft[2];
 };
 
 // A factor (U: n x k, V: m x k) in row-packed sparse form: row i holds
@@ -286,9 +288,15 @@ cudaError_t launch_spmm_combine(const SellDev& S, int k, T* Y, int64_t ldy,
 // first S.h1 rows of F.htab staged in shared memory (TMA bulk copies;
 // `wait_limit` bounds the wait for them); tier 2: the rows h1 .. h - 1 read
 // from F.htab in global memory (L2).  Runs after launch_spmm (and the
-// combine), tier 1 before tier 2, one CTA per SM.
+// combine), tier 1 before tier 2, one CTA per SM.  Each warp streams its
+// chunk's entries through a ring of kFreqStages stages of 32 entries in
+// shared memory (cp.async).
 constexpr int kHThreads = 1024;
+constexpr int kFreqStages = 3;
 constexpr size_t kHTableBytes = 200 * 1024;    // largest dense table staged
+// entries per row of a tier are padded to a multiple of this (the entries a
+// warp of spmm_freq adds per step, at least four)
+int freq_pad(int ld);
 constexpr size_t kH2TableBytes = 16u << 20;    // largest table of both tiers
 constexpr int kMinTier2Rows = 256;             // a smaller second tier is not built
 cudaError_t launch_spmm_h(const SellDev& S, const EllDev& F, float* Y, int sm_count,
@@ -428,11 +436,13 @@ template <typename T>
 cudaError_t launch_seq_append(int64_t rows, const int32_t* cnt, const int32_t* col, const T* val,
                               int ld, int k2, T* H, int ld1, int j0, cudaStream_t st);
 
-// out = sum of squares of val[0, count) and val2[0, count2) (val2 may be
-// NULL), in a fixed order.
+// out = sum of squares of val[0, count) and of the values of the entries
+// ent2[0, count2) and ent3[0, count3) of the frequent tiers (NULL: none), in
+// a fixed order.
 template <typename T>
-cudaError_t launch_norm2(const T* val, int64_t count, const T* val2, int64_t count2,
-                         double* part, int nparts, double* out, cudaStream_t st);
+cudaError_t launch_norm2(const T* val, int64_t count, const uint2* ent2, int64_t count2,
+                         const uint2* ent3, int64_t count3, double* part, int nparts,
+                         double* out, cudaStream_t st);
 
 // E for arbitrary U, V: cross term <U, Y> with Y = A V given.
 template <typename T>

@@ -586,29 +586,40 @@ int choose_frequent(const std::vector<int64_t>& weight, int64_t nnz, int ld, int
     return (int)order.size();
 }
 
-// Splits a CSR matrix into the entries of frequent gathered rows (per
-// output row: slot and value) and the rest (a CSR matrix for build_sell).
+// Splits a CSR matrix into the entries of frequent gathered rows, per tier
+// and output row as (byte offset of the gathered row in its table, value)
+// padded with entries on the zero row to a multiple of freq_pad(ld), and
+// the rest (a CSR matrix for build_sell).  False (nothing built) if a
+// tier's entries exceed what its 32-bit row ends can address.
+struct FreqTierHost {
+    std::vector<int64_t> ptr;      // [rows + 1] stored entries before each output row
+    hvec<uint2> ent;
+    std::vector<int2> rows;        // (output row, end / 4) of the rows with entries
+    std::vector<int32_t> chunk;
+    int64_t nnz = 0;
+};
 struct FreqHost {
     int h = 0, h1 = 0;
     std::vector<int32_t> slot_of;
-    std::vector<int64_t> hptr;     // tier 1 (slots < h1)
-    hvec<uint16_t> hidx;
-    hvec<float> hval;
-    std::vector<int32_t> hwarp;
-    std::vector<int64_t> h2ptr;    // tier 2 (slots h1 .. h - 1)
-    hvec<uint16_t> h2idx;
-    hvec<float> h2val;
-    std::vector<int32_t> h2warp;
+    FreqTierHost t[2];             // slots < h1 (staged); slots h1 .. h - 1
 };
 
-void split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
-                    FreqHost& F, std::vector<int64_t>& lptr, hvec<int32_t>& lind,
+bool split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
+                    int ld, FreqHost& F, std::vector<int64_t>& lptr, hvec<int32_t>& lind,
                     hvec<double>& lval)
 {
-    F.hptr.assign(rows + 1, 0);
-    F.h2ptr.assign(rows + 1, 0);
-    lptr.assign(rows + 1, 0);
+    const int64_t pad = freq_pad(ld);
+    const uint32_t row_bytes = (uint32_t)ld * 4u;
     const int h1 = F.h1;
+    // the zero row: after the staged rows (tier 1), the factor table's row h
+    // (tier 2)
+    const uint32_t zero_off[2] = {(uint32_t)h1 * row_bytes, (uint32_t)F.h * row_bytes};
+    std::vector<int64_t> cnt[2];
+    for (int u = 0; u < 2; ++u) {
+        F.t[u].ptr.assign(rows + 1, 0);
+        cnt[u].assign(rows, 0);
+    }
+    lptr.assign(rows + 1, 0);
     parallel_weighted(rows, ptr, [&](int64_t r0, int64_t r1) {
         for (int64_t r = r0; r < r1; ++r) {
             int64_t n1 = 0, n2 = 0;
@@ -617,89 +628,103 @@ void split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const 
                 n1 += sl >= 0 && sl < h1;
                 n2 += sl >= h1;
             }
-            F.hptr[r + 1] = n1;
-            F.h2ptr[r + 1] = n2;
+            cnt[0][r] = n1;
+            cnt[1][r] = n2;
+            F.t[0].ptr[r + 1] = (n1 + pad - 1) / pad * pad;
+            F.t[1].ptr[r + 1] = (n2 + pad - 1) / pad * pad;
             lptr[r + 1] = ptr[r + 1] - ptr[r] - n1 - n2;
         }
     });
     for (int64_t r = 0; r < rows; ++r) {
-        F.hptr[r + 1] += F.hptr[r];
-        F.h2ptr[r + 1] += F.h2ptr[r];
+        for (int u = 0; u < 2; ++u) {
+            F.t[u].ptr[r + 1] += F.t[u].ptr[r];
+            F.t[u].nnz += cnt[u][r];
+        }
         lptr[r + 1] += lptr[r];
     }
-    F.hidx.resize(F.hptr[rows]);
-    F.hval.resize(F.hptr[rows]);
-    F.h2idx.resize(F.h2ptr[rows]);
-    F.h2val.resize(F.h2ptr[rows]);
+    for (int u = 0; u < 2; ++u)
+        if (F.t[u].ptr[rows] / 4 > (int64_t)INT32_MAX) return false;
+    for (int u = 0; u < 2; ++u) F.t[u].ent.resize(F.t[u].ptr[rows]);
     lind.resize(lptr[rows]);
     lval.resize(lptr[rows]);
     parallel_weighted(rows, ptr, [&](int64_t r0, int64_t r1) {
         for (int64_t r = r0; r < r1; ++r) {
-            int64_t a = F.hptr[r], a2 = F.h2ptr[r], b = lptr[r];
+            int64_t at[2] = {F.t[0].ptr[r], F.t[1].ptr[r]};
+            int64_t b = lptr[r];
             for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) {
                 const int32_t sl = F.slot_of[ind[q]];
-                if (sl >= 0 && sl < h1) {
-                    F.hidx[a] = (uint16_t)sl;
-                    F.hval[a++] = (float)vals[q];
-                } else if (sl >= h1) {
-                    F.h2idx[a2] = (uint16_t)sl;
-                    F.h2val[a2++] = (float)vals[q];
+                const float v = (float)vals[q];
+                if (sl >= 0) {
+                    const int u = sl < h1 ? 0 : 1;
+                    uint32_t vb;
+                    std::memcpy(&vb, &v, 4);
+                    F.t[u].ent[at[u]++] = make_uint2((uint32_t)sl * row_bytes, vb);
                 } else {
                     lind[b] = ind[q];
                     lval[b++] = vals[q];
                 }
             }
+            for (int u = 0; u < 2; ++u)
+                for (; at[u] < F.t[u].ptr[r + 1]; ++at[u])
+                    F.t[u].ent[at[u]] = make_uint2(zero_off[u], 0u);
         }
     });
+    for (int u = 0; u < 2; ++u) {
+        FreqTierHost& T = F.t[u];
+        for (int64_t r = 0; r < rows; ++r)
+            if (T.ptr[r + 1] > T.ptr[r]) T.rows.push_back(make_int2((int)r, (int)(T.ptr[r + 1] / 4)));
+    }
+    return true;
 }
 
-// Chunks of output rows for the warps of spmm_freq: contiguous ranges of
-// about equal cost (entries, plus a fixed cost per row that has any).
-void balance_rows(int64_t rows, int nwarps, const std::vector<int64_t>& ptr,
-                  std::vector<int32_t>& chunks)
+// Chunks of a tier's rows for the warps of spmm_freq: contiguous ranges of
+// about equal cost (entries, plus a fixed cost per row).
+void balance_tier(int nchunks, FreqTierHost& T)
 {
-    std::vector<int64_t> cost(rows + 1, 0);
-    for (int64_t r = 0; r < rows; ++r) {
-        const int64_t e = ptr[r + 1] - ptr[r];
-        cost[r + 1] = cost[r] + (e > 0 ? e + 8 : 0);
+    const int64_t nr = (int64_t)T.rows.size();
+    std::vector<int64_t> cost(nr + 1, 0);
+    int64_t prev = 0;
+    for (int64_t j = 0; j < nr; ++j) {
+        const int64_t end = 4ll * T.rows[j].y;
+        cost[j + 1] = cost[j] + (end - prev) + 8;
+        prev = end;
     }
-    chunks.assign(nwarps + 1, 0);
-    int64_t r = 0;
-    for (int w = 1; w < nwarps; ++w) {
-        const double target = (double)cost[rows] * w / nwarps;
-        while (r < rows && (double)cost[r] < target) ++r;
-        chunks[w] = (int32_t)r;
+    T.chunk.assign(nchunks + 1, 0);
+    int64_t j = 0;
+    for (int c = 1; c < nchunks; ++c) {
+        const double target = (double)cost[nr] * c / nchunks;
+        while (j < nr && (double)cost[j] < target) ++j;
+        T.chunk[c] = (int32_t)j;
     }
-    chunks[nwarps] = (int32_t)rows;
+    T.chunk[nchunks] = (int32_t)nr;
 }
 
-void balance_frequent(int64_t rows, int nwarps, FreqHost& F)
+void balance_frequent(int nchunks, FreqHost& F)
 {
-    balance_rows(rows, nwarps, F.hptr, F.hwarp);
-    if (F.h > F.h1) balance_rows(rows, nwarps, F.h2ptr, F.h2warp);
+    balance_tier(nchunks, F.t[0]);
+    if (F.h > F.h1) balance_tier(nchunks, F.t[1]);
+}
+
+espnmf_status upload_tier(espnmf_ctx* ctx, const FreqTierHost& H, FreqTierDev& D)
+{
+    D.nnz = H.nnz;
+    D.nent = (int64_t)H.ent.size();
+    D.nrows = (int)H.rows.size();
+    D.nchunks = (int)H.chunk.size() - 1;
+    TRY(dupload(ctx, &D.ent, H.ent.data(), H.ent.size() * sizeof(uint2)));
+    TRY(dupload(ctx, &D.rows, H.rows.data(), H.rows.size() * sizeof(int2)));
+    TRY(dupload(ctx, &D.chunk, H.chunk.data(), H.chunk.size() * 4));
+    TRY(dmalloc(ctx, &D.counter, sizeof(int)));
+    return ESPNMF_OK;
 }
 
 espnmf_status upload_frequent(espnmf_ctx* ctx, const FreqHost& H, SellDev& D)
 {
     D.h = H.h;
     D.h1 = H.h1;
-    D.hnnz = (int64_t)H.hidx.size();
-    D.hwarps = (int)H.hwarp.size() - 1;
     TRY(dupload(ctx, &D.slot_of, H.slot_of.data(), H.slot_of.size() * 4));
-    TRY(dupload(ctx, &D.hptr, H.hptr.data(), H.hptr.size() * 8));
-    TRY(dupload(ctx, &D.hidx, H.hidx.data(), H.hidx.size() * 2));
-    TRY(dupload(ctx, &D.hval, H.hval.data(), H.hval.size() * 4));
-    TRY(dupload(ctx, &D.hwarp, H.hwarp.data(), H.hwarp.size() * 4));
-    TRY(dmalloc(ctx, &D.hcounter, sizeof(int)));
-    if (H.h > H.h1) {
-        D.h2nnz = (int64_t)H.h2idx.size();
-        D.h2warps = (int)H.h2warp.size() - 1;
-        TRY(dupload(ctx, &D.h2ptr, H.h2ptr.data(), H.h2ptr.size() * 8));
-        TRY(dupload(ctx, &D.h2idx, H.h2idx.data(), H.h2idx.size() * 2));
-        TRY(dupload(ctx, &D.h2val, H.h2val.data(), H.h2val.size() * 4));
-        TRY(dupload(ctx, &D.h2warp, H.h2warp.data(), H.h2warp.size() * 4));
-        TRY(dmalloc(ctx, &D.h2counter, sizeof(int)));
-    }
+    TRY(upload_tier(ctx, H.t[0], D.ft[0]));
+    if (H.h > H.h1) TRY(upload_tier(ctx, H.t[1], D.ft[1]));
     CU(cudaStreamSynchronize(ctx->st));
     return ESPNMF_OK;
 }
@@ -754,22 +779,18 @@ espnmf_status do_spmm(espnmf_ctx* ctx, bool transA, const EllDev& F)
                                : launch_spmm_combine<float>(S, (int)ctx->ldy, (float*)ctx->Y, ctx->ldy, ctx->st);
         }));
     }
-    if (S.h1 > 0 && S.hnnz > 0) {
-        // entries (slot + value), row pointers, Y read and written back
-        const double hb = (double)S.hnnz * 6.0 + (double)(S.rows + 1) * 8.0 +
-                          2.0 * (double)S.rows * ctx->ldy * 4.0;
-        TRY(run(ctx, transA ? K_SPMM_H_T : K_SPMM_H, hb, ctx->st, [&] {
+    for (int tier = 1; tier <= 2; ++tier) {
+        const FreqTierDev& T = S.ft[tier - 1];
+        if (S.h == 0 || T.nrows == 0 || (tier == 2 && S.h <= S.h1)) continue;
+        // entries (table row offset + value, padding included), row list,
+        // Y read and written back for the rows with entries
+        const double hb = (double)T.nent * 8.0 + (double)T.nrows * 8.0 +
+                          2.0 * (double)T.nrows * ctx->ldy * 4.0;
+        const KernelKind kind = tier == 1 ? (transA ? K_SPMM_H_T : K_SPMM_H)
+                                          : (transA ? K_SPMM_H2_T : K_SPMM_H2);
+        TRY(run(ctx, kind, hb, ctx->st, [&] {
             return launch_spmm_h(S, F, (float*)ctx->Y, ctx->sm_count, ctx->status_d,
-                                 ctx->wait_limit, ctx->st, 1);
-        }));
-    }
-    if (S.h > S.h1 && S.h2nnz > 0) {
-        // the second tier: its entries, row pointers, Y read and written back
-        const double hb = (double)S.h2nnz * 6.0 + (double)(S.rows + 1) * 8.0 +
-                          2.0 * (double)S.rows * ctx->ldy * 4.0;
-        TRY(run(ctx, transA ? K_SPMM_H2_T : K_SPMM_H2, hb, ctx->st, [&] {
-            return launch_spmm_h(S, F, (float*)ctx->Y, ctx->sm_count, ctx->status_d,
-                                 ctx->wait_limit, ctx->st, 2);
+                                 ctx->wait_limit, ctx->st, tier);
         }));
     }
     return ESPNMF_OK;
@@ -1572,12 +1593,13 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                 std::vector<int64_t> w(ngather);
                 for (int64_t g = 0; g < ngather; ++g) w[g] = optr[g + 1] - optr[g];
                 B.F.h = choose_frequent(w, ptr[rows], ld, t_rows, B.F.slot_of, B.F.h1);
+                std::vector<int64_t> lp;
+                hvec<int32_t> li;
+                hvec<double> lv;
+                if (B.F.h > 0 && !split_frequent(rows, ptr, ind, vals, ld, B.F, lp, li, lv))
+                    B.F = FreqHost{};
                 if (B.F.h > 0) {
-                    std::vector<int64_t> lp;
-                    hvec<int32_t> li;
-                    hvec<double> lv;
-                    split_frequent(rows, ptr, ind, vals, B.F, lp, li, lv);
-                    balance_frequent(rows, hwarps, B.F);
+                    balance_frequent(hwarps, B.F);
                     build_sell(rows, lp.data(), li.data(), lv.data(), B.h);
                 } else {
                     build_sell(rows, ptr, ind, vals, B.h);
@@ -1710,12 +1732,15 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         if (is_f64(ctx))
             TRY(run(ctx, K_NORM2, (double)ctx->sA.total * 8, ctx->st, [&] {
                 return launch_norm2<double>((const double*)ctx->sA.val, ctx->sA.total, nullptr, 0,
-                                            ctx->norm_part, ctx->sm_count, ctx->A2, ctx->st);
+                                            nullptr, 0, ctx->norm_part, ctx->sm_count, ctx->A2,
+                                            ctx->st);
             }));
         else
             TRY(run(ctx, K_NORM2, (double)ctx->sA.total * 4, ctx->st, [&] {
+                // the SELL part's values and both tiers of the frequent part
                 return launch_norm2<float>((const float*)ctx->sA.val, ctx->sA.total,
-                                           (const float*)ctx->sA.hval, ctx->sA.hnnz,
+                                           ctx->sA.ft[0].ent, ctx->sA.ft[0].nent,
+                                           ctx->sA.ft[1].ent, ctx->sA.ft[1].nent,
                                            ctx->norm_part, ctx->sm_count, ctx->A2, ctx->st);
             }));
 
@@ -2276,7 +2301,7 @@ espnmf_status espnmf_spmm_frequent(espnmf_ctx* ctx, int32_t product, int32_t* h,
         return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "product must be 0 or 1, outputs non-NULL");
     const SellDev& S = product == 0 ? ctx->sA : ctx->sAt;
     *h = S.h;
-    *hnnz = S.hnnz + S.h2nnz;
+    *hnnz = S.ft[0].nnz + S.ft[1].nnz;
     return ESPNMF_OK;
 }
 
@@ -2332,7 +2357,7 @@ espnmf_status espnmf_launches_per_sweep(espnmf_ctx* ctx, int32_t* count)
     // (+ U's table Gram), reduce; the V update likewise with A^T U
     const bool sv = survivor_path(ctx);
     auto freq_launches = [](const SellDev& S) {
-        return (S.h1 > 0 && S.hnnz > 0 ? 1 : 0) + (S.h > S.h1 && S.h2nnz > 0 ? 1 : 0);
+        return (S.h > 0 && S.ft[0].nrows > 0 ? 1 : 0) + (S.h > S.h1 && S.ft[1].nrows > 0 ? 1 : 0);
     };
     int per_half_A = 5 + (ctx->sA.nsplit > 0 ? 1 : 0) + freq_launches(ctx->sA) +
                      (sv && ctx->sAt.h > 0 ? 1 : 0);

@@ -1300,17 +1300,21 @@ cudaError_t launch_gram_inverse(const double* G, int k, double* Ginv64, T* GinvT
 
 template <typename T>
 __global__ void norm2_part_kernel(const T* __restrict__ v, int64_t count,
-                                  const T* __restrict__ v2, int64_t count2,
+                                  const uint2* __restrict__ v2, int64_t count2,
+                                  const uint2* __restrict__ v3, int64_t count3,
                                   double* part)
 {
     __shared__ double red[32];
-    const int64_t total = count + count2;
+    const int64_t total = count + count2 + count3;
     const int64_t chunk = (total + gridDim.x - 1) / gridDim.x;
     const int64_t b0 = (int64_t)blockIdx.x * chunk;
     const int64_t b1 = b0 + chunk < total ? b0 + chunk : total;
     double s = 0.0;
     for (int64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
-        const double x = e < count ? (double)v[e] : (double)v2[e - count];
+        double x;
+        if (e < count) x = (double)v[e];
+        else if (e < count + count2) x = (double)__uint_as_float(v2[e - count].y);
+        else x = (double)__uint_as_float(v3[e - count - count2].y);
         s += x * x;
     }
     s = warp_sum(s);
@@ -1333,11 +1337,13 @@ __global__ void sum_parts_kernel(const double* part, int n, double* out)
 }
 
 template <typename T>
-cudaError_t launch_norm2(const T* val, int64_t count, const T* val2, int64_t count2,
-                         double* part, int nparts, double* out, cudaStream_t st)
+cudaError_t launch_norm2(const T* val, int64_t count, const uint2* ent2, int64_t count2,
+                         const uint2* ent3, int64_t count3, double* part, int nparts,
+                         double* out, cudaStream_t st)
 {
-    if (val2 == nullptr) count2 = 0;
-    norm2_part_kernel<T><<<nparts, 256, 0, st>>>(val, count, val2, count2, part);
+    if (ent2 == nullptr) count2 = 0;
+    if (ent3 == nullptr) count3 = 0;
+    norm2_part_kernel<T><<<nparts, 256, 0, st>>>(val, count, ent2, count2, ent3, count3, part);
     sum_parts_kernel<<<1, 32, 0, st>>>(part, nparts, out);
     return cudaGetLastError();
 }
@@ -1521,8 +1527,8 @@ cudaError_t setup_factor()
                                         int64_t, double*, double*, int, cudaStream_t);          \
     template cudaError_t launch_gram_inverse<T>(const double*, int, double*, T*, unsigned*,         \
                                             cudaStream_t);                                      \
-    template cudaError_t launch_norm2<T>(const T*, int64_t, const T*, int64_t, double*, int,      \
-                                         double*, cudaStream_t);                                 \
+    template cudaError_t launch_norm2<T>(const T*, int64_t, const uint2*, int64_t, const uint2*, \
+                                         int64_t, double*, int, double*, cudaStream_t);         \
     template cudaError_t launch_ell_dot<T>(int64_t, int, EllDev, const T*, int64_t, double*,    \
                                            int, double*, cudaStream_t);                         \
     template cudaError_t launch_ell_to_colmajor<T>(int64_t, int, EllDev, T*, int64_t,          \

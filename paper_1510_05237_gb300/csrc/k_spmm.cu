@@ -25,11 +25,14 @@
 // a dense row of scattered loads.  These h rows are chosen once, when the
 // context is built (the gathered rows that the most entries of A reference,
 // as many as fit a 200 KB table); their entries are stored apart from the
-// SELL arrays, per output row.  One persistent CTA per SM stages the dense
-// copies of the h rows in shared memory with a TMA bulk copy; each warp walks
-// its output rows, a group of lanes per entry reading the entry's table row
-// with 128-bit shared loads (lanes over columns, conflict-free), and adds
-// its sum into the row of Y that the SELL part wrote.
+// SELL arrays, per output row, as (table row offset, value) with each row
+// padded to a multiple of the warp's step.  One persistent CTA per SM stages
+// the dense copies of the h rows in shared memory with a TMA bulk copy; each
+// warp streams a chunk of rows' entries through a ring in shared memory
+// (cp.async, two stages ahead), a group of lanes per entry reading the
+// entry's table row with 128-bit shared loads (lanes over columns,
+// conflict-free), and adds each row's sum into the row of Y that the SELL
+// part wrote.
 //
 // All sums are taken in a fixed order (storage order per lane, a fixed tree
 // across lanes, chunk order for very long rows, a fixed entry order per
@@ -448,25 +451,38 @@ spmm_sell1_f32_kernel(SpmmParams<float> p)
 // ---------------------------------------------------------------------------
 // Frequent part (FP32).
 
-// A group of LPG lanes (a power of two, >= KP / 4) handles one entry: lane
-// ql of the group holds the float4 of columns [4 ql, 4 ql + 4).  A warp step
-// processes G = 32 / LPG entries.
+// A group of LPG lanes (a power of two, >= KP / 4, at least two) handles
+// one entry: lane ql of the group holds the float4 of columns [4 ql, 4 ql +
+// 4).  A warp step adds STEP = 2 G entries, two per group (G = 32 / LPG).
+constexpr int freq_lanes(int kp)
+{
+    return kp / 4 <= 2 ? 2 : kp / 4 <= 4 ? 4 : kp / 4 <= 8 ? 8 : kp / 4 <= 16 ? 16 : 32;
+}
 template <int KP>
 struct FreqShape {
     static constexpr int Q = KP / 4;
-    static constexpr int LPG = Q <= 1 ? 1 : Q <= 2 ? 2 : Q <= 4 ? 4 : Q <= 8 ? 8 : Q <= 16 ? 16 : 32;
+    static constexpr int LPG = freq_lanes(KP);
     static constexpr int G = 32 / LPG;
+    static constexpr int STEP = 2 * G;
 };
 
+int freq_pad(int ld)
+{
+    const int step = 2 * (32 / freq_lanes(ld));
+    return step > 4 ? step : 4;
+}
+
+// the ring of entry stages of all warps of a CTA (32 entries of 8 bytes each)
+constexpr uint32_t kFreqRingBytes = (uint32_t)(kHThreads / 32) * kFreqStages * 256u;
+
 struct FreqParams {
-    const int64_t* hptr;
-    const uint16_t* hidx;
-    const float* hval;
-    const int32_t* hwarp;
+    const uint2* ent;      // (table row byte offset, value bits), rows padded
+    const int2* rows;      // (output row, end of its entries / 4)
+    const int32_t* chunk;  // [nchunks + 1] ranges of rows
     int nchunks;
     int* counter;
-    const float* htab;     // [h][KP] (a zero row of the factor is zeros)
-    int h;
+    const float* htab;     // the factor's table [h_all + 1][KP] (row h_all zero)
+    int h;                 // tier 1: rows staged (a zero row after them); tier 2: h_all
     float* Y;              // rows x KP: holds the SELL part, receives the sum
     unsigned* status;
     long long wait_limit;
@@ -515,25 +531,39 @@ __device__ __forceinline__ bool mbar_wait_phase0(uint32_t mbar, long long limit)
 // rows and a zero row after them); GLOBAL = true: the second tier, table
 // rows read from the factor's table in global memory (p.htab, p.h rows and
 // its zero row h), which stays in the L2.
+//
+// A warp takes a chunk of rows and streams the chunk's entries (one
+// contiguous run) through its ring of kFreqStages stages of 32 entries,
+// filled by cp.async two stages ahead of the one being added.  Step by
+// step, group g adds the entry pair (STEP i + 2 g, STEP i + 2 g + 1) of the
+// row with packed two-lane FMAs (each lane rounds as fmaf does) into two
+// accumulators; a zero table row adds +0.  Rows are padded to a multiple of
+// the step, so a row ends at a step boundary: there the groups' sums are
+// combined in a fixed tree and group 0 adds them to the row of Y.  Every
+// row is summed by one warp in a fixed order, whichever warp takes it.
 template <int KP, bool GLOBAL>
 __global__ void __launch_bounds__(kHThreads, 1)
 spmm_freq_f32_kernel(FreqParams p)
 {
     using S = FreqShape<KP>;
-    constexpr int Q = S::Q, LPG = S::LPG, G = S::G;
+    constexpr int Q = S::Q, LPG = S::LPG, STEP = S::STEP;
+    constexpr int NST = kFreqStages;
     constexpr unsigned FULL = 0xffffffffu;
     constexpr uint32_t ROW = KP * 4;   // bytes per table row
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
-    __shared__ __align__(16) int2 wstage[kHThreads];
-    float* tab = reinterpret_cast<float*>(smem_raw);   // [h + 1][KP], row h zero
     const int tid = threadIdx.x;
-    const uint32_t bar = smem_addr(&mbar);
-    const uint32_t bytes = (uint32_t)p.h * ROW;   // a multiple of 16
+    const int lane = tid & 31, warp = tid >> 5;
+    // the table and its zero row (tier 1), then the warps' rings
+    const uint32_t tab_bytes = GLOBAL ? 0u : ((uint32_t)p.h + 1u) * ROW;
+    const uint32_t ring = smem_addr(smem_raw) + tab_bytes + (uint32_t)warp * (NST * 256u);
 
     // stage the dense table: TMA bulk copies (32 KB each) completing on one
     // mbarrier; the zero row after it by plain stores meanwhile
     if constexpr (!GLOBAL) {
+    float* tab = reinterpret_cast<float*>(smem_raw);   // [h + 1][KP], row h zero
+    const uint32_t bar = smem_addr(&mbar);
+    const uint32_t bytes = (uint32_t)p.h * ROW;   // a multiple of 16
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(1u) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -561,106 +591,113 @@ spmm_freq_f32_kernel(FreqParams p)
     }
     }
 
-    const int lane = tid & 31;
     const int grp = lane / LPG, ql = lane % LPG;
     const bool colact = ql < Q;
+    const bool writer = grp == 0 && colact;
     const uint32_t zero_off = (uint32_t)p.h * ROW;
-    const uint32_t lane_base = GLOBAL ? 0u : smem_addr(tab) + 16u * (uint32_t)ql;
+    const uint32_t lane_base = GLOBAL ? 0u : smem_addr(smem_raw) + 16u * (uint32_t)ql;
     const unsigned char* gbase = reinterpret_cast<const unsigned char*>(p.htab) + 16u * (uint32_t)ql;
-    // A chunk of up to 32 of a row's entries is staged per warp as (byte
-    // offset of the table row, value); the chunk is padded to a multiple of
-    // four with entries on the zero row.  Group g takes the entry pairs
-    // (2j, 2j + 1) for j = g, g + G, ... (one 128-bit shared load per pair)
-    // and adds them with packed two-lane FMAs (each lane rounds as fmaf
-    // does) into two accumulators.  A zero table row adds +0.
-    int2* stage = wstage + (tid >> 5) * 32;
-    // The warps take chunks of rows in turn (a CTA that starts late, e.g.
-    // on an SM shared with another kernel, does not hold the others up);
-    // every row is summed by one warp in a fixed order, so the result does
-    // not depend on which warp takes it.
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // The warps take chunks in turn (a CTA that starts late, e.g. on an SM
+    // shared with another kernel, does not hold the others up).
     for (;;) {
         int ch = 0;
         if (lane == 0) ch = atomicAdd(p.counter, 1);
         ch = __shfl_sync(FULL, ch, 0);
         if (ch >= p.nchunks) break;
-        const int r0 = p.hwarp[ch], r1 = p.hwarp[ch + 1];
-        if (r0 >= r1) continue;
-        // this chunk's entries are one contiguous run: ask the L2 for it
-        if (lane == 0) {
-            const int64_t e0 = p.hptr[r0], e1 = p.hptr[r1];
-            if (e1 > e0) {
-                const uintptr_t ia = reinterpret_cast<uintptr_t>(p.hidx + e0) & ~(uintptr_t)15;
-                const uintptr_t ib = (reinterpret_cast<uintptr_t>(p.hidx + e1) + 15) & ~(uintptr_t)15;
-                const uintptr_t va = reinterpret_cast<uintptr_t>(p.hval + e0) & ~(uintptr_t)15;
-                const uintptr_t vb = (reinterpret_cast<uintptr_t>(p.hval + e1) + 15) & ~(uintptr_t)15;
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
-                             :: "l"(ia), "r"((unsigned)(ib - ia)) : "memory");
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
-                             :: "l"(va), "r"((unsigned)(vb - va)) : "memory");
+        const int k0 = p.chunk[ch], k1 = p.chunk[ch + 1];
+        if (k0 >= k1) continue;
+        const int qa = k0 > 0 ? p.rows[k0 - 1].y : 0;   // the chunk's entries: 4 qa ..
+        const int ne = 4 * (p.rows[k1 - 1].y - qa);     // .. 4 qa + ne
+        const uint2* src = p.ent + 4ll * qa;
+        if (lane == 0 && ne > 0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                         :: "l"(src), "r"((unsigned)ne * 8u) : "memory");
+        // stage s holds the chunk's entries [32 s, 32 s + 32) in slot s % NST;
+        // lanes 0..15 copy 16 bytes each.  Every lane commits a group per
+        // stage (empty beyond the chunk), so waiting for all but the last
+        // NST - 1 groups means stage s has landed.
+        auto issue = [&](int st) {
+            const int e = 32 * st + 2 * lane;
+            if (lane < 16 && e < ne) {
+                const uint32_t dst = ring + (uint32_t)(st % NST) * 256u + 16u * (uint32_t)lane;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                             :: "r"(dst), "l"(src + e) : "memory");
             }
-        }
-        int64_t q0 = p.hptr[r0];
-        for (int r = r0; r < r1; ++r) {
-            const int64_t q1 = p.hptr[r + 1];
-            if (q1 == q0) continue;
-            // the row's SELL part, loaded early
-            float4* yr = reinterpret_cast<float4*>(p.Y + (int64_t)r * KP) + ql;
-            float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (grp == 0 && colact) yv = *yr;
-            unsigned long long a0xy = 0ull, a0zw = 0ull, a1xy = 0ull, a1zw = 0ull;
-            for (int64_t qb = q0; qb < q1; qb += 32) {
-                const int64_t e = qb + lane;
-                uint32_t off = zero_off;
-                float a = 0.f;
-                if (e < q1) {
-                    const unsigned sl = p.hidx[e];
-                    if (ESPNMF_CHECK(sl < (unsigned)p.h, CHK_SLOT)) {
-                        off = sl * ROW;
-                        a = p.hval[e];
-                    }
-                }
-                stage[lane] = make_int2((int)off, __float_as_int(a));
-                __syncwarp();
-                const int n = q1 - qb < 32 ? (int)(q1 - qb) : 32;
-                const int n4 = (n + 3) & ~3;
-                for (int j = 2 * grp; j < n4; j += 2 * G) {
-                    const int4 ee = *reinterpret_cast<const int4*>(stage + j);   // entries j, j + 1
-                    if (colact) {
-                        unsigned long long v0x, v0y, v1x, v1y;
-                        if constexpr (GLOBAL) {
-                            asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2];"
-                                         : "=l"(v0x), "=l"(v0y) : "l"(gbase + (uint32_t)ee.x));
-                            asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2];"
-                                         : "=l"(v1x), "=l"(v1y) : "l"(gbase + (uint32_t)ee.z));
-                        } else {
-                            asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
-                                         : "=l"(v0x), "=l"(v0y) : "r"(lane_base + (uint32_t)ee.x));
-                            asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
-                                         : "=l"(v1x), "=l"(v1y) : "r"(lane_base + (uint32_t)ee.z));
-                        }
-                        const unsigned long long a0 = pack2(__int_as_float(ee.y));
-                        const unsigned long long a1 = pack2(__int_as_float(ee.w));
-                        fma2(a0xy, a0, v0x);
-                        fma2(a0zw, a0, v0y);
-                        fma2(a1xy, a1, v1x);
-                        fma2(a1zw, a1, v1y);
-                    }
-                }
-                __syncwarp();
-            }
-            const float4 acc0 = unpack4(a0xy, a0zw), acc1 = unpack4(a1xy, a1zw);
-            float4 acc = make_float4(acc0.x + acc1.x, acc0.y + acc1.y, acc0.z + acc1.z, acc0.w + acc1.w);
-            // the groups' sums in a fixed tree; group 0 adds to the SELL part
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        __syncwarp();   // the previous chunk's reads of the ring are done
 #pragma unroll
-            for (int off = LPG; off < 32; off <<= 1) {
-                acc.x += __shfl_xor_sync(FULL, acc.x, off);
-                acc.y += __shfl_xor_sync(FULL, acc.y, off);
-                acc.z += __shfl_xor_sync(FULL, acc.z, off);
-                acc.w += __shfl_xor_sync(FULL, acc.w, off);
+        for (int st = 0; st < NST - 1; ++st) issue(st);
+        int j = k0;                        // the row being summed
+        int2 cur = p.rows[k0];
+        int rend = 4 * (cur.y - qa);       // its end within the chunk
+        int2 nxt = j + 1 < k1 ? p.rows[j + 1] : cur;
+        float4* yr = reinterpret_cast<float4*>(p.Y + (int64_t)cur.x * KP) + ql;
+        float4 yv = writer ? *yr : zero4;
+        unsigned long long a0xy = 0ull, a0zw = 0ull, a1xy = 0ull, a1zw = 0ull;
+        for (int st = 0; 32 * st < ne; ++st) {
+            __syncwarp();   // stage st - 1 is read: its slot takes stage st + NST - 1
+            issue(st + NST - 1);
+            asm volatile("cp.async.wait_group %0;" :: "n"(NST - 1) : "memory");
+            __syncwarp();   // every lane's copies of stage st have landed
+            const uint32_t sb = ring + (uint32_t)(st % NST) * 256u + 16u * (uint32_t)grp;
+            const int e0 = 32 * st;
+            const int se = ne - e0 < 32 ? ne - e0 : 32;
+            for (int jj = 0; jj < se; jj += STEP) {
+                int4 ee;   // this group's entries jj + 2 grp, jj + 2 grp + 1
+                asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(ee.x), "=r"(ee.y), "=r"(ee.z), "=r"(ee.w)
+                             : "r"(sb + 8u * (uint32_t)jj));
+                if (!ESPNMF_CHECK((uint32_t)ee.x <= zero_off && (uint32_t)ee.z <= zero_off &&
+                                  (((uint32_t)ee.x | (uint32_t)ee.z) & 15u) == 0u, CHK_SLOT)) {
+                    ee = make_int4((int)zero_off, 0, (int)zero_off, 0);
+                }
+                if (colact) {
+                    unsigned long long v0x, v0y, v1x, v1y;
+                    if constexpr (GLOBAL) {
+                        asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2];"
+                                     : "=l"(v0x), "=l"(v0y) : "l"(gbase + (uint32_t)ee.x));
+                        asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2];"
+                                     : "=l"(v1x), "=l"(v1y) : "l"(gbase + (uint32_t)ee.z));
+                    } else {
+                        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
+                                     : "=l"(v0x), "=l"(v0y) : "r"(lane_base + (uint32_t)ee.x));
+                        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
+                                     : "=l"(v1x), "=l"(v1y) : "r"(lane_base + (uint32_t)ee.z));
+                    }
+                    const unsigned long long a0 = pack2(__int_as_float(ee.y));
+                    const unsigned long long a1 = pack2(__int_as_float(ee.w));
+                    fma2(a0xy, a0, v0x);
+                    fma2(a0zw, a0, v0y);
+                    fma2(a1xy, a1, v1x);
+                    fma2(a1zw, a1, v1y);
+                }
+                if (e0 + jj + STEP == rend) {
+                    // the row is complete: the groups' sums in a fixed tree,
+                    // group 0 adds them to the SELL part
+                    const float4 acc0 = unpack4(a0xy, a0zw), acc1 = unpack4(a1xy, a1zw);
+                    float4 acc = make_float4(acc0.x + acc1.x, acc0.y + acc1.y,
+                                             acc0.z + acc1.z, acc0.w + acc1.w);
+#pragma unroll
+                    for (int off = LPG; off < 32; off <<= 1) {
+                        acc.x += __shfl_xor_sync(FULL, acc.x, off);
+                        acc.y += __shfl_xor_sync(FULL, acc.y, off);
+                        acc.z += __shfl_xor_sync(FULL, acc.z, off);
+                        acc.w += __shfl_xor_sync(FULL, acc.w, off);
+                    }
+                    if (writer)
+                        *yr = make_float4(yv.x + acc.x, yv.y + acc.y, yv.z + acc.z, yv.w + acc.w);
+                    a0xy = a0zw = a1xy = a1zw = 0ull;
+                    if (++j < k1) {
+                        cur = nxt;
+                        rend = 4 * (cur.y - qa);
+                        yr = reinterpret_cast<float4*>(p.Y + (int64_t)cur.x * KP) + ql;
+                        yv = writer ? *yr : zero4;
+                        if (j + 1 < k1) nxt = p.rows[j + 1];
+                    }
+                }
             }
-            if (grp == 0 && colact)
-                *yr = make_float4(yv.x + acc.x, yv.y + acc.y, yv.z + acc.z, yv.w + acc.w);
-            q0 = q1;
         }
     }
 }
@@ -912,9 +949,10 @@ template <int KP>
 static cudaError_t launch_freq(const FreqParams& p, int grid, bool global, cudaStream_t st)
 {
     if (global) {
-        spmm_freq_f32_kernel<KP, true><<<grid, kHThreads, 0, st>>>(p);
+        spmm_freq_f32_kernel<KP, true><<<grid, kHThreads, kFreqRingBytes, st>>>(p);
     } else {
-        const size_t smem = (size_t)(p.h + 1) * KP * 4;   // the table and a zero row
+        // the table, a zero row and the rings
+        const size_t smem = (size_t)(p.h + 1) * KP * 4 + kFreqRingBytes;
         spmm_freq_f32_kernel<KP, false><<<grid, kHThreads, smem, st>>>(p);
     }
     return cudaGetLastError();
@@ -924,15 +962,15 @@ cudaError_t launch_spmm_h(const SellDev& S, const EllDev& F, float* Y, int sm_co
                           unsigned* status, long long wait_limit, cudaStream_t st, int tier)
 {
     const bool global = tier == 2;
-    if (global ? (S.h <= S.h1 || S.h2nnz == 0) : (S.h1 <= 0 || S.hnnz == 0)) return cudaSuccess;
+    const FreqTierDev& T = S.ft[global ? 1 : 0];
+    if (S.h <= 0 || T.nrows == 0 || (global && S.h <= S.h1)) return cudaSuccess;
     if (F.htab == nullptr || F.h != S.h) return cudaErrorInvalidValue;
     FreqParams p;
-    p.hptr = global ? S.h2ptr : S.hptr;
-    p.hidx = global ? S.h2idx : S.hidx;
-    p.hval = static_cast<const float*>(global ? S.h2val : S.hval);
-    p.hwarp = global ? S.h2warp : S.hwarp;
-    p.nchunks = global ? S.h2warps : S.hwarps;
-    p.counter = global ? S.h2counter : S.hcounter;
+    p.ent = T.ent;
+    p.rows = T.rows;
+    p.chunk = T.chunk;
+    p.nchunks = T.nchunks;
+    p.counter = T.counter;
     p.htab = static_cast<const float*>(F.htab);
     p.h = global ? S.h : S.h1;
     p.Y = Y;
@@ -986,9 +1024,10 @@ static cudaError_t setup_sell_occupancy()
 template <int KP>
 static cudaError_t setup_f32()
 {
+    // the largest table (kHTableBytes and a row), its zero row and the rings
     cudaError_t e = cudaFuncSetAttribute(spmm_freq_f32_kernel<KP, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kHTableBytes + kHTableBytes / 16));
+                                         (int)(kHTableBytes + 2 * KP * 4 + kFreqRingBytes));
     if constexpr (KP >= 16) {
         if (e == cudaSuccess) e = setup_sell_occupancy<KP, 2>();
         if (e == cudaSuccess) e = setup_sell_occupancy<KP, 4>();
