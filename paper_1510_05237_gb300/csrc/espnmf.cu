@@ -442,8 +442,8 @@ struct SellHost {
 // stored at slice_ptr[s] + (p / 4) * 128 + 4 l + p % 4 (SELL-32 with groups
 // of four), so each lane reads four entries with one 16-byte load and a
 // warp reads 512 consecutive bytes.
-template <typename T>
-void build_sell(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
+template <typename T, typename V>
+void build_sell(int64_t rows, const int64_t* ptr, const int32_t* ind, const V* vals,
                 SellHost<T>& S)
 {
     struct Grp {
@@ -589,8 +589,9 @@ int choose_frequent(const std::vector<int64_t>& weight, int64_t nnz, int ld, int
 // Splits a CSR matrix into the entries of frequent gathered rows, per tier
 // and output row as (byte offset of the gathered row in its table, value)
 // padded with entries on the zero row to a multiple of freq_pad(ld), and
-// the rest (a CSR matrix for build_sell).  False (nothing built) if a
-// tier's entries exceed what its 32-bit row ends can address.
+// the rest (a CSR matrix for build_sell, its values rounded to FP32 as the
+// layout stores them).  False (nothing built) if a tier's entries exceed
+// what its 32-bit row ends can address.
 struct FreqTierHost {
     std::vector<int64_t> ptr;      // [rows + 1] stored entries before each output row
     hvec<uint2> ent;
@@ -606,7 +607,7 @@ struct FreqHost {
 
 bool split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
                     int ld, FreqHost& F, std::vector<int64_t>& lptr, hvec<int32_t>& lind,
-                    hvec<double>& lval)
+                    hvec<float>& lval)
 {
     const int64_t pad = freq_pad(ld);
     const uint32_t row_bytes = (uint32_t)ld * 4u;
@@ -661,7 +662,7 @@ bool split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const 
                     F.t[u].ent[at[u]++] = make_uint2((uint32_t)sl * row_bytes, vb);
                 } else {
                     lind[b] = ind[q];
-                    lval[b++] = vals[q];
+                    lval[b++] = v;
                 }
             }
             for (int u = 0; u < 2; ++u)
@@ -1595,7 +1596,7 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
                 B.F.h = choose_frequent(w, ptr[rows], ld, t_rows, B.F.slot_of, B.F.h1);
                 std::vector<int64_t> lp;
                 hvec<int32_t> li;
-                hvec<double> lv;
+                hvec<float> lv;   // the rest's values, already rounded as the layout stores them
                 if (B.F.h > 0 && !split_frequent(rows, ptr, ind, vals, ld, B.F, lp, li, lv))
                     B.F = FreqHost{};
                 if (B.F.h > 0) {
