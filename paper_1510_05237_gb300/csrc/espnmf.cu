@@ -360,13 +360,14 @@ struct NoInitAlloc : std::allocator<T> {
 template <typename T>
 using hvec = std::vector<T, NoInitAlloc<T>>;
 
-// CSC of an n x m CSR matrix (= CSR of its transpose), rows ascending inside
-// each column: a counting sort by column over row ranges of about equal nnz,
-// one per host thread.  Thread t's entries of column j are placed after
-// those of threads < t, so every column lists its rows in ascending order,
-// exactly as one serial pass would.
-void transpose_csr(int64_t n, int64_t m, const int64_t* rp, const int32_t* ci, const double* vv,
-                   std::vector<int64_t>& cp, hvec<int32_t>& ri, hvec<double>& cv)
+// CSC of an n x m CSR matrix (= CSR of its transpose, values converted to
+// VO), rows ascending inside each column: a counting sort by column over
+// row ranges of about equal nnz, one per host thread.  Thread t's entries of
+// column j are placed after those of threads < t, so every column lists its
+// rows in ascending order, exactly as one serial pass would.
+template <typename VI, typename VO>
+void transpose_csr(int64_t n, int64_t m, const int64_t* rp, const int32_t* ci, const VI* vv,
+                   std::vector<int64_t>& cp, hvec<int32_t>& ri, hvec<VO>& cv)
 {
     const int64_t nnz = rp[n];
     int T = host_threads();
@@ -414,7 +415,7 @@ void transpose_csr(int64_t n, int64_t m, const int64_t* rp, const int32_t* ci, c
             for (int64_t p = rp[r]; p < rp[r + 1]; ++p) {
                 const int64_t q = o[ci[p]]++;
                 ri[q] = (int32_t)r;
-                cv[q] = vv[p];
+                cv[q] = (VO)vv[p];
             }
     });
 }
@@ -605,7 +606,8 @@ struct FreqHost {
     FreqTierHost t[2];             // slots < h1 (staged); slots h1 .. h - 1
 };
 
-bool split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const double* vals,
+template <typename V>
+bool split_frequent(int64_t rows, const int64_t* ptr, const int32_t* ind, const V* vals,
                     int ld, FreqHost& F, std::vector<int64_t>& lptr, hvec<int32_t>& lind,
                     hvec<float>& lval)
 {
@@ -704,6 +706,56 @@ void balance_frequent(int nchunks, FreqHost& F)
 {
     balance_tier(nchunks, F.t[0]);
     if (F.h > F.h1) balance_tier(nchunks, F.t[1]);
+}
+
+// One orientation's FP32 layouts: the frequent part when its gathered rows
+// are skewed enough (the frequent terms of a corpus), and the SELL part.
+// optr: the other orientation's row pointers, whose row lengths are the
+// entries that reference each gathered row; t_rows: the gathered factor's t
+// per column in column mode (the most rows that can be nonzero in all of
+// its columns), else 0.  vals in either precision: the layouts hold them
+// rounded to FP32.
+struct BuiltF32 {
+    FreqHost F;
+    SellHost<float> h;
+};
+
+template <typename V>
+void build_f32(int64_t rows, const int64_t* ptr, const int32_t* ind, const V* vals,
+               int64_t ngather, const int64_t* optr, int64_t t_rows, int ld, int nchunks,
+               BuiltF32& B)
+{
+    std::vector<int64_t> w(ngather);
+    for (int64_t g = 0; g < ngather; ++g) w[g] = optr[g + 1] - optr[g];
+    B.F.h = choose_frequent(w, ptr[rows], ld, t_rows, B.F.slot_of, B.F.h1);
+    std::vector<int64_t> lp;
+    hvec<int32_t> li;
+    hvec<float> lv;   // the rest's values, already rounded as the layout stores them
+    if (B.F.h > 0 && !split_frequent(rows, ptr, ind, vals, ld, B.F, lp, li, lv))
+        B.F = FreqHost{};
+    if (B.F.h > 0) {
+        balance_frequent(nchunks, B.F);
+        build_sell(rows, lp.data(), li.data(), lv.data(), B.h);
+    } else {
+        build_sell(rows, ptr, ind, vals, B.h);
+    }
+}
+
+// Both orientations on two host threads: rows of A (values va) gather rows
+// of V (documents), rows of A^T (CSR cp, ri, vt) rows of U (terms).
+template <typename VA, typename VT>
+void build_layouts_f32(int64_t n, int64_t m, const int64_t* rp, const int32_t* ci, const VA* va,
+                       const int64_t* cp, const int32_t* ri, const VT* vt, int ld, int nchunks,
+                       int64_t t_u, int64_t t_v, BuiltF32& ba, BuiltF32& bat)
+{
+    std::thread th([&] {
+        t_share = 2;
+        build_f32(m, cp, ri, vt, n, rp, t_u, ld, nchunks, bat);
+    });
+    t_share = 2;
+    build_f32(n, rp, ci, va, m, cp, t_v, ld, nchunks, ba);
+    t_share = 1;
+    th.join();
 }
 
 espnmf_status upload_tier(espnmf_ctx* ctx, const FreqTierHost& H, FreqTierDev& D)
@@ -1495,28 +1547,57 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             ci = A->colidx;
             vraw = static_cast<const unsigned char*>(A->values);
         }
-        hvec<double> vv(nnz);
-        parallel_chunks(nnz, [&](int64_t p0, int64_t p1) {
-            for (int64_t p = p0; p < p1; ++p) {
-                double x;
-                if (vsz == 8) {
-                    memcpy(&x, vraw + p * 8, 8);
-                } else if (vsz == 4) {
+        // A's values: in the FP32 form FP32 or BF16 ones are kept in FP32
+        // (FP32 ones read in place), otherwise they are widened to FP64;
+        // both exact, and every layout rounds them the same way
+        const bool vals32 = compute != ESPNMF_F64 && vsz <= 4;
+        hvec<double> vv;
+        hvec<float> vf_h;
+        const float* vf = nullptr;
+        if (vals32 && vsz == 4 && reinterpret_cast<uintptr_t>(vraw) % alignof(float) == 0) {
+            vf = reinterpret_cast<const float*>(vraw);
+        } else if (vals32) {
+            vf_h.resize(nnz);
+            parallel_chunks(nnz, [&](int64_t p0, int64_t p1) {
+                for (int64_t p = p0; p < p1; ++p) {
                     float f;
-                    memcpy(&f, vraw + p * 4, 4);
-                    x = f;
-                } else {
-                    // BF16: the high half of the FP32 word (exact)
-                    uint16_t b;
-                    memcpy(&b, vraw + p * 2, 2);
-                    const uint32_t w = (uint32_t)b << 16;
-                    float f;
-                    memcpy(&f, &w, 4);
-                    x = f;
+                    if (vsz == 4) {
+                        memcpy(&f, vraw + p * 4, 4);
+                    } else {
+                        // BF16: the high half of the FP32 word
+                        uint16_t b;
+                        memcpy(&b, vraw + p * 2, 2);
+                        const uint32_t w = (uint32_t)b << 16;
+                        memcpy(&f, &w, 4);
+                    }
+                    vf_h[p] = f;
                 }
-                vv[p] = x;
-            }
-        });
+            });
+            vf = vf_h.data();
+        } else {
+            vv.resize(nnz);
+            parallel_chunks(nnz, [&](int64_t p0, int64_t p1) {
+                for (int64_t p = p0; p < p1; ++p) {
+                    double x;
+                    if (vsz == 8) {
+                        memcpy(&x, vraw + p * 8, 8);
+                    } else if (vsz == 4) {
+                        float f;
+                        memcpy(&f, vraw + p * 4, 4);
+                        x = f;
+                    } else {
+                        // BF16: the high half of the FP32 word (exact)
+                        uint16_t b;
+                        memcpy(&b, vraw + p * 2, 2);
+                        const uint32_t w = (uint32_t)b << 16;
+                        float f;
+                        memcpy(&f, &w, 4);
+                        x = f;
+                    }
+                    vv[p] = x;
+                }
+            });
+        }
         if (rp[0] != 0 || rp[n] != nnz)
             return set_err(ctx, ESPNMF_ERR_BAD_MATRIX, "rowptr must run from 0 to nnz");
         for (int64_t r = 0; r < n; ++r)
@@ -1527,25 +1608,30 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             std::mutex bad_mu;
             int64_t bad_row = n;
             int bad_kind = 0;
-            parallel_weighted(n, rp, [&](int64_t r0, int64_t r1) {
-                for (int64_t r = r0; r < r1; ++r) {
-                    int kind = 0;
-                    for (int64_t p = rp[r]; p < rp[r + 1] && !kind; ++p) {
-                        if (ci[p] < 0 || ci[p] >= m) kind = 1;
-                        else if (p > rp[r] && ci[p] <= ci[p - 1]) kind = 2;
-                        else if (!std::isfinite(vv[p])) kind = 3;
-                        else if (vv[p] < 0.0) kind = 4;
-                    }
-                    if (kind) {
-                        std::lock_guard<std::mutex> lock(bad_mu);
-                        if (r < bad_row) {
-                            bad_row = r;
-                            bad_kind = kind;
+            auto check = [&](const auto* vals) {
+                parallel_weighted(n, rp, [&](int64_t r0, int64_t r1) {
+                    for (int64_t r = r0; r < r1; ++r) {
+                        int kind = 0;
+                        for (int64_t p = rp[r]; p < rp[r + 1] && !kind; ++p) {
+                            const double x = (double)vals[p];
+                            if (ci[p] < 0 || ci[p] >= m) kind = 1;
+                            else if (p > rp[r] && ci[p] <= ci[p - 1]) kind = 2;
+                            else if (!std::isfinite(x)) kind = 3;
+                            else if (x < 0.0) kind = 4;
                         }
-                        return;
+                        if (kind) {
+                            std::lock_guard<std::mutex> lock(bad_mu);
+                            if (r < bad_row) {
+                                bad_row = r;
+                                bad_kind = kind;
+                            }
+                            return;
+                        }
                     }
-                }
-            });
+                });
+            };
+            if (vf) check(vf);
+            else check(vv.data());
             static const char* what[] = {"", "column index out of range", "column indices not strictly increasing",
                                          "non-finite value", "negative value (A >= 0 is required)"};
             if (bad_kind)
@@ -1555,8 +1641,11 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
         // CSC (= CSR of A^T), rows ascending inside each column
         std::vector<int64_t> cp;
         hvec<int32_t> ri;
-        hvec<double> cv;
-        transpose_csr(n, m, rp, ci, vv.data(), cp, ri, cv);
+        hvec<double> cv;     // FP64 form
+        hvec<float> cv32;    // FP32 form: the values as its layouts store them
+        if (compute == ESPNMF_F64) transpose_csr(n, m, rp, ci, vv.data(), cp, ri, cv);
+        else if (vf) transpose_csr(n, m, rp, ci, vf, cp, ri, cv32);
+        else transpose_csr(n, m, rp, ci, vv.data(), cp, ri, cv32);
         phase("transpose");
         // The two orientations are laid out on two host threads; the uploads
         // follow on this thread.
@@ -1573,53 +1662,23 @@ espnmf_status espnmf_init(espnmf_ctx** out, const espnmf_csr* A, int32_t k, int6
             TRY(upload_sell(ctx, h1, ctx->sA));
             TRY(upload_sell(ctx, h2, ctx->sAt));
         } else {
-            // rows of A gather rows of V (documents), rows of A^T rows of U
-            // (terms); each product gets a frequent part when its gathered
-            // rows are skewed enough (the frequent terms of a corpus)
             const int ld = factor_ld(k);
-            // chunks of the frequent part's rows: four per warp of spmm_h
-            const int hwarps = 4 * ctx->sm_count * (kHThreads / 32);
-            struct Built {
-                FreqHost F;
-                SellHost<float> h;
-            };
+            // chunks of the frequent part's rows: four per warp of spmm_freq
+            const int nchunks = 4 * ctx->sm_count * (kHThreads / 32);
             const bool col_mode = mode == ESPNMF_TOPT_COLUMN;
-            // optr: the other orientation's row pointers, whose row lengths
-            // are the entries that reference each gathered row
-            // t_rows: the gathered factor's t per column (column mode), the
-            // most rows that can be nonzero in all of its columns
-            auto build_f32 = [&](int64_t rows, const int64_t* ptr, const int32_t* ind,
-                                 const double* vals, int64_t ngather, const int64_t* optr,
-                                 int64_t t_rows, Built& B) {
-                std::vector<int64_t> w(ngather);
-                for (int64_t g = 0; g < ngather; ++g) w[g] = optr[g + 1] - optr[g];
-                B.F.h = choose_frequent(w, ptr[rows], ld, t_rows, B.F.slot_of, B.F.h1);
-                std::vector<int64_t> lp;
-                hvec<int32_t> li;
-                hvec<float> lv;   // the rest's values, already rounded as the layout stores them
-                if (B.F.h > 0 && !split_frequent(rows, ptr, ind, vals, ld, B.F, lp, li, lv))
-                    B.F = FreqHost{};
-                if (B.F.h > 0) {
-                    balance_frequent(hwarps, B.F);
-                    build_sell(rows, lp.data(), li.data(), lv.data(), B.h);
-                } else {
-                    build_sell(rows, ptr, ind, vals, B.h);
-                }
-            };
-            auto upload_f32 = [&](const Built& B, SellDev& D) -> espnmf_status {
+            const int64_t tu = col_mode ? t_u : 0, tv = col_mode ? t_v : 0;
+            auto upload_f32 = [&](const BuiltF32& B, SellDev& D) -> espnmf_status {
                 TRY(upload_sell(ctx, B.h, D));
                 if (B.F.h > 0) TRY(upload_frequent(ctx, B.F, D));
                 return ESPNMF_OK;
             };
-            Built ba, bat;
-            std::thread th([&] {
-                t_share = 2;
-                build_f32(m, cp.data(), ri.data(), cv.data(), n, rp, col_mode ? t_u : 0, bat);
-            });
-            t_share = 2;
-            build_f32(n, rp, ci, vv.data(), m, cp.data(), col_mode ? t_v : 0, ba);
-            t_share = 1;
-            th.join();
+            BuiltF32 ba, bat;
+            if (vf)
+                build_layouts_f32(n, m, rp, ci, vf, cp.data(), ri.data(), cv32.data(), ld, nchunks,
+                                  tu, tv, ba, bat);
+            else
+                build_layouts_f32(n, m, rp, ci, vv.data(), cp.data(), ri.data(), cv32.data(), ld,
+                                  nchunks, tu, tv, ba, bat);
             phase("layouts built");
             TRY(upload_f32(ba, ctx->sA));
             TRY(upload_f32(bat, ctx->sAt));
