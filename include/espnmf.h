@@ -120,7 +120,9 @@ typedef struct espnmf_ctx espnmf_ctx;
  * A is brought to the host (copied back first when it is on the device),
  * validated there, and laid out by host code: its transpose, the two
  * sliced-ELLPACK layouts (rows of A and rows of A^T) with their
- * frequent-row parts; the layouts are then uploaded.  U0 is placed in the
+ * frequent-row parts; the layouts are then uploaded.  In the FP32 form,
+ * FP32 values are read in place and the layouts hold every value rounded
+ * to FP32; the FP64 form keeps them in FP64.  U0 is placed in the
  * row-packed sparse factor layout and its FP64 Gram U0^T U0 formed on the
  * device.  The call synchronises; its cost grows with nnz (host work). */
 espnmf_status espnmf_init(espnmf_ctx **out, const espnmf_csr *A, int32_t k,
@@ -424,8 +426,8 @@ espnmf_status espnmf_launches_per_sweep(espnmf_ctx *ctx, int32_t *count);
  * environment sets ESPNMF_CHECKED=1), the union of the bounds checks that
  * failed in any kernel since the last call, then cleared: bit 0 a gathered
  * factor row beyond the factor, bit 1 a pair's column beyond the row width,
- * bit 2 a row's pair count beyond its capacity, bit 3 a frequent-table slot
- * beyond the table, bit 4 an output or partial row out of range, bit 5 a
+ * bit 2 a row's pair count beyond its capacity, bit 3 a frequent-part entry
+ * whose table row lies beyond its table, bit 4 an output or partial row out of range, bit 5 a
  * candidate or survivor row beyond the column.  A failed check skips its
  * access.  0: every checked access was in range.  Any other build: *flags
  * = 0 and ESPNMF_ERR_UNSUPPORTED.  Reads device memory (synchronises with
