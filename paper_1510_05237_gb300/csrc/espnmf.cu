@@ -1773,68 +1773,25 @@ espnmf_status espnmf_get_factor(espnmf_ctx* ctx, espnmf_which which, espnmf_layo
     const int k = ctx->k;
     const EllDev& E = F.buf[F.cur];
     const int ld = E.ld;
-    std::vector<int32_t> cnt(rows), col((size_t)rows * ld);
-    std::vector<double> v((size_t)rows * ld);
+    if (layout != ESPNMF_DENSE_ROWMAJOR && layout != ESPNMF_CSR && layout != ESPNMF_CSC)
+        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "unknown layout");
+    // the row-packed arrays, copied into uninitialised host buffers; the
+    // values are read in the compute type
+    hvec<int32_t> cnt(rows), col((size_t)rows * ld);
     CU(cudaMemcpy(cnt.data(), E.cnt, 4 * rows, cudaMemcpyDeviceToHost));
     CU(cudaMemcpy(col.data(), E.col, 4 * rows * ld, cudaMemcpyDeviceToHost));
-    if (is_f64(ctx)) {
-        CU(cudaMemcpy(v.data(), E.val, 8 * rows * ld, cudaMemcpyDeviceToHost));
-    } else {
-        std::vector<float> f((size_t)rows * ld);
-        CU(cudaMemcpy(f.data(), E.val, 4 * rows * ld, cudaMemcpyDeviceToHost));
-        for (size_t i = 0; i < f.size(); ++i) v[i] = f[i];
-    }
     const size_t es = dtype == ESPNMF_F64 ? 8 : 4;
-    auto put = [&](std::vector<unsigned char>& dst, size_t i, double x) {
-        if (es == 8) memcpy(&dst[i * 8], &x, 8);
-        else {
-            float f = (float)x;
-            memcpy(&dst[i * 4], &f, 4);
-        }
-    };
-    int64_t nnz = 0;
-    for (auto c : cnt) nnz += c;
     std::vector<unsigned char> vo;
     std::vector<int64_t> po;
     std::vector<int32_t> io;
-    if (layout == ESPNMF_DENSE_ROWMAJOR) {
-        vo.assign((size_t)rows * k * es, 0);
-        for (int64_t r = 0; r < rows; ++r)
-            for (int q = 0; q < cnt[r]; ++q) put(vo, (size_t)r * k + col[r * ld + q], v[r * ld + q]);
-    } else if (layout == ESPNMF_CSR) {
-        po.assign(rows + 1, 0);
-        io.resize(nnz);
-        vo.resize(nnz * es);
-        int64_t o = 0;
-        std::vector<std::pair<int32_t, double>> tmp;
-        for (int64_t r = 0; r < rows; ++r) {
-            tmp.clear();
-            for (int q = 0; q < cnt[r]; ++q) tmp.push_back({col[r * ld + q], v[r * ld + q]});
-            std::sort(tmp.begin(), tmp.end());
-            for (auto& pr : tmp) {
-                io[o] = pr.first;
-                put(vo, o, pr.second);
-                ++o;
-            }
-            po[r + 1] = o;
-        }
-    } else if (layout == ESPNMF_CSC) {
-        po.assign(k + 1, 0);
-        for (int64_t r = 0; r < rows; ++r)
-            for (int q = 0; q < cnt[r]; ++q) po[col[r * ld + q] + 1]++;
-        for (int c = 0; c < k; ++c) po[c + 1] += po[c];
-        std::vector<int64_t> nx(po.begin(), po.end() - 1);
-        io.resize(nnz);
-        vo.resize(nnz * es);
-        for (int64_t r = 0; r < rows; ++r)   // rows ascending -> sorted columns
-            for (int q = 0; q < cnt[r]; ++q) {
-                const int c = col[r * ld + q];
-                const int64_t o = nx[c]++;
-                io[o] = (int32_t)r;
-                put(vo, o, v[r * ld + q]);
-            }
+    if (is_f64(ctx)) {
+        hvec<double> v((size_t)rows * ld);
+        CU(cudaMemcpy(v.data(), E.val, 8 * rows * ld, cudaMemcpyDeviceToHost));
+        pack_factor(rows, k, ld, cnt.data(), col.data(), v.data(), layout, es, vo, po, io);
     } else {
-        return set_err(ctx, ESPNMF_ERR_INVALID_ARG, "unknown layout");
+        hvec<float> v((size_t)rows * ld);
+        CU(cudaMemcpy(v.data(), E.val, 4 * rows * ld, cudaMemcpyDeviceToHost));
+        pack_factor(rows, k, ld, cnt.data(), col.data(), v.data(), layout, es, vo, po, io);
     }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
     if (!vo.empty()) CU(cudaMemcpy(val, vo.data(), vo.size(), kind));

@@ -6,7 +6,9 @@
 //   * choose_frequent / split_frequent / balance_frequent: the FP32 form's
 //     frequent part (the entries whose gathered factor row is one of the
 //     most referenced ones), in two tiers, and the rest for build_sell;
-//   * build_layouts_f32: both orientations of the FP32 form.
+//   * build_layouts_f32: both orientations of the FP32 form;
+//   * pack_factor:   a row-packed factor in an export layout
+//     (espnmf_get_factor).
 //
 // Host code only (no CUDA calls); the vector types come from the CUDA
 // headers.  The device side of these layouts is described with SellDev and
@@ -22,6 +24,7 @@
 #include <thread>
 #include <vector>
 
+#include "../../include/espnmf.h"
 #include "common.cuh"
 
 namespace espnmf {
@@ -493,6 +496,76 @@ void build_layouts_f32(int64_t n, int64_t m, const int64_t* rp, const int32_t* c
     build_f32(n, rp, ci, va, m, cp, t_v, ld, nchunks, ba);
     t_share = 1;
     th.join();
+}
+
+
+// A factor in row-packed form (row r: cnt[r] pairs (col, val) at
+// [r * ld, r * ld + cnt[r]), columns distinct) written in an export layout
+// with values of es bytes (8: FP64, 4: FP32, rounded from V):
+//   DENSE_ROWMAJOR: vo = rows x k values, zeros included;
+//   CSC: po[k + 1], io = rows ascending within each column;
+//   CSR: po[rows + 1], io = columns ascending within each row.
+// False for an unknown layout.
+template <typename V>
+bool pack_factor(int64_t rows, int k, int ld, const int32_t* cnt, const int32_t* col,
+                 const V* val, espnmf_layout layout, size_t es, std::vector<unsigned char>& vo,
+                 std::vector<int64_t>& po, std::vector<int32_t>& io)
+{
+    auto put = [&](size_t i, V x) {
+        if (es == 8) {
+            const double d = (double)x;
+            std::memcpy(&vo[i * 8], &d, 8);
+        } else {
+            const float f = (float)x;
+            std::memcpy(&vo[i * 4], &f, 4);
+        }
+    };
+    int64_t nnz = 0;
+    for (int64_t r = 0; r < rows; ++r) nnz += cnt[r];
+    vo.clear();
+    po.clear();
+    io.clear();
+    if (layout == ESPNMF_DENSE_ROWMAJOR) {
+        vo.assign((size_t)rows * k * es, 0);
+        for (int64_t r = 0; r < rows; ++r)
+            for (int q = 0; q < cnt[r]; ++q)
+                put((size_t)r * k + col[r * ld + q], val[r * ld + q]);
+    } else if (layout == ESPNMF_CSR) {
+        po.assign(rows + 1, 0);
+        io.resize(nnz);
+        vo.resize(nnz * es);
+        int64_t o = 0;
+        std::vector<std::pair<int32_t, V>> tmp;
+        for (int64_t r = 0; r < rows; ++r) {
+            tmp.clear();
+            for (int q = 0; q < cnt[r]; ++q) tmp.push_back({col[r * ld + q], val[r * ld + q]});
+            std::sort(tmp.begin(), tmp.end());
+            for (auto& pr : tmp) {
+                io[o] = pr.first;
+                put(o, pr.second);
+                ++o;
+            }
+            po[r + 1] = o;
+        }
+    } else if (layout == ESPNMF_CSC) {
+        po.assign(k + 1, 0);
+        for (int64_t r = 0; r < rows; ++r)
+            for (int q = 0; q < cnt[r]; ++q) po[col[r * ld + q] + 1]++;
+        for (int c = 0; c < k; ++c) po[c + 1] += po[c];
+        std::vector<int64_t> nx(po.begin(), po.end() - 1);
+        io.resize(nnz);
+        vo.resize(nnz * es);
+        for (int64_t r = 0; r < rows; ++r)   // rows ascending -> sorted columns
+            for (int q = 0; q < cnt[r]; ++q) {
+                const int c = col[r * ld + q];
+                const int64_t o = nx[c]++;
+                io[o] = (int32_t)r;
+                put(o, val[r * ld + q]);
+            }
+    } else {
+        return false;
+    }
+    return true;
 }
 
 }  // namespace layout

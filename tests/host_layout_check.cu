@@ -7,7 +7,9 @@
 //   3. every entry of A, and nothing else, recovered from each orientation's
 //      SELL part and the two tiers of its frequent part, each with its row,
 //      column and FP32 value; the tiers' padding, row list and work chunks
-//      well formed.
+//      well formed;
+//   4. pack_factor (the export of a row-packed factor) against a dense
+//      reference in all three layouts, FP32 and FP64 values and outputs.
 //
 // Usage: host_layout_check <prefix> <n> <m> <ld> <t_u> <t_v>
 // reads <prefix>_rp.bin (int64[n+1]), <prefix>_ci.bin (int32[nnz]) and
@@ -215,6 +217,89 @@ bool same_entries(std::vector<Entry> a, std::vector<Entry> b)
     return true;
 }
 
+// A random row-packed factor (rows x k, ld >= k, distinct columns per row,
+// values > 0) exported by pack_factor and compared with a dense reference.
+template <class V>
+void check_pack(int64_t rows, int k, int ld, unsigned seed)
+{
+    uint64_t st = seed * 2654435761ull + 1;
+    auto next = [&]() {
+        st ^= st << 13;
+        st ^= st >> 7;
+        st ^= st << 17;
+        return st;
+    };
+    std::vector<int32_t> cnt(rows), col((size_t)rows * ld, -7);
+    std::vector<V> val((size_t)rows * ld, (V)-3);
+    std::vector<double> dense((size_t)rows * k, 0.0);
+    for (int64_t r = 0; r < rows; ++r) {
+        std::vector<int32_t> perm(k);
+        for (int c = 0; c < k; ++c) perm[c] = c;
+        for (int c = k - 1; c > 0; --c) std::swap(perm[c], perm[next() % (uint64_t)(c + 1)]);
+        cnt[r] = (int32_t)(next() % (uint64_t)(k + 1));
+        for (int q = 0; q < cnt[r]; ++q) {
+            const V x = (V)((double)(next() % 1000000 + 1) / 7.0);
+            col[r * ld + q] = perm[q];
+            val[r * ld + q] = x;
+            dense[(size_t)r * k + perm[q]] = (double)x;
+        }
+    }
+    for (size_t es : {size_t(4), size_t(8)}) {
+        auto as = [&](double x, unsigned char* out) {
+            if (es == 8) std::memcpy(out, &x, 8);
+            else {
+                const float f = (float)x;
+                std::memcpy(out, &f, 4);
+            }
+        };
+        std::vector<unsigned char> vo;
+        std::vector<int64_t> po;
+        std::vector<int32_t> io;
+        // dense
+        pack_factor(rows, k, ld, cnt.data(), col.data(), val.data(), ESPNMF_DENSE_ROWMAJOR, es,
+                    vo, po, io);
+        std::vector<unsigned char> ref(dense.size() * es);
+        for (size_t i = 0; i < dense.size(); ++i) as(dense[i], &ref[i * es]);
+        if (vo != ref || !po.empty() || !io.empty()) fail("pack_factor dense");
+        // CSR: columns ascending per row
+        std::vector<int64_t> rp{0};
+        std::vector<int32_t> ri;
+        std::vector<unsigned char> rv;
+        for (int64_t r = 0; r < rows; ++r) {
+            for (int c = 0; c < k; ++c)
+                if (dense[(size_t)r * k + c] != 0.0) {
+                    ri.push_back(c);
+                    rv.resize(rv.size() + es);
+                    as(dense[(size_t)r * k + c], &rv[rv.size() - es]);
+                }
+            rp.push_back((int64_t)ri.size());
+        }
+        pack_factor(rows, k, ld, cnt.data(), col.data(), val.data(), ESPNMF_CSR, es, vo, po, io);
+        if (po != rp || io != ri || vo != rv) fail("pack_factor CSR");
+        // CSC: rows ascending per column
+        rp.assign(1, 0);
+        ri.clear();
+        rv.clear();
+        for (int c = 0; c < k; ++c) {
+            for (int64_t r = 0; r < rows; ++r)
+                if (dense[(size_t)r * k + c] != 0.0) {
+                    ri.push_back((int32_t)r);
+                    rv.resize(rv.size() + es);
+                    as(dense[(size_t)r * k + c], &rv[rv.size() - es]);
+                }
+            rp.push_back((int64_t)ri.size());
+        }
+        pack_factor(rows, k, ld, cnt.data(), col.data(), val.data(), ESPNMF_CSC, es, vo, po, io);
+        if (po != rp || io != ri || vo != rv) fail("pack_factor CSC");
+    }
+    std::vector<unsigned char> vo;
+    std::vector<int64_t> po;
+    std::vector<int32_t> io;
+    if (pack_factor(rows, k, ld, cnt.data(), col.data(), val.data(), (espnmf_layout)7, 4, vo, po,
+                    io))
+        fail("pack_factor accepted an unknown layout");
+}
+
 }  // namespace
 
 int main(int argc, char** argv)
@@ -236,6 +321,13 @@ int main(int argc, char** argv)
     }
     const int64_t nnz = rp[n];
     std::vector<double> vv(vf.begin(), vf.end());
+
+    // 4. factor export (independent of A)
+    check_pack<float>(1000, 13, 16, 1);
+    check_pack<double>(1000, 13, 16, 2);
+    check_pack<float>(300, 50, 52, 3);
+    check_pack<double>(64, 1, 4, 4);
+    check_pack<float>(0, 5, 8, 5);
 
     // 1. transposes
     std::vector<int64_t> cp0;
