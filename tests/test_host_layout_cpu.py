@@ -8,7 +8,10 @@ library's own header:
   widened to FP64 are bitwise equal (the set-up keeps FP32 input in FP32);
 * every entry of A -- row, column and FP32 value -- and nothing else is
   recovered from each orientation's SELL part and frequent tiers, whose
-  padding, row lists and work chunks are well formed.
+  padding, row lists and work chunks are well formed;
+* each product's frequent part has the size (h rows, h1 of them in shared
+  memory) that its choice rule, restated here, gives;
+* the factor export (pack_factor) matches a dense reference.
 
 Corpora: the small Zipf corpus, a 60k x 40k Zipf corpus whose A^T U gets
 both frequent tiers at k = 100, its transpose (both tiers in A V), the
@@ -16,6 +19,7 @@ widest padding (ld = 8), whole-matrix/none modes (no t per column), a
 scaled planted corpus, and a matrix with explicit zeros, empty rows and
 empty columns."""
 import os
+import re
 import subprocess
 
 import numpy as np
@@ -89,6 +93,29 @@ CASES = {
 }
 
 
+def expected_frequent(weights: np.ndarray, nnz: int, ld: int, t_rows: int):
+    """(h, h1) of a product's frequent part by its stated rule: candidates are
+    the gathered rows referenced at least max(16, 4 x mean) times, by
+    decreasing weight; the shared-memory tier takes as many as fit 200 KB
+    (at most 65535); with t_rows = t (column mode) the part takes up to t
+    candidates (and at most 16 MB of table) when that adds at least 256 rows
+    beyond the first tier; the part is kept only if it covers a tenth of
+    the entries."""
+    ng = len(weights)
+    if ng == 0 or nnz == 0:
+        return 0, 0
+    cap1 = min(200 * 1024 // (ld * 4), 65535)
+    cap_all = min((16 << 20) // (ld * 4), 65535)
+    floor_w = max(16.0, 4.0 * nnz / ng)
+    order = sorted(np.nonzero(weights >= floor_w)[0], key=lambda g: (-weights[g], g))
+    want = min(len(order), t_rows, cap_all)
+    cap = want if want - cap1 >= 256 else cap1
+    order = order[:cap]
+    if not order or int(weights[order].sum()) * 10 < nnz:
+        return 0, 0
+    return len(order), min(len(order), cap1)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_host_layouts(checker, tmp_path, name):
     make, ld, t_u, t_v = CASES[name]
@@ -103,3 +130,10 @@ def test_host_layouts(checker, tmp_path, name):
     assert r.stdout.strip().endswith(": ok"), r.stdout
     if name.startswith("zipf_two_tiers"):
         assert "h=1200 (h1=457" in r.stdout, r.stdout      # both tiers present
+    # the frequent parts of A V (gathered: documents, weights = their
+    # lengths) and A^T U (gathered: terms, weights = their frequencies)
+    doc_len = np.bincount(A.colidx, minlength=A.m)
+    term_freq = np.diff(A.rowptr)
+    got = re.findall(r"h=(\d+) \(h1=(\d+)", r.stdout)
+    assert got == [tuple(str(x) for x in expected_frequent(doc_len, A.nnz, ld, t_v)),
+                   tuple(str(x) for x in expected_frequent(term_freq, A.nnz, ld, t_u))], r.stdout
