@@ -359,6 +359,13 @@ int main(int argc, char** argv)
                       nchunks, t_u, t_v, a64, at64);
     if (!same_sell(a32.h, a64.h) || !same_freq(a32.F, a64.F)) fail("A: FP32 vs FP64 values");
     if (!same_sell(at32.h, at64.h) || !same_freq(at32.F, at64.F)) fail("A^T: FP32 vs FP64 values");
+    // FP64 input in the FP32 form: A's values in FP64, A^T's transposed to FP32
+    BuiltF32 amix, atmix;
+    build_layouts_f32(n, m, rp.data(), ci.data(), vv.data(), cpd.data(), rid.data(), cvd.data(),
+                      ld, nchunks, t_u, t_v, amix, atmix);
+    if (!same_sell(a32.h, amix.h) || !same_freq(a32.F, amix.F) || !same_sell(at32.h, atmix.h) ||
+        !same_freq(at32.F, atmix.F))
+        fail("FP64 input in the FP32 form");
 
     // 3. every entry recovered from each orientation
     if (!same_entries(recover(a32, ld, m), entries_of(n, rp.data(), ci.data(), vf.data())))
